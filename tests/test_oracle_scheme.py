@@ -1,0 +1,274 @@
+"""Pins of the oracle's numerical scheme (Section 3 of arXiv 2012.11130:
+PLM with the hybrid van Leer / generalised minmod limiter, MUSCL-Hancock,
+relativistic HLLC/HLLE, conservative update, retry, CFL) against special
+cases, symmetries, conservation, the exact Riemann solution and smooth
+convergence. CPU only."""
+import numpy as np
+
+EPS = np.finfo(np.float64).eps
+
+
+def _cons(oracle, W):
+    C, st = oracle.prim2con(np.asarray(W, float).reshape(5, -1))
+    assert np.all(st == 0)
+    return C
+
+
+def test_limiter_properties(oracle):
+    s = oracle.limited_slope
+    assert s(1.0, -1.0, 1.5) == 0.0 and s(0.0, 2.0, 1.5) == 0.0       # extrema -> 0
+    assert s(0.3, 0.3, 1.5) == 0.3                                    # linear data exact
+    assert s(1.0, 3.0, 0.0) == 0.0                                    # theta = 0 is PCM
+    for dl, dr in ((1.0, 3.0), (2.0, 0.1), (1e-9, 5e-9)):
+        for th in (0.5, 1.0, 1.5, 2.0):
+            a = s(dl, dr, th)
+            assert a == s(dr, dl, th) and s(-dl, -dr, th) == -a       # symmetric, odd
+            vl = 2 * dl * dr / (dl + dr)
+            gm = min(th * dl, th * dr, 0.5 * (dl + dr))
+            assert a <= vl * (1 + 1e-15) and a <= gm * (1 + 1e-15)    # min of the two
+            assert a == min(vl, gm)
+
+
+def test_riemann_consistency_and_upwinding(oracle):
+    rng = np.random.default_rng(1)
+    for _ in range(50):
+        W = np.array([10 ** rng.uniform(-3, 3), *rng.normal(0, 3, 3), 10 ** rng.uniform(-3, 3)])
+        for d in range(3):
+            F = oracle.phys_flux(d, W)
+            for solver in (0, 1):
+                Fr, _ = oracle.riemann_flux(d, W, W, solver)
+                assert np.allclose(Fr, F, rtol=1e-13, atol=1e-13 * np.abs(F).max())
+    # supersonic flow to +x: both outer speeds positive -> left flux exactly
+    WL = np.array([1.0, 50.0, 0.0, 0.0, 1e-3])
+    WR = np.array([2.0, 40.0, 1.0, 0.0, 2e-3])
+    F, _ = oracle.riemann_flux(0, WL, WR, 0)
+    assert np.array_equal(F, oracle.phys_flux(0, WL))
+
+
+def test_hllc_resolves_contacts(oracle):
+    # A contact (equal p and velocity, different density) is an exact
+    # solution; HLLC (Mignone & Bodo) returns its flux, HLLE diffuses it.
+    p = 0.7
+    for U in (0.0, 0.3, -2.0, 50.0):
+        WL = np.array([1.0, U, 0.0, 0.0, p])
+        WR = np.array([1e-3, U, 0.0, 0.0, p])
+        F, fb = oracle.riemann_flux(0, WL, WR, 0)
+        assert fb == 0
+        Fup = oracle.phys_flux(0, WL if U >= 0 else WR)
+        if U == 0.0:
+            assert np.allclose(F, [0, p, 0, 0, 0], atol=1e-15 * p)
+        else:
+            assert np.allclose(F, Fup, rtol=1e-12, atol=1e-12 * np.abs(Fup).max())
+        if abs(U) < 1:  # subsonic contact: HLLE smears it
+            Fe, _ = oracle.riemann_flux(0, WL, WR, 1)
+            assert abs(Fe[0] - Fup[0]) > 1e-6
+
+
+def _uniform_block(oracle, W, n=8):
+    C = _cons(oracle, W)[:, 0]
+    return np.broadcast_to(C[:, None, None, None], (5, n + 4, n + 4, n + 4)).copy()
+
+
+def test_uniform_state_unchanged(oracle):
+    for W in ([1.0, 0.0, 0.0, 0.0, 1.0], [1e-3, 3.0, -4.0, 5.0, 1e-7], [2.0, 1e5, 0, 0, 1e4]):
+        G = _uniform_block(oracle, W)
+        r = oracle.advance_block(G, (8, 8, 8), (1, 1, 1), 1e-3, 1e-2)
+        assert r["status"] == 0 and r["retries"] == 0
+        assert np.array_equal(r["out"], G[:, 2:-2, 2:-2, 2:-2])
+
+
+def _random_smooth_block(oracle, rng, shape, amp=0.3):
+    nz, ny, nx = shape
+    z, y, x = np.meshgrid(*(np.arange(s) / s for s in shape), indexing="ij")
+    ph = rng.uniform(0, 2 * np.pi, 5)
+    rho = 1 + amp * np.sin(2 * np.pi * (x + 2 * y) + ph[0])
+    p = 1 + amp * np.sin(2 * np.pi * (y - z) + ph[1])
+    Ux = 0.5 * np.sin(2 * np.pi * (x + z) + ph[2])
+    Uy = 0.5 * np.cos(2 * np.pi * (x - y) + ph[3])
+    Uz = 0.5 * np.sin(2 * np.pi * (z) + ph[4])
+    W = np.stack([rho, Ux, Uy, Uz, p]).reshape(5, -1)
+    return _cons(oracle, W).reshape(5, nz, ny, nx)
+
+
+def test_mirror_symmetry(oracle):
+    rng = np.random.default_rng(5)
+    C = _random_smooth_block(oracle, rng, (12, 12, 12))
+    Cm = C[:, :, :, ::-1].copy()
+    Cm[1] *= -1
+    a = oracle.advance_block(C, (8, 8, 8), (1, 1, 1), 2e-3, 1 / 12)
+    b = oracle.advance_block(Cm, (8, 8, 8), (1, 1, 1), 2e-3, 1 / 12)
+    bm = b["out"][:, :, :, ::-1].copy()
+    bm[1] *= -1
+    scale = np.abs(a["out"]).max(axis=(1, 2, 3))[:, None, None, None]
+    assert np.all(np.abs(a["out"] - bm) <= 1e-13 * scale)
+
+
+def test_direction_permutation(oracle):
+    # The same 1-D problem along x, y or z gives identical results.
+    N = 24
+    x = (np.arange(N) + 0.5) / N
+    W = np.vstack([1 + 0.5 * (x > 0.5), 0.2 * np.sin(2 * np.pi * x), np.zeros(N), np.zeros(N),
+                   1 + (x < 0.3)])
+    res = []
+    for d in range(3):
+        Wd = W.copy()
+        Wd[[1, 1 + d]] = Wd[[1 + d, 1]]
+        C = _cons(oracle, Wd)
+        shape = [1, 1, 1]
+        shape[2 - d] = N
+        act = [0, 0, 0]
+        act[d] = 1
+        G = oracle.fill_ghosts(C.reshape(5, *shape), act, "outflow")
+        n = [1, 1, 1]
+        n[d] = N
+        out = oracle.advance_block(G, tuple(n), tuple(act), 4e-3, 1 / N)["out"].reshape(5, N)
+        out[[1, 1 + d]] = out[[1 + d, 1]]
+        res.append(out)
+    assert np.array_equal(res[0], res[1]) and np.array_equal(res[0], res[2])
+
+
+def test_periodic_conservation(oracle):
+    rng = np.random.default_rng(9)
+    C = _random_smooth_block(oracle, rng, (16, 16, 16))
+    tot0 = C.reshape(5, -1).sum(1)
+    dh = 1 / 16
+    for _ in range(4):
+        dt = oracle.cfl_dt(C, dh)
+        r = oracle.advance_block(oracle.fill_ghosts(C, (1, 1, 1), "periodic"), (16, 16, 16),
+                                 (1, 1, 1), dt, dh)
+        assert r["status"] == 0 and r["retries"] == 0
+        C = r["out"]
+    tot = C.reshape(5, -1).sum(1)
+    scale = np.abs(C.reshape(5, -1)).sum(1)
+    assert np.all(np.abs(tot - tot0) <= 1e-13 * scale)
+
+
+def _shock_tube(oracle, N, riemann=0):
+    dh = 1.0 / N
+    x = (np.arange(N) + 0.5) * dh
+    W = np.vstack([np.ones(N), np.zeros(N), np.zeros(N), np.zeros(N),
+                   np.where(x < 0.5, 1e3, 1e-2)])
+    res = oracle.evolve(_cons(oracle, W).reshape(5, 1, 1, N), (1, 0, 0), dh, 0.4, "outflow",
+                        riemann=riemann)
+    prim = oracle.con2pri(res["cons"].reshape(5, -1))["prim"]
+    rho, U, p, info = oracle.exact_riemann((1, 0, 1e3), (1, 0, 1e-2), 0.5, 0.4, x)
+    return np.mean(np.abs(1 - prim[0] / rho)), np.mean(np.abs(prim[0] - rho)), res
+
+
+def test_shock_tube_converges_to_exact(oracle):
+    # 1-D shock tube (rho=1, p=1e3 | rho=1, p=1e-2, t=0.4, CFL 0.5,
+    # PLM + MUSCL-Hancock + HLLC, outflow): the L1 error against the exact
+    # TM solution (Appendix C) falls with resolution, at about first order
+    # as expected with discontinuities.
+    errs = [_shock_tube(oracle, N)[1] for N in (128, 256, 512, 1024)]
+    assert all(b < a for a, b in zip(errs, errs[1:]))
+    order = np.log2(errs[1] / errs[3]) / 2
+    assert 0.6 < order < 1.2
+    rel1024, _, res = _shock_tube(oracle, 1024)
+    assert res["retries"] == 0
+    assert rel1024 < 0.4
+    # HLLE is more diffusive but converges too
+    e_hlle = _shock_tube(oracle, 512, riemann=1)[1]
+    assert e_hlle < errs[1]
+
+
+def test_smooth_advection_second_order(oracle):
+    # A density wave in uniform p and velocity is advected exactly
+    # (contact); with gamma = 10 and hot gas (T ~ 1) the L1 error of
+    # Eq. (relative L1 error) falls as about N^-2 (Section 4.1).
+    errs = []
+    Ux = np.sqrt(99.0)
+    v = Ux / 10.0
+    t_end = 1.0 / v
+    for N in (32, 64, 128):
+        dh = 1.0 / N
+        x = (np.arange(N) + 0.5) * dh
+        W = np.vstack([1 + 0.5 * np.sin(2 * np.pi * x), np.full(N, Ux), np.zeros(N), np.zeros(N),
+                       np.ones(N)])
+        res = oracle.evolve(_cons(oracle, W).reshape(5, 1, 1, N), (1, 0, 0), dh, t_end,
+                            "periodic")
+        prim = oracle.con2pri(res["cons"].reshape(5, -1))["prim"]
+        exact = 1 + 0.5 * np.sin(2 * np.pi * (x - v * t_end))
+        errs.append(np.mean(np.abs(1 - prim[0] / exact)))
+    order = np.log2(errs[1] / errs[2])
+    assert order > 1.7, errs
+
+
+def test_cfl_limits(oracle):
+    # Section 3.2: non-relativistic limit C dh / (|vx|+|vy|+|vz| + 3 c_s)
+    # and gamma >> 1 limit C dh / c.
+    T = 1e-8
+    W = np.array([1.0, 1e-5, -2e-5, 3e-5, T])
+    C = _cons(oracle, W)
+    cs = np.sqrt(oracle.cs2_of_T(T))
+    dt = oracle.cfl_dt(C, 0.1, cfl=0.5)
+    nr = 0.5 * 0.1 / (6e-5 + 3 * cs)
+    assert abs(dt / nr - 1) < 1e-4
+    W = np.array([1.0, 1e6, 0, 0, 1.0])
+    dt = oracle.cfl_dt(_cons(oracle, W), 0.1, cfl=0.5)
+    assert abs(dt / 0.05 - 1) < 1e-10
+    assert oracle.cfl_dt(_cons(oracle, W), 0.1, cfl=0.5, cfl_mode=1) == 0.05
+
+
+def test_retry_reaches_physical_state(oracle):
+    # Section 3.3 (1): a rough patch whose first update is unphysical is
+    # recomputed with smaller limiter coefficients; the result passes
+    # Eq. (Unphysical result).
+    rng = np.random.default_rng(0)
+    n = 12 ** 3
+    rho = 10 ** rng.uniform(-1, 1, n)
+    T = 10 ** rng.uniform(-1, 1, n)
+    g = 10 ** rng.uniform(0, 1.5, n)
+    d = rng.normal(size=(3, n))
+    d /= np.linalg.norm(d, axis=0)
+    C = _cons(oracle, np.vstack([rho, np.sqrt(g * g - 1) * d, rho * T])).reshape(5, 12, 12, 12)
+    dt = oracle.cfl_dt(C, 1 / 64)
+    r = oracle.advance_block(C, (8, 8, 8), (1, 1, 1), dt, 1 / 64)
+    assert r["retries"] > 0 and r["status"] == 0
+    c2p = oracle.con2pri(r["out"].reshape(5, -1))
+    assert np.all(c2p["A"] > 2e-16)
+    # and a smooth patch needs none
+    C = _random_smooth_block(oracle, rng, (12, 12, 12))
+    r = oracle.advance_block(C, (8, 8, 8), (1, 1, 1), 1e-3, 1 / 12)
+    assert r["retries"] == 0 and r["status"] == 0
+
+
+def test_patch_batch_matches_block(oracle):
+    rng = np.random.default_rng(2)
+    P = np.stack([_random_smooth_block(oracle, rng, (12, 12, 12)) for _ in range(3)])
+    dt_dh = np.array([[1e-3, 0.1], [2e-3, 0.05], [5e-4, 0.2]])
+    r = oracle.advance_patches(P, dt_dh, want_flux=True)
+    for i in range(3):
+        b = oracle.advance_block(P[i], (8, 8, 8), (1, 1, 1), dt_dh[i, 0], dt_dh[i, 1],
+                                 want_flux=True)
+        assert np.array_equal(b["out"], r["out"][i])
+        assert np.array_equal(b["flux"], r["flux"][i].reshape(-1))
+
+
+def test_characteristic_speeds(oracle):
+    # Wave-speed bounds of the Riemann solver. For flow along the normal they
+    # are the relativistic sums (v +/- c_s)/(1 +/- v c_s); in general they
+    # equal the three-velocity form of Mignone & Bodo,
+    # [v_d (1-cs2) +/- cs sqrt((1-v^2)(1 - v^2 cs2 - v_d^2 (1-cs2)))] / (1 - v^2 cs2),
+    # of which the oracle evaluates the four-velocity rewrite.
+    rng = np.random.default_rng(4)
+    for _ in range(200):
+        T = 10 ** rng.uniform(-4, 3)
+        U = rng.normal(0, 2, 3)
+        W = np.array([1.0, *U, T])
+        cs2 = oracle.cs2_of_T(T)
+        cs = np.sqrt(cs2)
+        g = np.sqrt(1 + U @ U)
+        v = U / g
+        v2 = v @ v
+        for d in range(3):
+            lm, lp = oracle.char_speeds(d, W)
+            r = cs * np.sqrt((1 - v2) * (1 - v2 * cs2 - v[d] ** 2 * (1 - cs2)))
+            ref_m = (v[d] * (1 - cs2) - r) / (1 - v2 * cs2)
+            ref_p = (v[d] * (1 - cs2) + r) / (1 - v2 * cs2)
+            assert abs(lm - ref_m) < 1e-12 and abs(lp - ref_p) < 1e-12
+        W1 = np.array([1.0, U[0], 0.0, 0.0, T])
+        lm, lp = oracle.char_speeds(0, W1)
+        vx = U[0] / np.sqrt(1 + U[0] ** 2)
+        assert abs(lm - (vx - cs) / (1 - vx * cs)) < 1e-13
+        assert abs(lp - (vx + cs) / (1 + vx * cs)) < 1e-13
