@@ -1,0 +1,478 @@
+#!/usr/bin/env python
+"""Benchmark of the per-patch SRHD fluid update on GB300 (cell updates/s).
+
+Workload: the 3-D periodic smooth-advection problem at 256^3 cells
+(rho = 1 + 0.5 sin(2 pi (x+y+z)), p = 1, gamma = 10 along the diagonal),
+tiled into 32768 patches of 8^3 cells with 2 ghost cells. One step is one
+srhd_advance_patches launch over the whole batch: con2pri, PLM, the
+MUSCL-Hancock half step, HLLC, the conservative update with the unphysical
+check and retry, and the fused CFL minimum (plus its one-block finalize).
+The ghosted inputs (1.13 GB mixed, 2.26 GB FP64) are resident in HBM and
+larger than L2, so no flush is needed between steps.
+
+The headline is the mixed path (float storage and arithmetic, A of the
+con2pri equation in double); the FP64 path is measured in the same run and
+reported under "fp64". Multi-GPU (torchrun): every rank advances its own
+copy of the batch (weak scaling, no data-path collective); the value is
+all cells updated / max time over ranks.
+
+--impl reference times the FP64 CPU oracle on the host cores instead (a
+bounded sample of the same workload per step).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_GRID = 256
+CELLS_PER_PATCH = 512
+METRIC = "cell updates/sec on 1 GB300 (mixed vs FP64) at stated L1 error; % HBM roofline"
+UNIT = "cell updates/s"
+WORKLOAD = ("3-D periodic smooth advection 256^3 (rho=1+0.5 sin(2pi(x+y+z)), p=1, gamma=10 "
+            "along (1,1,1)); 32768 patches of 8^3 + 2 ghost cells; one fused MUSCL-Hancock/HLLC "
+            "step with limiter retry and CFL min-reduction per step")
+
+# Algorithmic work per cell update, counted by the oracle's op-counting
+# instantiation (oracle/count_flops.py): adds+subs, muls, divs, sqrts of one
+# MUSCL-Hancock step of the benchmark state in the large-block limit, plus
+# the CFL bound of the updated cell.
+FLOPS_PER_CELL_UPDATE = 4583.2
+# Algorithmic bytes per cell update: 5 conserved values read + 5 written.
+BYTES_PER_CELL_UPDATE = {"mixed": 40, "fp64": 80}
+# Peaks: FP32 from the unit counts (152 SMs x 128 FP32 lanes x 2 flops x
+# 2070 MHz); FP64 at the nominal 1.25 TFLOP/s of GB300; HBM measured.
+PEAK_FP32_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+PEAK_FP64_TFLOPS = 1.25
+# DRAM traffic per launch of the patch kernel from one ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum), keyed by precision, valid
+# only for the kernel sources with the recorded hash.
+NCU_TRAFFIC = {"sources_sha": None, "mixed": None, "fp64": None}
+
+
+def kernel_sources_sha() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2012_11130_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.startswith("srhd_") and f.endswith((".cu", ".cuh", ".inl")):
+            h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"bench_clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return None
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for name, flag in zip(names, f[5:9]):
+                if flag.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# distributed helpers (torchrun)
+# ---------------------------------------------------------------------------
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+# ---------------------------------------------------------------------------
+# workload on the device
+# ---------------------------------------------------------------------------
+def build_workload(torch, srhd, ctx, prec, n=N_GRID):
+    from paper_2012_11130_gb300 import workloads
+    W = workloads.advection_prims(n)                       # float64 [5][n][n][n]
+    Wd = torch.from_numpy(W).to("cuda")
+    del W
+    C = ctx.prim2con(Wd.reshape(5, -1)).reshape(5, n, n, n)
+    del Wd
+    npx = n // 8
+    P = C.reshape(5, npx, 8, npx, 8, npx, 8).permute(1, 3, 5, 0, 2, 4, 6).reshape(-1, 5, 8, 8, 8)
+    dtype = torch.float32 if prec == "mixed" else torch.float64
+    P = P.to(dtype).contiguous()
+    del C
+    G = ctx.fill_ghosts_uniform(P, npx, npx, npx)
+    del P
+    npatch = G.shape[0]
+    dh = 1.0 / n
+    dt_dh = torch.tensor([[0.4 * dh, dh]], dtype=torch.float64, device="cuda").repeat(npatch, 1)
+    return G, dt_dh
+
+
+def time_device(torch, ctx, G, dt_dh, steps, warmup, barrier):
+    npatch = G.shape[0]
+    out = torch.empty((npatch, 5, 8, 8, 8), dtype=G.dtype, device="cuda")
+    dn = torch.empty(1, dtype=torch.float64, device="cuda")
+    st = torch.empty(npatch, dtype=torch.int32, device="cuda")
+    stream = torch.cuda.current_stream()
+    for _ in range(warmup):
+        ctx.advance_patches(G, dt_dh, cons_out=out, dt_next=dn, patch_status=st)
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(steps)]
+    barrier()
+    torch.cuda.synchronize()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for e0, e1 in evs:
+        e0.record(stream)
+        ctx.advance_patches(G, dt_dh, cons_out=out, dt_next=dn, patch_status=st)
+        e1.record(stream)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    total_ms = t0.elapsed_time(t1)
+    per = [e0.elapsed_time(e1) for e0, e1 in evs]
+    status_max = int(st.abs().max().item())
+    return total_ms, per, dn.item(), status_max
+
+
+def time_e2e(torch, ctx, G, dt_dh, steps, warmup):
+    """Public API with host buffers: every step copies the ghosted batch
+    from pinned host memory, runs the step and reads back the updated
+    interiors and the next time step."""
+    Gh = torch.empty(G.shape, dtype=G.dtype, pin_memory=True)
+    Gh.copy_(G)
+    dth = dt_dh.cpu().pin_memory()
+    outh = torch.empty((G.shape[0], 5, 8, 8, 8), dtype=G.dtype, pin_memory=True)
+    dnh = torch.empty(1, dtype=torch.float64, pin_memory=True)
+    for _ in range(warmup):
+        ctx.advance_patches(Gh, dth, cons_out=outh, dt_next=dnh)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    for _ in range(steps):
+        ctx.advance_patches(Gh, dth, cons_out=outh, dt_next=dnh)
+    torch.cuda.synchronize()
+    secs = time.perf_counter() - t
+    h2d = Gh.numel() * Gh.element_size() + dth.numel() * 8
+    d2h = outh.numel() * outh.element_size() + 8
+    del Gh, outh
+    return secs, h2d, d2h
+
+
+def l1_one_period(torch, srhd, prec, n=64):
+    """L1 error of rho (Eq. relative L1 error) after one period of the
+    diagonal wave at n^3, evolved on the GPU with the fused CFL."""
+    import numpy as np
+    from paper_2012_11130_gb300 import workloads
+    ctx = srhd.Context(srhd.Params())
+    W = torch.from_numpy(workloads.advection_prims(n)).to("cuda")
+    C = ctx.prim2con(W.reshape(5, -1)).reshape(5, n, n, n)
+    npx = n // 8
+    dtype = torch.float32 if prec == "mixed" else torch.float64
+    U = C.reshape(5, npx, 8, npx, 8, npx, 8).permute(1, 3, 5, 0, 2, 4, 6).reshape(
+        -1, 5, 8, 8, 8).to(dtype).contiguous()
+    v = math.sqrt(99.0 / 3.0) / math.sqrt(100.0)
+    t_end = 1.0 / (3 * v)
+    dh = 1.0 / n
+    dd = torch.empty((U.shape[0], 2), dtype=torch.float64, device="cuda")
+    dn = torch.empty(1, dtype=torch.float64, device="cuda")
+    out = torch.empty_like(U)
+    dt = ctx.cfl_dt(U, dh).item()
+    t = 0.0
+    steps = 0
+    while t < t_end and steps < 100000:
+        dt = min(dt, t_end - t)
+        dd[:, 0] = dt
+        dd[:, 1] = dh
+        G = ctx.fill_ghosts_uniform(U, npx, npx, npx)
+        ctx.advance_patches(G, dd, cons_out=out, dt_next=dn)
+        U, out = out, U
+        t += dt
+        steps += 1
+        dt = dn.item()
+    Pd = ctx.con2pri(U.permute(1, 0, 2, 3, 4).reshape(5, -1).contiguous())
+    rho = Pd[0].double().reshape(npx, npx, npx, 8, 8, 8).permute(0, 3, 1, 4, 2, 5).reshape(
+        n, n, n).cpu().numpy()
+    exact = workloads.advection_prims(n, t=t_end)[0]
+    return float(np.mean(np.abs(1.0 - rho / exact))), steps
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle baseline (host cores)
+# ---------------------------------------------------------------------------
+def _oracle_chunk(args):
+    start, count = args
+    import numpy as np
+    from oracle import oracle as O
+    from paper_2012_11130_gb300 import workloads
+    idx = np.arange(start, start + count)
+    Wp = workloads.advection_ghosted_patch_prims(N_GRID, idx)
+    C, _ = O.prim2con(Wp.transpose(1, 0, 2, 3, 4).reshape(5, -1))
+    C = C.reshape(5, count, 12, 12, 12).transpose(1, 0, 2, 3, 4).copy()
+    dh = 1.0 / N_GRID
+    dt_dh = np.tile([0.4 * dh, dh], (count, 1))
+    t = time.perf_counter()
+    r = O.advance_patches(C, dt_dh)
+    for q in range(count):
+        O.cfl_dt(r["out"][q].reshape(5, -1), dh)  # the fused CFL of the step
+    return time.perf_counter() - t
+
+
+class OracleSampler:
+    """Times the FP64 oracle on bounded samples of the workload's patches,
+    spread over a persistent pool of spawned processes (one per host core)."""
+
+    def __init__(self, cores: int):
+        import multiprocessing as mp
+        from oracle import oracle as O
+        O.build()
+        self.cores = cores
+        self.pool = mp.get_context("spawn").Pool(cores)
+        self.pool.map(_oracle_chunk, [(c, 1) for c in range(cores)])  # import + warm
+        self.per_patch = max(_oracle_chunk((0, 8)) / 8, 1e-5)
+
+    def sample(self, npatch_total: int, target_s: float, offset: int = 0):
+        """Returns (cells/s, patches, wall seconds) of one sample."""
+        per_core = max(1, int(target_s / self.per_patch))
+        span = max(1, npatch_total - per_core)
+        chunks = [((offset + c * per_core) % span, per_core) for c in range(self.cores)]
+        t = time.perf_counter()
+        self.pool.map(_oracle_chunk, chunks)
+        wall = time.perf_counter() - t
+        n = per_core * self.cores
+        return n * CELLS_PER_PATCH / wall, n, wall
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    cores = os.cpu_count() or 1
+    npatch = (N_GRID // 8) ** 3
+    per_step = max(2.0, min(8.0, 150.0 / max(1, args.steps + args.warmup)))
+    sampler = OracleSampler(cores)
+    for w in range(args.warmup):
+        sampler.sample(npatch, per_step / 4, offset=97 * w)
+    walls, ns = [], []
+    for s in range(args.steps):
+        _, n, wall = sampler.sample(npatch, per_step, offset=1013 * (s + 1))
+        walls.append(wall)
+        ns.append(n)
+    sampler.close()
+    value = sum(ns) * CELLS_PER_PATCH / sum(walls)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * sum(walls) / len(walls), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "reference": "FP64 CPU oracle (the paper's method "
+                   "restated, test infrastructure), host cores", "sample_patches_per_step":
+                   int(statistics.median(ns))},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{int(statistics.median(ns))} of 32768 patches per step "
+                                   f"(one step each with CFL, FP64, {cores} spawned processes)"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# ---------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+        barrier = lambda: dist.barrier(device_ids=[local])  # noqa: E731
+    else:
+        torch.cuda.set_device(0)
+        barrier = lambda: None  # noqa: E731
+    from paper_2012_11130_gb300 import build as b
+    if rank == 0 or world == 1:
+        b.build()
+    if world > 1:
+        barrier()
+    from paper_2012_11130_gb300 import srhd
+    ctx = srhd.Context(srhd.Params())
+    npatch = (args.grid // 8) ** 3
+    cells = npatch * CELLS_PER_PATCH
+    peaks = measured_peaks()
+    hbm_peak = float(peaks.get("hbm_gbs", 6789.3))
+    sha = kernel_sources_sha()
+
+    results = {}
+    precs = ("mixed", "fp64") if args.prec == "both" else (args.prec,)
+    for prec in precs:
+        G, dt_dh = build_workload(torch, srhd, ctx, prec, args.grid)
+        torch.cuda.synchronize()
+        with ClockSampler(local) as clk:
+            total_ms, per, dt_next, smax = time_device(torch, ctx, G, dt_dh, args.steps,
+                                                       args.warmup, barrier)
+        clocks = clk.summary()
+        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+        if world > 1:
+            import torch.distributed as dist
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = t.item()
+        e2e = None
+        if not args.no_e2e:
+            secs, h2d, d2h = time_e2e(torch, ctx, G, dt_dh, max(3, args.steps // 4), 1)
+            e2e = {"value": world * cells * max(3, args.steps // 4) / secs, "unit": UNIT,
+                   "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+        launch_ms = statistics.mean(per)
+        flops = FLOPS_PER_CELL_UPDATE * cells
+        peak_alu = PEAK_FP32_TFLOPS if prec == "mixed" else PEAK_FP64_TFLOPS
+        achieved = flops / (launch_ms * 1e-3) / 1e12
+        traffic = NCU_TRAFFIC.get(prec) if NCU_TRAFFIC.get("sources_sha") == sha else None
+        alg_bytes = BYTES_PER_CELL_UPDATE[prec] * cells
+        results[prec] = {
+            "value": world * cells * args.steps / (total_ms * 1e-3),
+            "ms_per_step": total_ms / args.steps,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_alu,
+                         "unit": "TFLOP/s", "frac": achieved / peak_alu, "traffic": traffic,
+                         "peak_source": ("derived: 152 SM x 128 FP32 lanes x 2 x 2070 MHz"
+                                         if prec == "mixed" else "nominal GB300 FP64 1.25 TFLOP/s"),
+                         "flops_per_cell_update": FLOPS_PER_CELL_UPDATE},
+            "hbm_roofline": {"bound": "hbm", "achieved": alg_bytes / (launch_ms * 1e-3) / 1e9,
+                             "peak": hbm_peak, "unit": "GB/s",
+                             "frac": alg_bytes / (launch_ms * 1e-3) / 1e9 / hbm_peak,
+                             "bytes_per_cell_update": BYTES_PER_CELL_UPDATE[prec],
+                             "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)"},
+            "clocks": clocks, "e2e": e2e, "dt_next": dt_next, "patch_status_max": smax,
+            "launch_ms_mean": launch_ms, "launch_ms_min": min(per),
+        }
+        del G, dt_dh
+        torch.cuda.empty_cache()
+
+    l1 = {}
+    if not args.no_l1 and rank == 0:
+        for prec in precs:
+            l1[prec], l1_steps = l1_one_period(torch, srhd, prec)
+        l1["grid"] = "64^3, one period, fused CFL 0.5"
+
+    if rank != 0:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+        return 0
+
+    cpu = None
+    if world == 1 and not args.no_cpu:
+        sampler = OracleSampler(os.cpu_count() or 1)
+        v, n, wall = sampler.sample(npatch, args.cpu_seconds)
+        sampler.close()
+        cpu = {"value": v, "unit": UNIT, "cores": os.cpu_count() or 1, "kind": "oracle",
+               "sample": f"{n} of 32768 patches (one FP64 oracle step each, with CFL), "
+                         f"{os.cpu_count()} spawned processes, {wall:.1f} s"}
+    m = results[precs[0]]
+    line = {
+        "metric": METRIC, "value": m["value"], "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": m["ms_per_step"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+f64" if precs[0] == "mixed" else "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD if args.grid == N_GRID else
+                   WORKLOAD.replace("256^3", f"{args.grid}^3").replace("32768", str(npatch)),
+                   "cells": cells, "patches": npatch,
+                   "precision": ("mixed: float storage/arithmetic, con2pri A in double"
+                                 if precs[0] == "mixed" else "fp64"),
+                   "l2": "inputs larger than L2 (ghosted batch resident in HBM), no flush",
+                   "parallelism": f"replicas x{world}"},
+        "roofline": m["roofline"], "hbm_roofline": m["hbm_roofline"],
+        "clocks": m["clocks"], "e2e": m["e2e"], "cpu_baseline": cpu,
+        "gpu_launches": 2 * args.steps,
+        "fp64": ({k: results["fp64"][k] for k in ("value", "ms_per_step", "roofline",
+                                                   "hbm_roofline", "clocks", "e2e")}
+                 if "fp64" in results and precs[0] != "fp64" else None),
+        "l1_rho": l1 or None,
+        "kernel_sources_sha": sha,
+    }
+    print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-l1", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--grid", type=int, default=N_GRID,
+                    help="cells per axis of the advection grid (multiple of 8)")
+    ap.add_argument("--prec", choices=["both", "mixed", "fp64"], default="both")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)  # at least 3 untimed warm-up steps
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,193 @@
+/*
+ * srhd.h - C ABI of libsrhd.so, the GB300 (sm_103a) per-patch fluid update of
+ * special-relativistic hydrodynamics with the Taub-Mathews equation of state,
+ * following Tseng, Schive & Chiueh, "GAMER-SR" (arXiv 2012.11130).
+ *
+ * Conventions (all entry points)
+ *   Units c = m = k_B = 1 (Section 1); T means k_B T / m c^2.
+ *   Primitive variables W = (rho, U^x, U^y, U^z, p): proper density, spatial
+ *   four-velocity (Eq. new expression of Lorentz factor), pressure.
+ *   Conserved variables U = (D, M^x, M^y, M^z, Etilde): D = rho gamma
+ *   (Eq. density), M = D h U (Eq. momentum), Etilde = E - D (Eq. ETilde).
+ *   Arrays are structure-of-arrays: variable v of element i is at
+ *   base[v * var_stride + i]. Patch arrays are [npatch][5][cells] with
+ *   x fastest: a ghosted patch holds 12^3 cells (an 8^3 interior plus two
+ *   ghost cells on every side, Section 3.1), an interior patch 8^3 cells.
+ *   Precision: SRHD_FP64 = double storage and double arithmetic;
+ *   SRHD_MIXED = float storage, float arithmetic, except the left-hand side
+ *   A of Eq. (transcendental equation) / Eq. (Unphysical result), which is
+ *   formed in double in every conserved-to-primitive conversion.
+ *
+ * Ownership and execution
+ *   Every data pointer is a caller-owned DEVICE pointer on the context's
+ *   device unless stated otherwise. The library allocates device memory only
+ *   in srhd_create (the context's scratch) and frees it in srhd_destroy.
+ *   Calls are asynchronous on the given stream (a cudaStream_t passed as
+ *   void*, NULL = legacy default stream) and never synchronise the device.
+ *   A context must not be used by two streams at once: its scratch is
+ *   shared by the calls that use it (srhd_advance_patches with dt_next,
+ *   srhd_cfl_dt).
+ *
+ * Errors
+ *   Every call returns an srhd_status. Argument errors are detected on the
+ *   host before any launch (SRHD_ERR_ARG) and launch failures are reported
+ *   as SRHD_ERR_CUDA; srhd_last_error() returns a description of the last
+ *   failure on the calling thread. Device-side outcomes (unphysical cells,
+ *   retries, Newton non-convergence) are written to the caller's status
+ *   arrays; no kernel traps, asserts or spins, and every loop is bounded.
+ */
+#ifndef SRHD_H
+#define SRHD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum srhd_status {
+  SRHD_OK = 0,
+  SRHD_ERR_ARG = 1,   /* invalid argument (null pointer, size, enum, ...) */
+  SRHD_ERR_CUDA = 2,  /* a CUDA runtime call or launch failed */
+} srhd_status;
+
+typedef enum srhd_prec {
+  SRHD_FP64 = 0,   /* double storage, double arithmetic */
+  SRHD_MIXED = 1,  /* float storage and arithmetic; A of Eq. (transcendental
+                      equation) in double */
+} srhd_prec;
+
+typedef enum srhd_riemann { SRHD_HLLC = 0, SRHD_HLLE = 1 } srhd_riemann;
+typedef enum srhd_cfl_mode { SRHD_CFL_SIGNAL = 0, SRHD_CFL_LIGHT = 1 } srhd_cfl_mode;
+typedef enum srhd_bc { SRHD_BC_PERIODIC = 0, SRHD_BC_OUTFLOW = 1 } srhd_bc;
+
+/* Per-cell status codes written by srhd_con2pri (cell_status). */
+enum {
+  SRHD_CELL_OK = 0,
+  SRHD_CELL_UNPHYSICAL = 1, /* Eq. (Unphysical result) fails: A <= eps_machine
+                               (2e-16, Section 3.3); outputs are NaN */
+  SRHD_CELL_NOCONV = 2,     /* Newton-Raphson hit its iteration cap; outputs
+                               hold the last iterate */
+};
+
+/* Per-patch status of srhd_advance_patches / srhd_flux_patches:
+ * (code << 8) | retries, where retries (0..255) counts the limiter
+ * reductions of Section 3.3 (1) and code is a bit set of: */
+enum {
+  SRHD_PATCH_UNPHYSICAL = 1, /* still unphysical with piecewise-constant data */
+  SRHD_PATCH_BAD_INPUT = 2,  /* a cell of the ghosted input is unphysical */
+  SRHD_PATCH_NOCONV = 4,     /* some Newton solve hit its iteration cap */
+};
+
+/* Run-time parameters (Sections 3.1-3.3). */
+typedef struct srhd_params {
+  double cfl;             /* C_CFL of Eq. (time_step_sound_speed); default 0.5 */
+  double theta;           /* minmod coefficient of the PLM limiter; default 1.5 */
+  double retry_factor;    /* limiter reduction per retry (Section 3.3); 0.75 */
+  double theta_floor;     /* below theta_floor * theta the retry uses theta = 0
+                             (piecewise constant); default 1e-2 */
+  int32_t riemann;        /* srhd_riemann; default SRHD_HLLC */
+  int32_t cfl_mode;       /* srhd_cfl_mode; default SRHD_CFL_SIGNAL */
+  int32_t ndim;           /* active dimensions in the CFL bound
+                             (Eq. time_step_U_max uses 3); default 3 */
+  int32_t newton_max_iter;/* Newton iteration cap; 0 = 50 (FP64) / 30 (FP32) */
+} srhd_params;
+
+typedef struct srhd_ctx srhd_ctx;
+
+/* Fills *p with the defaults listed above. Returns SRHD_ERR_ARG if p is NULL. */
+srhd_status srhd_default_params(srhd_params* p);
+
+/* Creates a context on the current CUDA device: validates *p (NULL means
+ * defaults), queries the SM count and allocates the scratch used by the CFL
+ * reduction. *ctx receives the handle (NULL on failure). */
+srhd_status srhd_create(srhd_ctx** ctx, const srhd_params* p);
+
+/* Frees the context and its scratch. The caller must make sure no work that
+ * uses the context is still running. NULL is accepted. */
+srhd_status srhd_destroy(srhd_ctx* ctx);
+
+/* Description of the last error on the calling thread ("" if none). */
+const char* srhd_last_error(void);
+
+/* Primitive -> conserved, n independent cells (Section 2.3: Eq. density,
+ * Eq. momentum, Eq. T_to_HTilde, Eq. E_D, with f from Eq. transcendental
+ * equation).
+ *   prim  [5 * var_stride] input, cons [5 * var_stride] output, element type
+ *         double (SRHD_FP64) or float (SRHD_MIXED); var_stride >= n.
+ *   Cells with rho <= 0 or p <= 0 produce NaN. n == 0 is a no-op. */
+srhd_status srhd_prim2con(srhd_ctx* ctx, srhd_prec prec, const void* prim, void* cons,
+                          int64_t n, int64_t var_stride, void* stream);
+
+/* Conserved -> primitive, n independent cells (Section 2.3: Newton-Raphson
+ * on Eq. transcendental equation in htilde with the initial guesses and
+ * derivative of Appendix A, then Eq. four-velocity, Eq. new expression of
+ * Lorentz factor, Eq. density, Eq. T of h, Eq. p=rhoT).
+ *   cons, prim as in srhd_prim2con.
+ *   cell_status [n] int32 (nullable): SRHD_CELL_* per cell. */
+srhd_status srhd_con2pri(srhd_ctx* ctx, srhd_prec prec, const void* cons, void* prim,
+                         int64_t n, int64_t var_stride, int32_t* cell_status, void* stream);
+
+/* Riemann fluxes of a batch of ghosted patches: the first part of
+ * srhd_advance_patches (con2pri of the tile, PLM, MUSCL-Hancock half step,
+ * con2pri of the predicted face states, HLLC/HLLE; Section 3.1), stopping
+ * before the update.
+ *   cons_ghosted [npatch][5][12^3]; face_flux [npatch][3][5][576] output,
+ *   direction d faces ordered with extent 9 along d and 8 across, x fastest
+ *   (face index i along d sits between interior cells i-1 and i);
+ *   dt_dh [npatch][2] device doubles (dt, dh) per patch;
+ *   patch_status [npatch] int32 (nullable): code bits only (no retry is made
+ *   without an update). */
+srhd_status srhd_flux_patches(srhd_ctx* ctx, srhd_prec prec, const void* cons_ghosted,
+                              void* face_flux, int32_t npatch, const double* dt_dh,
+                              int32_t* patch_status, void* stream);
+
+/* One MUSCL-Hancock step of a batch of independent ghosted patches
+ * (Sections 3.1-3.3): con2pri, PLM with the hybrid van Leer / generalised
+ * minmod limiter, Hancock half step, con2pri of predicted face states,
+ * HLLC (HLLE option and fallback), conservative update (Eq. conservative
+ * form with Eq. ETilde evolution), the unphysical check Eq. (Unphysical
+ * result) with the whole-patch limiter retry, and optionally the CFL time
+ * step of the updated state (Eqs. time_step_U_max, SMax,
+ * time_step_sound_speed).
+ *   cons_ghosted [npatch][5][12^3] input (not modified).
+ *   cons_out     [npatch][5][8^3] output; must not overlap the input.
+ *   patch_face_flux (nullable) [npatch][6][5][64]: fluxes through the six
+ *                patch faces (-x,+x,-y,+y,-z,+z), 8x8 each, for coarse-fine
+ *                flux correction.
+ *   npatch >= 0; dt_dh [npatch][2] device doubles (dt, dh) per patch.
+ *   worklist (nullable) [npatch] int32: the launch processes patches
+ *                worklist[0..npatch) (indices into every per-patch array);
+ *                NULL means 0..npatch-1. Indices are not range checked on
+ *                the device; the caller guarantees they are valid.
+ *   dt_next (nullable): one device double receiving min over the processed
+ *                patches of C_CFL dh / S_max of the updated cells, or NaN if
+ *                some updated cell is unphysical.
+ *   patch_status (nullable) [npatch] int32, see SRHD_PATCH_*. */
+srhd_status srhd_advance_patches(srhd_ctx* ctx, srhd_prec prec, const void* cons_ghosted,
+                                 void* cons_out, void* patch_face_flux, int32_t npatch,
+                                 const double* dt_dh, const int32_t* worklist, double* dt_next,
+                                 int32_t* patch_status, void* stream);
+
+/* CFL time step (Section 3.2) of a batch of interior patches:
+ * dt_out = min over all cells of C_CFL dh / S_max (signal mode) or
+ * C_CFL dh (light mode); NaN if some cell is unphysical.
+ *   cons [npatch][5][8^3]; dt_out: one device double. */
+srhd_status srhd_cfl_dt(srhd_ctx* ctx, srhd_prec prec, const void* cons, int32_t npatch,
+                        double dh, double* dt_out, void* stream);
+
+/* Ghost-zone fill of a uniform grid tiled by npx*npy*npz patches (patch
+ * (ix,iy,iz) at index (iz*npy + iy)*npx + ix), with periodic or outflow
+ * (zero-gradient copy) boundaries per axis. Not part of the paper's solver:
+ * a harness for uniform-grid runs, where all patches are on one level.
+ *   interior [np][5][8^3] input, ghosted [np][5][12^3] output;
+ *   bc[3] host array of srhd_bc for x, y, z. */
+srhd_status srhd_fill_ghosts_uniform(srhd_ctx* ctx, srhd_prec prec, const void* interior,
+                                     void* ghosted, int32_t npx, int32_t npy, int32_t npz,
+                                     const int32_t* bc, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SRHD_H */

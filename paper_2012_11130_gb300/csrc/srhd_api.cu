@@ -1,0 +1,350 @@
+// C ABI of libsrhd (declared in include/srhd.h): context management,
+// argument validation and launches. Device work is in srhd_kernels.cuh.
+#include <cfloat>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "srhd.h"
+#include "srhd_kernels.cuh"
+
+namespace srhd {
+extern template struct Launch<double>;
+extern template struct Launch<float>;
+
+__global__ void cfl_finalize_kernel(const double* partial, const int32_t* bad, int n,
+                                    double* dt_out) {
+  __shared__ double s_m[32];
+  __shared__ int s_b[32];
+  double m = DBL_MAX;
+  int b = 0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    m = fmin(m, partial[i]);
+    b |= bad[i];
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    m = fmin(m, __shfl_xor_sync(0xffffffffu, m, o));
+    b |= __shfl_xor_sync(0xffffffffu, b, o);
+  }
+  if ((threadIdx.x & 31) == 0) { s_m[threadIdx.x >> 5] = m; s_b[threadIdx.x >> 5] = b; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double mm = DBL_MAX;
+    int bb = 0;
+    for (int w = 0; w < int(blockDim.x >> 5); ++w) { mm = fmin(mm, s_m[w]); bb |= s_b[w]; }
+    if (bb) mm = __longlong_as_double(0x7ff8000000000000ULL);
+    else if (mm == DBL_MAX) mm = __longlong_as_double(0x7ff0000000000000ULL);  // +inf: no cells
+    dt_out[0] = mm;
+  }
+}
+}  // namespace srhd
+
+struct srhd_ctx {
+  srhd_params params;
+  int device;
+  int num_sms;
+  int patch_grid[2];      // persistent grid per precision
+  int scratch_slots;      // capacity of the partial-minimum arrays
+  double* partial_dt;     // scratch [scratch_slots]
+  int32_t* partial_bad;   // scratch [scratch_slots]
+};
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+srhd_status fail(srhd_status st, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+  return st;
+}
+
+srhd_status cuda_fail(cudaError_t e, const char* what) {
+  return fail(SRHD_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+bool valid_prec(srhd_prec p) { return p == SRHD_FP64 || p == SRHD_MIXED; }
+
+int newton_maxit(const srhd_ctx* c, srhd_prec prec) {
+  if (c->params.newton_max_iter > 0) return c->params.newton_max_iter;
+  return prec == SRHD_FP64 ? 50 : 30;
+}
+
+int grid_for(const srhd_ctx* c, int64_t n, int per_sm) {
+  int64_t g = (n + 255) / 256;
+  int64_t cap = (int64_t)c->num_sms * per_sm;
+  if (g > cap) g = cap;
+  return g < 1 ? 1 : int(g);
+}
+
+srhd_status check_params(const srhd_params* p) {
+  if (!(p->cfl > 0.0) || !(p->cfl <= 1.0)) return fail(SRHD_ERR_ARG, "cfl must be in (0, 1]");
+  if (!(p->theta >= 0.0) || !(p->theta <= 2.0)) return fail(SRHD_ERR_ARG, "theta must be in [0, 2]");
+  if (!(p->retry_factor > 0.0) || !(p->retry_factor < 1.0))
+    return fail(SRHD_ERR_ARG, "retry_factor must be in (0, 1)");
+  if (!(p->theta_floor > 0.0) || !(p->theta_floor < 1.0))
+    return fail(SRHD_ERR_ARG, "theta_floor must be in (0, 1)");
+  if (p->riemann != SRHD_HLLC && p->riemann != SRHD_HLLE)
+    return fail(SRHD_ERR_ARG, "riemann must be SRHD_HLLC or SRHD_HLLE");
+  if (p->cfl_mode != SRHD_CFL_SIGNAL && p->cfl_mode != SRHD_CFL_LIGHT)
+    return fail(SRHD_ERR_ARG, "cfl_mode must be SRHD_CFL_SIGNAL or SRHD_CFL_LIGHT");
+  if (p->ndim < 1 || p->ndim > 3) return fail(SRHD_ERR_ARG, "ndim must be 1, 2 or 3");
+  if (p->newton_max_iter < 0 || p->newton_max_iter > 1000)
+    return fail(SRHD_ERR_ARG, "newton_max_iter must be in [0, 1000]");
+  return SRHD_OK;
+}
+
+srhd_status check_ctx(const srhd_ctx* c) {
+  if (!c) return fail(SRHD_ERR_ARG, "ctx is NULL");
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev != c->device)
+    return fail(SRHD_ERR_ARG, "ctx was created on device %d but device %d is current", c->device,
+                dev);
+  return SRHD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+srhd_status srhd_default_params(srhd_params* p) {
+  if (!p) return fail(SRHD_ERR_ARG, "params is NULL");
+  p->cfl = 0.5;
+  p->theta = 1.5;
+  p->retry_factor = 0.75;
+  p->theta_floor = 1e-2;
+  p->riemann = SRHD_HLLC;
+  p->cfl_mode = SRHD_CFL_SIGNAL;
+  p->ndim = 3;
+  p->newton_max_iter = 0;
+  return SRHD_OK;
+}
+
+const char* srhd_last_error(void) { return g_err; }
+
+srhd_status srhd_create(srhd_ctx** out, const srhd_params* p) {
+  if (!out) return fail(SRHD_ERR_ARG, "ctx output pointer is NULL");
+  *out = nullptr;
+  srhd_params prm;
+  if (p) prm = *p; else srhd_default_params(&prm);
+  srhd_status st = check_params(&prm);
+  if (st != SRHD_OK) return st;
+  int dev = 0, nsm = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceGetAttribute");
+  if ((e = srhd::Launch<double>::setup()) != cudaSuccess) return cuda_fail(e, "setup fp64");
+  if ((e = srhd::Launch<float>::setup()) != cudaSuccess) return cuda_fail(e, "setup mixed");
+  srhd_ctx* c = new (std::nothrow) srhd_ctx;
+  if (!c) return fail(SRHD_ERR_ARG, "out of host memory");
+  c->params = prm;
+  c->device = dev;
+  c->num_sms = nsm;
+  int b64 = srhd::Launch<double>::patch_blocks_per_sm();
+  int b32 = srhd::Launch<float>::patch_blocks_per_sm();
+  if (b64 < 1 || b32 < 1) {
+    delete c;
+    return fail(SRHD_ERR_CUDA, "patch kernel does not fit on an SM (blocks/SM %d, %d)", b64, b32);
+  }
+  c->patch_grid[SRHD_FP64] = nsm * b64;
+  c->patch_grid[SRHD_MIXED] = nsm * b32;
+  c->scratch_slots = nsm * 8;
+  c->partial_dt = nullptr;
+  c->partial_bad = nullptr;
+  e = cudaMalloc(&c->partial_dt, sizeof(double) * c->scratch_slots);
+  if (e == cudaSuccess) e = cudaMalloc(&c->partial_bad, sizeof(int32_t) * c->scratch_slots);
+  if (e != cudaSuccess) {
+    cudaFree(c->partial_dt);
+    delete c;
+    return cuda_fail(e, "cudaMalloc scratch");
+  }
+  *out = c;
+  g_err[0] = 0;
+  return SRHD_OK;
+}
+
+srhd_status srhd_destroy(srhd_ctx* c) {
+  if (!c) return SRHD_OK;
+  cudaFree(c->partial_dt);
+  cudaFree(c->partial_bad);
+  delete c;
+  return SRHD_OK;
+}
+
+srhd_status srhd_prim2con(srhd_ctx* c, srhd_prec prec, const void* prim, void* cons, int64_t n,
+                          int64_t var_stride, void* stream) {
+  srhd_status st = check_ctx(c);
+  if (st != SRHD_OK) return st;
+  if (!valid_prec(prec)) return fail(SRHD_ERR_ARG, "invalid precision %d", int(prec));
+  if (n < 0 || var_stride < n) return fail(SRHD_ERR_ARG, "need 0 <= n <= var_stride");
+  if (n == 0) return SRHD_OK;
+  if (!prim || !cons) return fail(SRHD_ERR_ARG, "prim/cons is NULL");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int grid = grid_for(c, n, 16);
+  cudaError_t e = prec == SRHD_FP64
+                      ? srhd::Launch<double>::prim2con(prim, cons, n, var_stride, grid, s)
+                      : srhd::Launch<float>::prim2con(prim, cons, n, var_stride, grid, s);
+  return e == cudaSuccess ? SRHD_OK : cuda_fail(e, "prim2con launch");
+}
+
+srhd_status srhd_con2pri(srhd_ctx* c, srhd_prec prec, const void* cons, void* prim, int64_t n,
+                         int64_t var_stride, int32_t* cell_status, void* stream) {
+  srhd_status st = check_ctx(c);
+  if (st != SRHD_OK) return st;
+  if (!valid_prec(prec)) return fail(SRHD_ERR_ARG, "invalid precision %d", int(prec));
+  if (n < 0 || var_stride < n) return fail(SRHD_ERR_ARG, "need 0 <= n <= var_stride");
+  if (n == 0) return SRHD_OK;
+  if (!prim || !cons) return fail(SRHD_ERR_ARG, "prim/cons is NULL");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int grid = grid_for(c, n, 16);
+  int maxit = newton_maxit(c, prec);
+  cudaError_t e =
+      prec == SRHD_FP64
+          ? srhd::Launch<double>::con2pri(cons, prim, n, var_stride, cell_status, maxit, grid, s)
+          : srhd::Launch<float>::con2pri(cons, prim, n, var_stride, cell_status, maxit, grid, s);
+  return e == cudaSuccess ? SRHD_OK : cuda_fail(e, "con2pri launch");
+}
+
+static srhd_status launch_patches(srhd_ctx* c, srhd_prec prec, srhd::PatchArgs& a,
+                                  double* dt_next, cudaStream_t s) {
+  int grid = c->patch_grid[prec];
+  if (grid > a.npatch) grid = a.npatch;
+  if (dt_next) {
+    a.partial_dt = c->partial_dt;
+    a.partial_bad = c->partial_bad;
+  }
+  cudaError_t e = cudaSuccess;
+  if (a.npatch > 0) {
+    e = prec == SRHD_FP64 ? srhd::Launch<double>::patches(a, grid, s)
+                          : srhd::Launch<float>::patches(a, grid, s);
+    if (e != cudaSuccess) return cuda_fail(e, "patch kernel launch");
+  } else {
+    grid = 0;
+  }
+  if (dt_next) {
+    srhd::cfl_finalize_kernel<<<1, 256, 0, s>>>(c->partial_dt, c->partial_bad, grid, dt_next);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "cfl finalize launch");
+  }
+  return SRHD_OK;
+}
+
+static void fill_common(const srhd_ctx* c, srhd_prec prec, srhd::PatchArgs& a) {
+  a.theta0 = c->params.theta;
+  a.retry_factor = c->params.retry_factor;
+  a.theta_floor = c->params.theta_floor;
+  a.cfl = c->params.cfl;
+  a.riemann = c->params.riemann;
+  a.cfl_mode = c->params.cfl_mode;
+  a.ndim = c->params.ndim;
+  a.maxit = newton_maxit(c, prec);
+  a.partial_dt = nullptr;
+  a.partial_bad = nullptr;
+}
+
+srhd_status srhd_flux_patches(srhd_ctx* c, srhd_prec prec, const void* cons_ghosted,
+                              void* face_flux, int32_t npatch, const double* dt_dh,
+                              int32_t* patch_status, void* stream) {
+  srhd_status st = check_ctx(c);
+  if (st != SRHD_OK) return st;
+  if (!valid_prec(prec)) return fail(SRHD_ERR_ARG, "invalid precision %d", int(prec));
+  if (npatch < 0) return fail(SRHD_ERR_ARG, "npatch < 0");
+  if (npatch == 0) return SRHD_OK;
+  if (!cons_ghosted || !face_flux || !dt_dh)
+    return fail(SRHD_ERR_ARG, "cons_ghosted/face_flux/dt_dh is NULL");
+  srhd::PatchArgs a;
+  fill_common(c, prec, a);
+  a.in = cons_ghosted;
+  a.out = nullptr;
+  a.pflux = nullptr;
+  a.face_flux = face_flux;
+  a.npatch = npatch;
+  a.dt_dh = dt_dh;
+  a.worklist = nullptr;
+  a.status = patch_status;
+  a.flux_only = 1;
+  return launch_patches(c, prec, a, nullptr, static_cast<cudaStream_t>(stream));
+}
+
+srhd_status srhd_advance_patches(srhd_ctx* c, srhd_prec prec, const void* cons_ghosted,
+                                 void* cons_out, void* patch_face_flux, int32_t npatch,
+                                 const double* dt_dh, const int32_t* worklist, double* dt_next,
+                                 int32_t* patch_status, void* stream) {
+  srhd_status st = check_ctx(c);
+  if (st != SRHD_OK) return st;
+  if (!valid_prec(prec)) return fail(SRHD_ERR_ARG, "invalid precision %d", int(prec));
+  if (npatch < 0) return fail(SRHD_ERR_ARG, "npatch < 0");
+  if (npatch > 0 && (!cons_ghosted || !cons_out || !dt_dh))
+    return fail(SRHD_ERR_ARG, "cons_ghosted/cons_out/dt_dh is NULL");
+  if (npatch == 0 && !dt_next) return SRHD_OK;
+  srhd::PatchArgs a;
+  fill_common(c, prec, a);
+  a.in = cons_ghosted;
+  a.out = cons_out;
+  a.pflux = patch_face_flux;
+  a.face_flux = nullptr;
+  a.npatch = npatch;
+  a.dt_dh = dt_dh;
+  a.worklist = worklist;
+  a.status = patch_status;
+  a.flux_only = 0;
+  return launch_patches(c, prec, a, dt_next, static_cast<cudaStream_t>(stream));
+}
+
+srhd_status srhd_cfl_dt(srhd_ctx* c, srhd_prec prec, const void* cons, int32_t npatch, double dh,
+                        double* dt_out, void* stream) {
+  srhd_status st = check_ctx(c);
+  if (st != SRHD_OK) return st;
+  if (!valid_prec(prec)) return fail(SRHD_ERR_ARG, "invalid precision %d", int(prec));
+  if (npatch < 0) return fail(SRHD_ERR_ARG, "npatch < 0");
+  if (!dt_out) return fail(SRHD_ERR_ARG, "dt_out is NULL");
+  if (npatch > 0 && !cons) return fail(SRHD_ERR_ARG, "cons is NULL");
+  if (!(dh > 0.0) || !std::isfinite(dh)) return fail(SRHD_ERR_ARG, "dh must be positive");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int64_t ncell = (int64_t)npatch * srhd::kNC;
+  int grid = 0;
+  cudaError_t e = cudaSuccess;
+  if (ncell > 0) {
+    grid = int(std::min<int64_t>((ncell + srhd::kCflThreads - 1) / srhd::kCflThreads,
+                                 (int64_t)c->scratch_slots));
+    int maxit = newton_maxit(c, prec);
+    e = prec == SRHD_FP64
+            ? srhd::Launch<double>::cfl(cons, ncell, dh, c->params.cfl, c->params.ndim,
+                                        c->params.cfl_mode, maxit, c->partial_dt, c->partial_bad,
+                                        grid, s)
+            : srhd::Launch<float>::cfl(cons, ncell, dh, c->params.cfl, c->params.ndim,
+                                       c->params.cfl_mode, maxit, c->partial_dt, c->partial_bad,
+                                       grid, s);
+    if (e != cudaSuccess) return cuda_fail(e, "cfl launch");
+  }
+  srhd::cfl_finalize_kernel<<<1, 256, 0, s>>>(c->partial_dt, c->partial_bad, grid, dt_out);
+  e = cudaGetLastError();
+  return e == cudaSuccess ? SRHD_OK : cuda_fail(e, "cfl finalize launch");
+}
+
+srhd_status srhd_fill_ghosts_uniform(srhd_ctx* c, srhd_prec prec, const void* interior,
+                                     void* ghosted, int32_t npx, int32_t npy, int32_t npz,
+                                     const int32_t* bc, void* stream) {
+  srhd_status st = check_ctx(c);
+  if (st != SRHD_OK) return st;
+  if (!valid_prec(prec)) return fail(SRHD_ERR_ARG, "invalid precision %d", int(prec));
+  if (npx < 1 || npy < 1 || npz < 1) return fail(SRHD_ERR_ARG, "patch counts must be >= 1");
+  if (!interior || !ghosted || !bc) return fail(SRHD_ERR_ARG, "interior/ghosted/bc is NULL");
+  for (int d = 0; d < 3; ++d)
+    if (bc[d] != SRHD_BC_PERIODIC && bc[d] != SRHD_BC_OUTFLOW)
+      return fail(SRHD_ERR_ARG, "bc[%d] must be SRHD_BC_PERIODIC or SRHD_BC_OUTFLOW", d);
+  int64_t total = (int64_t)npx * npy * npz * 5 * srhd::kGC;
+  int grid = grid_for(c, total, 16);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t e = prec == SRHD_FP64
+                      ? srhd::Launch<double>::fill_ghosts(interior, ghosted, npx, npy, npz, bc, grid, s)
+                      : srhd::Launch<float>::fill_ghosts(interior, ghosted, npx, npy, npz, bc, grid, s);
+  return e == cudaSuccess ? SRHD_OK : cuda_fail(e, "fill_ghosts launch");
+}
+
+}  // extern "C"

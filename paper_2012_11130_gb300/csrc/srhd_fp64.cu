@@ -1,0 +1,6 @@
+// Double-precision instantiation of the libsrhd kernels (SRHD_FP64).
+#include "srhd_launch.inl"
+
+namespace srhd {
+template struct Launch<double>;
+}

@@ -1,0 +1,497 @@
+// Kernels of libsrhd (sm_103a): the fused per-patch MUSCL-Hancock step
+// (Sections 3.1-3.3 of arXiv 2012.11130), batched conversions, the CFL
+// reduction (Section 3.2) and a uniform-grid ghost fill.
+//
+// Fused patch kernel (one CTA per 8^3 patch, persistent over the batch):
+//   phase 1  con2pri of the 1376 cells of the 12^3 tile that the step reads
+//            -> primitive tile in shared memory [5][12^3]
+//   phase 2  for the 896 cells whose face states are used (the 8^3 interior
+//            and one layer around it, edges excluded): PLM slopes in x, y, z,
+//            six face states, their conserved form and physical fluxes, and
+//            the Hancock half step; the 3456 predicted face states that a
+//            flux uses go to shared memory [3][2][5][576]
+//   phase 3  per face (3 x 576): con2pri of both predicted states, HLLC or
+//            HLLE; the flux overwrites the left state in place
+//   phase 4  conservative update of the interior, Eq. (Unphysical result)
+//            check, optional CFL bound of the new state
+//   retry    if any predicted state or updated cell is unphysical, phases 2-4
+//            are redone with the limiter coefficient times retry_factor
+//            (block-wide vote), down to theta = 0 (piecewise constant)
+// Shared memory: 25920 elements of S (207 KB double, 101 KB float).
+#pragma once
+
+#include <cfloat>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "srhd_physics.cuh"
+
+namespace srhd {
+
+constexpr int kG = 12;              // ghosted patch edge
+constexpr int kN = 8;               // interior edge
+constexpr int kGC = kG * kG * kG;   // 1728 ghosted cells
+constexpr int kNC = kN * kN * kN;   // 512 interior cells
+constexpr int kNF = 9 * 8 * 8;      // 576 faces per direction
+constexpr int kRC = 512 + 6 * 64;   // 896 reconstructed cells
+
+enum { CODE_UNPHYSICAL = 1, CODE_BAD_INPUT = 2, CODE_NOCONV = 4 };
+
+struct PatchArgs {
+  const void* in;         // [np][5][12^3]
+  void* out;              // [np][5][8^3] (advance) or nullptr
+  void* pflux;            // [np][6][5][64] (nullable)
+  void* face_flux;        // [np][3][5][576] (flux mode)
+  int npatch;
+  const double* dt_dh;    // [np][2]
+  const int32_t* worklist;
+  int32_t* status;        // [np] (nullable)
+  double* partial_dt;     // [grid] CFL partial minima (nullable = no CFL)
+  int32_t* partial_bad;   // [grid]
+  double theta0, retry_factor, theta_floor, cfl;
+  int riemann, cfl_mode, ndim, maxit;
+  int flux_only;
+};
+
+template <class S> struct SmemLayout {
+  static constexpr size_t prim_elems = 5 * kGC;
+  static constexpr size_t face_elems = 3 * 2 * 5 * kNF;
+  static constexpr size_t bytes = (prim_elems + face_elems) * sizeof(S);
+};
+
+// Class of a ghosted coordinate: 0 interior [2,9], 1 first ghost layer,
+// 2 second ghost layer.
+__device__ __forceinline__ int gclass(int g) {
+  return (g >= 2 && g <= 9) ? 0 : ((g == 1 || g == 10) ? 1 : 2);
+}
+
+// Cells of the 12^3 tile whose primitives the step reads: at most one
+// coordinate in the ghost zone, or two coordinates both in the first layer.
+__device__ __forceinline__ bool tile_cell_needed(int gx, int gy, int gz) {
+  int a = gclass(gx), b = gclass(gy), c = gclass(gz);
+  int nout = (a > 0) + (b > 0) + (c > 0);
+  if (nout <= 1) return true;
+  return nout == 2 && a <= 1 && b <= 1 && c <= 1;
+}
+
+// r-th reconstructed cell, interior coordinates in [-1, 8].
+__device__ __forceinline__ void recon_cell(int r, int& i, int& j, int& k) {
+  if (r < kNC) {
+    i = r & 7; j = (r >> 3) & 7; k = r >> 6;
+    return;
+  }
+  r -= kNC;
+  int layer = r >> 6, q = r & 63, a = q & 7, b = q >> 3;
+  int side = (layer & 1) ? 8 : -1;
+  switch (layer >> 1) {
+    case 0: i = side; j = a; k = b; break;
+    case 1: i = a; j = side; k = b; break;
+    default: i = a; j = b; k = side; break;
+  }
+}
+
+__device__ __forceinline__ int tile_index(int i, int j, int k) {  // interior coords
+  return ((k + 2) * kG + (j + 2)) * kG + (i + 2);
+}
+
+// Face index along d at face coordinate fd (0..8), transverse coordinates
+// of the two others; faces ordered with extent 9 along d, x fastest.
+template <int d> __device__ __forceinline__ int face_index(int i, int j, int k, int fd) {
+  if (d == 0) return (k * 8 + j) * 9 + fd;
+  if (d == 1) return (k * 9 + fd) * 8 + i;
+  return (fd * 8 + j) * 8 + i;
+}
+
+template <class S> __device__ __forceinline__ S* face_slot(S* face, int d, int side, int v) {
+  return face + ((d * 2 + side) * 5 + v) * kNF;
+}
+
+template <int d, class R, class S>
+__device__ __forceinline__ void recon_direction(const S* prim, int tc, const PrimX<R>& W, R theta,
+                                                int i, int j, int k, bool interior, S* face,
+                                                R dF[5], int& bad) {
+  constexpr int off = (d == 0) ? 1 : ((d == 1) ? kG : kG * kG);
+  R wc[5] = {W.rho, W.u[0], W.u[1], W.u[2], W.p};
+  PrimX<R> Wm, Wp;
+  R fm[5], fp[5];
+#pragma unroll
+  for (int v = 0; v < 5; ++v) {
+    R lo = R(prim[v * kGC + tc - off]);
+    R hi = R(prim[v * kGC + tc + off]);
+    R dW = limited_slope(wc[v] - lo, hi - wc[v], theta);
+    fm[v] = wc[v] - R(0.5) * dW;
+    fp[v] = wc[v] + R(0.5) * dW;
+  }
+  Wm.rho = fm[0]; Wm.u[0] = fm[1]; Wm.u[1] = fm[2]; Wm.u[2] = fm[3]; Wm.p = fm[4];
+  Wp.rho = fp[0]; Wp.u[0] = fp[1]; Wp.u[1] = fp[2]; Wp.u[2] = fp[3]; Wp.p = fp[4];
+  R Um[5], Up[5], Fm[5], Fp[5];
+  if (!prim2con(Wm, Um)) bad = 1;
+  if (!prim2con(Wp, Up)) bad = 1;
+  phys_flux<d>(Wm, Um, Fm);
+  phys_flux<d>(Wp, Up, Fp);
+#pragma unroll
+  for (int v = 0; v < 5; ++v) dF[v] = dF[v] + (Fp[v] - Fm[v]);
+  const int cd = (d == 0) ? i : ((d == 1) ? j : k);
+  // A face state is stored only where a flux uses it: the transverse
+  // coordinates are interior and the face lies in 0..8 along d.
+  const bool trans = interior || (cd < 0 || cd > 7);
+  if (trans && cd >= 0) {
+    int fi = face_index<d>(i, j, k, cd);
+#pragma unroll
+    for (int v = 0; v < 5; ++v) face_slot(face, d, 1, v)[fi] = S(Um[v]);
+  }
+  if (trans && cd <= 7) {
+    int fi = face_index<d>(i, j, k, cd + 1);
+#pragma unroll
+    for (int v = 0; v < 5; ++v) face_slot(face, d, 0, v)[fi] = S(Up[v]);
+  }
+}
+
+template <int d, class R, class S>
+__device__ __forceinline__ void halfstep_direction(int i, int j, int k, bool interior, S* face,
+                                                   const R dF[5], R half) {
+  const int cd = (d == 0) ? i : ((d == 1) ? j : k);
+  const bool trans = interior || (cd < 0 || cd > 7);
+  if (trans && cd >= 0) {
+    int fi = face_index<d>(i, j, k, cd);
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+      S* s = face_slot(face, d, 1, v) + fi;
+      *s = S(R(*s) - half * dF[v]);
+    }
+  }
+  if (trans && cd <= 7) {
+    int fi = face_index<d>(i, j, k, cd + 1);
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+      S* s = face_slot(face, d, 0, v) + fi;
+      *s = S(R(*s) - half * dF[v]);
+    }
+  }
+}
+
+template <int d, class R, class S>
+__device__ __forceinline__ int face_flux(S* face, int fi, int solver, int maxit, int& code) {
+  R UL[5], UR[5];
+#pragma unroll
+  for (int v = 0; v < 5; ++v) {
+    UL[v] = R(face_slot(face, d, 0, v)[fi]);
+    UR[v] = R(face_slot(face, d, 1, v)[fi]);
+  }
+  PrimX<R> WL, WR;
+  int sl = con2pri<R, S>(S(UL[0]), S(UL[1]), S(UL[2]), S(UL[3]), S(UL[4]), WL, maxit);
+  int sr = con2pri<R, S>(S(UR[0]), S(UR[1]), S(UR[2]), S(UR[3]), S(UR[4]), WR, maxit);
+  if (sl == 2 || sr == 2) code |= CODE_NOCONV;
+  int fail = (sl == 1 || sr == 1);
+  R F[5];
+  riemann<d>(solver, WL, UL, WR, UR, F);
+#pragma unroll
+  for (int v = 0; v < 5; ++v) face_slot(face, d, 0, v)[fi] = S(F[v]);
+  return fail;
+}
+
+template <class S, int NT, int MINB>
+__global__ void __launch_bounds__(NT, MINB) patch_kernel(PatchArgs a) {
+  using R = S;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  S* prim = reinterpret_cast<S*>(smem_raw);
+  S* face = prim + SmemLayout<S>::prim_elems;
+  __shared__ double s_red[NT / 32];
+  __shared__ int s_bad[NT / 32];
+  const int tid = threadIdx.x;
+  const int maxit = a.maxit;
+
+  double dt_min = DBL_MAX;
+  int cfl_bad = 0;
+
+  for (int w = blockIdx.x; w < a.npatch; w += gridDim.x) {
+    const int p = a.worklist ? a.worklist[w] : w;
+    const S* in = static_cast<const S*>(a.in) + (size_t)p * 5 * kGC;
+    const double dt = a.dt_dh[2 * p], dh = a.dt_dh[2 * p + 1];
+    int code = 0;
+
+    __syncthreads();  // the previous patch is done with shared memory
+    // ---- phase 1: primitive tile ------------------------------------------
+    for (int c = tid; c < kGC; c += NT) {
+      int gx = c % kG, gy = (c / kG) % kG, gz = c / (kG * kG);
+      if (!tile_cell_needed(gx, gy, gz)) continue;
+      PrimX<R> W;
+      int st = con2pri<R, S>(in[c], in[kGC + c], in[2 * kGC + c], in[3 * kGC + c],
+                             in[4 * kGC + c], W, maxit);
+      if (st == 1) code |= CODE_BAD_INPUT;
+      if (st == 2) code |= CODE_NOCONV;
+      prim[c] = S(W.rho);
+      prim[kGC + c] = S(W.u[0]);
+      prim[2 * kGC + c] = S(W.u[1]);
+      prim[3 * kGC + c] = S(W.u[2]);
+      prim[4 * kGC + c] = S(W.p);
+    }
+    const int bad_input = __syncthreads_or(code & CODE_BAD_INPUT);
+
+    int retries = 0;
+    int final_code = 0;
+    double att_min = DBL_MAX;
+    int att_bad = 0;
+    if (!bad_input) {
+      R theta = R(a.theta0);
+      const R half = R(0.5 * dt / dh);
+      const R coef = R(dt / dh);
+      for (;;) {
+        // ---- phase 2: reconstruction + Hancock half step --------------------
+        int fail = 0;
+        for (int r = tid; r < kRC; r += NT) {
+          int i, j, k;
+          recon_cell(r, i, j, k);
+          const bool interior = r < kNC;
+          const int tc = tile_index(i, j, k);
+          PrimX<R> W;
+          W.rho = R(prim[tc]);
+          W.u[0] = R(prim[kGC + tc]);
+          W.u[1] = R(prim[2 * kGC + tc]);
+          W.u[2] = R(prim[3 * kGC + tc]);
+          W.p = R(prim[4 * kGC + tc]);
+          R dF[5] = {R(0), R(0), R(0), R(0), R(0)};
+          recon_direction<0>(prim, tc, W, theta, i, j, k, interior, face, dF, fail);
+          recon_direction<1>(prim, tc, W, theta, i, j, k, interior, face, dF, fail);
+          recon_direction<2>(prim, tc, W, theta, i, j, k, interior, face, dF, fail);
+          halfstep_direction<0>(i, j, k, interior, face, dF, half);
+          halfstep_direction<1>(i, j, k, interior, face, dF, half);
+          halfstep_direction<2>(i, j, k, interior, face, dF, half);
+        }
+        __syncthreads();
+        // ---- phase 3: Riemann fluxes ----------------------------------------
+        for (int f = tid; f < 3 * kNF; f += NT) {
+          const int d = f / kNF, fi = f - d * kNF;
+          if (d == 0) fail |= face_flux<0, R>(face, fi, a.riemann, maxit, code);
+          else if (d == 1) fail |= face_flux<1, R>(face, fi, a.riemann, maxit, code);
+          else fail |= face_flux<2, R>(face, fi, a.riemann, maxit, code);
+        }
+        fail = __syncthreads_or(fail);
+        if (a.flux_only) {
+          if (fail) final_code |= CODE_UNPHYSICAL;
+          break;
+        }
+        const bool last = (theta == R(0));
+        // ---- phase 4: conservative update ----------------------------------
+        att_min = DBL_MAX;
+        att_bad = 0;
+        if (!fail || last) {
+          S* out = static_cast<S*>(a.out) + (size_t)p * 5 * kNC;
+          int fail4 = 0;
+          for (int c = tid; c < kNC; c += NT) {
+            const int i = c & 7, j = (c >> 3) & 7, k = c >> 6;
+            const int tc = tile_index(i, j, k);
+            const int fx0 = face_index<0>(i, j, k, i), fx1 = face_index<0>(i, j, k, i + 1);
+            const int fy0 = face_index<1>(i, j, k, j), fy1 = face_index<1>(i, j, k, j + 1);
+            const int fz0 = face_index<2>(i, j, k, k), fz1 = face_index<2>(i, j, k, k + 1);
+            S Un[5];
+#pragma unroll
+            for (int v = 0; v < 5; ++v) {
+              R div = R(0);
+              div = div + (R(face_slot(face, 0, 0, v)[fx1]) - R(face_slot(face, 0, 0, v)[fx0]));
+              div = div + (R(face_slot(face, 1, 0, v)[fy1]) - R(face_slot(face, 1, 0, v)[fy0]));
+              div = div + (R(face_slot(face, 2, 0, v)[fz1]) - R(face_slot(face, 2, 0, v)[fz0]));
+              Un[v] = S(R(in[v * kGC + tc]) - coef * div);
+              out[v * kNC + c] = Un[v];
+            }
+            double m2;
+            double A = A_of_cons(Un[0], Un[1], Un[2], Un[3], Un[4], m2);
+            const bool ok = (double(Un[0]) > 0.0) && (A > kEpsUnphysical);
+            if (!ok) fail4 = 1;
+            if (a.partial_dt) {
+              if (a.cfl_mode == 1) {
+                att_min = fmin(att_min, a.cfl * dh);
+              } else if (ok) {
+                PrimX<R> W;
+                con2pri<R, S>(Un[0], Un[1], Un[2], Un[3], Un[4], W, maxit);
+                double sm = double(smax_of(W, a.ndim));
+                att_min = fmin(att_min, a.cfl * dh / sm);
+              } else {
+                att_bad = 1;
+              }
+            }
+          }
+          fail = __syncthreads_or(fail4) | fail;
+        }
+        if (!fail) break;
+        if (last) { final_code |= CODE_UNPHYSICAL; break; }
+        ++retries;
+        theta = theta * R(a.retry_factor);
+        if (theta < R(a.theta_floor * a.theta0)) theta = R(0);
+      }
+      dt_min = fmin(dt_min, att_min);
+      cfl_bad |= att_bad;
+    } else {
+      final_code |= CODE_BAD_INPUT;
+      cfl_bad = 1;
+      if (!a.flux_only) {
+        S* out = static_cast<S*>(a.out) + (size_t)p * 5 * kNC;
+        for (int c = tid; c < 5 * kNC; c += NT) out[c] = S(__longlong_as_double(0x7ff8000000000000ULL));
+      }
+    }
+    // ---- outputs ----------------------------------------------------------
+    if (a.flux_only && !bad_input) {
+      S* ff = static_cast<S*>(a.face_flux) + (size_t)p * 3 * 5 * kNF;
+      for (int q = tid; q < 3 * 5 * kNF; q += NT) {
+        int d = q / (5 * kNF), rem = q - d * 5 * kNF;
+        ff[q] = face[(d * 2) * 5 * kNF + rem];
+      }
+    }
+    if (a.pflux && !a.flux_only && !bad_input) {
+      S* pf = static_cast<S*>(a.pflux) + (size_t)p * 6 * 5 * 64;
+      for (int q = tid; q < 6 * 5 * 64; q += NT) {
+        int side = q / 320, rem = q - side * 320, v = rem >> 6, t = rem & 63;
+        int d = side >> 1, fd = (side & 1) ? 8 : 0;
+        int a0 = t & 7, b0 = t >> 3;  // transverse coordinates, lower axis fastest
+        int fi = (d == 0) ? face_index<0>(0, a0, b0, fd)
+                          : (d == 1) ? face_index<1>(a0, 0, b0, fd) : face_index<2>(a0, b0, 0, fd);
+        pf[q] = face_slot(face, d, 0, v)[fi];
+      }
+    }
+    code = __syncthreads_or(code & CODE_NOCONV);
+    if (tid == 0 && a.status) {
+      final_code |= code ? CODE_NOCONV : 0;
+      a.status[p] = (final_code << 8) | (retries < 255 ? retries : 255);
+    }
+  }
+
+  // ---- CFL partial minimum of this CTA -------------------------------------
+  if (a.partial_dt) {
+    for (int o = 16; o > 0; o >>= 1) {
+      dt_min = fmin(dt_min, __shfl_xor_sync(0xffffffffu, dt_min, o));
+      cfl_bad |= __shfl_xor_sync(0xffffffffu, cfl_bad, o);
+    }
+    if ((tid & 31) == 0) { s_red[tid >> 5] = dt_min; s_bad[tid >> 5] = cfl_bad; }
+    __syncthreads();
+    if (tid == 0) {
+      double m = DBL_MAX;
+      int b = 0;
+      for (int q = 0; q < NT / 32; ++q) { m = fmin(m, s_red[q]); b |= s_bad[q]; }
+      a.partial_dt[blockIdx.x] = m;
+      a.partial_bad[blockIdx.x] = b;
+    }
+  }
+}
+
+// Final reduction of the CFL partial minima (one block).
+__global__ void cfl_finalize_kernel(const double* partial, const int32_t* bad, int n,
+                                    double* dt_out);
+
+// ---- batched conversions ----------------------------------------------------
+template <class S>
+__global__ void prim2con_kernel(const S* prim, S* cons, int64_t n, int64_t stride) {
+  using R = S;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    PrimX<R> W;
+    W.rho = prim[i];
+    W.u[0] = prim[stride + i];
+    W.u[1] = prim[2 * stride + i];
+    W.u[2] = prim[3 * stride + i];
+    W.p = prim[4 * stride + i];
+    R U[5];
+    prim2con(W, U);
+#pragma unroll
+    for (int v = 0; v < 5; ++v) cons[v * stride + i] = U[v];
+  }
+}
+
+template <class S>
+__global__ void con2pri_kernel(const S* cons, S* prim, int64_t n, int64_t stride,
+                               int32_t* status, int maxit) {
+  using R = S;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    PrimX<R> W;
+    int st = con2pri<R, S>(cons[i], cons[stride + i], cons[2 * stride + i],
+                           cons[3 * stride + i], cons[4 * stride + i], W, maxit);
+    prim[i] = W.rho;
+    prim[stride + i] = W.u[0];
+    prim[2 * stride + i] = W.u[1];
+    prim[3 * stride + i] = W.u[2];
+    prim[4 * stride + i] = W.p;
+    if (status) status[i] = st;
+  }
+}
+
+// CFL bound over interior patches [np][5][8^3]; per-block partial minima.
+template <class S, int NT>
+__global__ void __launch_bounds__(NT) cfl_kernel(const S* cons, int64_t ncell, double dh,
+                                                 double cfl, int ndim, int mode, int maxit,
+                                                 double* partial, int32_t* bad_out) {
+  using R = S;
+  __shared__ double s_red[NT / 32];
+  __shared__ int s_bad[NT / 32];
+  double m = DBL_MAX;
+  int bad = 0;
+  for (int64_t q = blockIdx.x * (int64_t)NT + threadIdx.x; q < ncell;
+       q += (int64_t)gridDim.x * NT) {
+    const int64_t p = q / kNC, c = q - p * kNC;
+    const S* b = cons + p * 5 * kNC + c;
+    PrimX<R> W;
+    int st = con2pri<R, S>(b[0], b[kNC], b[2 * kNC], b[3 * kNC], b[4 * kNC], W, maxit);
+    if (st == 1) { bad = 1; continue; }
+    if (mode == 1) m = fmin(m, cfl * dh);
+    else m = fmin(m, cfl * dh / double(smax_of(W, ndim)));
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    m = fmin(m, __shfl_xor_sync(0xffffffffu, m, o));
+    bad |= __shfl_xor_sync(0xffffffffu, bad, o);
+  }
+  if ((threadIdx.x & 31) == 0) { s_red[threadIdx.x >> 5] = m; s_bad[threadIdx.x >> 5] = bad; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double mm = DBL_MAX;
+    int bb = 0;
+    for (int w = 0; w < NT / 32; ++w) { mm = fmin(mm, s_red[w]); bb |= s_bad[w]; }
+    partial[blockIdx.x] = mm;
+    bad_out[blockIdx.x] = bb;
+  }
+}
+
+// Ghost fill of a uniform grid of patches (periodic or outflow per axis).
+template <class S>
+__global__ void fill_ghosts_kernel(const S* interior, S* ghosted, int npx, int npy, int npz,
+                                   int bcx, int bcy, int bcz) {
+  const int64_t np = (int64_t)npx * npy * npz;
+  const int64_t total = np * 5 * kGC;
+  const int nx = npx * kN, ny = npy * kN, nz = npz * kN;
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t p = q / (5 * kGC);
+    const int rem = int(q - p * 5 * kGC);
+    const int v = rem / kGC, c = rem - v * kGC;
+    const int px = int(p % npx), py = int((p / npx) % npy), pz = int(p / ((int64_t)npx * npy));
+    int x = px * kN + (c % kG) - 2, y = py * kN + ((c / kG) % kG) - 2, z = pz * kN + c / (kG * kG) - 2;
+    auto wrap = [](int g, int n, int bc) {
+      if (bc == 0) return ((g % n) + n) % n;
+      return g < 0 ? 0 : (g >= n ? n - 1 : g);
+    };
+    x = wrap(x, nx, bcx);
+    y = wrap(y, ny, bcy);
+    z = wrap(z, nz, bcz);
+    const int64_t sp = ((int64_t)(z / kN) * npy + (y / kN)) * npx + (x / kN);
+    const int sc = ((z % kN) * kN + (y % kN)) * kN + (x % kN);
+    ghosted[q] = interior[sp * 5 * kNC + v * kNC + sc];
+  }
+}
+
+// Per-precision launchers (explicitly instantiated in srhd_fp64.cu and
+// srhd_mixed.cu).
+template <class S> struct Launch {
+  static cudaError_t setup();
+  static int patch_blocks_per_sm();
+  static cudaError_t patches(const PatchArgs& a, int grid, cudaStream_t s);
+  static cudaError_t prim2con(const void* prim, void* cons, int64_t n, int64_t stride, int grid,
+                              cudaStream_t s);
+  static cudaError_t con2pri(const void* cons, void* prim, int64_t n, int64_t stride,
+                             int32_t* status, int maxit, int grid, cudaStream_t s);
+  static cudaError_t cfl(const void* cons, int64_t ncell, double dh, double cfl, int ndim, int mode,
+                         int maxit, double* partial, int32_t* bad, int grid, cudaStream_t s);
+  static cudaError_t fill_ghosts(const void* interior, void* ghosted, int npx, int npy, int npz,
+                                 const int32_t* bc, int grid, cudaStream_t s);
+};
+
+constexpr int kCflThreads = 256;
+
+}  // namespace srhd

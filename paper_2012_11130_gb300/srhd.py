@@ -1,0 +1,254 @@
+"""Python binding of libsrhd: the C-ABI entry points under the same names,
+taking torch tensors (argument marshalling only; every step of the update
+runs in the library's CUDA kernels).
+
+Precision follows the tensor dtype: float64 -> SRHD_FP64, float32 ->
+SRHD_MIXED (float storage; A of Eq. transcendental equation in double).
+Layouts are those of include/srhd.h: SoA [5][n] for cell batches,
+[npatch][5][12][12][12] ghosted patches, [npatch][5][8][8][8] interiors.
+
+Tensors on the CPU are accepted by ``advance_patches`` and ``con2pri``: the
+call then copies them to the device (pinned host memory makes the copies
+asynchronous), runs there and copies the results back, which is the
+end-to-end path a host-resident caller uses.
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass
+
+import torch
+
+from . import _native as N
+
+__all__ = ["Params", "Context", "prim2con", "con2pri", "flux_patches", "advance_patches",
+           "cfl_dt", "fill_ghosts_uniform", "default_context"]
+
+
+@dataclass
+class Params:
+    """Run-time parameters (Sections 3.1-3.3 of arXiv 2012.11130)."""
+    cfl: float = 0.5
+    theta: float = 1.5
+    retry_factor: float = 0.75
+    theta_floor: float = 1e-2
+    riemann: str = "hllc"        # "hllc" | "hlle"
+    cfl_mode: str = "signal"     # "signal" | "light"
+    ndim: int = 3
+    newton_max_iter: int = 0
+
+    def to_c(self) -> N.Params:
+        return N.Params(self.cfl, self.theta, self.retry_factor, self.theta_floor,
+                        {"hllc": N.SRHD_HLLC, "hlle": N.SRHD_HLLE}[self.riemann],
+                        {"signal": N.SRHD_CFL_SIGNAL, "light": N.SRHD_CFL_LIGHT}[self.cfl_mode],
+                        self.ndim, self.newton_max_iter)
+
+
+def _prec(t: torch.Tensor) -> int:
+    if t.dtype == torch.float64:
+        return N.SRHD_FP64
+    if t.dtype == torch.float32:
+        return N.SRHD_MIXED
+    raise TypeError(f"unsupported dtype {t.dtype}: use float64 (FP64) or float32 (mixed)")
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _need_cuda(t: torch.Tensor, name: str, dtype=None):
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+
+
+class Context:
+    """Owns an srhd_ctx* on one device (scratch for the CFL reduction)."""
+
+    def __init__(self, params: Params | None = None, device: int | None = None):
+        self._L = N.load()
+        self.params = params or Params()
+        self.device = torch.cuda.current_device() if device is None else device
+        self._h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            p = self.params.to_c()
+            N.check(self._L.srhd_create(ctypes.byref(self._h), ctypes.byref(p)), "srhd_create")
+
+    def close(self):
+        if self._h:
+            self._L.srhd_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---- Section 2.3 ---------------------------------------------------------
+    def prim2con(self, prim, cons=None, stream=None):
+        _need_cuda(prim, "prim")
+        n = prim.shape[-1]
+        if cons is None:
+            cons = torch.empty_like(prim)
+        _need_cuda(cons, "cons", prim.dtype)
+        N.check(self._L.srhd_prim2con(self._h, _prec(prim), _ptr(prim), _ptr(cons), n, n,
+                                      _stream(stream)), "srhd_prim2con")
+        return cons
+
+    def con2pri(self, cons, prim=None, cell_status=None, stream=None):
+        host = not cons.is_cuda
+        if host:
+            dev = torch.device("cuda", self.device)
+            cons_d = cons.to(dev, non_blocking=True)
+        else:
+            cons_d = cons
+        _need_cuda(cons_d, "cons")
+        n = cons_d.shape[-1]
+        prim_d = torch.empty_like(cons_d) if (prim is None or host) else prim
+        _need_cuda(prim_d, "prim", cons_d.dtype)
+        st_d = cell_status
+        if host and cell_status is not None:
+            st_d = torch.empty(n, dtype=torch.int32, device=cons_d.device)
+        if st_d is not None:
+            _need_cuda(st_d, "cell_status", torch.int32)
+        N.check(self._L.srhd_con2pri(self._h, _prec(cons_d), _ptr(cons_d), _ptr(prim_d), n, n,
+                                     _ptr(st_d), _stream(stream)), "srhd_con2pri")
+        if host:
+            out = prim if prim is not None else torch.empty(prim_d.shape, dtype=prim_d.dtype,
+                                                            pin_memory=True)
+            out.copy_(prim_d, non_blocking=True)
+            if cell_status is not None:
+                cell_status.copy_(st_d, non_blocking=True)
+            torch.cuda.current_stream().synchronize()
+            return out
+        return prim_d
+
+    # ---- Section 3.1-3.3 -----------------------------------------------------
+    def flux_patches(self, cons_ghosted, dt_dh, face_flux=None, patch_status=None, stream=None):
+        _need_cuda(cons_ghosted, "cons_ghosted")
+        npatch = cons_ghosted.shape[0]
+        if face_flux is None:
+            face_flux = torch.empty((npatch, 3, 5, 576), dtype=cons_ghosted.dtype,
+                                    device=cons_ghosted.device)
+        _need_cuda(face_flux, "face_flux", cons_ghosted.dtype)
+        _need_cuda(dt_dh, "dt_dh", torch.float64)
+        if patch_status is not None:
+            _need_cuda(patch_status, "patch_status", torch.int32)
+        N.check(self._L.srhd_flux_patches(self._h, _prec(cons_ghosted), _ptr(cons_ghosted),
+                                          _ptr(face_flux), npatch, _ptr(dt_dh), _ptr(patch_status),
+                                          _stream(stream)), "srhd_flux_patches")
+        return face_flux
+
+    def advance_patches(self, cons_ghosted, dt_dh, cons_out=None, patch_face_flux=None,
+                        worklist=None, dt_next=None, patch_status=None, npatch=None, stream=None):
+        """One step of a batch of ghosted patches. Device tensors in, device
+        tensors out; with a CPU ``cons_ghosted`` the call copies it in, runs
+        and copies ``cons_out`` (and ``dt_next`` if given) back to the host."""
+        if not cons_ghosted.is_cuda:
+            return self._advance_host(cons_ghosted, dt_dh, cons_out, dt_next, patch_status, stream)
+        _need_cuda(cons_ghosted, "cons_ghosted")
+        if npatch is None:
+            npatch = worklist.numel() if worklist is not None else cons_ghosted.shape[0]
+        if cons_out is None:
+            cons_out = torch.empty((cons_ghosted.shape[0], 5, 8, 8, 8), dtype=cons_ghosted.dtype,
+                                   device=cons_ghosted.device)
+        _need_cuda(cons_out, "cons_out", cons_ghosted.dtype)
+        _need_cuda(dt_dh, "dt_dh", torch.float64)
+        for name, t, dt in (("patch_face_flux", patch_face_flux, cons_ghosted.dtype),
+                            ("worklist", worklist, torch.int32), ("dt_next", dt_next, torch.float64),
+                            ("patch_status", patch_status, torch.int32)):
+            if t is not None:
+                _need_cuda(t, name, dt)
+        N.check(self._L.srhd_advance_patches(
+            self._h, _prec(cons_ghosted), _ptr(cons_ghosted), _ptr(cons_out),
+            _ptr(patch_face_flux), npatch, _ptr(dt_dh), _ptr(worklist), _ptr(dt_next),
+            _ptr(patch_status), _stream(stream)), "srhd_advance_patches")
+        return cons_out
+
+    def _advance_host(self, cons_ghosted, dt_dh, cons_out, dt_next, patch_status, stream):
+        dev = torch.device("cuda", self.device)
+        g = cons_ghosted.to(dev, non_blocking=True)
+        dd = dt_dh.to(dev, non_blocking=True)
+        out_d = torch.empty((g.shape[0], 5, 8, 8, 8), dtype=g.dtype, device=dev)
+        dn_d = torch.empty(1, dtype=torch.float64, device=dev) if dt_next is not None else None
+        st_d = torch.empty(g.shape[0], dtype=torch.int32, device=dev) \
+            if patch_status is not None else None
+        self.advance_patches(g, dd, cons_out=out_d, dt_next=dn_d, patch_status=st_d,
+                             stream=stream)
+        if cons_out is None:
+            cons_out = torch.empty(out_d.shape, dtype=out_d.dtype, pin_memory=True)
+        cons_out.copy_(out_d, non_blocking=True)
+        if dt_next is not None:
+            dt_next.copy_(dn_d, non_blocking=True)
+        if patch_status is not None:
+            patch_status.copy_(st_d, non_blocking=True)
+        (stream or torch.cuda.current_stream()).synchronize()
+        return cons_out
+
+    def cfl_dt(self, cons, dh, dt_out=None, stream=None):
+        _need_cuda(cons, "cons")
+        if dt_out is None:
+            dt_out = torch.empty(1, dtype=torch.float64, device=cons.device)
+        _need_cuda(dt_out, "dt_out", torch.float64)
+        N.check(self._L.srhd_cfl_dt(self._h, _prec(cons), _ptr(cons), cons.shape[0], float(dh),
+                                    _ptr(dt_out), _stream(stream)), "srhd_cfl_dt")
+        return dt_out
+
+    def fill_ghosts_uniform(self, interior, npx, npy, npz, bc=("periodic",) * 3, ghosted=None,
+                            stream=None):
+        _need_cuda(interior, "interior")
+        if ghosted is None:
+            ghosted = torch.empty((interior.shape[0], 5, 12, 12, 12), dtype=interior.dtype,
+                                  device=interior.device)
+        _need_cuda(ghosted, "ghosted", interior.dtype)
+        code = {"periodic": N.SRHD_BC_PERIODIC, "outflow": N.SRHD_BC_OUTFLOW}
+        bcs = (ctypes.c_int32 * 3)(*[code[b] for b in bc])
+        N.check(self._L.srhd_fill_ghosts_uniform(self._h, _prec(interior), _ptr(interior),
+                                                 _ptr(ghosted), npx, npy, npz, bcs,
+                                                 _stream(stream)), "srhd_fill_ghosts_uniform")
+        return ghosted
+
+
+_default = {}
+
+
+def default_context(params: Params | None = None) -> Context:
+    dev = torch.cuda.current_device()
+    key = (dev, None if params is None else tuple(vars(params).items()))
+    if key not in _default:
+        _default[key] = Context(params, dev)
+    return _default[key]
+
+
+def prim2con(prim, cons=None, stream=None):
+    return default_context().prim2con(prim, cons, stream)
+
+
+def con2pri(cons, prim=None, cell_status=None, stream=None):
+    return default_context().con2pri(cons, prim, cell_status, stream)
+
+
+def flux_patches(cons_ghosted, dt_dh, face_flux=None, patch_status=None, stream=None):
+    return default_context().flux_patches(cons_ghosted, dt_dh, face_flux, patch_status, stream)
+
+
+def advance_patches(cons_ghosted, dt_dh, **kw):
+    return default_context().advance_patches(cons_ghosted, dt_dh, **kw)
+
+
+def cfl_dt(cons, dh, dt_out=None, stream=None):
+    return default_context().cfl_dt(cons, dh, dt_out, stream)
+
+
+def fill_ghosts_uniform(interior, npx, npy, npz, bc=("periodic",) * 3, ghosted=None, stream=None):
+    return default_context().fill_ghosts_uniform(interior, npx, npy, npz, bc, ghosted, stream)

@@ -1,0 +1,102 @@
+"""GPU parity of the batched conversions (srhd_prim2con, srhd_con2pri)
+against the oracle on the con2pri stress batch (rho 1e-6..1e2, T 1e-8..1e4,
+gamma 1..1e6, random direction), through the C ABI."""
+import numpy as np
+import pytest
+
+from gpu_common import (BASE_FP64, BASE_MIXED, EPS64, kappa_of_prims, prim_rel_err,
+                        require_gpu, to_dev, to_np)
+from paper_2012_11130_gb300 import workloads
+
+pytestmark = pytest.mark.gpu
+
+
+def _inputs(oracle, n, seed, prec):
+    W = workloads.stress_batch_prims(n, seed=seed)
+    C, st = oracle.prim2con(W)
+    assert np.all(st == 0)
+    if prec == "mixed":
+        C = C.astype(np.float32).astype(np.float64)
+    return W, C
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("n", [1, 997, 3 * 65536 + 37])
+def test_con2pri_parity(oracle, prec, n):
+    torch, srhd = require_gpu()
+    dtype = torch.float64 if prec == "fp64" else torch.float32
+    W, C = _inputs(oracle, n, 1000 + n, prec)
+    ref = oracle.con2pri(C)
+    st = torch.full((n,), -7, dtype=torch.int32, device="cuda")
+    P = srhd.con2pri(to_dev(torch, C, dtype), cell_status=st)
+    torch.cuda.synchronize()
+    Pg, stg = to_np(P), st.cpu().numpy()
+    assert set(np.unique(stg)) <= {0, 1}
+    kappa = kappa_of_prims(oracle, W)
+    clear = kappa * EPS64 <= 1e-3
+    # well-conditioned cells: same status, values within the tolerance
+    assert np.array_equal(stg[clear], ref["status"][clear])
+    ok = clear & (ref["status"] == 0)
+    base = BASE_FP64 if prec == "fp64" else BASE_MIXED
+    tol = np.maximum(base, 10 * kappa * EPS64)
+    err = prim_rel_err(Pg, ref["prim"])
+    bad = ok & ~(err <= tol)
+    assert not bad.any(), (np.nonzero(bad)[0][:5], err[bad][:5], tol[bad][:5])
+    # unphysical cells are NaN, accepted cells are finite everywhere
+    assert np.all(np.isnan(Pg[:, stg == 1]))
+    assert np.all(np.isfinite(Pg[:, stg == 0]))
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_prim2con_parity(oracle, prec):
+    torch, srhd = require_gpu()
+    dtype = torch.float64 if prec == "fp64" else torch.float32
+    n = 65536 + 129
+    W = workloads.stress_batch_prims(n, seed=77)
+    if prec == "mixed":
+        W = W.astype(np.float32).astype(np.float64)
+    ref, _ = oracle.prim2con(W)
+    C = to_np(srhd.prim2con(to_dev(torch, W, dtype)))
+    tol = 1e-13 if prec == "fp64" else 1e-5
+    rel = np.abs(C - ref) / np.maximum(np.abs(ref), np.sqrt((ref[1:4] ** 2).sum(0)))
+    assert rel.max() <= tol, rel.max()
+
+
+def test_conversion_edge_cases(oracle):
+    torch, srhd = require_gpu()
+    ctx = srhd.default_context()
+    # n = 0 is a no-op
+    empty = torch.empty((5, 0), dtype=torch.float64, device="cuda")
+    ctx.con2pri(empty)
+    ctx.prim2con(empty)
+    # unphysical conserved states: D <= 0, |M| too large, Etilde <= 0
+    C = np.array([[-1.0, 1.0, 1.0, 0.0],
+                  [0.0, 5.0, 0.0, 0.0],
+                  [0.0, 0.0, 0.0, 0.0],
+                  [0.0, 0.0, 0.0, 0.0],
+                  [1.0, 1.0, -1.0, 0.0]])
+    for dtype in (torch.float64, torch.float32):
+        st = torch.empty(4, dtype=torch.int32, device="cuda")
+        P = ctx.con2pri(to_dev(torch, C, dtype), cell_status=st)
+        assert st.cpu().tolist() == [1, 1, 1, 1]
+        assert torch.isnan(P).all()
+    ref = oracle.con2pri(C)
+    assert ref["status"].tolist() == [1, 1, 1, 1]
+
+
+def test_round_trip_tracks_conditioning(oracle):
+    # Appendix B on the GPU (FP64): T = 1e-8, Mach 1e-4..1e6 along x=y=z;
+    # the htilde error stays within a small multiple of (1+Mach^2) eps.
+    torch, srhd = require_gpu()
+    T = 1e-8
+    cs2 = oracle.cs2_of_T(T)
+    Us = np.sqrt(cs2 / (1 - cs2))
+    mach = np.logspace(-4, 6, 201)
+    n = mach.size
+    W = np.vstack([np.ones(n), np.tile(mach * Us / np.sqrt(3), (3, 1)), np.full(n, T)])
+    Wd = to_dev(torch, W, torch.float64)
+    P = to_np(srhd.con2pri(srhd.prim2con(Wd)))
+    ht0 = oracle.htilde_of_T(T)
+    ht2 = oracle.htilde_of_T(P[4] / P[0])
+    err = np.abs(1 - ht0 / ht2)
+    assert np.all(err <= 64 * (1 + mach ** 2) * EPS64)

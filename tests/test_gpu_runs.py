@@ -1,0 +1,164 @@
+"""Multi-step GPU runs against the oracle: the 1-D shock tube to t = 0.4
+(compared with the exact TM solution), and the 3-D smooth advection
+(per-cell parity, conservation, convergence), plus a sampled check of one
+full-size 256^3 step in the launch configuration the benchmark times."""
+import numpy as np
+import pytest
+
+from gpu_common import cons_rel_err, require_gpu, to_dev, to_np
+from paper_2012_11130_gb300 import workloads
+
+pytestmark = pytest.mark.gpu
+
+
+def _gpu_evolve(torch, srhd, ctx, C_patches, npx, npy, npz, bc, dh, t_end, dtype,
+                fixed_dt=None, max_steps=100000):
+    """Ghost fill + fused step with the fused CFL, until t_end."""
+    U = to_dev(torch, C_patches, dtype)
+    npatch = U.shape[0]
+    dd = torch.empty((npatch, 2), dtype=torch.float64, device="cuda")
+    dn = torch.empty(1, dtype=torch.float64, device="cuda")
+    st = torch.empty(npatch, dtype=torch.int32, device="cuda")
+    out = torch.empty_like(U)
+    if fixed_dt is None:
+        dt = ctx.cfl_dt(U, dh).item()
+    t, steps, retries = 0.0, 0, 0
+    while t < t_end and steps < max_steps:
+        if fixed_dt is not None:
+            dt = fixed_dt
+        if t + dt > t_end:
+            dt = t_end - t
+        dd[:, 0] = dt
+        dd[:, 1] = dh
+        G = ctx.fill_ghosts_uniform(U, npx, npy, npz, bc=bc)
+        ctx.advance_patches(G, dd, cons_out=out, dt_next=dn, patch_status=st)
+        U, out = out, U
+        s = st.cpu().numpy()
+        assert np.all((s >> 8) == 0), s[s != 0][:5]
+        retries += int((s & 255).sum())
+        t += dt
+        steps += 1
+        dt = dn.item()
+    return U, steps, retries
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_shock_tube_vs_exact_and_oracle(oracle, prec):
+    # 1024 cells, (1, 0, 1e3) | (1, 0, 1e-2), t = 0.4, CFL 0.5 with the 1-D
+    # signal-speed bound, outflow; the patch grid is 128 x 1 x 1 with
+    # periodic (uniform) y and z.
+    torch, srhd = require_gpu()
+    N = 1024
+    W, x = workloads.shock_tube_prims(N)
+    C, _ = oracle.prim2con(W)
+    if prec == "mixed":
+        C = C.astype(np.float32).astype(np.float64)
+    F = np.broadcast_to(C.reshape(5, 1, 1, N), (5, 8, 8, N)).copy()
+    ctx = srhd.Context(srhd.Params(ndim=1))
+    dtype = torch.float64 if prec == "fp64" else torch.float32
+    U, steps, retries = _gpu_evolve(torch, srhd, ctx, workloads.patchify(F), N // 8, 1, 1,
+                                    ("outflow", "periodic", "periodic"), 1.0 / N, 0.4, dtype)
+    G = workloads.unpatchify(to_np(U), N // 8, 1, 1)
+    # y/z-uniform: every row equals the first
+    assert np.array_equal(G, np.broadcast_to(G[:, :1, :1, :], G.shape))
+    Pg = oracle.con2pri(G[:, 0, 0, :])["prim"]
+    ref = oracle.evolve(C.reshape(5, 1, 1, N), (1, 0, 0), 1.0 / N, 0.4, "outflow")
+    Pr = oracle.con2pri(ref["cons"].reshape(5, -1))["prim"]
+    rho, _, _, _ = oracle.exact_riemann((1, 0, 1e3), (1, 0, 1e-2), 0.5, 0.4, x)
+    l1_gpu = np.mean(np.abs(1 - Pg[0] / rho))
+    l1_ref = np.mean(np.abs(1 - Pr[0] / rho))
+    assert abs(steps - ref["steps"]) <= 1
+    # L1 error against the exact solution matches the oracle's to 2 digits
+    assert abs(l1_gpu / l1_ref - 1) < 0.005, (l1_gpu, l1_ref)
+    if prec == "fp64":
+        assert np.max(np.abs(Pg[0] / Pr[0] - 1)) < 1e-6
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_advection_steps_parity_and_conservation(oracle, prec):
+    torch, srhd = require_gpu()
+    N = 32
+    Wf = workloads.advection_prims(N)
+    C, _ = oracle.prim2con(Wf.reshape(5, -1))
+    if prec == "mixed":
+        C = C.astype(np.float32).astype(np.float64)
+    C = C.reshape(5, N, N, N)
+    dh = 1.0 / N
+    dt = 0.45 * dh
+    nsteps = 8
+    ctx = srhd.Context(srhd.Params())
+    dtype = torch.float64 if prec == "fp64" else torch.float32
+    U, steps, _ = _gpu_evolve(torch, srhd, ctx, workloads.patchify(C), 4, 4, 4, ("periodic",) * 3,
+                              dh, nsteps * dt * (1 - 1e-12), dtype, fixed_dt=dt)
+    assert steps == nsteps
+    G = workloads.unpatchify(to_np(U), 4, 4, 4)
+    R = C.copy()
+    for _ in range(nsteps):
+        r = oracle.advance_block(oracle.fill_ghosts(R, (1, 1, 1), "periodic"), (N, N, N),
+                                 (1, 1, 1), dt, dh)
+        assert r["status"] == 0
+        R = r["out"]
+    err = cons_rel_err(G, R)
+    assert err.max() <= (1e-11 if prec == "fp64" else 2e-5), err.max()
+    tot0 = C.reshape(5, -1).sum(1)
+    totg = G.reshape(5, -1).sum(1)
+    scale = np.abs(G.reshape(5, -1)).sum(1)
+    tol = 1e-13 if prec == "fp64" else 1e-5
+    assert np.all(np.abs(totg - tot0) <= tol * scale)
+
+
+def test_advection_convergence_mixed_vs_fp64(oracle):
+    # One period of the diagonal wave at 16^3 and 32^3: L1(rho) of Eq.
+    # (relative L1 error) falls at about second order in both precisions and
+    # the mixed L1 equals the FP64 L1 to two digits.
+    torch, srhd = require_gpu()
+    l1 = {}
+    for prec in ("fp64", "mixed"):
+        dtype = torch.float64 if prec == "fp64" else torch.float32
+        for N in (16, 32):
+            Wf = workloads.advection_prims(N)
+            C, _ = oracle.prim2con(Wf.reshape(5, -1))
+            v = float(np.sqrt(99.0 / 3.0) / np.sqrt(1.0 + 99.0))
+            T_period = 1.0 / (3 * v)
+            ctx = srhd.Context(srhd.Params())
+            U, steps, _ = _gpu_evolve(torch, srhd, ctx, workloads.patchify(C.reshape(5, N, N, N)),
+                                      N // 8, N // 8, N // 8, ("periodic",) * 3, 1.0 / N, T_period,
+                                      dtype)
+            G = workloads.unpatchify(to_np(U), N // 8, N // 8, N // 8)
+            rho = oracle.con2pri(G.reshape(5, -1))["prim"][0]
+            exact = workloads.advection_prims(N, t=T_period)[0].reshape(-1)
+            l1[prec, N] = np.mean(np.abs(1 - rho / exact))
+    for prec in ("fp64", "mixed"):
+        assert np.log2(l1[prec, 16] / l1[prec, 32]) > 1.6, l1
+    assert abs(l1["mixed", 32] / l1["fp64", 32] - 1) < 0.01, l1
+
+
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_full_size_step_sampled(oracle, prec):
+    # One step of the 256^3 smooth-advection batch (32768 patches) in the
+    # configuration the benchmark times (fused CFL, status, one launch);
+    # 24 sampled patches are recomputed by the oracle from the same inputs.
+    torch, srhd = require_gpu()
+    N = 256
+    Wf = workloads.advection_prims(N)
+    C, _ = oracle.prim2con(Wf.reshape(5, -1))
+    C = C.reshape(5, N, N, N)
+    if prec == "mixed":
+        C = C.astype(np.float32)
+    G = workloads.ghosted_patches(C.astype(np.float64) if prec == "fp64" else C)
+    dtype = torch.float64 if prec == "fp64" else torch.float32
+    npatch = G.shape[0]
+    dh = 1.0 / N
+    dd = torch.tensor([[0.4 * dh, dh]], dtype=torch.float64, device="cuda").repeat(npatch, 1)
+    st = torch.empty(npatch, dtype=torch.int32, device="cuda")
+    dn = torch.empty(1, dtype=torch.float64, device="cuda")
+    out = srhd.advance_patches(to_dev(torch, G, dtype), dd, dt_next=dn, patch_status=st)
+    torch.cuda.synchronize()
+    assert int(st.abs().max()) == 0
+    rng = np.random.default_rng(11)
+    pick = np.concatenate([[0, npatch - 1], rng.choice(npatch, 22, replace=False)])
+    ref = oracle.advance_patches(G[pick].astype(np.float64), np.tile([0.4 * dh, dh], (pick.size, 1)))
+    o = to_np(out[torch.as_tensor(pick, device="cuda")])
+    err = cons_rel_err(o.transpose(1, 0, 2, 3, 4), ref["out"].transpose(1, 0, 2, 3, 4))
+    assert err.max() <= (1e-12 if prec == "fp64" else 1e-5), err.max()
+    assert np.isfinite(dn.item()) and dn.item() > 0
