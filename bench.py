@@ -56,7 +56,10 @@ PEAK_FP64_TFLOPS = 1.25
 # DRAM traffic per launch of the patch kernel from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum), keyed by precision, valid
 # only for the kernel sources with the recorded hash.
-NCU_TRAFFIC = {"sources_sha": None, "mixed": None, "fp64": None}
+# Captured at 128^3 (4096 patches) and scaled by 8 to the 32768-patch launch
+# (profiles/patch_kernel_advection128.md).
+NCU_TRAFFIC = {"sources_sha": "19dd3907075f225c", "mixed": 8 * (141.704704e6 + 24.683520e6),
+               "fp64": 8 * (274.028032e6 + 66.898944e6)}
 
 
 def kernel_sources_sha() -> str:

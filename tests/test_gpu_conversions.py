@@ -32,7 +32,12 @@ def test_con2pri_parity(oracle, prec, n):
     torch.cuda.synchronize()
     Pg, stg = to_np(P), st.cpu().numpy()
     assert set(np.unique(stg)) <= {0, 1}
-    kappa = kappa_of_prims(oracle, W)
+    # conditioning of the state the input actually encodes (in the mixed
+    # path the float rounding of Etilde can move a cold, fast cell far from
+    # the drawn state), from the oracle's inversion of the same input
+    with np.errstate(invalid="ignore"):
+        kappa = np.where(ref["status"] == 0, kappa_of_prims(oracle, np.nan_to_num(ref["prim"], nan=1.0)),
+                         np.inf)
     clear = kappa * EPS64 <= 1e-3
     # well-conditioned cells: same status, values within the tolerance
     assert np.array_equal(stg[clear], ref["status"][clear])
