@@ -186,6 +186,27 @@ srhd_status srhd_fill_ghosts_uniform(srhd_ctx* ctx, srhd_prec prec, const void* 
                                      void* ghosted, int32_t npx, int32_t npy, int32_t npz,
                                      const int32_t* bc, void* stream);
 
+/* CFL time step of a batch of interior patches, like srhd_cfl_dt, for
+ * callers that cannot allocate device memory. (The paper has no counterpart:
+ * this is a deployment variant of srhd_cfl_dt.) Some callers cannot call
+ * cudaMalloc: an application whose device memory all comes from its own pool
+ * allocator, or a time-step loop that must not let an allocation synchronise
+ * the device. srhd_cfl_dt needs a context and srhd_create allocates, so this
+ * entry point takes no context and allocates nothing.
+ *   cons [npatch][5][8^3]; 0 <= npatch <= 131072 (larger batches are refused
+ *   with SRHD_ERR_ARG); dh > 0; params (nullable: defaults) supplies cfl,
+ *   cfl_mode, ndim and newton_max_iter; dt_out: one device double receiving
+ *   min over cells of C_CFL dh / S_max, NaN if a cell is unphysical, +inf if
+ *   npatch == 0.
+ * Its scratch is a fixed 1.5 MB static device array that every GPU loading
+ * the library holds until the process exits. The first call on each device
+ * looks up that array's device address (cudaGetSymbolAddress) with the
+ * device current, so make that first call before any stream capture begins.
+ * All calls share the array and leave their per-patch results in it: calls
+ * whose work overlaps on the GPU race and must be ordered by the caller. */
+srhd_status srhd_cfl_dt_noalloc(srhd_prec prec, const void* cons, int32_t npatch, double dh,
+                                const srhd_params* params, double* dt_out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

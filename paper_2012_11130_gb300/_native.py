@@ -23,7 +23,7 @@ PATCH_UNPHYSICAL, PATCH_BAD_INPUT, PATCH_NOCONV = 1, 2, 4
 # Every symbol declared in include/srhd.h.
 EXPORTS = ("srhd_default_params", "srhd_create", "srhd_destroy", "srhd_last_error",
            "srhd_prim2con", "srhd_con2pri", "srhd_flux_patches", "srhd_advance_patches",
-           "srhd_cfl_dt", "srhd_fill_ghosts_uniform")
+           "srhd_cfl_dt", "srhd_fill_ghosts_uniform", "srhd_cfl_dt_noalloc")
 
 
 class Params(ctypes.Structure):

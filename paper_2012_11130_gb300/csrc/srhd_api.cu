@@ -109,6 +109,12 @@ srhd_status check_ctx(const srhd_ctx* c) {
 
 }  // namespace
 
+namespace srhd {
+// Sets the message returned by srhd_last_error() on the calling thread (used
+// by entry points defined in other translation units).
+void set_last_error(const char* msg) { snprintf(g_err, sizeof(g_err), "%s", msg); }
+}  // namespace srhd
+
 extern "C" {
 
 srhd_status srhd_default_params(srhd_params* p) {
