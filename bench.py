@@ -10,9 +10,12 @@ check and retry, and the fused CFL minimum (plus its one-block finalize).
 The ghosted inputs (1.13 GB mixed, 2.26 GB FP64) are resident in HBM and
 larger than L2, so no flush is needed between steps.
 
-The headline is the mixed path (float storage and arithmetic, A of the
-con2pri equation in double); the FP64 path is measured in the same run and
-reported under "fp64". Multi-GPU (torchrun): every rank advances its own
+The headline is the float path "mixed_cf" (float storage and arithmetic;
+the cancellation-critical A of the con2pri equation by error-free float
+products and a compensated sum, so no FP64 instruction at all). The mixed
+path with A in double ("mixed", the design that keeps FP64 inside con2pri)
+and the FP64 path are measured in the same run and reported under their
+names. Multi-GPU (torchrun): every rank advances its own
 copy of the batch (weak scaling, no data-path collective); the value is
 all cells updated / max time over ranks.
 
@@ -48,7 +51,7 @@ WORKLOAD = ("3-D periodic smooth advection 256^3 (rho=1+0.5 sin(2pi(x+y+z)), p=1
 # the CFL bound of the updated cell.
 FLOPS_PER_CELL_UPDATE = 4583.2
 # Algorithmic bytes per cell update: 5 conserved values read + 5 written.
-BYTES_PER_CELL_UPDATE = {"mixed": 40, "fp64": 80}
+BYTES_PER_CELL_UPDATE = {"mixed_cf": 40, "mixed": 40, "fp64": 80}
 # Peaks: FP32 from the unit counts (152 SMs x 128 FP32 lanes x 2 flops x
 # 2070 MHz); FP64 at the nominal 1.25 TFLOP/s of GB300; HBM measured.
 PEAK_FP32_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
@@ -59,7 +62,7 @@ PEAK_FP64_TFLOPS = 1.25
 # Captured at 128^3 (4096 patches) and scaled by 8 to the 32768-patch launch
 # (profiles/patch_kernel_advection128.md).
 NCU_TRAFFIC = {"sources_sha": "19dd3907075f225c", "mixed": 8 * (141.704704e6 + 24.683520e6),
-               "fp64": 8 * (274.028032e6 + 66.898944e6)}
+               "mixed_cf": None, "fp64": 8 * (274.028032e6 + 66.898944e6)}
 
 
 def kernel_sources_sha() -> str:
@@ -142,6 +145,26 @@ def dist_env():
     return world, rank, local
 
 
+def job_throughput(local_ms: float, units_per_rank: int, steps: int, device=None):
+    """Whole-job throughput of a weak-scaled run: every rank processed
+    units_per_rank units per step for `steps` steps; the job took the
+    slowest rank's time. Returns (units/s, max ms over ranks). Uses an
+    all-reduce(MAX) when a process group is initialised (nccl on the GPU,
+    gloo on the CPU), which is the only collective of the benchmark."""
+    import torch
+    world = 1
+    t = torch.tensor([local_ms], dtype=torch.float64, device=device)
+    try:
+        import torch.distributed as dist
+        if dist.is_available() and dist.is_initialized():
+            world = dist.get_world_size()
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    except ImportError:
+        pass
+    max_ms = float(t.item())
+    return world * units_per_rank * steps / (max_ms * 1e-3), max_ms
+
+
 # ---------------------------------------------------------------------------
 # workload on the device
 # ---------------------------------------------------------------------------
@@ -154,7 +177,7 @@ def build_workload(torch, srhd, ctx, prec, n=N_GRID):
     del Wd
     npx = n // 8
     P = C.reshape(5, npx, 8, npx, 8, npx, 8).permute(1, 3, 5, 0, 2, 4, 6).reshape(-1, 5, 8, 8, 8)
-    dtype = torch.float32 if prec == "mixed" else torch.float64
+    dtype = torch.float64 if prec == "fp64" else torch.float32
     P = P.to(dtype).contiguous()
     del C
     G = ctx.fill_ghosts_uniform(P, npx, npx, npx)
@@ -165,14 +188,14 @@ def build_workload(torch, srhd, ctx, prec, n=N_GRID):
     return G, dt_dh
 
 
-def time_device(torch, ctx, G, dt_dh, steps, warmup, barrier):
+def time_device(torch, ctx, G, dt_dh, steps, warmup, barrier, prec):
     npatch = G.shape[0]
     out = torch.empty((npatch, 5, 8, 8, 8), dtype=G.dtype, device="cuda")
     dn = torch.empty(1, dtype=torch.float64, device="cuda")
     st = torch.empty(npatch, dtype=torch.int32, device="cuda")
     stream = torch.cuda.current_stream()
     for _ in range(warmup):
-        ctx.advance_patches(G, dt_dh, cons_out=out, dt_next=dn, patch_status=st)
+        ctx.advance_patches(G, dt_dh, cons_out=out, dt_next=dn, patch_status=st, prec=prec)
     torch.cuda.synchronize()
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
            for _ in range(steps)]
@@ -183,7 +206,7 @@ def time_device(torch, ctx, G, dt_dh, steps, warmup, barrier):
     t0.record(stream)
     for e0, e1 in evs:
         e0.record(stream)
-        ctx.advance_patches(G, dt_dh, cons_out=out, dt_next=dn, patch_status=st)
+        ctx.advance_patches(G, dt_dh, cons_out=out, dt_next=dn, patch_status=st, prec=prec)
         e1.record(stream)
     t1.record(stream)
     torch.cuda.synchronize()
@@ -194,7 +217,7 @@ def time_device(torch, ctx, G, dt_dh, steps, warmup, barrier):
     return total_ms, per, dn.item(), status_max
 
 
-def time_e2e(torch, ctx, G, dt_dh, steps, warmup):
+def time_e2e(torch, ctx, G, dt_dh, steps, warmup, prec):
     """Public API with host buffers: every step copies the ghosted batch
     from pinned host memory, runs the step and reads back the updated
     interiors and the next time step."""
@@ -204,11 +227,11 @@ def time_e2e(torch, ctx, G, dt_dh, steps, warmup):
     outh = torch.empty((G.shape[0], 5, 8, 8, 8), dtype=G.dtype, pin_memory=True)
     dnh = torch.empty(1, dtype=torch.float64, pin_memory=True)
     for _ in range(warmup):
-        ctx.advance_patches(Gh, dth, cons_out=outh, dt_next=dnh)
+        ctx.advance_patches(Gh, dth, cons_out=outh, dt_next=dnh, prec=prec)
     torch.cuda.synchronize()
     t = time.perf_counter()
     for _ in range(steps):
-        ctx.advance_patches(Gh, dth, cons_out=outh, dt_next=dnh)
+        ctx.advance_patches(Gh, dth, cons_out=outh, dt_next=dnh, prec=prec)
     torch.cuda.synchronize()
     secs = time.perf_counter() - t
     h2d = Gh.numel() * Gh.element_size() + dth.numel() * 8
@@ -226,7 +249,7 @@ def l1_one_period(torch, srhd, prec, n=64):
     W = torch.from_numpy(workloads.advection_prims(n)).to("cuda")
     C = ctx.prim2con(W.reshape(5, -1)).reshape(5, n, n, n)
     npx = n // 8
-    dtype = torch.float32 if prec == "mixed" else torch.float64
+    dtype = torch.float64 if prec == "fp64" else torch.float32
     U = C.reshape(5, npx, 8, npx, 8, npx, 8).permute(1, 3, 5, 0, 2, 4, 6).reshape(
         -1, 5, 8, 8, 8).to(dtype).contiguous()
     v = math.sqrt(99.0 / 3.0) / math.sqrt(100.0)
@@ -235,7 +258,7 @@ def l1_one_period(torch, srhd, prec, n=64):
     dd = torch.empty((U.shape[0], 2), dtype=torch.float64, device="cuda")
     dn = torch.empty(1, dtype=torch.float64, device="cuda")
     out = torch.empty_like(U)
-    dt = ctx.cfl_dt(U, dh).item()
+    dt = ctx.cfl_dt(U, dh, prec=prec).item()
     t = 0.0
     steps = 0
     while t < t_end and steps < 100000:
@@ -243,12 +266,12 @@ def l1_one_period(torch, srhd, prec, n=64):
         dd[:, 0] = dt
         dd[:, 1] = dh
         G = ctx.fill_ghosts_uniform(U, npx, npx, npx)
-        ctx.advance_patches(G, dd, cons_out=out, dt_next=dn)
+        ctx.advance_patches(G, dd, cons_out=out, dt_next=dn, prec=prec)
         U, out = out, U
         t += dt
         steps += 1
         dt = dn.item()
-    Pd = ctx.con2pri(U.permute(1, 0, 2, 3, 4).reshape(5, -1).contiguous())
+    Pd = ctx.con2pri(U.permute(1, 0, 2, 3, 4).reshape(5, -1).contiguous(), prec=prec)
     rho = Pd[0].double().reshape(npx, npx, npx, 8, 8, 8).permute(0, 3, 1, 4, 2, 5).reshape(
         n, n, n).cpu().numpy()
     exact = workloads.advection_prims(n, t=t_end)[0]
@@ -365,37 +388,33 @@ def run_ours(args):
     sha = kernel_sources_sha()
 
     results = {}
-    precs = ("mixed", "fp64") if args.prec == "both" else (args.prec,)
+    precs = ("mixed_cf", "mixed", "fp64") if args.prec == "all" else (args.prec,)
     for prec in precs:
         G, dt_dh = build_workload(torch, srhd, ctx, prec, args.grid)
         torch.cuda.synchronize()
         with ClockSampler(local) as clk:
             total_ms, per, dt_next, smax = time_device(torch, ctx, G, dt_dh, args.steps,
-                                                       args.warmup, barrier)
+                                                       args.warmup, barrier, prec)
         clocks = clk.summary()
-        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-        if world > 1:
-            import torch.distributed as dist
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = t.item()
+        value, total_ms = job_throughput(total_ms, cells, args.steps, device="cuda")
         e2e = None
         if not args.no_e2e:
-            secs, h2d, d2h = time_e2e(torch, ctx, G, dt_dh, max(3, args.steps // 4), 1)
+            secs, h2d, d2h = time_e2e(torch, ctx, G, dt_dh, max(3, args.steps // 4), 1, prec)
             e2e = {"value": world * cells * max(3, args.steps // 4) / secs, "unit": UNIT,
                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
         launch_ms = statistics.mean(per)
         flops = FLOPS_PER_CELL_UPDATE * cells
-        peak_alu = PEAK_FP32_TFLOPS if prec == "mixed" else PEAK_FP64_TFLOPS
+        peak_alu = PEAK_FP64_TFLOPS if prec == "fp64" else PEAK_FP32_TFLOPS
         achieved = flops / (launch_ms * 1e-3) / 1e12
         traffic = NCU_TRAFFIC.get(prec) if NCU_TRAFFIC.get("sources_sha") == sha else None
         alg_bytes = BYTES_PER_CELL_UPDATE[prec] * cells
         results[prec] = {
-            "value": world * cells * args.steps / (total_ms * 1e-3),
+            "value": value,
             "ms_per_step": total_ms / args.steps,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_alu,
                          "unit": "TFLOP/s", "frac": achieved / peak_alu, "traffic": traffic,
-                         "peak_source": ("derived: 152 SM x 128 FP32 lanes x 2 x 2070 MHz"
-                                         if prec == "mixed" else "nominal GB300 FP64 1.25 TFLOP/s"),
+                         "peak_source": ("nominal GB300 FP64 1.25 TFLOP/s" if prec == "fp64" else
+                                         "derived: 152 SM x 128 FP32 lanes x 2 x 2070 MHz"),
                          "flops_per_cell_update": FLOPS_PER_CELL_UPDATE},
             "hbm_roofline": {"bound": "hbm", "achieved": alg_bytes / (launch_ms * 1e-3) / 1e9,
                              "peak": hbm_peak, "unit": "GB/s",
@@ -433,20 +452,23 @@ def run_ours(args):
         "metric": METRIC, "value": m["value"], "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": m["ms_per_step"],
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32+f64" if precs[0] == "mixed" else "f64", "data": "synthetic",
+        "dtype": {"mixed_cf": "f32", "mixed": "f32+f64", "fp64": "f64"}[precs[0]],
+        "data": "synthetic",
         "config": {"workload": WORKLOAD if args.grid == N_GRID else
                    WORKLOAD.replace("256^3", f"{args.grid}^3").replace("32768", str(npatch)),
                    "cells": cells, "patches": npatch,
-                   "precision": ("mixed: float storage/arithmetic, con2pri A in double"
-                                 if precs[0] == "mixed" else "fp64"),
+                   "precision": {"mixed_cf": "mixed_cf: float storage and arithmetic, con2pri A "
+                                             "by error-free float products + compensated sum",
+                                 "mixed": "mixed: float storage/arithmetic, con2pri A in double",
+                                 "fp64": "fp64"}[precs[0]],
                    "l2": "inputs larger than L2 (ghosted batch resident in HBM), no flush",
                    "parallelism": f"replicas x{world}"},
         "roofline": m["roofline"], "hbm_roofline": m["hbm_roofline"],
         "clocks": m["clocks"], "e2e": m["e2e"], "cpu_baseline": cpu,
         "gpu_launches": 2 * args.steps,
-        "fp64": ({k: results["fp64"][k] for k in ("value", "ms_per_step", "roofline",
-                                                   "hbm_roofline", "clocks", "e2e")}
-                 if "fp64" in results and precs[0] != "fp64" else None),
+        "other_precisions": {q: {k: results[q][k] for k in ("value", "ms_per_step", "roofline",
+                                                             "hbm_roofline", "clocks", "e2e")}
+                             for q in precs[1:]} or None,
         "l1_rho": l1 or None,
         "kernel_sources_sha": sha,
     }
@@ -469,7 +491,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--grid", type=int, default=N_GRID,
                     help="cells per axis of the advection grid (multiple of 8)")
-    ap.add_argument("--prec", choices=["both", "mixed", "fp64"], default="both")
+    ap.add_argument("--prec", choices=["all", "mixed_cf", "mixed", "fp64"], default="all")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)  # at least 3 untimed warm-up steps
     if args.impl == "reference":

@@ -16,7 +16,9 @@
  *   Precision: SRHD_FP64 = double storage and double arithmetic;
  *   SRHD_MIXED = float storage, float arithmetic, except the left-hand side
  *   A of Eq. (transcendental equation) / Eq. (Unphysical result), which is
- *   formed in double in every conserved-to-primitive conversion.
+ *   formed in double in every conserved-to-primitive conversion;
+ *   SRHD_MIXED_CF = as SRHD_MIXED but with A formed by compensated float
+ *   arithmetic (see srhd_prec).
  *
  * Ownership and execution
  *   Every data pointer is a caller-owned DEVICE pointer on the context's
@@ -52,9 +54,14 @@ typedef enum srhd_status {
 } srhd_status;
 
 typedef enum srhd_prec {
-  SRHD_FP64 = 0,   /* double storage, double arithmetic */
-  SRHD_MIXED = 1,  /* float storage and arithmetic; A of Eq. (transcendental
-                      equation) in double */
+  SRHD_FP64 = 0,     /* double storage, double arithmetic */
+  SRHD_MIXED = 1,    /* float storage and arithmetic; A of Eq. (transcendental
+                        equation) in double */
+  SRHD_MIXED_CF = 2, /* float storage and arithmetic; A of Eq. (transcendental
+                        equation) from error-free float products and a
+                        compensated float sum (about 2^-44 of the cancelling
+                        terms instead of 2^-53), so no double arithmetic at
+                        all; element type float */
 } srhd_prec;
 
 typedef enum srhd_riemann { SRHD_HLLC = 0, SRHD_HLLE = 1 } srhd_riemann;

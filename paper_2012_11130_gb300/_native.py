@@ -13,7 +13,7 @@ PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(PKG, "libsrhd.so")
 
 SRHD_OK, SRHD_ERR_ARG, SRHD_ERR_CUDA = 0, 1, 2
-SRHD_FP64, SRHD_MIXED = 0, 1
+SRHD_FP64, SRHD_MIXED, SRHD_MIXED_CF = 0, 1, 2
 SRHD_HLLC, SRHD_HLLE = 0, 1
 SRHD_CFL_SIGNAL, SRHD_CFL_LIGHT = 0, 1
 SRHD_BC_PERIODIC, SRHD_BC_OUTFLOW = 0, 1

@@ -20,7 +20,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libsrhd.so")
-SOURCES = ["srhd_api.cu", "srhd_fp64.cu", "srhd_mixed.cu", "srhd_noalloc.cu"]
+SOURCES = ["srhd_api.cu", "srhd_fp64.cu", "srhd_mixed.cu", "srhd_mixed_cf.cu", "srhd_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-ftz=true",
               "-prec-div=false", "-prec-sqrt=false", "--expt-relaxed-constexpr"]

@@ -11,8 +11,9 @@
 #include "srhd_kernels.cuh"
 
 namespace srhd {
-extern template struct Launch<double>;
-extern template struct Launch<float>;
+extern template struct Launch<PrecFP64>;
+extern template struct Launch<PrecMixed>;
+extern template struct Launch<PrecMixedCF>;
 
 __global__ void cfl_finalize_kernel(const double* partial, const int32_t* bad, int n,
                                     double* dt_out) {
@@ -45,7 +46,7 @@ struct srhd_ctx {
   srhd_params params;
   int device;
   int num_sms;
-  int patch_grid[2];      // persistent grid per precision
+  int patch_grid[3];      // persistent grid per precision
   int scratch_slots;      // capacity of the partial-minimum arrays
   double* partial_dt;     // scratch [scratch_slots]
   int32_t* partial_bad;   // scratch [scratch_slots]
@@ -67,7 +68,16 @@ srhd_status cuda_fail(cudaError_t e, const char* what) {
   return fail(SRHD_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
-bool valid_prec(srhd_prec p) { return p == SRHD_FP64 || p == SRHD_MIXED; }
+bool valid_prec(srhd_prec p) { return p == SRHD_FP64 || p == SRHD_MIXED || p == SRHD_MIXED_CF; }
+
+// Calls f with the launcher of the precision tag that prec selects.
+template <class F> cudaError_t dispatch(srhd_prec prec, F&& f) {
+  switch (prec) {
+    case SRHD_FP64: return f(srhd::Launch<srhd::PrecFP64>{});
+    case SRHD_MIXED: return f(srhd::Launch<srhd::PrecMixed>{});
+    default: return f(srhd::Launch<srhd::PrecMixedCF>{});
+  }
+}
 
 int newton_maxit(const srhd_ctx* c, srhd_prec prec) {
   if (c->params.newton_max_iter > 0) return c->params.newton_max_iter;
@@ -144,21 +154,26 @@ srhd_status srhd_create(srhd_ctx** out, const srhd_params* p) {
   if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
   e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceGetAttribute");
-  if ((e = srhd::Launch<double>::setup()) != cudaSuccess) return cuda_fail(e, "setup fp64");
-  if ((e = srhd::Launch<float>::setup()) != cudaSuccess) return cuda_fail(e, "setup mixed");
+  if ((e = srhd::Launch<srhd::PrecFP64>::setup()) != cudaSuccess) return cuda_fail(e, "setup fp64");
+  if ((e = srhd::Launch<srhd::PrecMixed>::setup()) != cudaSuccess) return cuda_fail(e, "setup mixed");
+  if ((e = srhd::Launch<srhd::PrecMixedCF>::setup()) != cudaSuccess)
+    return cuda_fail(e, "setup mixed_cf");
   srhd_ctx* c = new (std::nothrow) srhd_ctx;
   if (!c) return fail(SRHD_ERR_ARG, "out of host memory");
   c->params = prm;
   c->device = dev;
   c->num_sms = nsm;
-  int b64 = srhd::Launch<double>::patch_blocks_per_sm();
-  int b32 = srhd::Launch<float>::patch_blocks_per_sm();
-  if (b64 < 1 || b32 < 1) {
+  int b64 = srhd::Launch<srhd::PrecFP64>::patch_blocks_per_sm();
+  int b32 = srhd::Launch<srhd::PrecMixed>::patch_blocks_per_sm();
+  int bcf = srhd::Launch<srhd::PrecMixedCF>::patch_blocks_per_sm();
+  if (b64 < 1 || b32 < 1 || bcf < 1) {
     delete c;
-    return fail(SRHD_ERR_CUDA, "patch kernel does not fit on an SM (blocks/SM %d, %d)", b64, b32);
+    return fail(SRHD_ERR_CUDA, "patch kernel does not fit on an SM (blocks/SM %d, %d, %d)", b64,
+                b32, bcf);
   }
   c->patch_grid[SRHD_FP64] = nsm * b64;
   c->patch_grid[SRHD_MIXED] = nsm * b32;
+  c->patch_grid[SRHD_MIXED_CF] = nsm * bcf;
   c->scratch_slots = nsm * 8;
   c->partial_dt = nullptr;
   c->partial_bad = nullptr;
@@ -192,9 +207,9 @@ srhd_status srhd_prim2con(srhd_ctx* c, srhd_prec prec, const void* prim, void* c
   if (!prim || !cons) return fail(SRHD_ERR_ARG, "prim/cons is NULL");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   int grid = grid_for(c, n, 16);
-  cudaError_t e = prec == SRHD_FP64
-                      ? srhd::Launch<double>::prim2con(prim, cons, n, var_stride, grid, s)
-                      : srhd::Launch<float>::prim2con(prim, cons, n, var_stride, grid, s);
+  cudaError_t e = dispatch(prec, [&](auto L) {
+    return decltype(L)::prim2con(prim, cons, n, var_stride, grid, s);
+  });
   return e == cudaSuccess ? SRHD_OK : cuda_fail(e, "prim2con launch");
 }
 
@@ -209,10 +224,9 @@ srhd_status srhd_con2pri(srhd_ctx* c, srhd_prec prec, const void* cons, void* pr
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   int grid = grid_for(c, n, 16);
   int maxit = newton_maxit(c, prec);
-  cudaError_t e =
-      prec == SRHD_FP64
-          ? srhd::Launch<double>::con2pri(cons, prim, n, var_stride, cell_status, maxit, grid, s)
-          : srhd::Launch<float>::con2pri(cons, prim, n, var_stride, cell_status, maxit, grid, s);
+  cudaError_t e = dispatch(prec, [&](auto L) {
+    return decltype(L)::con2pri(cons, prim, n, var_stride, cell_status, maxit, grid, s);
+  });
   return e == cudaSuccess ? SRHD_OK : cuda_fail(e, "con2pri launch");
 }
 
@@ -226,8 +240,7 @@ static srhd_status launch_patches(srhd_ctx* c, srhd_prec prec, srhd::PatchArgs& 
   }
   cudaError_t e = cudaSuccess;
   if (a.npatch > 0) {
-    e = prec == SRHD_FP64 ? srhd::Launch<double>::patches(a, grid, s)
-                          : srhd::Launch<float>::patches(a, grid, s);
+    e = dispatch(prec, [&](auto L) { return decltype(L)::patches(a, grid, s); });
     if (e != cudaSuccess) return cuda_fail(e, "patch kernel launch");
   } else {
     grid = 0;
@@ -319,13 +332,10 @@ srhd_status srhd_cfl_dt(srhd_ctx* c, srhd_prec prec, const void* cons, int32_t n
     grid = int(std::min<int64_t>((ncell + srhd::kCflThreads - 1) / srhd::kCflThreads,
                                  (int64_t)c->scratch_slots));
     int maxit = newton_maxit(c, prec);
-    e = prec == SRHD_FP64
-            ? srhd::Launch<double>::cfl(cons, ncell, dh, c->params.cfl, c->params.ndim,
-                                        c->params.cfl_mode, maxit, c->partial_dt, c->partial_bad,
-                                        grid, s)
-            : srhd::Launch<float>::cfl(cons, ncell, dh, c->params.cfl, c->params.ndim,
-                                       c->params.cfl_mode, maxit, c->partial_dt, c->partial_bad,
-                                       grid, s);
+    e = dispatch(prec, [&](auto L) {
+      return decltype(L)::cfl(cons, ncell, dh, c->params.cfl, c->params.ndim, c->params.cfl_mode,
+                              maxit, c->partial_dt, c->partial_bad, grid, s);
+    });
     if (e != cudaSuccess) return cuda_fail(e, "cfl launch");
   }
   srhd::cfl_finalize_kernel<<<1, 256, 0, s>>>(c->partial_dt, c->partial_bad, grid, dt_out);
@@ -347,9 +357,9 @@ srhd_status srhd_fill_ghosts_uniform(srhd_ctx* c, srhd_prec prec, const void* in
   int64_t total = (int64_t)npx * npy * npz * 5 * srhd::kGC;
   int grid = grid_for(c, total, 16);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  cudaError_t e = prec == SRHD_FP64
-                      ? srhd::Launch<double>::fill_ghosts(interior, ghosted, npx, npy, npz, bc, grid, s)
-                      : srhd::Launch<float>::fill_ghosts(interior, ghosted, npx, npy, npz, bc, grid, s);
+  cudaError_t e = dispatch(prec, [&](auto L) {
+    return decltype(L)::fill_ghosts(interior, ghosted, npx, npy, npz, bc, grid, s);
+  });
   return e == cudaSuccess ? SRHD_OK : cuda_fail(e, "fill_ghosts launch");
 }
 

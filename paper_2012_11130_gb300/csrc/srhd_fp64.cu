@@ -2,5 +2,5 @@
 #include "srhd_launch.inl"
 
 namespace srhd {
-template struct Launch<double>;
+template struct Launch<PrecFP64>;
 }

@@ -53,7 +53,7 @@ struct PatchArgs {
   int flux_only;
 };
 
-template <class S> struct SmemLayout {
+template <class S> struct SmemLayout {  // S: storage type
   static constexpr size_t prim_elems = 5 * kGC;
   static constexpr size_t face_elems = 3 * 2 * 5 * kNF;
   static constexpr size_t bytes = (prim_elems + face_elems) * sizeof(S);
@@ -72,6 +72,34 @@ __device__ __forceinline__ bool tile_cell_needed(int gx, int gy, int gz) {
   int nout = (a > 0) + (b > 0) + (c > 0);
   if (nout <= 1) return true;
   return nout == 2 && a <= 1 && b <= 1 && c <= 1;
+}
+
+constexpr int kTileNeeded = 512 + 768 + 96;  // 1376 cells read by the step
+
+// r-th cell of the tile that the step reads (tile_cell_needed), as a
+// 12^3 index: the 8^3 interior, then the six faces two layers deep, then the
+// twelve edges of the first layer.
+__device__ __forceinline__ int needed_tile_cell(int r) {
+  int g[3];
+  if (r < 512) {
+    g[0] = 2 + (r & 7); g[1] = 2 + ((r >> 3) & 7); g[2] = 2 + (r >> 6);
+  } else if (r < 1280) {
+    const int q = r - 512, f = q >> 7, rem = q & 127;
+    const int axis = f >> 1, depth = 1 + (rem >> 6), t = rem & 63;
+    const int along = (f & 1) ? 9 + depth : 2 - depth;
+    const int u = 2 + (t & 7), v = 2 + (t >> 3);
+    if (axis == 0) { g[0] = along; g[1] = u; g[2] = v; }
+    else if (axis == 1) { g[0] = u; g[1] = along; g[2] = v; }
+    else { g[0] = u; g[1] = v; g[2] = along; }
+  } else {
+    const int q = r - 1280, e = q >> 3, w = 2 + (q & 7);
+    const int pair = e >> 2;
+    const int ca = (e & 1) ? 10 : 1, cb = (e & 2) ? 10 : 1;
+    if (pair == 0) { g[0] = ca; g[1] = cb; g[2] = w; }
+    else if (pair == 1) { g[0] = ca; g[1] = w; g[2] = cb; }
+    else { g[0] = w; g[1] = ca; g[2] = cb; }
+  }
+  return (g[2] * kG + g[1]) * kG + g[0];
 }
 
 // r-th reconstructed cell, interior coordinates in [-1, 8].
@@ -170,28 +198,39 @@ __device__ __forceinline__ void halfstep_direction(int i, int j, int k, bool int
   }
 }
 
-template <int d, class R, class S>
-__device__ __forceinline__ int face_flux(S* face, int fi, int solver, int maxit, int& code) {
-  R UL[5], UR[5];
+template <int d, class P, bool PAIR>
+__device__ __forceinline__ int face_flux(typename P::S* face, int fi, int solver, int maxit,
+                                         int& code) {
+  using S = typename P::S;
+  using R = S;
+  S UL[5], UR[5];
 #pragma unroll
   for (int v = 0; v < 5; ++v) {
-    UL[v] = R(face_slot(face, d, 0, v)[fi]);
-    UR[v] = R(face_slot(face, d, 1, v)[fi]);
+    UL[v] = face_slot(face, d, 0, v)[fi];
+    UR[v] = face_slot(face, d, 1, v)[fi];
   }
   PrimX<R> WL, WR;
-  int sl = con2pri<R, S>(S(UL[0]), S(UL[1]), S(UL[2]), S(UL[3]), S(UL[4]), WL, maxit);
-  int sr = con2pri<R, S>(S(UR[0]), S(UR[1]), S(UR[2]), S(UR[3]), S(UR[4]), WR, maxit);
+  int sl, sr;
+  if constexpr (PAIR) {
+    con2pri_x2<P>(UL, UR, WL, WR, maxit, sl, sr);
+  } else {
+    sl = con2pri<P>(UL[0], UL[1], UL[2], UL[3], UL[4], WL, maxit);
+    sr = con2pri<P>(UR[0], UR[1], UR[2], UR[3], UR[4], WR, maxit);
+  }
   if (sl == 2 || sr == 2) code |= CODE_NOCONV;
   int fail = (sl == 1 || sr == 1);
+  R FL_[5] = {R(UL[0]), R(UL[1]), R(UL[2]), R(UL[3]), R(UL[4])};
+  R FR_[5] = {R(UR[0]), R(UR[1]), R(UR[2]), R(UR[3]), R(UR[4])};
   R F[5];
-  riemann<d>(solver, WL, UL, WR, UR, F);
+  riemann<d>(solver, WL, FL_, WR, FR_, F);
 #pragma unroll
   for (int v = 0; v < 5; ++v) face_slot(face, d, 0, v)[fi] = S(F[v]);
   return fail;
 }
 
-template <class S, int NT, int MINB>
+template <class P, int NT, int MINB, bool PAIR>
 __global__ void __launch_bounds__(NT, MINB) patch_kernel(PatchArgs a) {
+  using S = typename P::S;
   using R = S;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   S* prim = reinterpret_cast<S*>(smem_raw);
@@ -212,25 +251,52 @@ __global__ void __launch_bounds__(NT, MINB) patch_kernel(PatchArgs a) {
 
     __syncthreads();  // the previous patch is done with shared memory
     // ---- phase 1: primitive tile ------------------------------------------
-    for (int c = tid; c < kGC; c += NT) {
-      int gx = c % kG, gy = (c / kG) % kG, gz = c / (kG * kG);
-      if (!tile_cell_needed(gx, gy, gz)) continue;
-      PrimX<R> W;
-      int st = con2pri<R, S>(in[c], in[kGC + c], in[2 * kGC + c], in[3 * kGC + c],
-                             in[4 * kGC + c], W, maxit);
-      if (st == 1) code |= CODE_BAD_INPUT;
-      if (st == 2) code |= CODE_NOCONV;
-      prim[c] = S(W.rho);
-      prim[kGC + c] = S(W.u[0]);
-      prim[2 * kGC + c] = S(W.u[1]);
-      prim[3 * kGC + c] = S(W.u[2]);
-      prim[4 * kGC + c] = S(W.p);
+    if constexpr (PAIR) {
+      for (int r = tid; r < kTileNeeded / 2; r += NT) {
+        const int ca = needed_tile_cell(r), cb = needed_tile_cell(r + kTileNeeded / 2);
+        S Ua[5], Ub[5];
+#pragma unroll
+        for (int v = 0; v < 5; ++v) {
+          Ua[v] = in[v * kGC + ca];
+          Ub[v] = in[v * kGC + cb];
+        }
+        PrimX<R> Wa, Wb;
+        int sa, sb;
+        con2pri_x2<P>(Ua, Ub, Wa, Wb, maxit, sa, sb);
+        if (sa == 1 || sb == 1) code |= CODE_BAD_INPUT;
+        if (sa == 2 || sb == 2) code |= CODE_NOCONV;
+        prim[ca] = S(Wa.rho);
+        prim[kGC + ca] = S(Wa.u[0]);
+        prim[2 * kGC + ca] = S(Wa.u[1]);
+        prim[3 * kGC + ca] = S(Wa.u[2]);
+        prim[4 * kGC + ca] = S(Wa.p);
+        prim[cb] = S(Wb.rho);
+        prim[kGC + cb] = S(Wb.u[0]);
+        prim[2 * kGC + cb] = S(Wb.u[1]);
+        prim[3 * kGC + cb] = S(Wb.u[2]);
+        prim[4 * kGC + cb] = S(Wb.p);
+      }
+    } else {
+      for (int r = tid; r < kTileNeeded; r += NT) {
+        const int c = needed_tile_cell(r);
+        PrimX<R> W;
+        int st = con2pri<P>(in[c], in[kGC + c], in[2 * kGC + c], in[3 * kGC + c],
+                            in[4 * kGC + c], W, maxit);
+        if (st == 1) code |= CODE_BAD_INPUT;
+        if (st == 2) code |= CODE_NOCONV;
+        prim[c] = S(W.rho);
+        prim[kGC + c] = S(W.u[0]);
+        prim[2 * kGC + c] = S(W.u[1]);
+        prim[3 * kGC + c] = S(W.u[2]);
+        prim[4 * kGC + c] = S(W.p);
+      }
     }
     const int bad_input = __syncthreads_or(code & CODE_BAD_INPUT);
 
     int retries = 0;
     int final_code = 0;
-    double att_min = DBL_MAX;
+    double att_min = DBL_MAX;   // light-speed mode: C dh
+    R att_smax = R(0);          // signal mode: largest S_max of the attempt
     int att_bad = 0;
     if (!bad_input) {
       R theta = R(a.theta0);
@@ -262,9 +328,9 @@ __global__ void __launch_bounds__(NT, MINB) patch_kernel(PatchArgs a) {
         // ---- phase 3: Riemann fluxes ----------------------------------------
         for (int f = tid; f < 3 * kNF; f += NT) {
           const int d = f / kNF, fi = f - d * kNF;
-          if (d == 0) fail |= face_flux<0, R>(face, fi, a.riemann, maxit, code);
-          else if (d == 1) fail |= face_flux<1, R>(face, fi, a.riemann, maxit, code);
-          else fail |= face_flux<2, R>(face, fi, a.riemann, maxit, code);
+          if (d == 0) fail |= face_flux<0, P, PAIR>(face, fi, a.riemann, maxit, code);
+          else if (d == 1) fail |= face_flux<1, P, PAIR>(face, fi, a.riemann, maxit, code);
+          else fail |= face_flux<2, P, PAIR>(face, fi, a.riemann, maxit, code);
         }
         fail = __syncthreads_or(fail);
         if (a.flux_only) {
@@ -274,40 +340,55 @@ __global__ void __launch_bounds__(NT, MINB) patch_kernel(PatchArgs a) {
         const bool last = (theta == R(0));
         // ---- phase 4: conservative update ----------------------------------
         att_min = DBL_MAX;
+        att_smax = R(0);
         att_bad = 0;
         if (!fail || last) {
           S* out = static_cast<S*>(a.out) + (size_t)p * 5 * kNC;
           int fail4 = 0;
-          for (int c = tid; c < kNC; c += NT) {
-            const int i = c & 7, j = (c >> 3) & 7, k = c >> 6;
-            const int tc = tile_index(i, j, k);
-            const int fx0 = face_index<0>(i, j, k, i), fx1 = face_index<0>(i, j, k, i + 1);
-            const int fy0 = face_index<1>(i, j, k, j), fy1 = face_index<1>(i, j, k, j + 1);
-            const int fz0 = face_index<2>(i, j, k, k), fz1 = face_index<2>(i, j, k, k + 1);
-            S Un[5];
+          // PAIR: each thread updates cells c0 and c0 + NT (NT = 256) and
+          // converts both in lockstep for the CFL bound
+          constexpr int NPC = PAIR ? 2 : 1;
+          for (int c0 = tid; c0 < kNC; c0 += NT * NPC) {
+            S Un[NPC][5];
+            bool ok[NPC];
 #pragma unroll
-            for (int v = 0; v < 5; ++v) {
-              R div = R(0);
-              div = div + (R(face_slot(face, 0, 0, v)[fx1]) - R(face_slot(face, 0, 0, v)[fx0]));
-              div = div + (R(face_slot(face, 1, 0, v)[fy1]) - R(face_slot(face, 1, 0, v)[fy0]));
-              div = div + (R(face_slot(face, 2, 0, v)[fz1]) - R(face_slot(face, 2, 0, v)[fz0]));
-              Un[v] = S(R(in[v * kGC + tc]) - coef * div);
-              out[v * kNC + c] = Un[v];
+            for (int q = 0; q < NPC; ++q) {
+              const int c = c0 + q * NT;
+              const int i = c & 7, j = (c >> 3) & 7, k = c >> 6;
+              const int tc = tile_index(i, j, k);
+              const int fx0 = face_index<0>(i, j, k, i), fx1 = face_index<0>(i, j, k, i + 1);
+              const int fy0 = face_index<1>(i, j, k, j), fy1 = face_index<1>(i, j, k, j + 1);
+              const int fz0 = face_index<2>(i, j, k, k), fz1 = face_index<2>(i, j, k, k + 1);
+#pragma unroll
+              for (int v = 0; v < 5; ++v) {
+                R div = R(0);
+                div = div + (R(face_slot(face, 0, 0, v)[fx1]) - R(face_slot(face, 0, 0, v)[fx0]));
+                div = div + (R(face_slot(face, 1, 0, v)[fy1]) - R(face_slot(face, 1, 0, v)[fy0]));
+                div = div + (R(face_slot(face, 2, 0, v)[fz1]) - R(face_slot(face, 2, 0, v)[fz0]));
+                Un[q][v] = S(R(in[v * kGC + tc]) - coef * div);
+                out[v * kNC + c] = Un[q][v];
+              }
+              typename P::AT Ac, m2c;
+              ok[q] = A_and_m2<P>(Un[q][0], Un[q][1], Un[q][2], Un[q][3], Un[q][4], Ac, m2c);
+              if (!ok[q]) fail4 = 1;
             }
-            double m2;
-            double A = A_of_cons(Un[0], Un[1], Un[2], Un[3], Un[4], m2);
-            const bool ok = (double(Un[0]) > 0.0) && (A > kEpsUnphysical);
-            if (!ok) fail4 = 1;
             if (a.partial_dt) {
               if (a.cfl_mode == 1) {
                 att_min = fmin(att_min, a.cfl * dh);
-              } else if (ok) {
-                PrimX<R> W;
-                con2pri<R, S>(Un[0], Un[1], Un[2], Un[3], Un[4], W, maxit);
-                double sm = double(smax_of(W, a.ndim));
-                att_min = fmin(att_min, a.cfl * dh / sm);
               } else {
-                att_bad = 1;
+                PrimX<R> W[NPC];
+                if constexpr (PAIR) {
+                  int s0, s1;
+                  con2pri_x2<P>(Un[0], Un[1], W[0], W[1], maxit, s0, s1);
+                } else {
+                  con2pri<P>(Un[0][0], Un[0][1], Un[0][2], Un[0][3], Un[0][4], W[0], maxit);
+                }
+#pragma unroll
+                for (int q = 0; q < NPC; ++q) {
+                  // the largest signal speed of the patch; dt = C dh / S_max once
+                  if (ok[q]) att_smax = fmax(att_smax, smax_of(W[q], a.ndim));
+                  else att_bad = 1;
+                }
               }
             }
           }
@@ -319,6 +400,7 @@ __global__ void __launch_bounds__(NT, MINB) patch_kernel(PatchArgs a) {
         theta = theta * R(a.retry_factor);
         if (theta < R(a.theta_floor * a.theta0)) theta = R(0);
       }
+      if (att_smax > R(0)) att_min = fmin(att_min, a.cfl * dh / double(att_smax));
       dt_min = fmin(dt_min, att_min);
       cfl_bad |= att_bad;
     } else {
@@ -396,15 +478,16 @@ __global__ void prim2con_kernel(const S* prim, S* cons, int64_t n, int64_t strid
   }
 }
 
-template <class S>
-__global__ void con2pri_kernel(const S* cons, S* prim, int64_t n, int64_t stride,
-                               int32_t* status, int maxit) {
+template <class P>
+__global__ void con2pri_kernel(const typename P::S* cons, typename P::S* prim, int64_t n,
+                               int64_t stride, int32_t* status, int maxit) {
+  using S = typename P::S;
   using R = S;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     PrimX<R> W;
-    int st = con2pri<R, S>(cons[i], cons[stride + i], cons[2 * stride + i],
-                           cons[3 * stride + i], cons[4 * stride + i], W, maxit);
+    int st = con2pri<P>(cons[i], cons[stride + i], cons[2 * stride + i], cons[3 * stride + i],
+                        cons[4 * stride + i], W, maxit);
     prim[i] = W.rho;
     prim[stride + i] = W.u[0];
     prim[2 * stride + i] = W.u[1];
@@ -415,10 +498,11 @@ __global__ void con2pri_kernel(const S* cons, S* prim, int64_t n, int64_t stride
 }
 
 // CFL bound over interior patches [np][5][8^3]; per-block partial minima.
-template <class S, int NT>
-__global__ void __launch_bounds__(NT) cfl_kernel(const S* cons, int64_t ncell, double dh,
-                                                 double cfl, int ndim, int mode, int maxit,
-                                                 double* partial, int32_t* bad_out) {
+template <class P, int NT>
+__global__ void __launch_bounds__(NT) cfl_kernel(const typename P::S* cons, int64_t ncell,
+                                                 double dh, double cfl, int ndim, int mode,
+                                                 int maxit, double* partial, int32_t* bad_out) {
+  using S = typename P::S;
   using R = S;
   __shared__ double s_red[NT / 32];
   __shared__ int s_bad[NT / 32];
@@ -429,7 +513,7 @@ __global__ void __launch_bounds__(NT) cfl_kernel(const S* cons, int64_t ncell, d
     const int64_t p = q / kNC, c = q - p * kNC;
     const S* b = cons + p * 5 * kNC + c;
     PrimX<R> W;
-    int st = con2pri<R, S>(b[0], b[kNC], b[2 * kNC], b[3 * kNC], b[4 * kNC], W, maxit);
+    int st = con2pri<P>(b[0], b[kNC], b[2 * kNC], b[3 * kNC], b[4 * kNC], W, maxit);
     if (st == 1) { bad = 1; continue; }
     if (mode == 1) m = fmin(m, cfl * dh);
     else m = fmin(m, cfl * dh / double(smax_of(W, ndim)));
@@ -476,9 +560,9 @@ __global__ void fill_ghosts_kernel(const S* interior, S* ghosted, int npx, int n
   }
 }
 
-// Per-precision launchers (explicitly instantiated in srhd_fp64.cu and
-// srhd_mixed.cu).
-template <class S> struct Launch {
+// Per-precision launchers (explicitly instantiated in srhd_fp64.cu,
+// srhd_mixed.cu and srhd_mixed_cf.cu for the tags of srhd_physics.cuh).
+template <class P> struct Launch {
   static cudaError_t setup();
   static int patch_blocks_per_sm();
   static cudaError_t patches(const PatchArgs& a, int grid, cudaStream_t s);

@@ -3,5 +3,5 @@
 #include "srhd_launch.inl"
 
 namespace srhd {
-template struct Launch<float>;
+template struct Launch<PrecMixed>;
 }

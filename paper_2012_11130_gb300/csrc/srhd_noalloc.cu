@@ -49,10 +49,12 @@ int32_t* g_bad_addr[kMaxDevices] = {};
 
 // One block per patch: the minimum of C dh / S_max over its 512 cells (or
 // C dh in light-speed mode) and a flag for unphysical cells.
-template <class S>
-__global__ void __launch_bounds__(kThreads) patch_cfl_kernel(const S* cons, double dh, double cfl,
-                                                             int ndim, int mode, int maxit,
-                                                             double* patch_dt, int32_t* patch_bad) {
+template <class P>
+__global__ void __launch_bounds__(kThreads) patch_cfl_kernel(const typename P::S* cons, double dh,
+                                                             double cfl, int ndim, int mode,
+                                                             int maxit, double* patch_dt,
+                                                             int32_t* patch_bad) {
+  using S = typename P::S;
   using R = S;
   __shared__ double s_m[kThreads / 32];
   __shared__ int s_b[kThreads / 32];
@@ -61,8 +63,8 @@ __global__ void __launch_bounds__(kThreads) patch_cfl_kernel(const S* cons, doub
   int bad = 0;
   for (int c = threadIdx.x; c < kCells; c += kThreads) {
     srhd::PrimX<R> W;
-    int st = srhd::con2pri<R, S>(base[c], base[kCells + c], base[2 * kCells + c],
-                                 base[3 * kCells + c], base[4 * kCells + c], W, maxit);
+    int st = srhd::con2pri<P>(base[c], base[kCells + c], base[2 * kCells + c],
+                              base[3 * kCells + c], base[4 * kCells + c], W, maxit);
     if (st == 1) { bad = 1; continue; }
     m = (mode == 1) ? fmin(m, cfl * dh) : fmin(m, cfl * dh / double(srhd::smax_of(W, ndim)));
   }
@@ -147,7 +149,8 @@ extern "C" srhd_status srhd_cfl_dt_noalloc(srhd_prec prec, const void* cons, int
                                            void* stream) {
   srhd_params p;
   if (params) p = *params; else srhd_default_params(&p);
-  if (prec != SRHD_FP64 && prec != SRHD_MIXED) return noalloc_fail(SRHD_ERR_ARG, "invalid precision");
+  if (prec != SRHD_FP64 && prec != SRHD_MIXED && prec != SRHD_MIXED_CF)
+    return noalloc_fail(SRHD_ERR_ARG, "invalid precision");
   if (npatch < 0) return noalloc_fail(SRHD_ERR_ARG, "npatch < 0");
   if (npatch > kMaxPatches)
     return noalloc_fail(SRHD_ERR_ARG,
@@ -169,13 +172,17 @@ extern "C" srhd_status srhd_cfl_dt_noalloc(srhd_prec prec, const void* cons, int
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (npatch > 0) {
     if (prec == SRHD_FP64)
-      patch_cfl_kernel<double><<<npatch, kThreads, 0, s>>>(static_cast<const double*>(cons), dh,
-                                                           p.cfl, p.ndim, p.cfl_mode, maxit,
-                                                           patch_dt, patch_bad);
+      patch_cfl_kernel<srhd::PrecFP64><<<npatch, kThreads, 0, s>>>(
+          static_cast<const double*>(cons), dh, p.cfl, p.ndim, p.cfl_mode, maxit, patch_dt,
+          patch_bad);
+    else if (prec == SRHD_MIXED)
+      patch_cfl_kernel<srhd::PrecMixed><<<npatch, kThreads, 0, s>>>(
+          static_cast<const float*>(cons), dh, p.cfl, p.ndim, p.cfl_mode, maxit, patch_dt,
+          patch_bad);
     else
-      patch_cfl_kernel<float><<<npatch, kThreads, 0, s>>>(static_cast<const float*>(cons), dh,
-                                                          p.cfl, p.ndim, p.cfl_mode, maxit,
-                                                          patch_dt, patch_bad);
+      patch_cfl_kernel<srhd::PrecMixedCF><<<npatch, kThreads, 0, s>>>(
+          static_cast<const float*>(cons), dh, p.cfl, p.ndim, p.cfl_mode, maxit, patch_dt,
+          patch_bad);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return noalloc_fail(SRHD_ERR_CUDA, cudaGetErrorString(e));
   }

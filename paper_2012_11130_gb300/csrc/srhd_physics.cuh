@@ -96,6 +96,24 @@ template <class R> __device__ __forceinline__ R newton_guess(R A, R m2) {
   return R(2) * A / (R(1.2) + sqrt(R(1.44) + R(4) * a * A));
 }
 
+// Precision tags. S is the storage and arithmetic type; AT is the type in
+// which A of Eq. (transcendental equation) is formed.
+struct PrecFP64 {     // SRHD_FP64: double everywhere
+  using S = double;
+  using AT = double;
+  static constexpr bool comp_a = false;
+};
+struct PrecMixed {    // SRHD_MIXED: float, A in double
+  using S = float;
+  using AT = double;
+  static constexpr bool comp_a = false;
+};
+struct PrecMixedCF {  // SRHD_MIXED_CF: float, A by a compensated float sum
+  using S = float;
+  using AT = float;
+  static constexpr bool comp_a = true;
+};
+
 // A = (Et/D)^2 + 2 Et/D - (|M|/D)^2 in double (Eq. transcendental equation,
 // left-hand side; Eq. Unphysical result) and m^2 = (|M|/D)^2.
 template <class S>
@@ -107,22 +125,99 @@ __device__ __forceinline__ double A_of_cons(S D, S Mx, S My, S Mz, S Et, double&
   return eD * (eD + 2.0) - m2;
 }
 
+// Error-free transformations in float (Knuth's TwoSum; the FMA form of
+// Dekker's TwoProduct): a*b = p + e and a+b = s + e exactly. The _rn
+// intrinsics keep the compiler from contracting them into other FMAs.
+__device__ __forceinline__ void two_prod(float a, float b, float& p, float& e) {
+  p = __fmul_rn(a, b);
+  e = fmaf(a, b, -p);
+}
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// A and m^2 from float conserved values without double arithmetic.
+// A D^2 = Et^2 + 2 Et D - (Mx^2 + My^2 + Mz^2): every product is split exactly
+// into a float pair and the sum of the ten parts is compensated, so the
+// cancellation between Et^2 + 2 Et D and |M|^2 (the source of the
+// (1 + Mach^2) error factor of Eq. ImprovedRelativeError) acts on a sum that
+// is accurate to about eps_float^2 of its terms instead of eps_float. The
+// inputs are first scaled by the power of two that brings D into [1, 2)
+// (exact), which keeps the products and their error parts clear of the float
+// overflow and underflow (flush-to-zero) ranges.
+__device__ __forceinline__ bool A_comp_float(float D, float Mx, float My, float Mz, float Et,
+                                             float& A, float& m2) {
+  const int ex = (__float_as_int(D) >> 23) & 0xff;
+  if (!(D > 0.0f) || ex > 253) return false;  // non-positive, denormal-flushed, huge or NaN
+  const float sc = __int_as_float((254 - ex) << 23);   // 2^(127 - ex): D * sc in [1, 2)
+  const float d = __fmul_rn(D, sc), e = __fmul_rn(Et, sc);
+  const float mx = __fmul_rn(Mx, sc), my = __fmul_rn(My, sc), mz = __fmul_rn(Mz, sc);
+  float p1, e1, p2, e2, p3, e3, p4, e4, p5, e5;
+  two_prod(e, e, p1, e1);
+  two_prod(e, d, p2, e2);
+  p2 = __fmul_rn(p2, 2.0f);
+  e2 = __fmul_rn(e2, 2.0f);
+  two_prod(mx, mx, p3, e3);
+  two_prod(my, my, p4, e4);
+  two_prod(mz, mz, p5, e5);
+  float sa, ta, sb, tb, t2, ss, ts;
+  two_sum(p1, p2, sa, ta);
+  two_sum(p3, p4, sb, tb);
+  two_sum(sb, p5, sb, t2);
+  tb = __fadd_rn(tb, t2);
+  two_sum(sa, -sb, ss, ts);
+  const float low = __fadd_rn(__fsub_rn(__fadd_rn(e1, e2), __fadd_rn(__fadd_rn(e3, e4), e5)),
+                              __fadd_rn(__fsub_rn(ta, tb), ts));
+  const float ad2 = __fadd_rn(ss, low);
+  // 1/d^2 from the hardware reciprocal refined by one Newton-Raphson step
+  // r <- r + r (1 - d^2 r), so that A and m^2 carry about one rounding each.
+  const float dd = __fmul_rn(d, d);
+  float rd2 = 1.0f / dd;
+  rd2 = fmaf(rd2, fmaf(-dd, rd2, 1.0f), rd2);
+  A = __fmul_rn(ad2, rd2);
+  m2 = __fmul_rn(__fadd_rn(sb, tb), rd2);
+  return true;
+}
+
+// A and m^2 of a conserved state in the precision of P; false when the
+// state fails Eq. (Unphysical result) (A <= eps_machine) or D <= 0.
+template <class P>
+__device__ __forceinline__ bool A_and_m2(typename P::S D, typename P::S Mx, typename P::S My,
+                                         typename P::S Mz, typename P::S Et,
+                                         typename P::AT& A, typename P::AT& m2) {
+  if constexpr (P::comp_a) {
+    if (!A_comp_float(D, Mx, My, Mz, Et, A, m2)) return false;
+    return A > float(kEpsUnphysical);
+  } else {
+    if (!(double(D) > 0.0)) return false;
+    double m2d;
+    double Ad = A_of_cons(D, Mx, My, Mz, Et, m2d);
+    A = Ad;
+    m2 = m2d;
+    return Ad > kEpsUnphysical;
+  }
+}
+
 // Conserved -> primitive (Section 2.3). Returns 0 ok, 1 unphysical, 2 no
 // convergence. Newton-Raphson on f(htilde) = A (monotone f), then
 // Eq. (four-velocity), Eq. (new expression of Lorentz factor), Eq. (density),
 // Eq. (T of h), Eq. (p=rhoT). A step that would make htilde non-positive
 // halves htilde instead. Stops when |dh| <= tol htilde, or when the step no
 // longer contracts at the rounding floor, or after maxit steps (status 2).
-template <class R, class S>
-__device__ __forceinline__ int con2pri(S D, S Mx, S My, S Mz, S Et, PrimX<R>& W, int maxit) {
-  double m2d;
-  double Ad = A_of_cons(D, Mx, My, Mz, Et, m2d);
-  if (!(double(D) > 0.0) || !(Ad > kEpsUnphysical)) {
+template <class P>
+__device__ __forceinline__ int con2pri(typename P::S D, typename P::S Mx, typename P::S My,
+                                       typename P::S Mz, typename P::S Et,
+                                       PrimX<typename P::S>& W, int maxit) {
+  using R = typename P::S;
+  typename P::AT Aa, m2a;
+  if (!A_and_m2<P>(D, Mx, My, Mz, Et, Aa, m2a)) {
     R nan = R(__longlong_as_double(0x7ff8000000000000ULL));
     W.rho = W.u[0] = W.u[1] = W.u[2] = W.p = W.T = W.h = W.gamma = nan;
     return 1;
   }
-  const R A = R(Ad), m2 = R(m2d);
+  const R A = R(Aa), m2 = R(m2a);
   R ht = newton_guess(A, m2);
   int status = 2;
   R prev = R(3.0e38);
@@ -152,6 +247,92 @@ __device__ __forceinline__ int con2pri(S D, S Mx, S My, S Mz, S Et, PrimX<R>& W,
   W.h = h;
   W.p = W.rho * W.T;
   return status;
+}
+
+// Primitives from a converged htilde (Eq. four-velocity, Eq. new expression
+// of Lorentz factor, Eq. density, Eq. T of h, Eq. p=rhoT).
+template <class R, class S>
+__device__ __forceinline__ void prims_from_htilde(S D, S Mx, S My, S Mz, R ht, PrimX<R>& W) {
+  R h = R(1) + ht;
+  R rDh = R(1) / (R(D) * h);
+  W.u[0] = R(Mx) * rDh;
+  W.u[1] = R(My) * rDh;
+  W.u[2] = R(Mz) * rDh;
+  R g2 = R(1) + (W.u[0] * W.u[0] + W.u[1] * W.u[1] + W.u[2] * W.u[2]);
+  R rg = rsqrt_r(g2);
+  W.gamma = g2 * rg;
+  W.rho = R(D) * rg;
+  W.T = T_of_htilde(ht);
+  W.h = h;
+  W.p = W.rho * W.T;
+}
+
+// Two conserved -> primitive conversions advanced in lockstep: the same
+// Newton-Raphson iteration and stopping rule as con2pri, applied to two
+// independent states so that their dependency chains interleave (the
+// single solve is a chain of dependent square roots and divisions). The loop
+// runs until both have stopped; a state that has stopped is not updated.
+template <class P>
+__device__ __forceinline__ void con2pri_x2(const typename P::S (&Ua)[5],
+                                           const typename P::S (&Ub)[5],
+                                           PrimX<typename P::S>& Wa, PrimX<typename P::S>& Wb,
+                                           int maxit, int& sta, int& stb) {
+  using R = typename P::S;
+  typename P::AT Aa_, ma_, Ab_, mb_;
+  const bool pa = A_and_m2<P>(Ua[0], Ua[1], Ua[2], Ua[3], Ua[4], Aa_, ma_);
+  const bool pb = A_and_m2<P>(Ub[0], Ub[1], Ub[2], Ub[3], Ub[4], Ab_, mb_);
+  // an unphysical state iterates on a harmless stand-in and is discarded
+  const R Aa = pa ? R(Aa_) : R(1), m2a = pa ? R(ma_) : R(0);
+  const R Ab = pb ? R(Ab_) : R(1), m2b = pb ? R(mb_) : R(0);
+  R ha = newton_guess(Aa, m2a), hb = newton_guess(Ab, m2b);
+  bool da = false, db = false;
+  sta = 2;
+  stb = 2;
+  R preva = R(3.0e38), prevb = R(3.0e38);
+  for (int k = 1; k <= maxit && !(da && db); ++k) {
+    R Ta, dTa, fa, dfa, Tb, dTb, fb, dfb;
+    T_dT_of_htilde(ha, Ta, dTa);
+    T_dT_of_htilde(hb, Tb, dTb);
+    f_df(ha, Ta, dTa, m2a, fa, dfa);
+    f_df(hb, Tb, dTb, m2b, fb, dfb);
+    R dha = (fa - Aa) / dfa;
+    R dhb = (fb - Ab) / dfb;
+    if (!da) {
+      R hn = ha - dha;
+      if (!(hn > R(0))) hn = R(0.5) * ha;
+      R adh = fabs(dha);
+      ha = hn;
+      if (adh <= NewtonCfg<R>::tol * ha ||
+          (k >= 3 && adh >= preva && adh <= NewtonCfg<R>::floor * ha)) {
+        da = true;
+        sta = 0;
+      }
+      preva = adh;
+    }
+    if (!db) {
+      R hn = hb - dhb;
+      if (!(hn > R(0))) hn = R(0.5) * hb;
+      R adh = fabs(dhb);
+      hb = hn;
+      if (adh <= NewtonCfg<R>::tol * hb ||
+          (k >= 3 && adh >= prevb && adh <= NewtonCfg<R>::floor * hb)) {
+        db = true;
+        stb = 0;
+      }
+      prevb = adh;
+    }
+  }
+  prims_from_htilde(Ua[0], Ua[1], Ua[2], Ua[3], ha, Wa);
+  prims_from_htilde(Ub[0], Ub[1], Ub[2], Ub[3], hb, Wb);
+  const R nan = R(__longlong_as_double(0x7ff8000000000000ULL));
+  if (!pa) {
+    Wa.rho = Wa.u[0] = Wa.u[1] = Wa.u[2] = Wa.p = Wa.T = Wa.h = Wa.gamma = nan;
+    sta = 1;
+  }
+  if (!pb) {
+    Wb.rho = Wb.u[0] = Wb.u[1] = Wb.u[2] = Wb.p = Wb.T = Wb.h = Wb.gamma = nan;
+    stb = 1;
+  }
 }
 
 // Primitive -> conserved (Eq. density, momentum, T_to_HTilde, E_D).

@@ -4,6 +4,9 @@ runs in the library's CUDA kernels).
 
 Precision follows the tensor dtype: float64 -> SRHD_FP64, float32 ->
 SRHD_MIXED (float storage; A of Eq. transcendental equation in double).
+Every call also takes ``prec="mixed_cf"`` (float tensors) to select
+SRHD_MIXED_CF, where A is formed by compensated float arithmetic and no
+double arithmetic runs at all.
 Layouts are those of include/srhd.h: SoA [5][n] for cell batches,
 [npatch][5][12][12][12] ghosted patches, [npatch][5][8][8][8] interiors.
 
@@ -44,7 +47,16 @@ class Params:
                         self.ndim, self.newton_max_iter)
 
 
-def _prec(t: torch.Tensor) -> int:
+_PREC = {"fp64": (N.SRHD_FP64, torch.float64), "mixed": (N.SRHD_MIXED, torch.float32),
+         "mixed_cf": (N.SRHD_MIXED_CF, torch.float32)}
+
+
+def _prec(t: torch.Tensor, prec: str | None = None) -> int:
+    if prec is not None:
+        code, dt = _PREC[prec]
+        if t.dtype != dt:
+            raise TypeError(f"precision {prec!r} needs {dt} tensors, got {t.dtype}")
+        return code
     if t.dtype == torch.float64:
         return N.SRHD_FP64
     if t.dtype == torch.float32:
@@ -95,17 +107,17 @@ class Context:
             pass
 
     # ---- Section 2.3 ---------------------------------------------------------
-    def prim2con(self, prim, cons=None, stream=None):
+    def prim2con(self, prim, cons=None, stream=None, prec=None):
         _need_cuda(prim, "prim")
         n = prim.shape[-1]
         if cons is None:
             cons = torch.empty_like(prim)
         _need_cuda(cons, "cons", prim.dtype)
-        N.check(self._L.srhd_prim2con(self._h, _prec(prim), _ptr(prim), _ptr(cons), n, n,
+        N.check(self._L.srhd_prim2con(self._h, _prec(prim, prec), _ptr(prim), _ptr(cons), n, n,
                                       _stream(stream)), "srhd_prim2con")
         return cons
 
-    def con2pri(self, cons, prim=None, cell_status=None, stream=None):
+    def con2pri(self, cons, prim=None, cell_status=None, stream=None, prec=None):
         host = not cons.is_cuda
         if host:
             dev = torch.device("cuda", self.device)
@@ -121,7 +133,7 @@ class Context:
             st_d = torch.empty(n, dtype=torch.int32, device=cons_d.device)
         if st_d is not None:
             _need_cuda(st_d, "cell_status", torch.int32)
-        N.check(self._L.srhd_con2pri(self._h, _prec(cons_d), _ptr(cons_d), _ptr(prim_d), n, n,
+        N.check(self._L.srhd_con2pri(self._h, _prec(cons_d, prec), _ptr(cons_d), _ptr(prim_d), n, n,
                                      _ptr(st_d), _stream(stream)), "srhd_con2pri")
         if host:
             out = prim if prim is not None else torch.empty(prim_d.shape, dtype=prim_d.dtype,
@@ -134,7 +146,8 @@ class Context:
         return prim_d
 
     # ---- Section 3.1-3.3 -----------------------------------------------------
-    def flux_patches(self, cons_ghosted, dt_dh, face_flux=None, patch_status=None, stream=None):
+    def flux_patches(self, cons_ghosted, dt_dh, face_flux=None, patch_status=None, stream=None,
+                     prec=None):
         _need_cuda(cons_ghosted, "cons_ghosted")
         npatch = cons_ghosted.shape[0]
         if face_flux is None:
@@ -144,18 +157,20 @@ class Context:
         _need_cuda(dt_dh, "dt_dh", torch.float64)
         if patch_status is not None:
             _need_cuda(patch_status, "patch_status", torch.int32)
-        N.check(self._L.srhd_flux_patches(self._h, _prec(cons_ghosted), _ptr(cons_ghosted),
+        N.check(self._L.srhd_flux_patches(self._h, _prec(cons_ghosted, prec), _ptr(cons_ghosted),
                                           _ptr(face_flux), npatch, _ptr(dt_dh), _ptr(patch_status),
                                           _stream(stream)), "srhd_flux_patches")
         return face_flux
 
     def advance_patches(self, cons_ghosted, dt_dh, cons_out=None, patch_face_flux=None,
-                        worklist=None, dt_next=None, patch_status=None, npatch=None, stream=None):
+                        worklist=None, dt_next=None, patch_status=None, npatch=None, stream=None,
+                        prec=None):
         """One step of a batch of ghosted patches. Device tensors in, device
         tensors out; with a CPU ``cons_ghosted`` the call copies it in, runs
         and copies ``cons_out`` (and ``dt_next`` if given) back to the host."""
         if not cons_ghosted.is_cuda:
-            return self._advance_host(cons_ghosted, dt_dh, cons_out, dt_next, patch_status, stream)
+            return self._advance_host(cons_ghosted, dt_dh, cons_out, dt_next, patch_status, stream,
+                                      prec)
         _need_cuda(cons_ghosted, "cons_ghosted")
         if npatch is None:
             npatch = worklist.numel() if worklist is not None else cons_ghosted.shape[0]
@@ -170,12 +185,12 @@ class Context:
             if t is not None:
                 _need_cuda(t, name, dt)
         N.check(self._L.srhd_advance_patches(
-            self._h, _prec(cons_ghosted), _ptr(cons_ghosted), _ptr(cons_out),
+            self._h, _prec(cons_ghosted, prec), _ptr(cons_ghosted), _ptr(cons_out),
             _ptr(patch_face_flux), npatch, _ptr(dt_dh), _ptr(worklist), _ptr(dt_next),
             _ptr(patch_status), _stream(stream)), "srhd_advance_patches")
         return cons_out
 
-    def _advance_host(self, cons_ghosted, dt_dh, cons_out, dt_next, patch_status, stream):
+    def _advance_host(self, cons_ghosted, dt_dh, cons_out, dt_next, patch_status, stream, prec):
         dev = torch.device("cuda", self.device)
         g = cons_ghosted.to(dev, non_blocking=True)
         dd = dt_dh.to(dev, non_blocking=True)
@@ -184,7 +199,7 @@ class Context:
         st_d = torch.empty(g.shape[0], dtype=torch.int32, device=dev) \
             if patch_status is not None else None
         self.advance_patches(g, dd, cons_out=out_d, dt_next=dn_d, patch_status=st_d,
-                             stream=stream)
+                             stream=stream, prec=prec)
         if cons_out is None:
             cons_out = torch.empty(out_d.shape, dtype=out_d.dtype, pin_memory=True)
         cons_out.copy_(out_d, non_blocking=True)
@@ -195,12 +210,12 @@ class Context:
         (stream or torch.cuda.current_stream()).synchronize()
         return cons_out
 
-    def cfl_dt(self, cons, dh, dt_out=None, stream=None):
+    def cfl_dt(self, cons, dh, dt_out=None, stream=None, prec=None):
         _need_cuda(cons, "cons")
         if dt_out is None:
             dt_out = torch.empty(1, dtype=torch.float64, device=cons.device)
         _need_cuda(dt_out, "dt_out", torch.float64)
-        N.check(self._L.srhd_cfl_dt(self._h, _prec(cons), _ptr(cons), cons.shape[0], float(dh),
+        N.check(self._L.srhd_cfl_dt(self._h, _prec(cons, prec), _ptr(cons), cons.shape[0], float(dh),
                                     _ptr(dt_out), _stream(stream)), "srhd_cfl_dt")
         return dt_out
 
@@ -230,24 +245,25 @@ def default_context(params: Params | None = None) -> Context:
     return _default[key]
 
 
-def prim2con(prim, cons=None, stream=None):
-    return default_context().prim2con(prim, cons, stream)
+def prim2con(prim, cons=None, stream=None, prec=None):
+    return default_context().prim2con(prim, cons, stream, prec)
 
 
-def con2pri(cons, prim=None, cell_status=None, stream=None):
-    return default_context().con2pri(cons, prim, cell_status, stream)
+def con2pri(cons, prim=None, cell_status=None, stream=None, prec=None):
+    return default_context().con2pri(cons, prim, cell_status, stream, prec)
 
 
-def flux_patches(cons_ghosted, dt_dh, face_flux=None, patch_status=None, stream=None):
-    return default_context().flux_patches(cons_ghosted, dt_dh, face_flux, patch_status, stream)
+def flux_patches(cons_ghosted, dt_dh, face_flux=None, patch_status=None, stream=None, prec=None):
+    return default_context().flux_patches(cons_ghosted, dt_dh, face_flux, patch_status, stream,
+                                          prec)
 
 
 def advance_patches(cons_ghosted, dt_dh, **kw):
     return default_context().advance_patches(cons_ghosted, dt_dh, **kw)
 
 
-def cfl_dt(cons, dh, dt_out=None, stream=None):
-    return default_context().cfl_dt(cons, dh, dt_out, stream)
+def cfl_dt(cons, dh, dt_out=None, stream=None, prec=None):
+    return default_context().cfl_dt(cons, dh, dt_out, stream, prec)
 
 
 def fill_ghosts_uniform(interior, npx, npy, npz, bc=("periodic",) * 3, ghosted=None, stream=None):

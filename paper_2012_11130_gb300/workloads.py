@@ -170,3 +170,75 @@ def ghosted_patches(field: np.ndarray, bc=("periodic", "periodic", "periodic")) 
                                 ix * PATCH:ix * PATCH + GP]
                 q += 1
     return out
+
+
+# ---- batched AMR: off-centre relativistic blast wave ---------------------
+def blast_prims_at(x, y, z, center=(0.6, 0.5, 0.5), r_shell=0.18, shell=0.01, width=0.002,
+                   rho_in=0.05, rho_shell=8.0, rho_amb=1.0, p_in=10.0, p_amb=1e-6,
+                   U_shell=4.0, xp=np):
+    """Primitive state of a synthetic evolved blast wave (a hot rarefied
+    interior, a dense shell moving outward with four-velocity ~U_shell, cold
+    ambient gas at rest; tanh transitions of the given width) at points
+    (x, y, z); returns [5][...]. xp is the array module (numpy or torch)."""
+    def step(zz):
+        return 0.5 * (1.0 + xp.tanh(zz / width))
+    dx, dy, dz = x - center[0], y - center[1], z - center[2]
+    r = xp.sqrt(dx * dx + dy * dy + dz * dz) + 1e-300
+    s_in = step(r - (r_shell - shell))
+    s_out = step(r - r_shell)
+    rho = rho_in + (rho_shell - rho_in) * s_in + (rho_amb - rho_shell) * s_out
+    p = p_in * (1.0 - s_out) + p_amb * s_out
+    Ur = U_shell * xp.clamp(r / r_shell, max=1.0) if xp is not np else \
+        U_shell * np.minimum(r / r_shell, 1.0)
+    Ur = Ur * (1.0 - s_out)
+    return xp.stack([rho, Ur * dx / r, Ur * dy / r, Ur * dz / r, p])
+
+
+def amr_blast_hierarchy(base: int = 64, levels: int = 5, center=(0.6, 0.5, 0.5),
+                        r_shell: float = 0.18, widths=(0.06, 0.03, 0.012, 0.004)):
+    """Octree of 8^3 patches on [0, 1]^3 (level l has cell size 1/(base 2^l)).
+    Level 0 holds all (base/8)^3 patches; a level-l patch is refined into its
+    8 children on level l+1 when its box comes within widths[l] of the shell
+    |x - center| = r_shell (the region where the gradient criterion fires on
+    the blast profile). Returns a list of (n_l, 3) int arrays (ix, iy, iz)."""
+    c = np.asarray(center)
+    n0 = base // PATCH
+    g = np.stack(np.meshgrid(np.arange(n0), np.arange(n0), np.arange(n0), indexing="ij"), -1)
+    lev = [g.reshape(-1, 3)[:, ::-1].copy()]  # (ix, iy, iz) with x fastest in the ordering
+    lev[0] = lev[0][np.lexsort((lev[0][:, 0], lev[0][:, 1], lev[0][:, 2]))]
+    for l in range(levels - 1):
+        size = PATCH / (base * 2 ** l)
+        lo = lev[l] * size
+        hi = lo + size
+        near = np.clip(c, lo, hi)
+        dmin = np.linalg.norm(near - c, axis=1)
+        far = np.where(np.abs(lo - c) > np.abs(hi - c), lo, hi)
+        dmax = np.linalg.norm(far - c, axis=1)
+        flag = (dmin <= r_shell + widths[l]) & (dmax >= r_shell - widths[l])
+        parents = lev[l][flag]
+        kids = (parents[:, None, :] * 2 + np.array([[i, j, k] for k in (0, 1) for j in (0, 1)
+                                                     for i in (0, 1)])[None]).reshape(-1, 3)
+        kids = kids[np.lexsort((kids[:, 0], kids[:, 1], kids[:, 2]))]
+        lev.append(kids)
+    return lev
+
+
+def amr_patch_prims(coords, level: int, base: int = 64, xp=np, device=None, **blast):
+    """[n][5][12][12][12] primitive values of the blast profile on the ghosted
+    patches (ix, iy, iz) of one level; ghost cells take the analytic profile
+    at the level's cell size. With xp=torch the values are made on `device`."""
+    dh = 1.0 / (base * 2 ** level)
+    if xp is np:
+        c = np.asarray(coords, dtype=np.float64)
+        g = np.arange(GP, dtype=np.float64) - GHOST + 0.5
+    else:
+        c = xp.as_tensor(np.asarray(coords), dtype=xp.float64, device=device)
+        g = xp.arange(GP, dtype=xp.float64, device=device) - GHOST + 0.5
+    x = (c[:, 0:1] * PATCH + g[None, :]) * dh    # [n][12]
+    y = (c[:, 1:2] * PATCH + g[None, :]) * dh
+    z = (c[:, 2:3] * PATCH + g[None, :]) * dh
+    X = x[:, None, None, :]
+    Y = y[:, None, :, None]
+    Z = z[:, :, None, None]
+    W = blast_prims_at(X + 0 * Y + 0 * Z, Y + 0 * X + 0 * Z, Z + 0 * X + 0 * Y, xp=xp, **blast)
+    return W.transpose(0, 1) if xp is not np else W.transpose(1, 0, 2, 3, 4)

@@ -4,7 +4,8 @@ between numpy and torch, and the tolerance rules.
 Tolerance rule (both precisions): a conversion of a cell whose conditioning
 kappa = 1 + Mach^2 (Eq. ImprovedRelativeError) is large loses log10(kappa)
 digits in any correct implementation, so per-cell relative differences are
-allowed up to max(base, 10 kappa eps64), with base = 1e-12 for the FP64 path
+allowed up to max(base, 10 kappa eps_A), eps_A the precision of A (eps64, or
+about 2^-44 for the compensated float A of mixed_cf), with base = 1e-12 for the FP64 path
 and 1e-5 for the mixed path (float storage and arithmetic with the hardware
 approximate division and square root, A in double; the observed tail of a
 2^18-cell stress batch is 8e-6, i.e. about 64 float ulps).
@@ -15,6 +16,15 @@ import pytest
 EPS64 = np.finfo(np.float64).eps
 BASE_FP64 = 1e-12
 BASE_MIXED = 1e-5
+# Relative precision of A in each path: double, double, and the compensated
+# float sum of the mixed_cf path (about 4 eps_float^2 of the cancelling terms).
+EPS_A = {"fp64": EPS64, "mixed": EPS64, "mixed_cf": 4 * 2.0 ** -46}
+BASE = {"fp64": BASE_FP64, "mixed": BASE_MIXED, "mixed_cf": BASE_MIXED}
+PRECS = ("fp64", "mixed", "mixed_cf")
+
+
+def torch_dtype(torch, prec):
+    return torch.float64 if prec == "fp64" else torch.float32
 
 
 def require_gpu():

@@ -4,8 +4,8 @@ gamma 1..1e6, random direction), through the C ABI."""
 import numpy as np
 import pytest
 
-from gpu_common import (BASE_FP64, BASE_MIXED, EPS64, kappa_of_prims, prim_rel_err,
-                        require_gpu, to_dev, to_np)
+from gpu_common import (BASE, EPS64, EPS_A, PRECS, kappa_of_prims, prim_rel_err, require_gpu,
+                        to_dev, to_np, torch_dtype)
 from paper_2012_11130_gb300 import workloads
 
 pytestmark = pytest.mark.gpu
@@ -15,20 +15,20 @@ def _inputs(oracle, n, seed, prec):
     W = workloads.stress_batch_prims(n, seed=seed)
     C, st = oracle.prim2con(W)
     assert np.all(st == 0)
-    if prec == "mixed":
+    if prec != "fp64":
         C = C.astype(np.float32).astype(np.float64)
     return W, C
 
 
-@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("prec", PRECS)
 @pytest.mark.parametrize("n", [1, 997, 3 * 65536 + 37])
 def test_con2pri_parity(oracle, prec, n):
     torch, srhd = require_gpu()
-    dtype = torch.float64 if prec == "fp64" else torch.float32
+    dtype = torch_dtype(torch, prec)
     W, C = _inputs(oracle, n, 1000 + n, prec)
     ref = oracle.con2pri(C)
     st = torch.full((n,), -7, dtype=torch.int32, device="cuda")
-    P = srhd.con2pri(to_dev(torch, C, dtype), cell_status=st)
+    P = srhd.con2pri(to_dev(torch, C, dtype), cell_status=st, prec=prec)
     torch.cuda.synchronize()
     Pg, stg = to_np(P), st.cpu().numpy()
     assert set(np.unique(stg)) <= {0, 1}
@@ -38,12 +38,11 @@ def test_con2pri_parity(oracle, prec, n):
     with np.errstate(invalid="ignore"):
         kappa = np.where(ref["status"] == 0, kappa_of_prims(oracle, np.nan_to_num(ref["prim"], nan=1.0)),
                          np.inf)
-    clear = kappa * EPS64 <= 1e-3
+    clear = kappa * EPS_A[prec] <= 1e-3
     # well-conditioned cells: same status, values within the tolerance
     assert np.array_equal(stg[clear], ref["status"][clear])
     ok = clear & (ref["status"] == 0)
-    base = BASE_FP64 if prec == "fp64" else BASE_MIXED
-    tol = np.maximum(base, 10 * kappa * EPS64)
+    tol = np.maximum(BASE[prec], 10 * kappa * EPS_A[prec])
     err = prim_rel_err(Pg, ref["prim"])
     bad = ok & ~(err <= tol)
     assert not bad.any(), (np.nonzero(bad)[0][:5], err[bad][:5], tol[bad][:5])
@@ -80,9 +79,9 @@ def test_conversion_edge_cases(oracle):
                   [0.0, 0.0, 0.0, 0.0],
                   [0.0, 0.0, 0.0, 0.0],
                   [1.0, 1.0, -1.0, 0.0]])
-    for dtype in (torch.float64, torch.float32):
+    for prec in PRECS:
         st = torch.empty(4, dtype=torch.int32, device="cuda")
-        P = ctx.con2pri(to_dev(torch, C, dtype), cell_status=st)
+        P = ctx.con2pri(to_dev(torch, C, torch_dtype(torch, prec)), cell_status=st, prec=prec)
         assert st.cpu().tolist() == [1, 1, 1, 1]
         assert torch.isnan(P).all()
     ref = oracle.con2pri(C)

@@ -5,15 +5,15 @@ limiter retry, edge cases."""
 import numpy as np
 import pytest
 
-from gpu_common import (BASE_FP64, BASE_MIXED, cons_rel_err, flux_rel_err, require_gpu, to_dev,
-                        to_np)
+from gpu_common import (BASE_FP64, PRECS, cons_rel_err, flux_rel_err, require_gpu, to_dev, to_np,
+                        torch_dtype)
 from paper_2012_11130_gb300 import workloads
 
 pytestmark = pytest.mark.gpu
 
 # Smooth patches: tolerances after one step (FP64 1e-12; mixed 1e-5, the
 # target for smooth flows).
-TOL = {"fp64": BASE_FP64, "mixed": 1e-5}
+TOL = {"fp64": BASE_FP64, "mixed": 1e-5, "mixed_cf": 1e-5}
 
 
 def _cons_patches(oracle, Wp, prec):
@@ -21,13 +21,13 @@ def _cons_patches(oracle, Wp, prec):
     C, st = oracle.prim2con(Wp.transpose(1, 0, 2, 3, 4).reshape(5, -1))
     assert np.all(st == 0)
     C = C.reshape(5, npatch, 12, 12, 12).transpose(1, 0, 2, 3, 4).copy()
-    if prec == "mixed":
+    if prec != "fp64":
         C = C.astype(np.float32).astype(np.float64)
     return C
 
 
 def _dtype(torch, prec):
-    return torch.float64 if prec == "fp64" else torch.float32
+    return torch_dtype(torch, prec)
 
 
 @pytest.fixture(scope="module")
@@ -42,6 +42,7 @@ def smooth_case(oracle):
         C = _cons_patches(oracle, Wp, prec)
         ref = oracle.advance_patches(C, dt_dh, want_flux=True)
         out[prec] = (C, ref)
+    out["mixed_cf"] = out["mixed"]  # same float inputs
     return dt_dh, out
 
 
@@ -62,7 +63,7 @@ def _ref_patch_faces(flux):
     return out
 
 
-@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("prec", PRECS)
 def test_advance_smooth_parity(oracle, smooth_case, prec):
     torch, srhd = require_gpu()
     dt_dh, cases = smooth_case
@@ -74,7 +75,7 @@ def test_advance_smooth_parity(oracle, smooth_case, prec):
     pf = torch.empty((npatch, 6, 5, 64), dtype=dtype, device="cuda")
     dn = torch.empty(1, dtype=torch.float64, device="cuda")
     out = ctx.advance_patches(to_dev(torch, C, dtype), to_dev(torch, dt_dh, torch.float64),
-                              patch_face_flux=pf, dt_next=dn, patch_status=st)
+                              patch_face_flux=pf, dt_next=dn, patch_status=st, prec=prec)
     torch.cuda.synchronize()
     assert np.all(ref["status"] == 0) and np.all(ref["retries"] == 0)
     assert np.all(st.cpu().numpy() == 0)
@@ -89,7 +90,7 @@ def test_advance_smooth_parity(oracle, smooth_case, prec):
     assert abs(dn.item() / min(dts) - 1) <= 10 * TOL[prec]
 
 
-@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("prec", PRECS)
 def test_flux_patches_parity(oracle, smooth_case, prec):
     torch, srhd = require_gpu()
     dt_dh, cases = smooth_case
@@ -98,7 +99,7 @@ def test_flux_patches_parity(oracle, smooth_case, prec):
     dtype = _dtype(torch, prec)
     st = torch.full((npatch,), -1, dtype=torch.int32, device="cuda")
     F = srhd.flux_patches(to_dev(torch, C, dtype), to_dev(torch, dt_dh, torch.float64),
-                          patch_status=st)
+                          patch_status=st, prec=prec)
     torch.cuda.synchronize()
     assert np.all(st.cpu().numpy() == 0)
     Fg = to_np(F).transpose(2, 0, 1, 3)          # [5][np][3][576]
@@ -131,7 +132,7 @@ def test_worklist_subset(oracle, smooth_case):
     assert np.all(stn[mask] == 0) and np.all(stn[~mask] == -1)
 
 
-@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("prec", PRECS)
 def test_rough_patches_retry_parity(oracle, prec):
     # Section 3.3 (1): rough patches are recomputed with the limiter
     # coefficient reduced by 0.75 per retry. In FP64 the GPU takes the same
@@ -150,7 +151,7 @@ def test_rough_patches_retry_parity(oracle, prec):
     dtype = _dtype(torch, prec)
     st = torch.full((npatch,), -1, dtype=torch.int32, device="cuda")
     out = srhd.advance_patches(to_dev(torch, C, dtype), to_dev(torch, dt_dh, torch.float64),
-                               patch_status=st)
+                               patch_status=st, prec=prec)
     torch.cuda.synchronize()
     stn = st.cpu().numpy()
     code, retries = stn >> 8, stn & 255
@@ -193,12 +194,13 @@ def test_bad_input_and_unused_corner(oracle):
 
 def test_uniform_state_is_fixed_point():
     torch, srhd = require_gpu()
-    for dtype in (torch.float64, torch.float32):
+    for prec in PRECS:
+        dtype = torch_dtype(torch, prec)
         W = torch.tensor([[2e-3], [30.0], [-4.0], [0.5], [7e-5]], dtype=dtype, device="cuda")
         U = srhd.prim2con(W)
         G = U.reshape(1, 5, 1, 1, 1).expand(4, 5, 12, 12, 12).contiguous()
         dd = torch.tensor([[1e-3, 1e-2]] * 4, dtype=torch.float64, device="cuda")
-        out = srhd.advance_patches(G, dd)
+        out = srhd.advance_patches(G, dd, prec=prec)
         assert torch.equal(out, G[:, :, 2:10, 2:10, 2:10])
 
 
@@ -214,7 +216,7 @@ def test_empty_batch():
     assert dt.item() == float("inf")
 
 
-@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("prec", PRECS)
 def test_cfl_dt_parity(oracle, prec):
     torch, srhd = require_gpu()
     npatch = 77
@@ -223,20 +225,20 @@ def test_cfl_dt_parity(oracle, prec):
     W = workloads.stress_batch_prims(npatch * 512, seed=9, lg_gamma_range=(0, 1.5),
                                      T_range=(-4, 3))
     C, _ = oracle.prim2con(W)
-    if prec == "mixed":
+    if prec != "fp64":
         C = C.astype(np.float32).astype(np.float64)
     Cp = C.reshape(5, npatch, 512).transpose(1, 0, 2).copy()
-    dt = srhd.cfl_dt(to_dev(torch, Cp, dtype), 0.01).item()
+    dt = srhd.cfl_dt(to_dev(torch, Cp, dtype), 0.01, prec=prec).item()
     ref = oracle.cfl_dt(C, 0.01)
     assert np.isfinite(ref) and abs(dt / ref - 1) <= (1e-12 if prec == "fp64" else 1e-5)
     # light-speed mode
     ctx = srhd.Context(srhd.Params(cfl_mode="light"))
-    assert ctx.cfl_dt(to_dev(torch, Cp, dtype), 0.01).item() == 0.5 * 0.01
+    assert ctx.cfl_dt(to_dev(torch, Cp, dtype), 0.01, prec=prec).item() == 0.5 * 0.01
     # a batch with an unphysical cell gives NaN on both sides
     C2 = C.copy()
     C2[4, 1234] = -1.0
     Cp2 = C2.reshape(5, npatch, 512).transpose(1, 0, 2).copy()
-    assert np.isnan(srhd.cfl_dt(to_dev(torch, Cp2, dtype), 0.01).item())
+    assert np.isnan(srhd.cfl_dt(to_dev(torch, Cp2, dtype), 0.01, prec=prec).item())
     assert np.isnan(oracle.cfl_dt(C2, 0.01))
 
 

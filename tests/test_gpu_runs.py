@@ -5,23 +5,23 @@ full-size 256^3 step in the launch configuration the benchmark times."""
 import numpy as np
 import pytest
 
-from gpu_common import cons_rel_err, require_gpu, to_dev, to_np
+from gpu_common import PRECS, cons_rel_err, require_gpu, to_dev, to_np, torch_dtype
 from paper_2012_11130_gb300 import workloads
 
 pytestmark = pytest.mark.gpu
 
 
-def _gpu_evolve(torch, srhd, ctx, C_patches, npx, npy, npz, bc, dh, t_end, dtype,
+def _gpu_evolve(torch, srhd, ctx, C_patches, npx, npy, npz, bc, dh, t_end, prec,
                 fixed_dt=None, max_steps=100000):
     """Ghost fill + fused step with the fused CFL, until t_end."""
-    U = to_dev(torch, C_patches, dtype)
+    U = to_dev(torch, C_patches, torch_dtype(torch, prec))
     npatch = U.shape[0]
     dd = torch.empty((npatch, 2), dtype=torch.float64, device="cuda")
     dn = torch.empty(1, dtype=torch.float64, device="cuda")
     st = torch.empty(npatch, dtype=torch.int32, device="cuda")
     out = torch.empty_like(U)
     if fixed_dt is None:
-        dt = ctx.cfl_dt(U, dh).item()
+        dt = ctx.cfl_dt(U, dh, prec=prec).item()
     t, steps, retries = 0.0, 0, 0
     while t < t_end and steps < max_steps:
         if fixed_dt is not None:
@@ -31,7 +31,7 @@ def _gpu_evolve(torch, srhd, ctx, C_patches, npx, npy, npz, bc, dh, t_end, dtype
         dd[:, 0] = dt
         dd[:, 1] = dh
         G = ctx.fill_ghosts_uniform(U, npx, npy, npz, bc=bc)
-        ctx.advance_patches(G, dd, cons_out=out, dt_next=dn, patch_status=st)
+        ctx.advance_patches(G, dd, cons_out=out, dt_next=dn, patch_status=st, prec=prec)
         U, out = out, U
         s = st.cpu().numpy()
         assert np.all((s >> 8) == 0), s[s != 0][:5]
@@ -42,7 +42,7 @@ def _gpu_evolve(torch, srhd, ctx, C_patches, npx, npy, npz, bc, dh, t_end, dtype
     return U, steps, retries
 
 
-@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("prec", PRECS)
 def test_shock_tube_vs_exact_and_oracle(oracle, prec):
     # 1024 cells, (1, 0, 1e3) | (1, 0, 1e-2), t = 0.4, CFL 0.5 with the 1-D
     # signal-speed bound, outflow; the patch grid is 128 x 1 x 1 with
@@ -51,13 +51,12 @@ def test_shock_tube_vs_exact_and_oracle(oracle, prec):
     N = 1024
     W, x = workloads.shock_tube_prims(N)
     C, _ = oracle.prim2con(W)
-    if prec == "mixed":
+    if prec != "fp64":
         C = C.astype(np.float32).astype(np.float64)
     F = np.broadcast_to(C.reshape(5, 1, 1, N), (5, 8, 8, N)).copy()
     ctx = srhd.Context(srhd.Params(ndim=1))
-    dtype = torch.float64 if prec == "fp64" else torch.float32
     U, steps, retries = _gpu_evolve(torch, srhd, ctx, workloads.patchify(F), N // 8, 1, 1,
-                                    ("outflow", "periodic", "periodic"), 1.0 / N, 0.4, dtype)
+                                    ("outflow", "periodic", "periodic"), 1.0 / N, 0.4, prec)
     G = workloads.unpatchify(to_np(U), N // 8, 1, 1)
     # y/z-uniform: every row equals the first
     assert np.array_equal(G, np.broadcast_to(G[:, :1, :1, :], G.shape))
@@ -74,22 +73,21 @@ def test_shock_tube_vs_exact_and_oracle(oracle, prec):
         assert np.max(np.abs(Pg[0] / Pr[0] - 1)) < 1e-6
 
 
-@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("prec", PRECS)
 def test_advection_steps_parity_and_conservation(oracle, prec):
     torch, srhd = require_gpu()
     N = 32
     Wf = workloads.advection_prims(N)
     C, _ = oracle.prim2con(Wf.reshape(5, -1))
-    if prec == "mixed":
+    if prec != "fp64":
         C = C.astype(np.float32).astype(np.float64)
     C = C.reshape(5, N, N, N)
     dh = 1.0 / N
     dt = 0.45 * dh
     nsteps = 8
     ctx = srhd.Context(srhd.Params())
-    dtype = torch.float64 if prec == "fp64" else torch.float32
     U, steps, _ = _gpu_evolve(torch, srhd, ctx, workloads.patchify(C), 4, 4, 4, ("periodic",) * 3,
-                              dh, nsteps * dt * (1 - 1e-12), dtype, fixed_dt=dt)
+                              dh, nsteps * dt * (1 - 1e-12), prec, fixed_dt=dt)
     assert steps == nsteps
     G = workloads.unpatchify(to_np(U), 4, 4, 4)
     R = C.copy()
@@ -113,8 +111,7 @@ def test_advection_convergence_mixed_vs_fp64(oracle):
     # the mixed L1 equals the FP64 L1 to two digits.
     torch, srhd = require_gpu()
     l1 = {}
-    for prec in ("fp64", "mixed"):
-        dtype = torch.float64 if prec == "fp64" else torch.float32
+    for prec in PRECS:
         for N in (16, 32):
             Wf = workloads.advection_prims(N)
             C, _ = oracle.prim2con(Wf.reshape(5, -1))
@@ -123,17 +120,18 @@ def test_advection_convergence_mixed_vs_fp64(oracle):
             ctx = srhd.Context(srhd.Params())
             U, steps, _ = _gpu_evolve(torch, srhd, ctx, workloads.patchify(C.reshape(5, N, N, N)),
                                       N // 8, N // 8, N // 8, ("periodic",) * 3, 1.0 / N, T_period,
-                                      dtype)
+                                      prec)
             G = workloads.unpatchify(to_np(U), N // 8, N // 8, N // 8)
             rho = oracle.con2pri(G.reshape(5, -1))["prim"][0]
             exact = workloads.advection_prims(N, t=T_period)[0].reshape(-1)
             l1[prec, N] = np.mean(np.abs(1 - rho / exact))
-    for prec in ("fp64", "mixed"):
+    for prec in PRECS:
         assert np.log2(l1[prec, 16] / l1[prec, 32]) > 1.6, l1
     assert abs(l1["mixed", 32] / l1["fp64", 32] - 1) < 0.01, l1
+    assert abs(l1["mixed_cf", 32] / l1["fp64", 32] - 1) < 0.01, l1
 
 
-@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+@pytest.mark.parametrize("prec", PRECS)
 def test_full_size_step_sampled(oracle, prec):
     # One step of the 256^3 smooth-advection batch (32768 patches) in the
     # configuration the benchmark times (fused CFL, status, one launch);
@@ -143,16 +141,16 @@ def test_full_size_step_sampled(oracle, prec):
     Wf = workloads.advection_prims(N)
     C, _ = oracle.prim2con(Wf.reshape(5, -1))
     C = C.reshape(5, N, N, N)
-    if prec == "mixed":
+    if prec != "fp64":
         C = C.astype(np.float32)
-    G = workloads.ghosted_patches(C.astype(np.float64) if prec == "fp64" else C)
-    dtype = torch.float64 if prec == "fp64" else torch.float32
+    G = workloads.ghosted_patches(C)
+    dtype = torch_dtype(torch, prec)
     npatch = G.shape[0]
     dh = 1.0 / N
     dd = torch.tensor([[0.4 * dh, dh]], dtype=torch.float64, device="cuda").repeat(npatch, 1)
     st = torch.empty(npatch, dtype=torch.int32, device="cuda")
     dn = torch.empty(1, dtype=torch.float64, device="cuda")
-    out = srhd.advance_patches(to_dev(torch, G, dtype), dd, dt_next=dn, patch_status=st)
+    out = srhd.advance_patches(to_dev(torch, G, dtype), dd, dt_next=dn, patch_status=st, prec=prec)
     torch.cuda.synchronize()
     assert int(st.abs().max()) == 0
     rng = np.random.default_rng(11)
