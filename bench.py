@@ -278,6 +278,55 @@ def l1_one_period(torch, srhd, prec, n=64):
     return float(np.mean(np.abs(1.0 - rho / exact))), steps
 
 
+def bench_amr(torch, srhd, steps: int, warmup: int, prec: str = "mixed_cf"):
+    """Batched AMR blast (5 levels, ~38k patches of uneven level): one fused
+    launch per level substep (31 per coarse step), eager and from a CUDA
+    graph of the whole coarse step."""
+    from paper_2012_11130_gb300 import amr, autotune
+    ctx = srhd.Context(srhd.Params())
+    batch, lev = amr.blast_batch(ctx, prec=prec)
+    best, times = autotune.tune(batch.G, batch.dt_dh, prec=prec, steps=2)
+    batch.ctx = srhd.Context(best)
+    stream = torch.cuda.current_stream()
+    for _ in range(warmup):
+        batch.step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        batch.step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    eager_ms = e0.elapsed_time(e1) / steps
+    batch.capture()
+    for _ in range(warmup):
+        batch.replay()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(steps):
+        batch.replay()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    graph_ms = e0.elapsed_time(e1) / steps
+    upd = batch.cell_updates_per_step
+    out = {
+        "workload": ("off-centre relativistic blast, [0,1]^3, base 64^3, 5 levels of 8^3 "
+                     "patches refined around the shell, static ghost zones; level l takes "
+                     "2^l substeps per coarse step, one fused launch per level substep"),
+        "precision": prec, "patches_per_level": batch.counts, "patches": sum(batch.counts),
+        "launches_per_coarse_step": batch.launches_per_step,
+        "cell_updates_per_coarse_step": upd,
+        "value_graph": upd / (graph_ms * 1e-3), "value_eager": upd / (eager_ms * 1e-3),
+        "unit": UNIT, "ms_per_coarse_step_graph": graph_ms, "ms_per_coarse_step_eager": eager_ms,
+        "patch_status_max": int(batch.status.abs().max().item()),
+        "autotune": {"chosen_variant": best.patch_variant,
+                     "ms_per_variant": {str(k): v for k, v in times.items()}},
+    }
+    del batch
+    torch.cuda.empty_cache()
+    return out
+
+
 # ---------------------------------------------------------------------------
 # CPU oracle baseline (host cores)
 # ---------------------------------------------------------------------------
@@ -389,9 +438,18 @@ def run_ours(args):
 
     results = {}
     precs = ("mixed_cf", "mixed", "fp64") if args.prec == "all" else (args.prec,)
+    from paper_2012_11130_gb300 import autotune
     for prec in precs:
         G, dt_dh = build_workload(torch, srhd, ctx, prec, args.grid)
         torch.cuda.synchronize()
+        tuned = None
+        if not args.no_tune:
+            best, times = autotune.tune(G, dt_dh, prec=prec, steps=2 if prec == "fp64" else 3)
+            ctx = srhd.Context(best)
+            tuned = {"chosen_variant": best.patch_variant,
+                     "ms_per_variant": {str(k): v for k, v in times.items()}}
+        else:
+            ctx = srhd.Context(srhd.Params())
         with ClockSampler(local) as clk:
             total_ms, per, dt_next, smax = time_device(torch, ctx, G, dt_dh, args.steps,
                                                        args.warmup, barrier, prec)
@@ -422,10 +480,16 @@ def run_ours(args):
                              "bytes_per_cell_update": BYTES_PER_CELL_UPDATE[prec],
                              "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)"},
             "clocks": clocks, "e2e": e2e, "dt_next": dt_next, "patch_status_max": smax,
+            "autotune": tuned,
             "launch_ms_mean": launch_ms, "launch_ms_min": min(per),
         }
         del G, dt_dh
         torch.cuda.empty_cache()
+
+    amr_res = None
+    if not args.no_amr and args.grid == N_GRID:
+        amr_res = bench_amr(torch, srhd, max(3, args.steps // 4), 2, precs[0] if precs[0] != "fp64"
+                            else "mixed_cf")
 
     l1 = {}
     if not args.no_l1 and rank == 0:
@@ -466,10 +530,13 @@ def run_ours(args):
         "roofline": m["roofline"], "hbm_roofline": m["hbm_roofline"],
         "clocks": m["clocks"], "e2e": m["e2e"], "cpu_baseline": cpu,
         "gpu_launches": 2 * args.steps,
+        "autotune": m["autotune"],
         "other_precisions": {q: {k: results[q][k] for k in ("value", "ms_per_step", "roofline",
-                                                             "hbm_roofline", "clocks", "e2e")}
+                                                             "hbm_roofline", "clocks", "e2e",
+                                                             "autotune")}
                              for q in precs[1:]} or None,
         "l1_rho": l1 or None,
+        "amr_blast": amr_res,
         "kernel_sources_sha": sha,
     }
     print(json.dumps(line))
@@ -488,6 +555,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-l1", action="store_true")
+    ap.add_argument("--no-amr", action="store_true")
+    ap.add_argument("--no-tune", action="store_true", help="skip the launch-variant autotuner")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--grid", type=int, default=N_GRID,
                     help="cells per axis of the advection grid (multiple of 8)")

@@ -98,6 +98,11 @@ typedef struct srhd_params {
   int32_t ndim;           /* active dimensions in the CFL bound
                              (Eq. time_step_U_max uses 3); default 3 */
   int32_t newton_max_iter;/* Newton iteration cap; 0 = 50 (FP64) / 30 (FP32) */
+  int32_t patch_variant;  /* launch variant of the fused patch kernel, 0..3
+                             (threads per CTA, CTAs per SM, one or two Newton
+                             solves per thread); 0 = default. Results do not
+                             depend on it beyond rounding-free reordering of
+                             independent work; chosen by an autotuner. */
 } srhd_params;
 
 typedef struct srhd_ctx srhd_ctx;

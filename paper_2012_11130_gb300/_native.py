@@ -30,7 +30,8 @@ class Params(ctypes.Structure):
     _fields_ = [("cfl", ctypes.c_double), ("theta", ctypes.c_double),
                 ("retry_factor", ctypes.c_double), ("theta_floor", ctypes.c_double),
                 ("riemann", ctypes.c_int32), ("cfl_mode", ctypes.c_int32),
-                ("ndim", ctypes.c_int32), ("newton_max_iter", ctypes.c_int32)]
+                ("ndim", ctypes.c_int32), ("newton_max_iter", ctypes.c_int32),
+                ("patch_variant", ctypes.c_int32)]
 
 
 class SrhdError(RuntimeError):

@@ -46,7 +46,7 @@ struct srhd_ctx {
   srhd_params params;
   int device;
   int num_sms;
-  int patch_grid[3];      // persistent grid per precision
+  int patch_grid[3][srhd::kPatchVariants];  // persistent grid per precision and variant
   int scratch_slots;      // capacity of the partial-minimum arrays
   double* partial_dt;     // scratch [scratch_slots]
   int32_t* partial_bad;   // scratch [scratch_slots]
@@ -105,6 +105,8 @@ srhd_status check_params(const srhd_params* p) {
   if (p->ndim < 1 || p->ndim > 3) return fail(SRHD_ERR_ARG, "ndim must be 1, 2 or 3");
   if (p->newton_max_iter < 0 || p->newton_max_iter > 1000)
     return fail(SRHD_ERR_ARG, "newton_max_iter must be in [0, 1000]");
+  if (p->patch_variant < 0 || p->patch_variant >= srhd::kPatchVariants)
+    return fail(SRHD_ERR_ARG, "patch_variant must be in [0, %d)", srhd::kPatchVariants);
   return SRHD_OK;
 }
 
@@ -137,6 +139,7 @@ srhd_status srhd_default_params(srhd_params* p) {
   p->cfl_mode = SRHD_CFL_SIGNAL;
   p->ndim = 3;
   p->newton_max_iter = 0;
+  p->patch_variant = 0;
   return SRHD_OK;
 }
 
@@ -163,17 +166,19 @@ srhd_status srhd_create(srhd_ctx** out, const srhd_params* p) {
   c->params = prm;
   c->device = dev;
   c->num_sms = nsm;
-  int b64 = srhd::Launch<srhd::PrecFP64>::patch_blocks_per_sm();
-  int b32 = srhd::Launch<srhd::PrecMixed>::patch_blocks_per_sm();
-  int bcf = srhd::Launch<srhd::PrecMixedCF>::patch_blocks_per_sm();
-  if (b64 < 1 || b32 < 1 || bcf < 1) {
-    delete c;
-    return fail(SRHD_ERR_CUDA, "patch kernel does not fit on an SM (blocks/SM %d, %d, %d)", b64,
-                b32, bcf);
+  for (int v = 0; v < srhd::kPatchVariants; ++v) {
+    int b64 = srhd::Launch<srhd::PrecFP64>::patch_blocks_per_sm(v);
+    int b32 = srhd::Launch<srhd::PrecMixed>::patch_blocks_per_sm(v);
+    int bcf = srhd::Launch<srhd::PrecMixedCF>::patch_blocks_per_sm(v);
+    if (b64 < 1 || b32 < 1 || bcf < 1) {
+      delete c;
+      return fail(SRHD_ERR_CUDA, "patch kernel variant %d does not fit on an SM (%d, %d, %d)", v,
+                  b64, b32, bcf);
+    }
+    c->patch_grid[SRHD_FP64][v] = nsm * b64;
+    c->patch_grid[SRHD_MIXED][v] = nsm * b32;
+    c->patch_grid[SRHD_MIXED_CF][v] = nsm * bcf;
   }
-  c->patch_grid[SRHD_FP64] = nsm * b64;
-  c->patch_grid[SRHD_MIXED] = nsm * b32;
-  c->patch_grid[SRHD_MIXED_CF] = nsm * bcf;
   c->scratch_slots = nsm * 8;
   c->partial_dt = nullptr;
   c->partial_bad = nullptr;
@@ -232,7 +237,8 @@ srhd_status srhd_con2pri(srhd_ctx* c, srhd_prec prec, const void* cons, void* pr
 
 static srhd_status launch_patches(srhd_ctx* c, srhd_prec prec, srhd::PatchArgs& a,
                                   double* dt_next, cudaStream_t s) {
-  int grid = c->patch_grid[prec];
+  const int variant = c->params.patch_variant;
+  int grid = c->patch_grid[prec][variant];
   if (grid > a.npatch) grid = a.npatch;
   if (dt_next) {
     a.partial_dt = c->partial_dt;
@@ -240,7 +246,7 @@ static srhd_status launch_patches(srhd_ctx* c, srhd_prec prec, srhd::PatchArgs& 
   }
   cudaError_t e = cudaSuccess;
   if (a.npatch > 0) {
-    e = dispatch(prec, [&](auto L) { return decltype(L)::patches(a, grid, s); });
+    e = dispatch(prec, [&](auto L) { return decltype(L)::patches(a, variant, grid, s); });
     if (e != cudaSuccess) return cuda_fail(e, "patch kernel launch");
   } else {
     grid = 0;

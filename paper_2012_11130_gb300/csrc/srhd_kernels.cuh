@@ -54,9 +54,10 @@ struct PatchArgs {
 };
 
 template <class S> struct SmemLayout {  // S: storage type
-  static constexpr size_t prim_elems = 5 * kGC;
-  static constexpr size_t face_elems = 3 * 2 * 5 * kNF;
-  static constexpr size_t bytes = (prim_elems + face_elems) * sizeof(S);
+  static constexpr size_t prim_elems = 5 * kGC;        // primitive tile
+  static constexpr size_t face_elems = 3 * 2 * 5 * kNF; // predicted faces / fluxes
+  static constexpr size_t ht_elems = kGC;               // htilde of the tile cells
+  static constexpr size_t bytes = (prim_elems + face_elems + ht_elems) * sizeof(S);
 };
 
 // Class of a ghosted coordinate: 0 interior [2,9], 1 first ghost layer,
@@ -198,11 +199,26 @@ __device__ __forceinline__ void halfstep_direction(int i, int j, int k, bool int
   }
 }
 
+// Tile index of the cell on the left (side 0) or right (side 1) of face fi
+// along d: the cell whose half-step face state sits in that slot.
+template <int d> __device__ __forceinline__ int face_owner(int fi, int side) {
+  int i, j, k, fd;
+  if (d == 0) { fd = fi % 9; j = (fi / 9) & 7; k = fi / 72; i = fd - 1 + side; }
+  else if (d == 1) { i = fi & 7; fd = (fi >> 3) % 9; k = (fi >> 3) / 9; j = fd - 1 + side; }
+  else { i = fi & 7; j = (fi >> 3) & 7; fd = fi >> 6; k = fd - 1 + side; }
+  return tile_index(i, j, k);
+}
+
+// Riemann flux of face fi along d from the two predicted states in its
+// slots; their Newton solves start from the converged htilde of the cells
+// they belong to (a warm start: the predicted state differs from the cell
+// state by half a limited slope and half a time step).
 template <int d, class P, bool PAIR>
-__device__ __forceinline__ int face_flux(typename P::S* face, int fi, int solver, int maxit,
-                                         int& code) {
+__device__ __forceinline__ int face_flux(typename P::S* face, const typename P::S* hts, int fi,
+                                         int solver, int maxit, int& code) {
   using S = typename P::S;
   using R = S;
+  const S gL = hts[face_owner<d>(fi, 0)], gR = hts[face_owner<d>(fi, 1)];
   S UL[5], UR[5];
 #pragma unroll
   for (int v = 0; v < 5; ++v) {
@@ -212,10 +228,10 @@ __device__ __forceinline__ int face_flux(typename P::S* face, int fi, int solver
   PrimX<R> WL, WR;
   int sl, sr;
   if constexpr (PAIR) {
-    con2pri_x2<P>(UL, UR, WL, WR, maxit, sl, sr);
+    con2pri_x2<P>(UL, UR, WL, WR, maxit, sl, sr, gL, gR);
   } else {
-    sl = con2pri<P>(UL[0], UL[1], UL[2], UL[3], UL[4], WL, maxit);
-    sr = con2pri<P>(UR[0], UR[1], UR[2], UR[3], UR[4], WR, maxit);
+    sl = con2pri<P>(UL[0], UL[1], UL[2], UL[3], UL[4], WL, maxit, gL);
+    sr = con2pri<P>(UR[0], UR[1], UR[2], UR[3], UR[4], WR, maxit, gR);
   }
   if (sl == 2 || sr == 2) code |= CODE_NOCONV;
   int fail = (sl == 1 || sr == 1);
@@ -230,11 +246,13 @@ __device__ __forceinline__ int face_flux(typename P::S* face, int fi, int solver
 
 template <class P, int NT, int MINB, bool PAIR>
 __global__ void __launch_bounds__(NT, MINB) patch_kernel(PatchArgs a) {
+  static_assert(NT % 32 == 0 && NT >= 64 && NT <= 1024, "block size");
   using S = typename P::S;
   using R = S;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   S* prim = reinterpret_cast<S*>(smem_raw);
   S* face = prim + SmemLayout<S>::prim_elems;
+  S* hts = face + SmemLayout<S>::face_elems;
   __shared__ double s_red[NT / 32];
   __shared__ int s_bad[NT / 32];
   const int tid = threadIdx.x;
@@ -270,6 +288,8 @@ __global__ void __launch_bounds__(NT, MINB) patch_kernel(PatchArgs a) {
         prim[2 * kGC + ca] = S(Wa.u[1]);
         prim[3 * kGC + ca] = S(Wa.u[2]);
         prim[4 * kGC + ca] = S(Wa.p);
+        hts[ca] = S(Wa.ht);
+        hts[cb] = S(Wb.ht);
         prim[cb] = S(Wb.rho);
         prim[kGC + cb] = S(Wb.u[0]);
         prim[2 * kGC + cb] = S(Wb.u[1]);
@@ -289,6 +309,7 @@ __global__ void __launch_bounds__(NT, MINB) patch_kernel(PatchArgs a) {
         prim[2 * kGC + c] = S(W.u[1]);
         prim[3 * kGC + c] = S(W.u[2]);
         prim[4 * kGC + c] = S(W.p);
+        hts[c] = S(W.ht);
       }
     }
     const int bad_input = __syncthreads_or(code & CODE_BAD_INPUT);
@@ -300,8 +321,10 @@ __global__ void __launch_bounds__(NT, MINB) patch_kernel(PatchArgs a) {
     int att_bad = 0;
     if (!bad_input) {
       R theta = R(a.theta0);
-      const R half = R(0.5 * dt / dh);
-      const R coef = R(dt / dh);
+      // dt/dh in the arithmetic type (a double division per thread and patch
+      // would occupy the FP64 pipe of the float kernels)
+      const R coef = R(dt) / R(dh);
+      const R half = R(0.5) * coef;
       for (;;) {
         // ---- phase 2: reconstruction + Hancock half step --------------------
         int fail = 0;
@@ -328,9 +351,9 @@ __global__ void __launch_bounds__(NT, MINB) patch_kernel(PatchArgs a) {
         // ---- phase 3: Riemann fluxes ----------------------------------------
         for (int f = tid; f < 3 * kNF; f += NT) {
           const int d = f / kNF, fi = f - d * kNF;
-          if (d == 0) fail |= face_flux<0, P, PAIR>(face, fi, a.riemann, maxit, code);
-          else if (d == 1) fail |= face_flux<1, P, PAIR>(face, fi, a.riemann, maxit, code);
-          else fail |= face_flux<2, P, PAIR>(face, fi, a.riemann, maxit, code);
+          if (d == 0) fail |= face_flux<0, P, PAIR>(face, hts, fi, a.riemann, maxit, code);
+          else if (d == 1) fail |= face_flux<1, P, PAIR>(face, hts, fi, a.riemann, maxit, code);
+          else fail |= face_flux<2, P, PAIR>(face, hts, fi, a.riemann, maxit, code);
         }
         fail = __syncthreads_or(fail);
         if (a.flux_only) {
@@ -345,17 +368,20 @@ __global__ void __launch_bounds__(NT, MINB) patch_kernel(PatchArgs a) {
         if (!fail || last) {
           S* out = static_cast<S*>(a.out) + (size_t)p * 5 * kNC;
           int fail4 = 0;
-          // PAIR: each thread updates cells c0 and c0 + NT (NT = 256) and
-          // converts both in lockstep for the CFL bound
+          // PAIR: the work item c0 in [0, 256) updates cells c0 and c0 + 256
+          // and converts both in lockstep for the CFL bound (for any NT)
           constexpr int NPC = PAIR ? 2 : 1;
-          for (int c0 = tid; c0 < kNC; c0 += NT * NPC) {
+          constexpr int kItems = kNC / NPC;
+          for (int c0 = tid; c0 < kItems; c0 += NT) {
             S Un[NPC][5];
+            S g0[NPC];  // htilde of the cell before the step: warm start of the CFL solve
             bool ok[NPC];
 #pragma unroll
             for (int q = 0; q < NPC; ++q) {
-              const int c = c0 + q * NT;
+              const int c = c0 + q * kItems;
               const int i = c & 7, j = (c >> 3) & 7, k = c >> 6;
               const int tc = tile_index(i, j, k);
+              g0[q] = hts[tc];
               const int fx0 = face_index<0>(i, j, k, i), fx1 = face_index<0>(i, j, k, i + 1);
               const int fy0 = face_index<1>(i, j, k, j), fy1 = face_index<1>(i, j, k, j + 1);
               const int fz0 = face_index<2>(i, j, k, k), fz1 = face_index<2>(i, j, k, k + 1);
@@ -379,9 +405,10 @@ __global__ void __launch_bounds__(NT, MINB) patch_kernel(PatchArgs a) {
                 PrimX<R> W[NPC];
                 if constexpr (PAIR) {
                   int s0, s1;
-                  con2pri_x2<P>(Un[0], Un[1], W[0], W[1], maxit, s0, s1);
+                  con2pri_x2<P>(Un[0], Un[1], W[0], W[1], maxit, s0, s1, g0[0], g0[NPC - 1]);
                 } else {
-                  con2pri<P>(Un[0][0], Un[0][1], Un[0][2], Un[0][3], Un[0][4], W[0], maxit);
+                  con2pri<P>(Un[0][0], Un[0][1], Un[0][2], Un[0][3], Un[0][4], W[0], maxit,
+                             g0[0]);
                 }
 #pragma unroll
                 for (int q = 0; q < NPC; ++q) {
@@ -400,7 +427,7 @@ __global__ void __launch_bounds__(NT, MINB) patch_kernel(PatchArgs a) {
         theta = theta * R(a.retry_factor);
         if (theta < R(a.theta_floor * a.theta0)) theta = R(0);
       }
-      if (att_smax > R(0)) att_min = fmin(att_min, a.cfl * dh / double(att_smax));
+      if (att_smax > R(0)) att_min = fmin(att_min, double(R(a.cfl * dh) / att_smax));
       dt_min = fmin(dt_min, att_min);
       cfl_bad |= att_bad;
     } else {
@@ -562,10 +589,12 @@ __global__ void fill_ghosts_kernel(const S* interior, S* ghosted, int npx, int n
 
 // Per-precision launchers (explicitly instantiated in srhd_fp64.cu,
 // srhd_mixed.cu and srhd_mixed_cf.cu for the tags of srhd_physics.cuh).
+constexpr int kPatchVariants = 4;  // launch variants of patch_kernel per precision
+
 template <class P> struct Launch {
   static cudaError_t setup();
-  static int patch_blocks_per_sm();
-  static cudaError_t patches(const PatchArgs& a, int grid, cudaStream_t s);
+  static int patch_blocks_per_sm(int variant);
+  static cudaError_t patches(const PatchArgs& a, int variant, int grid, cudaStream_t s);
   static cudaError_t prim2con(const void* prim, void* cons, int64_t n, int64_t stride, int grid,
                               cudaStream_t s);
   static cudaError_t con2pri(const void* cons, void* prim, int64_t n, int64_t stride,

@@ -8,45 +8,73 @@
 
 namespace srhd {
 
-template <class S> struct PatchCfg;
-// FP64: 207 KB of shared memory per CTA -> one CTA of 512 threads per SM;
-// the FP64 pipe is the bound, so conversions run one state per thread.
-template <> struct PatchCfg<double> {
-  static constexpr int threads = 512, minb = 1;
-  static constexpr bool pair = false;
-};
-// Float storage: 101 KB per CTA -> two CTAs of 256 threads per SM; latency
-// bound, so conversions run two states per thread in lockstep.
-template <> struct PatchCfg<float> {
-  static constexpr int threads = 256, minb = 2;
-  static constexpr bool pair = true;
+// Launch variants of the patch kernel (threads per CTA, CTAs per SM,
+// two Newton solves per thread in lockstep or one). Variant 0 is the
+// default; the rest are the search space of the autotuner
+// (paper_2012_11130_gb300/autotune.py). Shared memory per CTA is 207 KB for
+// double storage (one CTA per SM) and 101 KB for float storage (at most
+// two).
+template <class S, int V> struct PatchVariant;
+template <> struct PatchVariant<double, 0> { static constexpr int nt = 512, minb = 1; static constexpr bool pair = false; };
+template <> struct PatchVariant<double, 1> { static constexpr int nt = 256, minb = 1; static constexpr bool pair = false; };
+template <> struct PatchVariant<double, 2> { static constexpr int nt = 512, minb = 1; static constexpr bool pair = true; };
+template <> struct PatchVariant<double, 3> { static constexpr int nt = 384, minb = 1; static constexpr bool pair = false; };
+template <> struct PatchVariant<float, 0> { static constexpr int nt = 256, minb = 2; static constexpr bool pair = true; };
+template <> struct PatchVariant<float, 1> { static constexpr int nt = 256, minb = 2; static constexpr bool pair = false; };
+template <> struct PatchVariant<float, 2> { static constexpr int nt = 512, minb = 1; static constexpr bool pair = true; };
+template <> struct PatchVariant<float, 3> { static constexpr int nt = 384, minb = 2; static constexpr bool pair = true; };
+
+template <class P, int V> struct PatchKernel {
+  using S = typename P::S;
+  using Cfg = PatchVariant<S, V>;
+  static constexpr auto fn = patch_kernel<P, Cfg::nt, Cfg::minb, Cfg::pair>;
 };
 
-template <class P> cudaError_t Launch<P>::setup() {
-  using S = typename P::S;
-  constexpr int NT = PatchCfg<S>::threads, MB = PatchCfg<S>::minb;
-  constexpr bool PR = PatchCfg<S>::pair;
-  return cudaFuncSetAttribute(patch_kernel<P, NT, MB, PR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              int(SmemLayout<S>::bytes));
+template <class P, int V> static cudaError_t setup_variant() {
+  return cudaFuncSetAttribute(PatchKernel<P, V>::fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              int(SmemLayout<typename P::S>::bytes));
 }
 
-template <class P> int Launch<P>::patch_blocks_per_sm() {
-  using S = typename P::S;
-  constexpr int NT = PatchCfg<S>::threads, MB = PatchCfg<S>::minb;
-  constexpr bool PR = PatchCfg<S>::pair;
+template <class P> cudaError_t Launch<P>::setup() {
+  cudaError_t e = setup_variant<P, 0>();
+  if (e == cudaSuccess) e = setup_variant<P, 1>();
+  if (e == cudaSuccess) e = setup_variant<P, 2>();
+  if (e == cudaSuccess) e = setup_variant<P, 3>();
+  return e;
+}
+
+template <class P, int V> static int blocks_variant() {
   int nb = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, patch_kernel<P, NT, MB, PR>, NT,
-                                                    SmemLayout<S>::bytes) != cudaSuccess)
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, PatchKernel<P, V>::fn,
+                                                    PatchKernel<P, V>::Cfg::nt,
+                                                    SmemLayout<typename P::S>::bytes) != cudaSuccess)
     return 0;
   return nb;
 }
 
-template <class P> cudaError_t Launch<P>::patches(const PatchArgs& a, int grid, cudaStream_t s) {
-  using S = typename P::S;
-  constexpr int NT = PatchCfg<S>::threads, MB = PatchCfg<S>::minb;
-  constexpr bool PR = PatchCfg<S>::pair;
-  patch_kernel<P, NT, MB, PR><<<grid, NT, SmemLayout<S>::bytes, s>>>(a);
+template <class P> int Launch<P>::patch_blocks_per_sm(int variant) {
+  switch (variant) {
+    case 0: return blocks_variant<P, 0>();
+    case 1: return blocks_variant<P, 1>();
+    case 2: return blocks_variant<P, 2>();
+    default: return blocks_variant<P, 3>();
+  }
+}
+
+template <class P, int V>
+static cudaError_t launch_variant(const PatchArgs& a, int grid, cudaStream_t s) {
+  PatchKernel<P, V>::fn<<<grid, PatchKernel<P, V>::Cfg::nt, SmemLayout<typename P::S>::bytes, s>>>(a);
   return cudaGetLastError();
+}
+
+template <class P>
+cudaError_t Launch<P>::patches(const PatchArgs& a, int variant, int grid, cudaStream_t s) {
+  switch (variant) {
+    case 0: return launch_variant<P, 0>(a, grid, s);
+    case 1: return launch_variant<P, 1>(a, grid, s);
+    case 2: return launch_variant<P, 2>(a, grid, s);
+    default: return launch_variant<P, 3>(a, grid, s);
+  }
 }
 
 template <class P>

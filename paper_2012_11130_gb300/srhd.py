@@ -39,12 +39,13 @@ class Params:
     cfl_mode: str = "signal"     # "signal" | "light"
     ndim: int = 3
     newton_max_iter: int = 0
+    patch_variant: int = 0       # launch variant of the fused kernel (autotune.py)
 
     def to_c(self) -> N.Params:
         return N.Params(self.cfl, self.theta, self.retry_factor, self.theta_floor,
                         {"hllc": N.SRHD_HLLC, "hlle": N.SRHD_HLLE}[self.riemann],
                         {"signal": N.SRHD_CFL_SIGNAL, "light": N.SRHD_CFL_LIGHT}[self.cfl_mode],
-                        self.ndim, self.newton_max_iter)
+                        self.ndim, self.newton_max_iter, self.patch_variant)
 
 
 _PREC = {"fp64": (N.SRHD_FP64, torch.float64), "mixed": (N.SRHD_MIXED, torch.float32),
@@ -190,24 +191,59 @@ class Context:
             _ptr(patch_status), _stream(stream)), "srhd_advance_patches")
         return cons_out
 
-    def _advance_host(self, cons_ghosted, dt_dh, cons_out, dt_next, patch_status, stream, prec):
+    def _advance_host(self, cons_ghosted, dt_dh, cons_out, dt_next, patch_status, stream, prec,
+                      chunks: int = 8):
+        """Host-resident batch: the batch is cut into chunks whose
+        host-to-device copy, fused step and device-to-host copy run on three
+        streams, so copies of one chunk overlap the step of another (pinned
+        host tensors make the copies asynchronous). The per-chunk CFL minima
+        are combined at the end. Device buffers are kept for reuse."""
         dev = torch.device("cuda", self.device)
-        g = cons_ghosted.to(dev, non_blocking=True)
-        dd = dt_dh.to(dev, non_blocking=True)
-        out_d = torch.empty((g.shape[0], 5, 8, 8, 8), dtype=g.dtype, device=dev)
-        dn_d = torch.empty(1, dtype=torch.float64, device=dev) if dt_next is not None else None
-        st_d = torch.empty(g.shape[0], dtype=torch.int32, device=dev) \
-            if patch_status is not None else None
-        self.advance_patches(g, dd, cons_out=out_d, dt_next=dn_d, patch_status=st_d,
-                             stream=stream, prec=prec)
+        n = cons_ghosted.shape[0]
+        dtype = cons_ghosted.dtype
+        key = (n, dtype)
+        if getattr(self, "_host_buf_key", None) != key:
+            self._host_buf = dict(
+                g=torch.empty((n, 5, 12, 12, 12), dtype=dtype, device=dev),
+                dd=torch.empty((n, 2), dtype=torch.float64, device=dev),
+                out=torch.empty((n, 5, 8, 8, 8), dtype=dtype, device=dev),
+                st=torch.empty(n, dtype=torch.int32, device=dev),
+                wl=torch.arange(n, dtype=torch.int32, device=dev),
+                dn=torch.empty(chunks, dtype=torch.float64, device=dev),
+                streams=[torch.cuda.Stream(device=dev) for _ in range(3)])
+            self._host_buf_key = key
+        b = self._host_buf
+        h2d, comp, d2h = b["streams"]
         if cons_out is None:
-            cons_out = torch.empty(out_d.shape, dtype=out_d.dtype, pin_memory=True)
-        cons_out.copy_(out_d, non_blocking=True)
+            cons_out = torch.empty((n, 5, 8, 8, 8), dtype=dtype, pin_memory=True)
+        cur = stream or torch.cuda.current_stream(dev)
+        h2d.wait_stream(cur)
+        comp.wait_stream(cur)
+        d2h.wait_stream(cur)
+        bounds = [n * k // chunks for k in range(chunks + 1)]
+        used = 0
+        for k in range(chunks):
+            a, e = bounds[k], bounds[k + 1]
+            if a == e:
+                continue
+            used = k + 1
+            with torch.cuda.stream(h2d):
+                b["g"][a:e].copy_(cons_ghosted[a:e], non_blocking=True)
+                b["dd"][a:e].copy_(dt_dh[a:e], non_blocking=True)
+            comp.wait_stream(h2d)
+            self.advance_patches(b["g"], b["dd"], cons_out=b["out"], worklist=b["wl"][a:e],
+                                 npatch=e - a, dt_next=b["dn"][k:k + 1] if dt_next is not None
+                                 else None, patch_status=b["st"], stream=comp, prec=prec)
+            d2h.wait_stream(comp)
+            with torch.cuda.stream(d2h):
+                cons_out[a:e].copy_(b["out"][a:e], non_blocking=True)
+                if patch_status is not None:
+                    patch_status[a:e].copy_(b["st"][a:e], non_blocking=True)
+        d2h.synchronize()
         if dt_next is not None:
-            dt_next.copy_(dn_d, non_blocking=True)
-        if patch_status is not None:
-            patch_status.copy_(st_d, non_blocking=True)
-        (stream or torch.cuda.current_stream()).synchronize()
+            dn = b["dn"][:used].cpu()
+            dt_next.copy_(dn.min().reshape(1) if not torch.isnan(dn).any()
+                          else torch.full((1,), float("nan"), dtype=torch.float64))
         return cons_out
 
     def cfl_dt(self, cons, dh, dt_out=None, stream=None, prec=None):

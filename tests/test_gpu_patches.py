@@ -263,3 +263,28 @@ def test_argument_errors():
         srhd.Context(srhd.Params(cfl=2.0))
     with pytest.raises(TypeError):
         srhd.advance_patches(g.to(torch.float16), dd)
+
+
+@pytest.mark.parametrize("prec", ["mixed_cf", "fp64"])
+def test_host_buffer_path_matches_device_path(oracle, smooth_case, prec):
+    # The public call with pinned host tensors (chunked copies overlapping
+    # the fused steps on three streams) returns the device path's result.
+    torch, srhd = require_gpu()
+    dt_dh, cases = smooth_case
+    C, ref = cases[prec]
+    dtype = _dtype(torch, prec)
+    ctx = srhd.Context(srhd.Params())
+    g = to_dev(torch, C, dtype)
+    dd = to_dev(torch, dt_dh, torch.float64)
+    dn = torch.empty(1, dtype=torch.float64, device="cuda")
+    want = to_np(ctx.advance_patches(g, dd, dt_next=dn, prec=prec))
+    gh = g.cpu().pin_memory()
+    ddh = dd.cpu().pin_memory()
+    outh = torch.empty((C.shape[0], 5, 8, 8, 8), dtype=dtype).pin_memory()
+    dnh = torch.empty(1, dtype=torch.float64).pin_memory()
+    sth = torch.full((C.shape[0],), -1, dtype=torch.int32).pin_memory()
+    for _ in range(2):  # the second call reuses the device buffers
+        ctx.advance_patches(gh, ddh, cons_out=outh, dt_next=dnh, patch_status=sth, prec=prec)
+        assert np.array_equal(outh.double().numpy(), want)
+        assert dnh.item() == dn.item()
+        assert np.all(sth.numpy() == 0)
