@@ -61,8 +61,10 @@ PEAK_FP64_TFLOPS = 1.25
 # only for the kernel sources with the recorded hash.
 # Captured at 128^3 (4096 patches) and scaled by 8 to the 32768-patch launch
 # (profiles/patch_kernel_advection128.md).
-NCU_TRAFFIC = {"sources_sha": "19dd3907075f225c", "mixed": 8 * (141.704704e6 + 24.683520e6),
-               "mixed_cf": None, "fp64": 8 * (274.028032e6 + 66.898944e6)}
+NCU_TRAFFIC = {"sources_sha": "c34452f24989e938",
+               "mixed_cf": 8 * (142.862336e6 + 25.040384e6),
+               "mixed": 8 * (141.856512e6 + 23.923456e6),
+               "fp64": 8 * (273.881600e6 + 67.597568e6)}
 
 
 def kernel_sources_sha() -> str:
@@ -327,6 +329,88 @@ def bench_amr(torch, srhd, steps: int, warmup: int, prec: str = "mixed_cf"):
     return out
 
 
+def bench_con2pri_stress(torch, srhd, prec: str, log2n: int = 26, reps: int = 5):
+    """The con2pri stress batch (2^26 cells; rho 1e-6..1e2, T 1e-8..1e4,
+    gamma 1..1e6, random direction): cells/s of srhd_con2pri and the
+    round-trip error |1 - htilde0/htilde2| of prim -> cons -> prim, maximum
+    over the cells whose conditioning 1 + Mach^2 keeps it meaningful
+    (kappa eps_A <= 1e-3) and binned by Mach number."""
+    from paper_2012_11130_gb300 import workloads
+    n = 1 << log2n
+    ctx = srhd.Context(srhd.Params())
+    W = workloads.stress_batch_prims_torch(n, seed=12345)           # float64 on the device
+    dtype = torch.float64 if prec == "fp64" else torch.float32
+    C = ctx.prim2con(W).to(dtype)                                   # FP64 conversion, then stored
+    P = torch.empty_like(C)
+    st = torch.empty(n, dtype=torch.int32, device="cuda")
+    ctx.con2pri(C, P, st, prec=prec)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        ctx.con2pri(C, P, st, prec=prec)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    T0 = W[4] / W[0]
+    ht = lambda T: 2.5 * T + 2.25 * T * T / (1 + torch.sqrt(2.25 * T * T + 1))  # Eq. T_to_HTilde
+    Pd = P.double()
+    err = (1 - ht(T0) / ht(Pd[4] / Pd[0])).abs()
+    h0 = 1 + ht(T0)
+    cs2 = T0 * (5 * h0 - 8 * T0) / (3 * h0 * (h0 - T0))               # Eq. sound_speed
+    mach2 = (W[1] ** 2 + W[2] ** 2 + W[3] ** 2) / (cs2 / (1 - cs2))
+    eps_a = 2.2e-16 if prec != "mixed_cf" else 2.3e-13
+    ok = (st == 0) & ((1 + mach2) * eps_a <= 1e-3)
+    if prec != "fp64":  # float storage: the stored state itself is exact only to float
+        ok = ok & ((1 + mach2) * 6e-8 <= 1e-3)
+    bins = {}
+    lm = 0.5 * torch.log10(mach2.clamp(min=1e-30))
+    for lo in range(-4, 10, 2):
+        sel = ok & (lm >= lo) & (lm < lo + 2)
+        if int(sel.sum()) > 0:
+            bins[f"1e{lo}..1e{lo + 2}"] = float(err[sel].max())
+    out = {"cells": n, "cells_per_s": n / (ms * 1e-3), "ms": ms,
+           "unphysical_fraction": float((st == 1).double().mean()),
+           "max_roundtrip_error_by_mach": bins}
+    del W, C, P, st, Pd, err, T0, h0, cs2, mach2, lm, ok
+    torch.cuda.empty_cache()
+    return out
+
+
+def shock_tube_l1(torch, srhd, prec: str, n: int = 1024):
+    """Configuration 1 on the GPU: the 1-D shock tube to t = 0.4 (1024 cells,
+    (1, 0, 1e3) | (1, 0, 1e-2), PLM + MUSCL-Hancock + HLLC, CFL 0.5, outflow)
+    as 128 x 1 x 1 patches; returns the number of steps. The L1 error against
+    the exact solution is computed by the caller."""
+    from paper_2012_11130_gb300 import workloads
+    W, x = workloads.shock_tube_prims(n)
+    ctx = srhd.Context(srhd.Params(ndim=1))
+    Wd = torch.from_numpy(W).to("cuda")
+    C = ctx.prim2con(Wd).reshape(5, 1, 1, n).expand(5, 8, 8, n)
+    npx = n // 8
+    dtype = torch.float64 if prec == "fp64" else torch.float32
+    U = C.reshape(5, 8, 8, npx, 8).permute(3, 0, 1, 2, 4).to(dtype).contiguous()
+    dh = 1.0 / n
+    dd = torch.empty((npx, 2), dtype=torch.float64, device="cuda")
+    dn = torch.empty(1, dtype=torch.float64, device="cuda")
+    out = torch.empty_like(U)
+    dt = ctx.cfl_dt(U, dh, prec=prec).item()
+    t, steps = 0.0, 0
+    while t < 0.4 and steps < 100000:
+        dt = min(dt, 0.4 - t)
+        dd[:, 0] = dt
+        dd[:, 1] = dh
+        G = ctx.fill_ghosts_uniform(U, npx, 1, 1, bc=("outflow", "periodic", "periodic"))
+        ctx.advance_patches(G, dd, cons_out=out, dt_next=dn, prec=prec)
+        U, out = out, U
+        t += dt
+        steps += 1
+        dt = dn.item()
+    row = U[:, :, 0, 0, :].permute(1, 0, 2).reshape(5, n).contiguous()
+    rho = ctx.con2pri(row, prec=prec)[0].double().cpu().numpy()
+    return rho, x, steps
+
+
 # ---------------------------------------------------------------------------
 # CPU oracle baseline (host cores)
 # ---------------------------------------------------------------------------
@@ -443,7 +527,10 @@ def run_ours(args):
         G, dt_dh = build_workload(torch, srhd, ctx, prec, args.grid)
         torch.cuda.synchronize()
         tuned = None
-        if not args.no_tune:
+        if args.variant is not None:
+            ctx = srhd.Context(srhd.Params(patch_variant=args.variant))
+            tuned = {"chosen_variant": args.variant, "ms_per_variant": None}
+        elif not args.no_tune:
             best, times = autotune.tune(G, dt_dh, prec=prec, steps=2 if prec == "fp64" else 3)
             ctx = srhd.Context(best)
             tuned = {"chosen_variant": best.patch_variant,
@@ -492,10 +579,13 @@ def run_ours(args):
                             else "mixed_cf")
 
     l1 = {}
+    stress = {}
     if not args.no_l1 and rank == 0:
         for prec in precs:
             l1[prec], l1_steps = l1_one_period(torch, srhd, prec)
         l1["grid"] = "64^3, one period, fused CFL 0.5"
+        for prec in precs:
+            stress[prec] = bench_con2pri_stress(torch, srhd, prec)
 
     if rank != 0:
         if world > 1:
@@ -510,7 +600,20 @@ def run_ours(args):
         sampler.close()
         cpu = {"value": v, "unit": UNIT, "cores": os.cpu_count() or 1, "kind": "oracle",
                "sample": f"{n} of 32768 patches (one FP64 oracle step each, with CFL), "
-                         f"{os.cpu_count()} spawned processes, {wall:.1f} s"}
+                         f"{os.cpu_count()} spawned processes, {wall:.1f} s",
+               "value_1core": 8 * CELLS_PER_PATCH / _oracle_chunk((0, 8))}
+    st_l1 = None
+    if rank == 0 and not args.no_l1:
+        # configuration 1: shock-tube L1 of rho against the exact TM solution
+        # (stored by tests/golden/make_shock_tube_exact.py), per precision
+        import numpy as np
+        ex = np.loadtxt(os.path.join(ROOT, "tests", "golden", "shock_tube_exact_1024.txt"))
+        st_l1 = {}
+        for prec in precs:
+            rho, x, steps = shock_tube_l1(torch, srhd, prec)
+            st_l1[prec] = float(np.mean(np.abs(1 - rho / ex[:, 1])))
+        st_l1["steps"] = steps
+        st_l1["grid"] = "1024 cells, t = 0.4, CFL 0.5"
     m = results[precs[0]]
     line = {
         "metric": METRIC, "value": m["value"], "unit": UNIT, "n_gpus": world,
@@ -536,6 +639,8 @@ def run_ours(args):
                                                              "autotune")}
                              for q in precs[1:]} or None,
         "l1_rho": l1 or None,
+        "l1_shock_tube": st_l1,
+        "con2pri_stress": stress or None,
         "amr_blast": amr_res,
         "kernel_sources_sha": sha,
     }
@@ -557,6 +662,8 @@ def main():
     ap.add_argument("--no-l1", action="store_true")
     ap.add_argument("--no-amr", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="skip the launch-variant autotuner")
+    ap.add_argument("--variant", type=int, default=None,
+                    help="use this launch variant of the patch kernel (no autotuning)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--grid", type=int, default=N_GRID,
                     help="cells per axis of the advection grid (multiple of 8)")

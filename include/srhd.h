@@ -68,6 +68,16 @@ typedef enum srhd_riemann { SRHD_HLLC = 0, SRHD_HLLE = 1 } srhd_riemann;
 typedef enum srhd_cfl_mode { SRHD_CFL_SIGNAL = 0, SRHD_CFL_LIGHT = 1 } srhd_cfl_mode;
 typedef enum srhd_bc { SRHD_BC_PERIODIC = 0, SRHD_BC_OUTFLOW = 1 } srhd_bc;
 
+/* Energy formulation (Sections 2.1, 2.3 and 4). SRHD_SCHEME_REDUCED is the
+ * paper's scheme: the fifth conserved variable is Etilde = E - D with flux
+ * (Etilde + p) U^j / gamma (Eq. ETilde evolution) and conversions by
+ * Eq. E_D and the Etilde form of Eq. transcendental equation.
+ * SRHD_SCHEME_TOTAL is the "original scheme" the paper compares against: the
+ * fifth variable is the total energy E = D h gamma - p with flux M^j
+ * (Eq. E evoltion), inverted from (E/D)^2 - (|M|/D)^2 - 1, whose error grows
+ * as 4 eps / (3T) for cold gas (Eq. OriRelativeError). */
+typedef enum srhd_scheme { SRHD_SCHEME_REDUCED = 0, SRHD_SCHEME_TOTAL = 1 } srhd_scheme;
+
 /* Per-cell status codes written by srhd_con2pri (cell_status). */
 enum {
   SRHD_CELL_OK = 0,
@@ -103,6 +113,9 @@ typedef struct srhd_params {
                              solves per thread); 0 = default. Results do not
                              depend on it beyond rounding-free reordering of
                              independent work; chosen by an autotuner. */
+  int32_t scheme;         /* srhd_scheme; default SRHD_SCHEME_REDUCED. Applies to
+                             every call of the context: the fifth conserved
+                             variable of all arrays is then E instead of Etilde */
 } srhd_params;
 
 typedef struct srhd_ctx srhd_ctx;

@@ -67,24 +67,24 @@ def lib():
             L.or_limited_slope.restype = d
             L.or_limited_slope.argtypes = [d, d, d]
             L.or_prim2con.restype = None
-            L.or_prim2con.argtypes = [_dp, _dp, i64, _ip]
+            L.or_prim2con.argtypes = [_dp, _dp, i64, _ip, i32]
             L.or_con2pri.restype = None
-            L.or_con2pri.argtypes = [_dp, _dp, i64, _ip, _ip, _dp, _dp]
+            L.or_con2pri.argtypes = [_dp, _dp, i64, _ip, _ip, _dp, _dp, i32]
             L.or_phys_flux.restype = None
-            L.or_phys_flux.argtypes = [i32, _dp, _dp, _dp]
+            L.or_phys_flux.argtypes = [i32, _dp, _dp, _dp, i32]
             L.or_char_speeds.restype = None
             L.or_char_speeds.argtypes = [i32, _dp, _dp, _dp]
             L.or_riemann_flux.restype = i32
-            L.or_riemann_flux.argtypes = [i32, i32, _dp, _dp, _dp, _dp, _dp]
+            L.or_riemann_flux.argtypes = [i32, i32, _dp, _dp, _dp, _dp, _dp, i32]
             L.or_smax.restype = d
             L.or_smax.argtypes = [_dp, i32]
             L.or_advance_block.restype = i32
             L.or_advance_block.argtypes = [_dp, _dp, _dp, i32, i32, i32, i32, i32, i32, d, d, d,
-                                           d, d, i32, _ip]
+                                           d, d, i32, _ip, i32]
             L.or_advance_patches.restype = None
-            L.or_advance_patches.argtypes = [_dp, _dp, i64, _dp, d, d, d, i32, _ip, _ip, _dp]
+            L.or_advance_patches.argtypes = [_dp, _dp, i64, _dp, d, d, d, i32, _ip, _ip, _dp, i32]
             L.or_cfl_dt.restype = d
-            L.or_cfl_dt.argtypes = [_dp, i64, d, d, i32, i32]
+            L.or_cfl_dt.argtypes = [_dp, i64, d, d, i32, i32, i32]
             L.or_count_advance_block.restype = None
             L.or_count_advance_block.argtypes = [_dp, i32, i32, i32, i32, i32, i32, d, d, d, i32,
                                                  _up]
@@ -151,17 +151,22 @@ def limited_slope(dl, dr, theta):
 
 
 # --- Section 2.3: conversions -----------------------------------------------
-def prim2con(prim):
+# scheme 0: the paper's new scheme (reduced energy Etilde); scheme 1: the
+# "original" scheme it compares against (total energy E with flux M).
+NEW, ORIGINAL = 0, 1
+
+
+def prim2con(prim, scheme=NEW):
     """prim [5][n] -> (cons [5][n], status [n])."""
     prim = _f64(prim)
     n = prim.shape[1]
     cons = np.empty_like(prim)
     st = np.empty(n, np.int32)
-    lib().or_prim2con(_p(prim), _p(cons), n, _p(st, _ip))
+    lib().or_prim2con(_p(prim), _p(cons), n, _p(st, _ip), scheme)
     return cons, st
 
 
-def con2pri(cons):
+def con2pri(cons, scheme=NEW):
     """cons [5][n] -> dict(prim, status, iters, htilde, A)."""
     cons = _f64(cons)
     n = cons.shape[1]
@@ -170,16 +175,16 @@ def con2pri(cons):
     it = np.empty(n, np.int32)
     ht = np.empty(n)
     A = np.empty(n)
-    lib().or_con2pri(_p(cons), _p(prim), n, _p(st, _ip), _p(it, _ip), _p(ht), _p(A))
+    lib().or_con2pri(_p(cons), _p(prim), n, _p(st, _ip), _p(it, _ip), _p(ht), _p(A), scheme)
     return dict(prim=prim, status=st, iters=it, htilde=ht, A=A)
 
 
 # --- Section 3: scheme pieces ---------------------------------------------
-def phys_flux(d, W):
+def phys_flux(d, W, scheme=NEW):
     W = _f64(W)
-    U, st = prim2con(W.reshape(5, 1))
+    U, st = prim2con(W.reshape(5, 1), scheme)
     F = np.empty(5)
-    lib().or_phys_flux(d, _p(W), _p(_f64(U[:, 0])), _p(F))
+    lib().or_phys_flux(d, _p(W), _p(_f64(U[:, 0])), _p(F), scheme)
     return F
 
 
@@ -190,18 +195,18 @@ def char_speeds(d, W):
     return lm.value, lp.value
 
 
-def riemann_flux(d, WL, WR, solver=0, UL=None, UR=None):
+def riemann_flux(d, WL, WR, solver=0, UL=None, UR=None, scheme=NEW):
     """Riemann flux across a face normal to d (0 = HLLC, 1 = HLLE).
 
     Returns (F[5], fell_back_to_hlle)."""
     WL, WR = _f64(WL), _f64(WR)
     if UL is None:
-        UL = prim2con(WL.reshape(5, 1))[0][:, 0]
+        UL = prim2con(WL.reshape(5, 1), scheme)[0][:, 0]
     if UR is None:
-        UR = prim2con(WR.reshape(5, 1))[0][:, 0]
+        UR = prim2con(WR.reshape(5, 1), scheme)[0][:, 0]
     UL, UR = _f64(UL), _f64(UR)
     F = np.empty(5)
-    fb = lib().or_riemann_flux(d, solver, _p(WL), _p(UL), _p(WR), _p(UR), _p(F))
+    fb = lib().or_riemann_flux(d, solver, _p(WL), _p(UL), _p(WR), _p(UR), _p(F), scheme)
     return F, fb
 
 
@@ -215,7 +220,7 @@ THETA_FLOOR = 1e-2
 
 
 def advance_block(cons, n, act, dt, dh, theta=DEFAULT_THETA, riemann=0, want_flux=False,
-                  retry_factor=RETRY_FACTOR, theta_floor=THETA_FLOOR):
+                  retry_factor=RETRY_FACTOR, theta_floor=THETA_FLOOR, scheme=NEW):
     """One MUSCL-Hancock step of a block with ghosts.
 
     cons: [5][Nz][Ny][Nx] with N_d = n_d + 4 on active dims, n_d otherwise.
@@ -230,11 +235,11 @@ def advance_block(cons, n, act, dt, dh, theta=DEFAULT_THETA, riemann=0, want_flu
     r = np.zeros(1, np.int32)
     st = lib().or_advance_block(_p(cons), _p(out), _p(flux), nx, ny, nz, int(act[0]),
                                 int(act[1]), int(act[2]), dt, dh, theta, retry_factor,
-                                theta_floor, riemann, _p(r, _ip))
+                                theta_floor, riemann, _p(r, _ip), scheme)
     return dict(out=out, status=st, retries=int(r[0]), flux=flux)
 
 
-def advance_patches(cons, dt_dh, theta=DEFAULT_THETA, riemann=0, want_flux=False):
+def advance_patches(cons, dt_dh, theta=DEFAULT_THETA, riemann=0, want_flux=False, scheme=NEW):
     """Batched step of independent 8^3 patches with 2-cell ghosts.
 
     cons [np][5][12][12][12] -> dict(out [np][5][8][8][8], status, retries,
@@ -247,14 +252,14 @@ def advance_patches(cons, dt_dh, theta=DEFAULT_THETA, riemann=0, want_flux=False
     flux = np.empty((npatch, 3, 5, 576)) if want_flux else None
     dt_dh = _f64(dt_dh).reshape(npatch, 2)
     lib().or_advance_patches(_p(cons), _p(out), npatch, _p(dt_dh), theta, RETRY_FACTOR,
-                             THETA_FLOOR, riemann, _p(st, _ip), _p(rt, _ip), _p(flux))
+                             THETA_FLOOR, riemann, _p(st, _ip), _p(rt, _ip), _p(flux), scheme)
     return dict(out=out, status=st, retries=rt, flux=flux)
 
 
-def cfl_dt(cons, dh, cfl=0.5, ndim=3, cfl_mode=0):
+def cfl_dt(cons, dh, cfl=0.5, ndim=3, cfl_mode=0, scheme=NEW):
     """Eq. (time_step_sound_speed): min over cells cons [5][n]."""
     cons = _f64(cons).reshape(5, -1)
-    return lib().or_cfl_dt(_p(cons), cons.shape[1], dh, cfl, ndim, cfl_mode)
+    return lib().or_cfl_dt(_p(cons), cons.shape[1], dh, cfl, ndim, cfl_mode, scheme)
 
 
 def count_advance_block(cons, n, act, dt, dh, theta=DEFAULT_THETA, riemann=0):
@@ -302,7 +307,8 @@ def fill_ghosts(interior, act, bc):
     return np.pad(interior, pads, mode=mode)
 
 
-def evolve(cons, act, dh, t_end, bc, cfl=0.5, theta=DEFAULT_THETA, riemann=0, max_steps=10**7):
+def evolve(cons, act, dh, t_end, bc, cfl=0.5, theta=DEFAULT_THETA, riemann=0, max_steps=10**7,
+           scheme=NEW):
     """Advance the whole domain to t_end: each step takes the CFL time step
     of the current state (clipped to reach t_end exactly), fills ghosts and
     applies one block step. Returns dict(cons, t, steps, retries)."""
@@ -314,13 +320,13 @@ def evolve(cons, act, dh, t_end, bc, cfl=0.5, theta=DEFAULT_THETA, riemann=0, ma
     steps = 0
     retries = 0
     while t < t_end and steps < max_steps:
-        dt = cfl_dt(cons, dh, cfl=cfl, ndim=ndim)
+        dt = cfl_dt(cons, dh, cfl=cfl, ndim=ndim, scheme=scheme)
         if not np.isfinite(dt):
             raise RuntimeError("unphysical state in CFL")
         if t + dt > t_end:
             dt = t_end - t
         r = advance_block(fill_ghosts(cons, act, bc), n, act, dt, dh, theta=theta,
-                          riemann=riemann)
+                          riemann=riemann, scheme=scheme)
         if r["status"] not in (BLK_OK, BLK_NOCONV):
             raise RuntimeError(f"block step failed with status {r['status']}")
         retries += r["retries"]

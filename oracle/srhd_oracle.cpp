@@ -133,7 +133,12 @@ template <class R> R df_dhtilde(R ht, R T, R dT, R m2) {
 // Primitive -> conserved (Section 2.3, Eqs. density, momentum, T_to_HTilde,
 // E_D). W = (rho, Ux, Uy, Uz, p) -> U = (D, Mx, My, Mz, Etilde).
 // ----------------------------------------------------------------------------
-template <class R> int prim2con(const R W[5], R U[5]) {
+// ori = 1 selects the "original scheme" the paper compares against (its
+// Sections 2.3 and 4): the fifth conserved variable is the total energy
+// E = D h gamma - p (Eq. definition of reduced energy, first form) instead of
+// Etilde, evolved with the flux M (Eq. E evoltion), and inverted from
+// (E/D)^2 - (|M|/D)^2 - 1, which cancels catastrophically for cold gas.
+template <class R> int prim2con(const R W[5], R U[5], int ori = 0) {
   R rho = W[0], ux = W[1], uy = W[2], uz = W[3], p = W[4];
   if (!(val(rho) > 0.0) || !(val(p) > 0.0)) return UNPHYSICAL;
   R T = p / rho;
@@ -147,6 +152,10 @@ template <class R> int prim2con(const R W[5], R U[5]) {
   U[1] = Dh * ux;                     // Eq. (momentum)
   U[2] = Dh * uy;
   U[3] = Dh * uz;
+  if (ori) {
+    U[4] = Dh * gamma - p;            // E = D h gamma - p
+    return OK;
+  }
   R m2 = h * h * u2;                  // (|M|/D)^2
   R f = f_of_htilde(ht, T, m2);
   R s = m2 + f;
@@ -157,12 +166,13 @@ template <class R> int prim2con(const R W[5], R U[5]) {
 // Left-hand side of Eq. (transcendental equation) and of Eq. (Unphysical
 // result): A = (Et/D)^2 + 2 (Et/D) - (|M|/D)^2, evaluated as
 // eD*(eD+2) - m2 with eD = Et/D and m2 = (Mx^2+My^2+Mz^2)/D^2.
-template <class R> R A_of_cons(const R U[5], R* m2_out) {
+template <class R> R A_of_cons(const R U[5], R* m2_out, int ori = 0) {
   R D = U[0];
   R M2 = U[1] * U[1] + U[2] * U[2] + U[3] * U[3];
   R m2 = M2 / (D * D);
   R eD = U[4] / D;
   *m2_out = m2;
+  if (ori) return (eD * eD - m2) - R(1.0);   // (E/D)^2 - (|M|/D)^2 - 1
   return eD * (eD + R(2.0)) - m2;
 }
 
@@ -193,7 +203,7 @@ struct Con2PriInfo { int iters; double htilde; double A; };
 // the step stops contracting at the rounding floor (|dh| >= |dh_prev| with
 // |dh| <= 1e-12 htilde); otherwise NOCONV after kNewtonMaxIter steps. A step
 // that would make htilde non-positive is replaced by halving htilde.
-template <class R> int con2pri(const R U[5], R W[5], R* ht_out, Con2PriInfo* info) {
+template <class R> int con2pri(const R U[5], R W[5], R* ht_out, Con2PriInfo* info, int ori = 0) {
   R D = U[0];
   if (!(val(D) > 0.0) || !is_finite(U[4])) {
     for (int v = 0; v < 5; ++v) W[v] = R(NAN);
@@ -201,7 +211,7 @@ template <class R> int con2pri(const R U[5], R W[5], R* ht_out, Con2PriInfo* inf
     return UNPHYSICAL;
   }
   R m2;
-  R A = A_of_cons(U, &m2);
+  R A = A_of_cons(U, &m2, ori);
   if (info) { info->A = val(A); info->iters = 0; }
   if (!(val(A) > kEpsUnphysical)) {      // Eq. (Unphysical result)
     for (int v = 0; v < 5; ++v) W[v] = R(NAN);
@@ -266,6 +276,7 @@ struct Params {
   int ndim;              // active dimensions for the CFL bound
   double cfl;            // C_CFL (Eq. time_step_sound_speed)
   int cfl_mode;          // 0 = signal speed (Eq. SMax), 1 = speed of light
+  int ori;               // 1 = original scheme (total energy E, flux M)
 };
 
 // Hybrid van Leer / generalised minmod slope limiter (Section 4.2 names it;
@@ -283,7 +294,7 @@ template <class R> R limited_slope(R dl, R dr, R theta) {
 
 // Physical flux in direction d (Eqs. D evolution, M evolution, ETilde
 // evolution): F = (D v, M v + p e_d, (Etilde + p) v), v = U^d / gamma.
-template <class R> void phys_flux(int d, const R W[5], const R U[5], R F[5]) {
+template <class R> void phys_flux(int d, const R W[5], const R U[5], R F[5], int ori = 0) {
   R u2 = W[1] * W[1] + W[2] * W[2] + W[3] * W[3];
   R gamma = sqrt(R(1.0) + u2);
   R v = W[1 + d] / gamma;
@@ -292,7 +303,7 @@ template <class R> void phys_flux(int d, const R W[5], const R U[5], R F[5]) {
   F[2] = U[2] * v;
   F[3] = U[3] * v;
   F[1 + d] = F[1 + d] + W[4];
-  F[4] = (U[4] + W[4]) * v;
+  F[4] = ori ? U[1 + d] : (U[4] + W[4]) * v;   // flux of E is M_d (Eq. E evoltion)
 }
 
 // Relativistic characteristic speeds lambda_-/+ along direction d with the TM
@@ -322,10 +333,10 @@ template <class R> void char_speeds(int d, const R W[5], R* lm, R* lp) {
 // mass flux, which for every state used here equals (Etilde + p) v.
 // Returns 1 if HLLC fell back to HLLE, else 0.
 template <class R> int riemann_flux(int d, int solver, const R WL[5], const R UL[5],
-                                    const R WR[5], const R UR[5], R F[5]) {
+                                    const R WR[5], const R UR[5], R F[5], int ori = 0) {
   R FL[5], FR[5];
-  phys_flux(d, WL, UL, FL);
-  phys_flux(d, WR, UR, FR);
+  phys_flux(d, WL, UL, FL, ori);
+  phys_flux(d, WR, UR, FR, ori);
   R lmL, lpL, lmR, lpR;
   char_speeds(d, WL, &lmL, &lpL);
   char_speeds(d, WR, &lmR, &lpR);
@@ -343,8 +354,8 @@ template <class R> int riemann_flux(int d, int solver, const R WL[5], const R UL
   if (solver == 0) {
     // Contact speed: smaller root of FE lam^2 - (E + Fm) lam + m = 0 on the
     // HLL state (total energy), in the cancellation-free form.
-    R E = Uhll[4] + Uhll[0];
-    R FE = Fhll[4] + Fhll[0];
+    R E = ori ? Uhll[4] : Uhll[4] + Uhll[0];
+    R FE = ori ? Fhll[4] : Fhll[4] + Fhll[0];
     R m = Uhll[1 + d];
     R Fm = Fhll[1 + d];
     R B = E + Fm;
@@ -408,6 +419,7 @@ template <class R> R smax_of_prim(const R W[5], int ndim) {
 // ----------------------------------------------------------------------------
 template <class R> struct Block {
   int n[3], g[3], N[3], act[3];
+  int ori;                     // original scheme (total energy)
   std::vector<R> W;            // prims [5][Ncells]
   std::vector<int8_t> Wstat;   // -1 not computed, else con2pri status
   std::vector<R> face;         // predicted face cons [Ncells][3][2][5]
@@ -425,7 +437,7 @@ template <class R> int block_prim(Block<R>& B, int i, int j, int k, R out[5]) {
   if (B.Wstat[c] < 0) {
     R U[5], W[5];
     for (int v = 0; v < 5; ++v) U[v] = B.in[v * nc + c];
-    int st = con2pri(U, W, (R*)nullptr, (Con2PriInfo*)nullptr);
+    int st = con2pri(U, W, (R*)nullptr, (Con2PriInfo*)nullptr, B.ori);
     for (int v = 0; v < 5; ++v) B.W[v * nc + c] = W[v];
     B.Wstat[c] = (int8_t)st;
   }
@@ -459,8 +471,8 @@ template <class R> int block_faces(Block<R>& B, int i, int j, int k, R theta, R 
       Wf[d][1][v] = W[v] + R(0.5) * dW;
     }
     for (int s = 0; s < 2; ++s) {
-      if (prim2con(Wf[d][s], Uf[d][s]) != OK) bad = 1;
-      phys_flux(d, Wf[d][s], Uf[d][s], Ff[d][s]);
+      if (prim2con(Wf[d][s], Uf[d][s], B.ori) != OK) bad = 1;
+      phys_flux(d, Wf[d][s], Uf[d][s], Ff[d][s], B.ori);
     }
   }
   R dF[5];
@@ -494,6 +506,7 @@ int advance_block(const R* in, R* out, R* flux_out, const int n[3], const int ac
     B.N[d] = n[d] + 2 * B.g[d];
   }
   B.in = in;
+  B.ori = P.ori;
   int nc = B.ncell();
   B.W.assign((size_t)5 * nc, R(0.0));
   B.Wstat.assign(nc, -1);
@@ -537,12 +550,12 @@ int advance_block(const R* in, R* out, R* flux_out, const int n[3], const int ac
               UL[v] = B.face[((size_t)cl * 6 + d * 2 + 1) * 5 + v];
               UR[v] = B.face[((size_t)cr * 6 + d * 2 + 0) * 5 + v];
             }
-            int a = con2pri(UL, WL, (R*)nullptr, (Con2PriInfo*)nullptr);
-            int b = con2pri(UR, WR, (R*)nullptr, (Con2PriInfo*)nullptr);
+            int a = con2pri(UL, WL, (R*)nullptr, (Con2PriInfo*)nullptr, P.ori);
+            int b = con2pri(UR, WR, (R*)nullptr, (Con2PriInfo*)nullptr, P.ori);
             if (a == UNPHYSICAL || b == UNPHYSICAL) { fail = 1; break; }
             if (a == NOCONV || b == NOCONV) noconv = 1;
             R F[5];
-            riemann_flux(d, P.riemann, WL, UL, WR, UR, F);
+            riemann_flux(d, P.riemann, WL, UL, WR, UR, F, P.ori);
             int fi = (kk * ext[1] + jj) * ext[0] + ii;
             for (int v = 0; v < 5; ++v) Fd[d][(size_t)v * nf[d] + fi] = F[v];
           }
@@ -577,7 +590,7 @@ int advance_block(const R* in, R* out, R* flux_out, const int n[3], const int ac
               out[(size_t)v * nint + o] = Un[v];
             }
             R m2;
-            R A = A_of_cons(Un, &m2);
+            R A = A_of_cons(Un, &m2, P.ori);
             if (!(val(Un[0]) > 0.0) || !(val(A) > kEpsUnphysical)) fail = 1;
           }
     }
@@ -893,11 +906,11 @@ double or_htilde_bisect(double A, double m2) { return htilde_bisect(A, m2); }
 double or_limited_slope(double dl, double dr, double theta) { return limited_slope(dl, dr, theta); }
 
 // Batched prim2con: prim [5][n] -> cons [5][n]; status [n] (nullable).
-void or_prim2con(const double* prim, double* cons, int64_t n, int32_t* status) {
+void or_prim2con(const double* prim, double* cons, int64_t n, int32_t* status, int scheme) {
   for (int64_t i = 0; i < n; ++i) {
     double W[5], U[5];
     for (int v = 0; v < 5; ++v) W[v] = prim[v * n + i];
-    int st = prim2con(W, U);
+    int st = prim2con(W, U, scheme);
     for (int v = 0; v < 5; ++v) cons[v * n + i] = U[v];
     if (status) status[i] = st;
   }
@@ -906,12 +919,12 @@ void or_prim2con(const double* prim, double* cons, int64_t n, int32_t* status) {
 // Batched con2pri: cons [5][n] -> prim [5][n]; status, iters, htilde, A
 // (each nullable).
 void or_con2pri(const double* cons, double* prim, int64_t n, int32_t* status,
-                int32_t* iters, double* htilde, double* A) {
+                int32_t* iters, double* htilde, double* A, int scheme) {
   for (int64_t i = 0; i < n; ++i) {
     double U[5], W[5], ht = NAN;
     for (int v = 0; v < 5; ++v) U[v] = cons[v * n + i];
     Con2PriInfo info;
-    int st = con2pri(U, W, &ht, &info);
+    int st = con2pri(U, W, &ht, &info, scheme);
     for (int v = 0; v < 5; ++v) prim[v * n + i] = W[v];
     if (status) status[i] = st;
     if (iters) iters[i] = info.iters;
@@ -921,11 +934,13 @@ void or_con2pri(const double* cons, double* prim, int64_t n, int32_t* status,
 }
 
 // One physical flux / Riemann flux evaluation (for unit tests).
-void or_phys_flux(int d, const double* W, const double* U, double* F) { phys_flux(d, W, U, F); }
+void or_phys_flux(int d, const double* W, const double* U, double* F, int scheme) {
+  phys_flux(d, W, U, F, scheme);
+}
 void or_char_speeds(int d, const double* W, double* lm, double* lp) { char_speeds(d, W, lm, lp); }
 int or_riemann_flux(int d, int solver, const double* WL, const double* UL, const double* WR,
-                    const double* UR, double* F) {
-  return riemann_flux(d, solver, WL, UL, WR, UR, F);
+                    const double* UR, double* F, int scheme) {
+  return riemann_flux(d, solver, WL, UL, WR, UR, F, scheme);
 }
 double or_smax(const double* W, int ndim) { return smax_of_prim(W, ndim); }
 
@@ -933,10 +948,11 @@ double or_smax(const double* W, int ndim) { return smax_of_prim(W, ndim); }
 // receives the face fluxes, direction-major [d][5][faces of d].
 int or_advance_block(const double* in, double* out, double* flux_out, int nx, int ny, int nz,
                      int actx, int acty, int actz, double dt, double dh, double theta,
-                     double retry_factor, double theta_floor, int riemann, int32_t* retries) {
+                     double retry_factor, double theta_floor, int riemann, int32_t* retries,
+                     int scheme) {
   int n[3] = {nx, ny, nz};
   int act[3] = {actx, acty, actz};
-  Params P{theta, retry_factor, theta_floor, riemann, actx + acty + actz, 0.5, 0};
+  Params P{theta, retry_factor, theta_floor, riemann, actx + acty + actz, 0.5, 0, scheme};
   int r = 0;
   int st = advance_block(in, out, flux_out, n, act, dt, dh, P, &r);
   if (retries) *retries = r;
@@ -948,10 +964,10 @@ int or_advance_block(const double* in, double* out, double* flux_out, int nx, in
 // status [np] and retries [np] (nullable).
 void or_advance_patches(const double* in, double* out, int64_t npatch, const double* dt_dh,
                         double theta, double retry_factor, double theta_floor, int riemann,
-                        int32_t* status, int32_t* retries, double* flux_out) {
+                        int32_t* status, int32_t* retries, double* flux_out, int scheme) {
   const int n[3] = {8, 8, 8};
   const int act[3] = {1, 1, 1};
-  Params P{theta, retry_factor, theta_floor, riemann, 3, 0.5, 0};
+  Params P{theta, retry_factor, theta_floor, riemann, 3, 0.5, 0, scheme};
   const size_t nflux = (size_t)3 * 5 * 9 * 64;
   for (int64_t p = 0; p < npatch; ++p) {
     int r = 0;
@@ -966,13 +982,14 @@ void or_advance_patches(const double* in, double* out, int64_t npatch, const dou
 // CFL time step over cells cons [5][n] (Eq. time_step_sound_speed): returns
 // min_i C dh / S_max,i (cfl_mode 0) or C dh (cfl_mode 1, speed of light);
 // NaN if any cell is unphysical.
-double or_cfl_dt(const double* cons, int64_t n, double dh, double cfl, int ndim, int cfl_mode) {
+double or_cfl_dt(const double* cons, int64_t n, double dh, double cfl, int ndim, int cfl_mode,
+                 int scheme) {
   if (cfl_mode == 1) return cfl * dh;
   double smax = 0.0;
   for (int64_t i = 0; i < n; ++i) {
     double U[5], W[5];
     for (int v = 0; v < 5; ++v) U[v] = cons[v * n + i];
-    int st = con2pri(U, W, (double*)nullptr, (Con2PriInfo*)nullptr);
+    int st = con2pri(U, W, (double*)nullptr, (Con2PriInfo*)nullptr, scheme);
     if (st == UNPHYSICAL) return NAN;
     smax = std::max(smax, smax_of_prim(W, ndim));
   }
@@ -986,7 +1003,7 @@ void or_count_advance_block(const double* in, int nx, int ny, int nz, int actx, 
                             uint64_t* counts) {
   int n[3] = {nx, ny, nz};
   int act[3] = {actx, acty, actz};
-  Params P{theta, 0.75, 1e-2, riemann, actx + acty + actz, 0.5, 0};
+  Params P{theta, 0.75, 1e-2, riemann, actx + acty + actz, 0.5, 0, 0};
   int nin = 1;
   for (int d = 0; d < 3; ++d) nin *= n[d] + (act[d] ? 4 : 0);
   std::vector<OpCount> cin((size_t)5 * nin), cout((size_t)5 * nx * ny * nz);

@@ -17,6 +17,7 @@ SRHD_FP64, SRHD_MIXED, SRHD_MIXED_CF = 0, 1, 2
 SRHD_HLLC, SRHD_HLLE = 0, 1
 SRHD_CFL_SIGNAL, SRHD_CFL_LIGHT = 0, 1
 SRHD_BC_PERIODIC, SRHD_BC_OUTFLOW = 0, 1
+SRHD_SCHEME_REDUCED, SRHD_SCHEME_TOTAL = 0, 1
 CELL_OK, CELL_UNPHYSICAL, CELL_NOCONV = 0, 1, 2
 PATCH_UNPHYSICAL, PATCH_BAD_INPUT, PATCH_NOCONV = 1, 2, 4
 
@@ -31,7 +32,7 @@ class Params(ctypes.Structure):
                 ("retry_factor", ctypes.c_double), ("theta_floor", ctypes.c_double),
                 ("riemann", ctypes.c_int32), ("cfl_mode", ctypes.c_int32),
                 ("ndim", ctypes.c_int32), ("newton_max_iter", ctypes.c_int32),
-                ("patch_variant", ctypes.c_int32)]
+                ("patch_variant", ctypes.c_int32), ("scheme", ctypes.c_int32)]
 
 
 class SrhdError(RuntimeError):

@@ -105,6 +105,8 @@ srhd_status check_params(const srhd_params* p) {
   if (p->ndim < 1 || p->ndim > 3) return fail(SRHD_ERR_ARG, "ndim must be 1, 2 or 3");
   if (p->newton_max_iter < 0 || p->newton_max_iter > 1000)
     return fail(SRHD_ERR_ARG, "newton_max_iter must be in [0, 1000]");
+  if (p->scheme != SRHD_SCHEME_REDUCED && p->scheme != SRHD_SCHEME_TOTAL)
+    return fail(SRHD_ERR_ARG, "scheme must be SRHD_SCHEME_REDUCED or SRHD_SCHEME_TOTAL");
   if (p->patch_variant < 0 || p->patch_variant >= srhd::kPatchVariants)
     return fail(SRHD_ERR_ARG, "patch_variant must be in [0, %d)", srhd::kPatchVariants);
   return SRHD_OK;
@@ -140,6 +142,7 @@ srhd_status srhd_default_params(srhd_params* p) {
   p->ndim = 3;
   p->newton_max_iter = 0;
   p->patch_variant = 0;
+  p->scheme = SRHD_SCHEME_REDUCED;
   return SRHD_OK;
 }
 
@@ -213,7 +216,7 @@ srhd_status srhd_prim2con(srhd_ctx* c, srhd_prec prec, const void* prim, void* c
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   int grid = grid_for(c, n, 16);
   cudaError_t e = dispatch(prec, [&](auto L) {
-    return decltype(L)::prim2con(prim, cons, n, var_stride, grid, s);
+    return decltype(L)::prim2con(prim, cons, n, var_stride, c->params.scheme, grid, s);
   });
   return e == cudaSuccess ? SRHD_OK : cuda_fail(e, "prim2con launch");
 }
@@ -230,7 +233,8 @@ srhd_status srhd_con2pri(srhd_ctx* c, srhd_prec prec, const void* cons, void* pr
   int grid = grid_for(c, n, 16);
   int maxit = newton_maxit(c, prec);
   cudaError_t e = dispatch(prec, [&](auto L) {
-    return decltype(L)::con2pri(cons, prim, n, var_stride, cell_status, maxit, grid, s);
+    return decltype(L)::con2pri(cons, prim, n, var_stride, cell_status, maxit, c->params.scheme,
+                                grid, s);
   });
   return e == cudaSuccess ? SRHD_OK : cuda_fail(e, "con2pri launch");
 }
@@ -268,6 +272,7 @@ static void fill_common(const srhd_ctx* c, srhd_prec prec, srhd::PatchArgs& a) {
   a.cfl_mode = c->params.cfl_mode;
   a.ndim = c->params.ndim;
   a.maxit = newton_maxit(c, prec);
+  a.ori = c->params.scheme == SRHD_SCHEME_TOTAL ? 1 : 0;
   a.partial_dt = nullptr;
   a.partial_bad = nullptr;
 }
@@ -340,7 +345,7 @@ srhd_status srhd_cfl_dt(srhd_ctx* c, srhd_prec prec, const void* cons, int32_t n
     int maxit = newton_maxit(c, prec);
     e = dispatch(prec, [&](auto L) {
       return decltype(L)::cfl(cons, ncell, dh, c->params.cfl, c->params.ndim, c->params.cfl_mode,
-                              maxit, c->partial_dt, c->partial_bad, grid, s);
+                              maxit, c->params.scheme, c->partial_dt, c->partial_bad, grid, s);
     });
     if (e != cudaSuccess) return cuda_fail(e, "cfl launch");
   }

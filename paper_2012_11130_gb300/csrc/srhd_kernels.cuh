@@ -51,6 +51,7 @@ struct PatchArgs {
   double theta0, retry_factor, theta_floor, cfl;
   int riemann, cfl_mode, ndim, maxit;
   int flux_only;
+  int ori;                // 1: original scheme (total energy E, flux M)
 };
 
 template <class S> struct SmemLayout {  // S: storage type
@@ -138,7 +139,7 @@ template <class S> __device__ __forceinline__ S* face_slot(S* face, int d, int s
 template <int d, class R, class S>
 __device__ __forceinline__ void recon_direction(const S* prim, int tc, const PrimX<R>& W, R theta,
                                                 int i, int j, int k, bool interior, S* face,
-                                                R dF[5], int& bad) {
+                                                R dF[5], int& bad, int ori) {
   constexpr int off = (d == 0) ? 1 : ((d == 1) ? kG : kG * kG);
   R wc[5] = {W.rho, W.u[0], W.u[1], W.u[2], W.p};
   PrimX<R> Wm, Wp;
@@ -154,10 +155,10 @@ __device__ __forceinline__ void recon_direction(const S* prim, int tc, const Pri
   Wm.rho = fm[0]; Wm.u[0] = fm[1]; Wm.u[1] = fm[2]; Wm.u[2] = fm[3]; Wm.p = fm[4];
   Wp.rho = fp[0]; Wp.u[0] = fp[1]; Wp.u[1] = fp[2]; Wp.u[2] = fp[3]; Wp.p = fp[4];
   R Um[5], Up[5], Fm[5], Fp[5];
-  if (!prim2con(Wm, Um)) bad = 1;
-  if (!prim2con(Wp, Up)) bad = 1;
-  phys_flux<d>(Wm, Um, Fm);
-  phys_flux<d>(Wp, Up, Fp);
+  if (!prim2con(Wm, Um, ori)) bad = 1;
+  if (!prim2con(Wp, Up, ori)) bad = 1;
+  phys_flux<d>(Wm, Um, Fm, ori);
+  phys_flux<d>(Wp, Up, Fp, ori);
 #pragma unroll
   for (int v = 0; v < 5; ++v) dF[v] = dF[v] + (Fp[v] - Fm[v]);
   const int cd = (d == 0) ? i : ((d == 1) ? j : k);
@@ -215,7 +216,7 @@ template <int d> __device__ __forceinline__ int face_owner(int fi, int side) {
 // state by half a limited slope and half a time step).
 template <int d, class P, bool PAIR>
 __device__ __forceinline__ int face_flux(typename P::S* face, const typename P::S* hts, int fi,
-                                         int solver, int maxit, int& code) {
+                                         int solver, int maxit, int& code, int ori) {
   using S = typename P::S;
   using R = S;
   const S gL = hts[face_owner<d>(fi, 0)], gR = hts[face_owner<d>(fi, 1)];
@@ -228,17 +229,17 @@ __device__ __forceinline__ int face_flux(typename P::S* face, const typename P::
   PrimX<R> WL, WR;
   int sl, sr;
   if constexpr (PAIR) {
-    con2pri_x2<P>(UL, UR, WL, WR, maxit, sl, sr, gL, gR);
+    con2pri_x2<P>(UL, UR, WL, WR, maxit, sl, sr, gL, gR, ori);
   } else {
-    sl = con2pri<P>(UL[0], UL[1], UL[2], UL[3], UL[4], WL, maxit, gL);
-    sr = con2pri<P>(UR[0], UR[1], UR[2], UR[3], UR[4], WR, maxit, gR);
+    sl = con2pri<P>(UL[0], UL[1], UL[2], UL[3], UL[4], WL, maxit, gL, ori);
+    sr = con2pri<P>(UR[0], UR[1], UR[2], UR[3], UR[4], WR, maxit, gR, ori);
   }
   if (sl == 2 || sr == 2) code |= CODE_NOCONV;
   int fail = (sl == 1 || sr == 1);
   R FL_[5] = {R(UL[0]), R(UL[1]), R(UL[2]), R(UL[3]), R(UL[4])};
   R FR_[5] = {R(UR[0]), R(UR[1]), R(UR[2]), R(UR[3]), R(UR[4])};
   R F[5];
-  riemann<d>(solver, WL, FL_, WR, FR_, F);
+  riemann<d>(solver, WL, FL_, WR, FR_, F, ori);
 #pragma unroll
   for (int v = 0; v < 5; ++v) face_slot(face, d, 0, v)[fi] = S(F[v]);
   return fail;
@@ -257,6 +258,7 @@ __global__ void __launch_bounds__(NT, MINB) patch_kernel(PatchArgs a) {
   __shared__ int s_bad[NT / 32];
   const int tid = threadIdx.x;
   const int maxit = a.maxit;
+  const int ori = a.ori;
 
   double dt_min = DBL_MAX;
   int cfl_bad = 0;
@@ -280,7 +282,7 @@ __global__ void __launch_bounds__(NT, MINB) patch_kernel(PatchArgs a) {
         }
         PrimX<R> Wa, Wb;
         int sa, sb;
-        con2pri_x2<P>(Ua, Ub, Wa, Wb, maxit, sa, sb);
+        con2pri_x2<P>(Ua, Ub, Wa, Wb, maxit, sa, sb, S(0), S(0), ori);
         if (sa == 1 || sb == 1) code |= CODE_BAD_INPUT;
         if (sa == 2 || sb == 2) code |= CODE_NOCONV;
         prim[ca] = S(Wa.rho);
@@ -301,7 +303,7 @@ __global__ void __launch_bounds__(NT, MINB) patch_kernel(PatchArgs a) {
         const int c = needed_tile_cell(r);
         PrimX<R> W;
         int st = con2pri<P>(in[c], in[kGC + c], in[2 * kGC + c], in[3 * kGC + c],
-                            in[4 * kGC + c], W, maxit);
+                            in[4 * kGC + c], W, maxit, S(0), ori);
         if (st == 1) code |= CODE_BAD_INPUT;
         if (st == 2) code |= CODE_NOCONV;
         prim[c] = S(W.rho);
@@ -340,9 +342,9 @@ __global__ void __launch_bounds__(NT, MINB) patch_kernel(PatchArgs a) {
           W.u[2] = R(prim[3 * kGC + tc]);
           W.p = R(prim[4 * kGC + tc]);
           R dF[5] = {R(0), R(0), R(0), R(0), R(0)};
-          recon_direction<0>(prim, tc, W, theta, i, j, k, interior, face, dF, fail);
-          recon_direction<1>(prim, tc, W, theta, i, j, k, interior, face, dF, fail);
-          recon_direction<2>(prim, tc, W, theta, i, j, k, interior, face, dF, fail);
+          recon_direction<0>(prim, tc, W, theta, i, j, k, interior, face, dF, fail, ori);
+          recon_direction<1>(prim, tc, W, theta, i, j, k, interior, face, dF, fail, ori);
+          recon_direction<2>(prim, tc, W, theta, i, j, k, interior, face, dF, fail, ori);
           halfstep_direction<0>(i, j, k, interior, face, dF, half);
           halfstep_direction<1>(i, j, k, interior, face, dF, half);
           halfstep_direction<2>(i, j, k, interior, face, dF, half);
@@ -351,9 +353,10 @@ __global__ void __launch_bounds__(NT, MINB) patch_kernel(PatchArgs a) {
         // ---- phase 3: Riemann fluxes ----------------------------------------
         for (int f = tid; f < 3 * kNF; f += NT) {
           const int d = f / kNF, fi = f - d * kNF;
-          if (d == 0) fail |= face_flux<0, P, PAIR>(face, hts, fi, a.riemann, maxit, code);
-          else if (d == 1) fail |= face_flux<1, P, PAIR>(face, hts, fi, a.riemann, maxit, code);
-          else fail |= face_flux<2, P, PAIR>(face, hts, fi, a.riemann, maxit, code);
+          if (d == 0) fail |= face_flux<0, P, PAIR>(face, hts, fi, a.riemann, maxit, code, ori);
+          else if (d == 1)
+            fail |= face_flux<1, P, PAIR>(face, hts, fi, a.riemann, maxit, code, ori);
+          else fail |= face_flux<2, P, PAIR>(face, hts, fi, a.riemann, maxit, code, ori);
         }
         fail = __syncthreads_or(fail);
         if (a.flux_only) {
@@ -395,7 +398,7 @@ __global__ void __launch_bounds__(NT, MINB) patch_kernel(PatchArgs a) {
                 out[v * kNC + c] = Un[q][v];
               }
               typename P::AT Ac, m2c;
-              ok[q] = A_and_m2<P>(Un[q][0], Un[q][1], Un[q][2], Un[q][3], Un[q][4], Ac, m2c);
+              ok[q] = A_and_m2<P>(Un[q][0], Un[q][1], Un[q][2], Un[q][3], Un[q][4], Ac, m2c, ori);
               if (!ok[q]) fail4 = 1;
             }
             if (a.partial_dt) {
@@ -405,10 +408,11 @@ __global__ void __launch_bounds__(NT, MINB) patch_kernel(PatchArgs a) {
                 PrimX<R> W[NPC];
                 if constexpr (PAIR) {
                   int s0, s1;
-                  con2pri_x2<P>(Un[0], Un[1], W[0], W[1], maxit, s0, s1, g0[0], g0[NPC - 1]);
+                  con2pri_x2<P>(Un[0], Un[1], W[0], W[1], maxit, s0, s1, g0[0], g0[NPC - 1],
+                                ori);
                 } else {
                   con2pri<P>(Un[0][0], Un[0][1], Un[0][2], Un[0][3], Un[0][4], W[0], maxit,
-                             g0[0]);
+                             g0[0], ori);
                 }
 #pragma unroll
                 for (int q = 0; q < NPC; ++q) {
@@ -488,7 +492,7 @@ __global__ void cfl_finalize_kernel(const double* partial, const int32_t* bad, i
 
 // ---- batched conversions ----------------------------------------------------
 template <class S>
-__global__ void prim2con_kernel(const S* prim, S* cons, int64_t n, int64_t stride) {
+__global__ void prim2con_kernel(const S* prim, S* cons, int64_t n, int64_t stride, int ori) {
   using R = S;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
@@ -499,7 +503,7 @@ __global__ void prim2con_kernel(const S* prim, S* cons, int64_t n, int64_t strid
     W.u[2] = prim[3 * stride + i];
     W.p = prim[4 * stride + i];
     R U[5];
-    prim2con(W, U);
+    prim2con(W, U, ori);
 #pragma unroll
     for (int v = 0; v < 5; ++v) cons[v * stride + i] = U[v];
   }
@@ -507,14 +511,14 @@ __global__ void prim2con_kernel(const S* prim, S* cons, int64_t n, int64_t strid
 
 template <class P>
 __global__ void con2pri_kernel(const typename P::S* cons, typename P::S* prim, int64_t n,
-                               int64_t stride, int32_t* status, int maxit) {
+                               int64_t stride, int32_t* status, int maxit, int ori) {
   using S = typename P::S;
   using R = S;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     PrimX<R> W;
     int st = con2pri<P>(cons[i], cons[stride + i], cons[2 * stride + i], cons[3 * stride + i],
-                        cons[4 * stride + i], W, maxit);
+                        cons[4 * stride + i], W, maxit, S(0), ori);
     prim[i] = W.rho;
     prim[stride + i] = W.u[0];
     prim[2 * stride + i] = W.u[1];
@@ -528,7 +532,8 @@ __global__ void con2pri_kernel(const typename P::S* cons, typename P::S* prim, i
 template <class P, int NT>
 __global__ void __launch_bounds__(NT) cfl_kernel(const typename P::S* cons, int64_t ncell,
                                                  double dh, double cfl, int ndim, int mode,
-                                                 int maxit, double* partial, int32_t* bad_out) {
+                                                 int maxit, double* partial, int32_t* bad_out,
+                                                 int ori) {
   using S = typename P::S;
   using R = S;
   __shared__ double s_red[NT / 32];
@@ -540,7 +545,7 @@ __global__ void __launch_bounds__(NT) cfl_kernel(const typename P::S* cons, int6
     const int64_t p = q / kNC, c = q - p * kNC;
     const S* b = cons + p * 5 * kNC + c;
     PrimX<R> W;
-    int st = con2pri<P>(b[0], b[kNC], b[2 * kNC], b[3 * kNC], b[4 * kNC], W, maxit);
+    int st = con2pri<P>(b[0], b[kNC], b[2 * kNC], b[3 * kNC], b[4 * kNC], W, maxit, S(0), ori);
     if (st == 1) { bad = 1; continue; }
     if (mode == 1) m = fmin(m, cfl * dh);
     else m = fmin(m, cfl * dh / double(smax_of(W, ndim)));
@@ -595,12 +600,13 @@ template <class P> struct Launch {
   static cudaError_t setup();
   static int patch_blocks_per_sm(int variant);
   static cudaError_t patches(const PatchArgs& a, int variant, int grid, cudaStream_t s);
-  static cudaError_t prim2con(const void* prim, void* cons, int64_t n, int64_t stride, int grid,
-                              cudaStream_t s);
+  static cudaError_t prim2con(const void* prim, void* cons, int64_t n, int64_t stride, int ori,
+                              int grid, cudaStream_t s);
   static cudaError_t con2pri(const void* cons, void* prim, int64_t n, int64_t stride,
-                             int32_t* status, int maxit, int grid, cudaStream_t s);
+                             int32_t* status, int maxit, int ori, int grid, cudaStream_t s);
   static cudaError_t cfl(const void* cons, int64_t ncell, double dh, double cfl, int ndim, int mode,
-                         int maxit, double* partial, int32_t* bad, int grid, cudaStream_t s);
+                         int maxit, int ori, double* partial, int32_t* bad, int grid,
+                         cudaStream_t s);
   static cudaError_t fill_ghosts(const void* interior, void* ghosted, int npx, int npy, int npz,
                                  const int32_t* bc, int grid, cudaStream_t s);
 };

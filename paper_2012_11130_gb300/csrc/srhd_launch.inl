@@ -78,30 +78,31 @@ cudaError_t Launch<P>::patches(const PatchArgs& a, int variant, int grid, cudaSt
 }
 
 template <class P>
-cudaError_t Launch<P>::prim2con(const void* prim, void* cons, int64_t n, int64_t stride, int grid,
-                                cudaStream_t s) {
+cudaError_t Launch<P>::prim2con(const void* prim, void* cons, int64_t n, int64_t stride, int ori,
+                                int grid, cudaStream_t s) {
   using S = typename P::S;
   prim2con_kernel<S><<<grid, 256, 0, s>>>(static_cast<const S*>(prim), static_cast<S*>(cons), n,
-                                          stride);
+                                          stride, ori);
   return cudaGetLastError();
 }
 
 template <class P>
 cudaError_t Launch<P>::con2pri(const void* cons, void* prim, int64_t n, int64_t stride,
-                               int32_t* status, int maxit, int grid, cudaStream_t s) {
+                               int32_t* status, int maxit, int ori, int grid, cudaStream_t s) {
   using S = typename P::S;
   con2pri_kernel<P><<<grid, 256, 0, s>>>(static_cast<const S*>(cons), static_cast<S*>(prim), n,
-                                         stride, status, maxit);
+                                         stride, status, maxit, ori);
   return cudaGetLastError();
 }
 
 template <class P>
 cudaError_t Launch<P>::cfl(const void* cons, int64_t ncell, double dh, double cfl, int ndim,
-                           int mode, int maxit, double* partial, int32_t* bad, int grid,
+                           int mode, int maxit, int ori, double* partial, int32_t* bad, int grid,
                            cudaStream_t s) {
   using S = typename P::S;
   cfl_kernel<P, kCflThreads><<<grid, kCflThreads, 0, s>>>(static_cast<const S*>(cons), ncell, dh,
-                                                          cfl, ndim, mode, maxit, partial, bad);
+                                                          cfl, ndim, mode, maxit, partial, bad,
+                                                          ori);
   return cudaGetLastError();
 }
 

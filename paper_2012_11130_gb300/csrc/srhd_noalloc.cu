@@ -53,7 +53,7 @@ template <class P>
 __global__ void __launch_bounds__(kThreads) patch_cfl_kernel(const typename P::S* cons, double dh,
                                                              double cfl, int ndim, int mode,
                                                              int maxit, double* patch_dt,
-                                                             int32_t* patch_bad) {
+                                                             int32_t* patch_bad, int ori) {
   using S = typename P::S;
   using R = S;
   __shared__ double s_m[kThreads / 32];
@@ -64,7 +64,8 @@ __global__ void __launch_bounds__(kThreads) patch_cfl_kernel(const typename P::S
   for (int c = threadIdx.x; c < kCells; c += kThreads) {
     srhd::PrimX<R> W;
     int st = srhd::con2pri<P>(base[c], base[kCells + c], base[2 * kCells + c],
-                              base[3 * kCells + c], base[4 * kCells + c], W, maxit);
+                              base[3 * kCells + c], base[4 * kCells + c], W, maxit,
+                              S(0), ori);
     if (st == 1) { bad = 1; continue; }
     m = (mode == 1) ? fmin(m, cfl * dh) : fmin(m, cfl * dh / double(srhd::smax_of(W, ndim)));
   }
@@ -164,6 +165,9 @@ extern "C" srhd_status srhd_cfl_dt_noalloc(srhd_prec prec, const void* cons, int
     return noalloc_fail(SRHD_ERR_ARG, "invalid cfl_mode");
   if (p.newton_max_iter < 0 || p.newton_max_iter > 1000)
     return noalloc_fail(SRHD_ERR_ARG, "newton_max_iter must be in [0, 1000]");
+  if (p.scheme != SRHD_SCHEME_REDUCED && p.scheme != SRHD_SCHEME_TOTAL)
+    return noalloc_fail(SRHD_ERR_ARG, "invalid scheme");
+  const int ori = p.scheme == SRHD_SCHEME_TOTAL ? 1 : 0;
   double* patch_dt = nullptr;
   int32_t* patch_bad = nullptr;
   srhd_status st = scratch_for_current_device(&patch_dt, &patch_bad);
@@ -174,15 +178,15 @@ extern "C" srhd_status srhd_cfl_dt_noalloc(srhd_prec prec, const void* cons, int
     if (prec == SRHD_FP64)
       patch_cfl_kernel<srhd::PrecFP64><<<npatch, kThreads, 0, s>>>(
           static_cast<const double*>(cons), dh, p.cfl, p.ndim, p.cfl_mode, maxit, patch_dt,
-          patch_bad);
+          patch_bad, ori);
     else if (prec == SRHD_MIXED)
       patch_cfl_kernel<srhd::PrecMixed><<<npatch, kThreads, 0, s>>>(
           static_cast<const float*>(cons), dh, p.cfl, p.ndim, p.cfl_mode, maxit, patch_dt,
-          patch_bad);
+          patch_bad, ori);
     else
       patch_cfl_kernel<srhd::PrecMixedCF><<<npatch, kThreads, 0, s>>>(
           static_cast<const float*>(cons), dh, p.cfl, p.ndim, p.cfl_mode, maxit, patch_dt,
-          patch_bad);
+          patch_bad, ori);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return noalloc_fail(SRHD_ERR_CUDA, cudaGetErrorString(e));
   }

@@ -125,12 +125,16 @@ struct PrecMixedCF {  // SRHD_MIXED_CF: float, A by a compensated float sum
 
 // A = (Et/D)^2 + 2 Et/D - (|M|/D)^2 in double (Eq. transcendental equation,
 // left-hand side; Eq. Unphysical result) and m^2 = (|M|/D)^2.
+// ori = 1: the original scheme's total energy E in the fifth slot, and
+// A = (E/D)^2 - (|M|/D)^2 - 1 (Section 2.3: the form that cancels for cold gas).
 template <class S>
-__device__ __forceinline__ double A_of_cons(S D, S Mx, S My, S Mz, S Et, double& m2) {
+__device__ __forceinline__ double A_of_cons(S D, S Mx, S My, S Mz, S Et, double& m2,
+                                            int ori = 0) {
   double rD = 1.0 / double(D);
   double eD = double(Et) * rD;
   double M2 = double(Mx) * double(Mx) + double(My) * double(My) + double(Mz) * double(Mz);
   m2 = M2 * rD * rD;
+  if (ori) return (eD * eD - m2) - 1.0;
   return eD * (eD + 2.0) - m2;
 }
 
@@ -157,7 +161,7 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
 // (exact), which keeps the products and their error parts clear of the float
 // overflow and underflow (flush-to-zero) ranges.
 __device__ __forceinline__ bool A_comp_float(float D, float Mx, float My, float Mz, float Et,
-                                             float& A, float& m2) {
+                                             float& A, float& m2, int ori = 0) {
   const int ex = (__float_as_int(D) >> 23) & 0xff;
   if (!(D > 0.0f) || ex > 253) return false;  // non-positive, denormal-flushed, huge or NaN
   const float sc = __int_as_float((254 - ex) << 23);   // 2^(127 - ex): D * sc in [1, 2)
@@ -165,9 +169,15 @@ __device__ __forceinline__ bool A_comp_float(float D, float Mx, float My, float 
   const float mx = __fmul_rn(Mx, sc), my = __fmul_rn(My, sc), mz = __fmul_rn(Mz, sc);
   float p1, e1, p2, e2, p3, e3, p4, e4, p5, e5;
   two_prod(e, e, p1, e1);
-  two_prod(e, d, p2, e2);
-  p2 = __fmul_rn(p2, 2.0f);
-  e2 = __fmul_rn(e2, 2.0f);
+  if (ori) {  // original scheme: A D^2 = E^2 - D^2 - |M|^2
+    two_prod(d, d, p2, e2);
+    p2 = -p2;
+    e2 = -e2;
+  } else {    // A D^2 = Et^2 + 2 Et D - |M|^2
+    two_prod(e, d, p2, e2);
+    p2 = __fmul_rn(p2, 2.0f);
+    e2 = __fmul_rn(e2, 2.0f);
+  }
   two_prod(mx, mx, p3, e3);
   two_prod(my, my, p4, e4);
   two_prod(mz, mz, p5, e5);
@@ -200,14 +210,14 @@ __device__ __forceinline__ bool A_comp_float(float D, float Mx, float My, float 
 template <class P>
 __device__ __forceinline__ bool A_and_m2(typename P::S D, typename P::S Mx, typename P::S My,
                                          typename P::S Mz, typename P::S Et,
-                                         typename P::AT& A, typename P::AT& m2) {
+                                         typename P::AT& A, typename P::AT& m2, int ori = 0) {
   if constexpr (P::comp_a) {
-    if (!A_comp_float(D, Mx, My, Mz, Et, A, m2)) return false;
+    if (!A_comp_float(D, Mx, My, Mz, Et, A, m2, ori)) return false;
     return A > float(kEpsUnphysical);
   } else {
     if (!(double(D) > 0.0)) return false;
     double m2d;
-    double Ad = A_of_cons(D, Mx, My, Mz, Et, m2d);
+    double Ad = A_of_cons(D, Mx, My, Mz, Et, m2d, ori);
     A = Ad;
     m2 = m2d;
     return Ad > kEpsUnphysical;
@@ -245,10 +255,10 @@ template <class P>
 __device__ __forceinline__ int con2pri(typename P::S D, typename P::S Mx, typename P::S My,
                                        typename P::S Mz, typename P::S Et,
                                        PrimX<typename P::S>& W, int maxit,
-                                       typename P::S guess = typename P::S(0)) {
+                                       typename P::S guess = typename P::S(0), int ori = 0) {
   using R = typename P::S;
   typename P::AT Aa, m2a;
-  if (!A_and_m2<P>(D, Mx, My, Mz, Et, Aa, m2a)) {
+  if (!A_and_m2<P>(D, Mx, My, Mz, Et, Aa, m2a, ori)) {
     R nan = R(__longlong_as_double(0x7ff8000000000000ULL));
     W.rho = W.u[0] = W.u[1] = W.u[2] = W.p = W.T = W.h = W.gamma = W.ht = nan;
     return 1;
@@ -285,11 +295,11 @@ __device__ __forceinline__ void con2pri_x2(const typename P::S (&Ua)[5],
                                            PrimX<typename P::S>& Wa, PrimX<typename P::S>& Wb,
                                            int maxit, int& sta, int& stb,
                                            typename P::S ga = typename P::S(0),
-                                           typename P::S gb = typename P::S(0)) {
+                                           typename P::S gb = typename P::S(0), int ori = 0) {
   using R = typename P::S;
   typename P::AT Aa_, ma_, Ab_, mb_;
-  const bool pa = A_and_m2<P>(Ua[0], Ua[1], Ua[2], Ua[3], Ua[4], Aa_, ma_);
-  const bool pb = A_and_m2<P>(Ub[0], Ub[1], Ub[2], Ub[3], Ub[4], Ab_, mb_);
+  const bool pa = A_and_m2<P>(Ua[0], Ua[1], Ua[2], Ua[3], Ua[4], Aa_, ma_, ori);
+  const bool pb = A_and_m2<P>(Ub[0], Ub[1], Ub[2], Ub[3], Ub[4], Ab_, mb_, ori);
   // an unphysical state iterates on a harmless stand-in and is discarded
   const R Aa = pa ? R(Aa_) : R(1), m2a = pa ? R(ma_) : R(0);
   const R Ab = pb ? R(Ab_) : R(1), m2b = pb ? R(mb_) : R(0);
@@ -347,7 +357,7 @@ __device__ __forceinline__ void con2pri_x2(const typename P::S (&Ua)[5],
 
 // Primitive -> conserved (Eq. density, momentum, T_to_HTilde, E_D).
 // Fills T, h, gamma of W. Returns false if rho <= 0 or p <= 0.
-template <class R> __device__ __forceinline__ bool prim2con(PrimX<R>& W, R U[5]) {
+template <class R> __device__ __forceinline__ bool prim2con(PrimX<R>& W, R U[5], int ori = 0) {
   if (!(W.rho > R(0)) || !(W.p > R(0))) {
     R nan = R(__longlong_as_double(0x7ff8000000000000ULL));
     for (int v = 0; v < 5; ++v) U[v] = nan;
@@ -364,11 +374,15 @@ template <class R> __device__ __forceinline__ bool prim2con(PrimX<R>& W, R U[5])
   U[1] = Dh * W.u[0];
   U[2] = Dh * W.u[1];
   U[3] = Dh * W.u[2];
-  R hh = h * h;
-  R m2 = hh * u2;
-  R f = ht * (ht + R(2)) - R(2) * T * h + T * T * (hh / (hh + m2));
-  R s = m2 + f;
-  U[4] = D * (s / (R(1) + sqrt(R(1) + s)));
+  if (ori) {
+    U[4] = Dh * gamma - W.p;  // original scheme: E = D h gamma - p
+  } else {
+    R hh = h * h;
+    R m2 = hh * u2;
+    R f = ht * (ht + R(2)) - R(2) * T * h + T * T * (hh / (hh + m2));
+    R s = m2 + f;
+    U[4] = D * (s / (R(1) + sqrt(R(1) + s)));
+  }
   W.T = T;
   W.h = h;
   W.gamma = gamma;
@@ -377,14 +391,14 @@ template <class R> __device__ __forceinline__ bool prim2con(PrimX<R>& W, R U[5])
 
 // Physical flux along d (Eqs. D evolution, M evolution, ETilde evolution).
 template <int d, class R>
-__device__ __forceinline__ void phys_flux(const PrimX<R>& W, const R U[5], R F[5]) {
+__device__ __forceinline__ void phys_flux(const PrimX<R>& W, const R U[5], R F[5], int ori = 0) {
   R v = W.u[d] / W.gamma;
   F[0] = U[0] * v;
   F[1] = U[1] * v;
   F[2] = U[2] * v;
   F[3] = U[3] * v;
   F[1 + d] += W.p;
-  F[4] = (U[4] + W.p) * v;
+  F[4] = ori ? U[1 + d] : (U[4] + W.p) * v;  // original scheme: flux of E is M_d
 }
 
 // Outer characteristic speeds along d with the TM sound speed, in the
@@ -412,10 +426,10 @@ __device__ __forceinline__ void char_speeds(const PrimX<R>& W, R& lm, R& lp) {
 // non-positive contact pressure). Returns 1 on fallback.
 template <int d, class R>
 __device__ __forceinline__ int riemann(int solver, const PrimX<R>& WL, const R UL[5],
-                                       const PrimX<R>& WR, const R UR[5], R F[5]) {
+                                       const PrimX<R>& WR, const R UR[5], R F[5], int ori = 0) {
   R FL[5], FR[5];
-  phys_flux<d>(WL, UL, FL);
-  phys_flux<d>(WR, UR, FR);
+  phys_flux<d>(WL, UL, FL, ori);
+  phys_flux<d>(WR, UR, FR, ori);
   R lmL, lpL, lmR, lpR;
   char_speeds<d>(WL, lmL, lpL);
   char_speeds<d>(WR, lmR, lpR);
@@ -439,8 +453,8 @@ __device__ __forceinline__ int riemann(int solver, const PrimX<R>& WL, const R U
     Fh[v] = (sR * FL[v] - sL * FR[v] + sL * sR * (UR[v] - UL[v])) * rds;
   }
   if (solver == 0) {
-    R E = Uh[4] + Uh[0];
-    R FE = Fh[4] + Fh[0];
+    R E = ori ? Uh[4] : Uh[4] + Uh[0];
+    R FE = ori ? Fh[4] : Fh[4] + Fh[0];
     R m = Uh[1 + d];
     R Fm = Fh[1 + d];
     R B = E + Fm;

