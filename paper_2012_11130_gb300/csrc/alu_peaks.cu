@@ -72,6 +72,40 @@ __global__ void sqrt_chain(T* out, T b, int iters) {
   if (s == T(-12345.678)) out[blockIdx.x] = s;
 }
 
+// Packed FP32 (sm_100 family): one instruction performs two FMAs, a <- a b + c
+// on float2, kChains independent chains per thread.
+__global__ void ffma2_chain(float* out, float b, float c, int iters) {
+  float2 a[kChains];
+  const float2 bb = make_float2(b, b), cc = make_float2(c, c);
+#pragma unroll
+  for (int k = 0; k < kChains; ++k)
+    a[k] = make_float2(float(threadIdx.x + k) * 1e-3f, float(threadIdx.x + 2 * k) * 1e-3f);
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int k = 0; k < kChains; ++k) a[k] = __ffma2_rn(a[k], bb, cc);
+  }
+  float s = 0;
+#pragma unroll
+  for (int k = 0; k < kChains; ++k) s += a[k].x + a[k].y;
+  if (s == -12345.678f) out[blockIdx.x] = s;
+}
+
+// FP32 approximate division (__fdividef: reciprocal on the special-function
+// unit and one multiply): x <- c / (x + b).
+__global__ void fdiv_chain(float* out, float b, float c, int iters) {
+  float a[kChains];
+#pragma unroll
+  for (int k = 0; k < kChains; ++k) a[k] = 1.f + float(threadIdx.x + k) * 1e-3f;
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int k = 0; k < kChains; ++k) a[k] = __fdividef(c, a[k] + b);
+  }
+  float s = 0;
+#pragma unroll
+  for (int k = 0; k < kChains; ++k) s += a[k];
+  if (s == -12345.678f) out[blockIdx.x] = s;
+}
+
 // Special-function unit: x <- rsqrtf(x + b) (approximate, one MUFU op + FADD).
 __global__ void rsqrt_chain(float* out, float b, int iters) {
   float a[kChains];
@@ -129,6 +163,8 @@ int main() {
   float t_d32 = time_ms([&] { div_chain<float><<<blocks, threads>>>(o32, 0.5f, 1.5f, itdiv32); }, e0, e1);
   float t_s32 = time_ms([&] { sqrt_chain<float><<<blocks, threads>>>(o32, 0.5f, itdiv32); }, e0, e1);
   float t_rsq = time_ms([&] { rsqrt_chain<<<blocks, threads>>>(o32, 0.5f, itmufu); }, e0, e1);
+  float t_f2 = time_ms([&] { ffma2_chain<<<blocks, threads>>>(o32, 0.999f, 1e-4f, it32); }, e0, e1);
+  float t_fd = time_ms([&] { fdiv_chain<<<blocks, threads>>>(o32, 0.5f, 1.5f, itmufu); }, e0, e1);
   CK(cudaGetLastError());
   CK(cudaDeviceSynchronize());
 
@@ -140,7 +176,9 @@ int main() {
   printf(" \"fp64_sqrt_gops\": %.3f,\n", rate(itdiv64, t_s64) / 1e9);
   printf(" \"fp32_ieee_div_gops\": %.3f,\n", rate(itdiv32, t_d32) / 1e9);
   printf(" \"fp32_ieee_sqrt_gops\": %.3f,\n", rate(itdiv32, t_s32) / 1e9);
-  printf(" \"fp32_rsqrt_mufu_gops\": %.3f}\n", rate(itmufu, t_rsq) / 1e9);
+  printf(" \"fp32_rsqrt_mufu_gops\": %.3f,\n", rate(itmufu, t_rsq) / 1e9);
+  printf(" \"fp32x2_ffma2_tflops\": %.3f,\n", 4.0 * rate(it32, t_f2) / 1e12);
+  printf(" \"fp32_fdividef_gops\": %.3f}\n", rate(itmufu, t_fd) / 1e9);
   cudaFree(out);
   return 0;
 }

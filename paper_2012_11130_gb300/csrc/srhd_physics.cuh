@@ -43,17 +43,28 @@ template <> struct NewtonCfg<float> {
 __device__ __forceinline__ float rsqrt_r(float x) { return rsqrtf(x); }
 __device__ __forceinline__ double rsqrt_r(double x) { return rsqrt(x); }
 
+// Quotient and reciprocal in the arithmetic type. In float they are the
+// hardware approximate division (at most 2 ulp, like the '/' operator under
+// -prec-div=false, but without its range scaling: valid for divisors of
+// magnitude below 2^126, which every denominator they are used on stays far
+// below); in double they are the IEEE operations.
+__device__ __forceinline__ float qdiv(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double qdiv(double a, double b) { return a / b; }
+__device__ __forceinline__ float qrcp(float b) { return __fdividef(1.0f, b); }
+__device__ __forceinline__ double qrcp(double b) { return 1.0 / b; }
+
 // Primitive state with the derived quantities reused downstream.
 template <class R> struct PrimX {
   R rho, u[3], p;   // W = (rho, U^x, U^y, U^z, p)
   R T, h, gamma;    // T = p/rho, h = 1 + htilde, gamma = sqrt(1 + U.U)
+  R rg;             // 1 / gamma (three-velocity v = U rg)
   R ht;             // htilde (set by the conversions from conserved variables)
 };
 
 // Eq. (T_to_HTilde): htilde(T) without subtraction.
 template <class R> __device__ __forceinline__ R htilde_of_T(R T) {
   R a = R(2.25) * T * T;
-  return R(2.5) * T + a / (R(1) + sqrt(a + R(1)));
+  return R(2.5) * T + qdiv(a, R(1) + sqrt(a + R(1)));
 }
 
 // Eq. (T of h) and its derivative Eq. (dT_dh), sharing one reciprocal square
@@ -64,14 +75,14 @@ template <class R> __device__ __forceinline__ void T_dT_of_htilde(R ht, R& T, R&
   R x = (R(9) * ht + R(18)) * ht + R(25);
   R rs = rsqrt_r(x);
   R den = R(5) * ht + R(5) + x * rs;
-  R rden = R(1) / den;
+  R rden = qrcp(den);
   T = (R(2) * ht + R(4)) * ht * rden;
   dT = ((R(4) * ht + R(4)) - T * ((R(9) * ht + R(9)) * rs + R(5))) * rden;
 }
 
 template <class R> __device__ __forceinline__ R T_of_htilde(R ht) {
   R x = (R(9) * ht + R(18)) * ht + R(25);
-  return (R(2) * ht + R(4)) * ht / (R(5) * ht + R(5) + sqrt(x));
+  return qdiv((R(2) * ht + R(4)) * ht, R(5) * ht + R(5) + sqrt(x));
 }
 
 // Eq. (sound_speed): c_s^2 = T (5h - 8T) / (3h (h - T)).
@@ -87,7 +98,7 @@ template <class R>
 __device__ __forceinline__ void f_df(R ht, R T, R dT, R m2, R& f, R& df) {
   R h = ht + R(1);
   R hh = h * h;
-  R rq = R(1) / (hh + m2);
+  R rq = qrcp(hh + m2);
   R a1 = hh * rq, a2 = m2 * rq;
   f = ht * (ht + R(2)) - R(2) * T * h + T * T * a1;
   df = R(2) * h - R(2) * T - R(2) * h * dT +
@@ -99,10 +110,10 @@ __device__ __forceinline__ void f_df(R ht, R T, R dT, R m2, R& f, R& df) {
 // transcendental eq) in cancellation-free form.
 template <class R> __device__ __forceinline__ R newton_guess(R A, R m2) {
   R P = R(1) + m2;
-  R tb = R(1800) * P / (R(437) * m2 + R(117));
+  R tb = qdiv(R(1800) * P, R(437) * m2 + R(117));
   if (A > tb * tb) return R(4.0 / 3.0) * sqrt(A);
-  R a = (R(43) * m2 + R(63)) / (R(125) * P);
-  return R(2) * A / (R(1.2) + sqrt(R(1.44) + R(4) * a * A));
+  R a = qdiv(R(43) * m2 + R(63), R(125) * P);
+  return qdiv(R(2) * A, R(1.2) + sqrt(R(1.44) + R(4) * a * A));
 }
 
 // Precision tags. S is the storage and arithmetic type; AT is the type in
@@ -196,7 +207,7 @@ __device__ __forceinline__ bool A_comp_float(float D, float Mx, float My, float 
   // rounding of the exact quotient.
   float dh, dl;
   two_prod(d, d, dh, dl);
-  float r = 1.0f / dh;
+  float r = qrcp(dh);
   r = fmaf(r, fmaf(-dh, r, 1.0f), r);
   float q = __fmul_rn(ad2, r);
   const float res = __fsub_rn(fmaf(-q, dh, ad2), __fmul_rn(q, dl));
@@ -236,6 +247,7 @@ __device__ __forceinline__ void prims_from_htilde(S D, S Mx, S My, S Mz, R ht, P
   R g2 = R(1) + (W.u[0] * W.u[0] + W.u[1] * W.u[1] + W.u[2] * W.u[2]);
   R rg = rsqrt_r(g2);
   W.gamma = g2 * rg;
+  W.rg = rg;
   W.rho = R(D) * rg;
   W.T = T_of_htilde(ht);
   W.h = h;
@@ -260,7 +272,7 @@ __device__ __forceinline__ int con2pri(typename P::S D, typename P::S Mx, typena
   typename P::AT Aa, m2a;
   if (!A_and_m2<P>(D, Mx, My, Mz, Et, Aa, m2a, ori)) {
     R nan = R(__longlong_as_double(0x7ff8000000000000ULL));
-    W.rho = W.u[0] = W.u[1] = W.u[2] = W.p = W.T = W.h = W.gamma = W.ht = nan;
+    W.rho = W.u[0] = W.u[1] = W.u[2] = W.p = W.T = W.h = W.gamma = W.rg = W.ht = nan;
     return 1;
   }
   const R A = R(Aa), m2 = R(m2a);
@@ -271,7 +283,7 @@ __device__ __forceinline__ int con2pri(typename P::S D, typename P::S Mx, typena
     R T, dT, f, df;
     T_dT_of_htilde(ht, T, dT);
     f_df(ht, T, dT, m2, f, df);
-    R dh = (f - A) / df;
+    R dh = qdiv(f - A, df);
     R hn = ht - dh;
     if (!(hn > R(0))) hn = R(0.5) * ht;
     R adh = fabs(dh);
@@ -315,8 +327,8 @@ __device__ __forceinline__ void con2pri_x2(const typename P::S (&Ua)[5],
     T_dT_of_htilde(hb, Tb, dTb);
     f_df(ha, Ta, dTa, m2a, fa, dfa);
     f_df(hb, Tb, dTb, m2b, fb, dfb);
-    R dha = (fa - Aa) / dfa;
-    R dhb = (fb - Ab) / dfb;
+    R dha = qdiv(fa - Aa, dfa);
+    R dhb = qdiv(fb - Ab, dfb);
     if (!da) {
       R hn = ha - dha;
       if (!(hn > R(0))) hn = R(0.5) * ha;
@@ -346,30 +358,40 @@ __device__ __forceinline__ void con2pri_x2(const typename P::S (&Ua)[5],
   prims_from_htilde(Ub[0], Ub[1], Ub[2], Ub[3], hb, Wb);
   const R nan = R(__longlong_as_double(0x7ff8000000000000ULL));
   if (!pa) {
-    Wa.rho = Wa.u[0] = Wa.u[1] = Wa.u[2] = Wa.p = Wa.T = Wa.h = Wa.gamma = Wa.ht = nan;
+    Wa.rho = Wa.u[0] = Wa.u[1] = Wa.u[2] = Wa.p = Wa.T = Wa.h = Wa.gamma = Wa.rg = Wa.ht = nan;
     sta = 1;
   }
   if (!pb) {
-    Wb.rho = Wb.u[0] = Wb.u[1] = Wb.u[2] = Wb.p = Wb.T = Wb.h = Wb.gamma = Wb.ht = nan;
+    Wb.rho = Wb.u[0] = Wb.u[1] = Wb.u[2] = Wb.p = Wb.T = Wb.h = Wb.gamma = Wb.rg = Wb.ht = nan;
     stb = 1;
   }
 }
 
-// Primitive -> conserved (Eq. density, momentum, T_to_HTilde, E_D).
-// Fills T, h, gamma of W. Returns false if rho <= 0 or p <= 0.
+// Primitive -> conserved (Eqs. density, momentum, T_to_HTilde and the
+// reduced energy). Fills T, h, gamma, rg of W. Returns false if rho <= 0 or
+// p <= 0. The reduced energy uses, instead of Eq. (E_D), the equivalent
+// subtraction-free form
+//   Et / D = h gamma - 1 - T / gamma = U^2 / (gamma + 1) + (htilde - T + htilde U^2) / gamma
+// (gamma - 1 = U^2 / (gamma + 1); htilde - T = 1.5 T + 2.25 T^2 / (1 + sqrt(1 + 2.25 T^2))),
+// which shares 1/gamma with the flux and needs one division and no square
+// root beyond those of htilde and gamma.
 template <class R> __device__ __forceinline__ bool prim2con(PrimX<R>& W, R U[5], int ori = 0) {
   if (!(W.rho > R(0)) || !(W.p > R(0))) {
     R nan = R(__longlong_as_double(0x7ff8000000000000ULL));
     for (int v = 0; v < 5; ++v) U[v] = nan;
     return false;
   }
-  R T = W.p / W.rho;
-  R ht = htilde_of_T(T);
-  R u2 = W.u[0] * W.u[0] + W.u[1] * W.u[1] + W.u[2] * W.u[2];
-  R gamma = sqrt(R(1) + u2);
-  R D = W.rho * gamma;
-  R h = R(1) + ht;
-  R Dh = D * h;
+  const R T = qdiv(W.p, W.rho);
+  const R a = R(2.25) * T * T;
+  const R t2 = qdiv(a, R(1) + sqrt(a + R(1)));  // htilde - 2.5 T
+  const R ht = R(2.5) * T + t2;
+  const R u2 = W.u[0] * W.u[0] + W.u[1] * W.u[1] + W.u[2] * W.u[2];
+  const R g2 = R(1) + u2;
+  const R rg = rsqrt_r(g2);
+  const R gamma = g2 * rg;
+  const R D = W.rho * gamma;
+  const R h = R(1) + ht;
+  const R Dh = D * h;
   U[0] = D;
   U[1] = Dh * W.u[0];
   U[2] = Dh * W.u[1];
@@ -377,22 +399,19 @@ template <class R> __device__ __forceinline__ bool prim2con(PrimX<R>& W, R U[5],
   if (ori) {
     U[4] = Dh * gamma - W.p;  // original scheme: E = D h gamma - p
   } else {
-    R hh = h * h;
-    R m2 = hh * u2;
-    R f = ht * (ht + R(2)) - R(2) * T * h + T * T * (hh / (hh + m2));
-    R s = m2 + f;
-    U[4] = D * (s / (R(1) + sqrt(R(1) + s)));
+    U[4] = D * (qdiv(u2, gamma + R(1)) + (R(1.5) * T + t2 + ht * u2) * rg);
   }
   W.T = T;
   W.h = h;
   W.gamma = gamma;
+  W.rg = rg;
   return true;
 }
 
 // Physical flux along d (Eqs. D evolution, M evolution, ETilde evolution).
 template <int d, class R>
 __device__ __forceinline__ void phys_flux(const PrimX<R>& W, const R U[5], R F[5], int ori = 0) {
-  R v = W.u[d] / W.gamma;
+  R v = W.u[d] * W.rg;
   F[0] = U[0] * v;
   F[1] = U[1] * v;
   F[2] = U[2] * v;
@@ -413,7 +432,7 @@ __device__ __forceinline__ void char_speeds(const PrimX<R>& W, R& lm, R& lp) {
   R ua = W.u[d == 0 ? 1 : 0], ub = W.u[d == 2 ? 1 : 2];
   R up2 = ua * ua + ub * ub;
   R u2 = up2 + ud * ud;
-  R rden = R(1) / (R(1) + u2 * omc);
+  R rden = qrcp(R(1) + u2 * omc);
   R a = W.gamma * ud * omc;
   R b = sqrt(cs2 * (R(1) + up2 * omc));
   lm = (a - b) * rden;
@@ -445,22 +464,20 @@ __device__ __forceinline__ int riemann(int solver, const PrimX<R>& WL, const R U
     for (int v = 0; v < 5; ++v) F[v] = FR[v];
     return 0;
   }
-  R rds = R(1) / (sR - sL);
-  R Uh[5], Fh[5];
-#pragma unroll
-  for (int v = 0; v < 5; ++v) {
-    Uh[v] = (sR * UR[v] - sL * UL[v] - FR[v] + FL[v]) * rds;
-    Fh[v] = (sR * FL[v] - sL * FR[v] + sL * sR * (UR[v] - UL[v])) * rds;
-  }
+  const R rds = qrcp(sR - sL);
+  // HLL state and flux of component v
+  auto hll_u = [&](int v) { return (sR * UR[v] - sL * UL[v] - FR[v] + FL[v]) * rds; };
+  auto hll_f = [&](int v) { return (sR * FL[v] - sL * FR[v] + sL * sR * (UR[v] - UL[v])) * rds; };
   if (solver == 0) {
-    R E = ori ? Uh[4] : Uh[4] + Uh[0];
-    R FE = ori ? Fh[4] : Fh[4] + Fh[0];
-    R m = Uh[1 + d];
-    R Fm = Fh[1 + d];
+    // the contact speed needs only the energy and normal-momentum components
+    R E = ori ? hll_u(4) : hll_u(4) + hll_u(0);
+    R FE = ori ? hll_f(4) : hll_f(4) + hll_f(0);
+    R m = hll_u(1 + d);
+    R Fm = hll_f(1 + d);
     R B = E + Fm;
     R disc = B * B - R(4) * FE * m;
     if (disc >= R(0) && B > R(0)) {
-      R lam = R(2) * m / (B + sqrt(disc));
+      R lam = qdiv(R(2) * m, B + sqrt(disc));
       R ps = Fm - lam * FE;
       if (lam > sL && lam < sR && ps > R(0)) {
         const bool left = lam >= R(0);
@@ -468,9 +485,9 @@ __device__ __forceinline__ int riemann(int solver, const PrimX<R>& WL, const R U
         const R* Uk = left ? UL : UR;
         const R* Fk = left ? FL : FR;
         R sk = left ? sL : sR;
-        R v = Wk.u[d] / Wk.gamma;
+        R v = Wk.u[d] * Wk.rg;
         R a = sk - v;
-        R rb = R(1) / (sk - lam);
+        R rb = qrcp(sk - lam);
         R Us[5];
         Us[0] = Uk[0] * a * rb;
 #pragma unroll
@@ -482,23 +499,22 @@ __device__ __forceinline__ int riemann(int solver, const PrimX<R>& WL, const R U
         return 0;
       }
     }
-#pragma unroll
-    for (int v = 0; v < 5; ++v) F[v] = Fh[v];
-    return 1;
   }
 #pragma unroll
-  for (int v = 0; v < 5; ++v) F[v] = Fh[v];
-  return 0;
+  for (int v = 0; v < 5; ++v) F[v] = hll_f(v);
+  return solver == 0;
 }
 
 // Hybrid van Leer / generalised minmod slope: 0 at extrema, else the smaller
 // in magnitude of 2 dl dr/(dl+dr) and minmod(theta dl, theta dr, (dl+dr)/2).
+// Where dl and dr share a sign, |2 dl dr/(dl+dr)| (their harmonic mean) is at
+// most |dl+dr|/2 (their arithmetic mean), so the third minmod argument never
+// decides the minimum and is left out.
 template <class R> __device__ __forceinline__ R limited_slope(R dl, R dr, R theta) {
   if (!(dl * dr > R(0))) return R(0);
-  R vl = R(2) * dl * dr / (dl + dr);
-  R gm = fmin(fmin(theta * fabs(dl), theta * fabs(dr)), R(0.5) * fabs(dl + dr));
-  R mag = fmin(fabs(vl), gm);
-  return dl > R(0) ? mag : -mag;
+  R vl = qdiv(R(2) * dl * dr, dl + dr);
+  R mag = fmin(fabs(vl), theta * fmin(fabs(dl), fabs(dr)));
+  return copysign(mag, dl);
 }
 
 // Signal speed bound S_max of one cell (Section 3.2, Eqs. time_step_U_max
@@ -506,7 +522,7 @@ template <class R> __device__ __forceinline__ R limited_slope(R dl, R dr, R thet
 template <class R> __device__ __forceinline__ R smax_of(const PrimX<R>& W, int ndim) {
   R cs2 = cs2_of(W.T, W.h);
   R omc = R(1) - cs2;
-  R us = sqrt(cs2 / omc);           // U_s = c_s / sqrt(1 - c_s^2)
+  R us = sqrt(qdiv(cs2, omc));      // U_s = c_s / sqrt(1 - c_s^2)
   R gs = rsqrt_r(omc);              // gamma_s = 1 / sqrt(1 - c_s^2)
   R su = fabs(W.u[0]) + fabs(W.u[1]) + fabs(W.u[2]);
   R umax = gs * su + R(ndim) * W.gamma * us;
