@@ -142,6 +142,37 @@ __device__ __forceinline__ void recon_direction(const S* prim, int tc, const Pri
                                                 R dF[5], int& bad, int ori) {
   constexpr int off = (d == 0) ? 1 : ((d == 1) ? kG : kG * kG);
   R wc[5] = {W.rho, W.u[0], W.u[1], W.u[2], W.p};
+  const int cd = (d == 0) ? i : ((d == 1) ? j : k);
+  // A face state is stored only where a flux uses it: the transverse
+  // coordinates are interior and the face lies in 0..8 along d.
+  const bool trans = interior || (cd < 0 || cd > 7);
+  if constexpr (sizeof(R) == 4) {
+    // float: the minus (lane x) and plus (lane y) face states in packed form
+    float2 Wq[5], Uq[5], Fq[5];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+      R lo = R(prim[v * kGC + tc - off]);
+      R hi = R(prim[v * kGC + tc + off]);
+      R dW = limited_slope(wc[v] - lo, hi - wc[v], theta);
+      Wq[v] = pk::fma(pk::s2(dW), make_float2(-0.5f, 0.5f), pk::s2(wc[v]));
+    }
+    bool okm, okp;
+    prim2con_flux_x2<d>(Wq, Uq, Fq, okm, okp, ori);
+    if (!okm || !okp) bad = 1;
+#pragma unroll
+    for (int v = 0; v < 5; ++v) dF[v] = dF[v] + (Fq[v].y - Fq[v].x);
+    if (trans && cd >= 0) {
+      int fi = face_index<d>(i, j, k, cd);
+#pragma unroll
+      for (int v = 0; v < 5; ++v) face_slot(face, d, 1, v)[fi] = S(Uq[v].x);
+    }
+    if (trans && cd <= 7) {
+      int fi = face_index<d>(i, j, k, cd + 1);
+#pragma unroll
+      for (int v = 0; v < 5; ++v) face_slot(face, d, 0, v)[fi] = S(Uq[v].y);
+    }
+    return;
+  }
   PrimX<R> Wm, Wp;
   R fm[5], fp[5];
 #pragma unroll
@@ -161,10 +192,6 @@ __device__ __forceinline__ void recon_direction(const S* prim, int tc, const Pri
   phys_flux<d>(Wp, Up, Fp, ori);
 #pragma unroll
   for (int v = 0; v < 5; ++v) dF[v] = dF[v] + (Fp[v] - Fm[v]);
-  const int cd = (d == 0) ? i : ((d == 1) ? j : k);
-  // A face state is stored only where a flux uses it: the transverse
-  // coordinates are interior and the face lies in 0..8 along d.
-  const bool trans = interior || (cd < 0 || cd > 7);
   if (trans && cd >= 0) {
     int fi = face_index<d>(i, j, k, cd);
 #pragma unroll
@@ -375,52 +402,94 @@ __global__ void __launch_bounds__(NT, MINB) patch_kernel(PatchArgs a) {
           // and converts both in lockstep for the CFL bound (for any NT)
           constexpr int NPC = PAIR ? 2 : 1;
           constexpr int kItems = kNC / NPC;
+          // the signal-speed CFL bound converts the new state; its status 1
+          // is the Eq. (Unphysical result) check, otherwise made directly
+          const bool signal = a.partial_dt && a.cfl_mode != 1;
           for (int c0 = tid; c0 < kItems; c0 += NT) {
             S Un[NPC][5];
             S g0[NPC];  // htilde of the cell before the step: warm start of the CFL solve
-            bool ok[NPC];
+            if constexpr (PAIR && sizeof(R) == 4) {
+              // both cells' divergences in packed arithmetic
+              int tcq[2], fq[2][6];
 #pragma unroll
-            for (int q = 0; q < NPC; ++q) {
-              const int c = c0 + q * kItems;
-              const int i = c & 7, j = (c >> 3) & 7, k = c >> 6;
-              const int tc = tile_index(i, j, k);
-              g0[q] = hts[tc];
-              const int fx0 = face_index<0>(i, j, k, i), fx1 = face_index<0>(i, j, k, i + 1);
-              const int fy0 = face_index<1>(i, j, k, j), fy1 = face_index<1>(i, j, k, j + 1);
-              const int fz0 = face_index<2>(i, j, k, k), fz1 = face_index<2>(i, j, k, k + 1);
+              for (int q = 0; q < 2; ++q) {
+                const int c = c0 + q * kItems;
+                const int i = c & 7, j = (c >> 3) & 7, k = c >> 6;
+                tcq[q] = tile_index(i, j, k);
+                g0[q] = hts[tcq[q]];
+                fq[q][0] = face_index<0>(i, j, k, i);
+                fq[q][1] = face_index<0>(i, j, k, i + 1);
+                fq[q][2] = face_index<1>(i, j, k, j);
+                fq[q][3] = face_index<1>(i, j, k, j + 1);
+                fq[q][4] = face_index<2>(i, j, k, k);
+                fq[q][5] = face_index<2>(i, j, k, k + 1);
+              }
+              const float2 mcoef = pk::s2(-float(coef));
 #pragma unroll
               for (int v = 0; v < 5; ++v) {
-                R div = R(0);
-                div = div + (R(face_slot(face, 0, 0, v)[fx1]) - R(face_slot(face, 0, 0, v)[fx0]));
-                div = div + (R(face_slot(face, 1, 0, v)[fy1]) - R(face_slot(face, 1, 0, v)[fy0]));
-                div = div + (R(face_slot(face, 2, 0, v)[fz1]) - R(face_slot(face, 2, 0, v)[fz0]));
-                Un[q][v] = S(R(in[v * kGC + tc]) - coef * div);
-                out[v * kNC + c] = Un[q][v];
+                auto ld = [&](int dd, int e) {
+                  const S* f = face_slot(face, dd, 0, v);
+                  return make_float2(f[fq[0][e]], f[fq[1][e]]);
+                };
+                const float2 div = pk::add(pk::add(pk::sub(ld(0, 1), ld(0, 0)),
+                                                   pk::sub(ld(1, 3), ld(1, 2))),
+                                           pk::sub(ld(2, 5), ld(2, 4)));
+                const float2 un = pk::fma(mcoef, div, make_float2(in[v * kGC + tcq[0]],
+                                                                  in[v * kGC + tcq[1]]));
+                Un[0][v] = un.x;
+                Un[1][v] = un.y;
+                out[v * kNC + c0] = un.x;
+                out[v * kNC + c0 + kItems] = un.y;
               }
-              typename P::AT Ac, m2c;
-              ok[q] = A_and_m2<P>(Un[q][0], Un[q][1], Un[q][2], Un[q][3], Un[q][4], Ac, m2c, ori);
-              if (!ok[q]) fail4 = 1;
-            }
-            if (a.partial_dt) {
-              if (a.cfl_mode == 1) {
-                att_min = fmin(att_min, a.cfl * dh);
-              } else {
-                PrimX<R> W[NPC];
-                if constexpr (PAIR) {
-                  int s0, s1;
-                  con2pri_x2<P>(Un[0], Un[1], W[0], W[1], maxit, s0, s1, g0[0], g0[NPC - 1],
-                                ori);
-                } else {
-                  con2pri<P>(Un[0][0], Un[0][1], Un[0][2], Un[0][3], Un[0][4], W[0], maxit,
-                             g0[0], ori);
-                }
+            } else {
 #pragma unroll
-                for (int q = 0; q < NPC; ++q) {
-                  // the largest signal speed of the patch; dt = C dh / S_max once
-                  if (ok[q]) att_smax = fmax(att_smax, smax_of(W[q], a.ndim));
-                  else att_bad = 1;
+              for (int q = 0; q < NPC; ++q) {
+                const int c = c0 + q * kItems;
+                const int i = c & 7, j = (c >> 3) & 7, k = c >> 6;
+                const int tc = tile_index(i, j, k);
+                g0[q] = hts[tc];
+                const int fx0 = face_index<0>(i, j, k, i), fx1 = face_index<0>(i, j, k, i + 1);
+                const int fy0 = face_index<1>(i, j, k, j), fy1 = face_index<1>(i, j, k, j + 1);
+                const int fz0 = face_index<2>(i, j, k, k), fz1 = face_index<2>(i, j, k, k + 1);
+#pragma unroll
+                for (int v = 0; v < 5; ++v) {
+                  R div = R(0);
+                  div = div + (R(face_slot(face, 0, 0, v)[fx1]) - R(face_slot(face, 0, 0, v)[fx0]));
+                  div = div + (R(face_slot(face, 1, 0, v)[fy1]) - R(face_slot(face, 1, 0, v)[fy0]));
+                  div = div + (R(face_slot(face, 2, 0, v)[fz1]) - R(face_slot(face, 2, 0, v)[fz0]));
+                  Un[q][v] = S(R(in[v * kGC + tc]) - coef * div);
+                  out[v * kNC + c] = Un[q][v];
                 }
               }
+            }
+            if (signal) {
+              PrimX<R> W[NPC];
+              int st[NPC];
+              if constexpr (PAIR) {
+                con2pri_x2<P>(Un[0], Un[1], W[0], W[1], maxit, st[0], st[1], g0[0], g0[NPC - 1],
+                              ori);
+              } else {
+                st[0] = con2pri<P>(Un[0][0], Un[0][1], Un[0][2], Un[0][3], Un[0][4], W[0], maxit,
+                                   g0[0], ori);
+              }
+#pragma unroll
+              for (int q = 0; q < NPC; ++q) {
+                // the largest signal speed of the patch; dt = C dh / S_max once
+                if (st[q] != 1) {
+                  att_smax = fmax(att_smax, smax_of(W[q], a.ndim));
+                } else {
+                  att_bad = 1;
+                  fail4 = 1;
+                }
+              }
+            } else {
+#pragma unroll
+              for (int q = 0; q < NPC; ++q) {
+                typename P::AT Ac, m2c;
+                if (!A_and_m2<P>(Un[q][0], Un[q][1], Un[q][2], Un[q][3], Un[q][4], Ac, m2c, ori))
+                  fail4 = 1;
+              }
+              if (a.partial_dt) att_min = fmin(att_min, a.cfl * dh);
             }
           }
           fail = __syncthreads_or(fail4) | fail;

@@ -105,6 +105,45 @@ __device__ __forceinline__ void f_df(R ht, R T, R dT, R m2, R& f, R& df) {
        R(2) * T * rq * (dT * hh * a1 + h * (h * dT + T) * a2);
 }
 
+// Packed FP32: the sm_100 family executes an add, a multiply or a fused
+// multiply-add on both lanes of a float2 as one instruction (each lane
+// rounded as its scalar counterpart). The paired Newton solves evaluate the
+// polynomial part of both states' iterations this way; reciprocals and
+// square roots stay per lane.
+namespace pk {
+__device__ __forceinline__ float2 s2(float a) { return make_float2(a, a); }
+// negation and subtraction as one packed instruction each (exact: x (-1))
+__device__ __forceinline__ float2 neg(float2 a) { return __fmul2_rn(a, s2(-1.f)); }
+__device__ __forceinline__ float2 add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 sub(float2 a, float2 b) { return __ffma2_rn(b, s2(-1.f), a); }
+__device__ __forceinline__ float2 mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 rcp(float2 a) { return make_float2(qrcp(a.x), qrcp(a.y)); }
+__device__ __forceinline__ float2 rsq(float2 a) { return make_float2(rsqrtf(a.x), rsqrtf(a.y)); }
+
+// T_dT_of_htilde and f_df on two lanes.
+__device__ __forceinline__ void T_dT_of_htilde(float2 ht, float2& T, float2& dT) {
+  const float2 x = fma(fma(ht, s2(9.f), s2(18.f)), ht, s2(25.f));
+  const float2 rs = rsq(x);
+  const float2 rden = rcp(fma(x, rs, fma(ht, s2(5.f), s2(5.f))));
+  T = mul(mul(fma(ht, s2(2.f), s2(4.f)), ht), rden);
+  // dT = [(4 ht + 4) + T ((-9 ht - 9) rs - 5)] rden
+  dT = mul(fma(T, fma(fma(ht, s2(-9.f), s2(-9.f)), rs, s2(-5.f)), fma(ht, s2(4.f), s2(4.f))),
+           rden);
+}
+__device__ __forceinline__ void f_df(float2 ht, float2 T, float2 dT, float2 m2, float2& f,
+                                     float2& df) {
+  const float2 h = add(ht, s2(1.f));
+  const float2 hh = mul(h, h);
+  const float2 rq = rcp(add(hh, m2));
+  const float2 a1 = mul(hh, rq), a2 = mul(m2, rq);
+  f = fma(mul(T, T), a1, fma(mul(s2(-2.f), T), h, mul(ht, add(ht, s2(2.f)))));
+  const float2 inner = fma(dT, mul(hh, a1), mul(mul(h, fma(h, dT, T)), a2));
+  // df = 2 [h (1 - dT) - T + T rq inner]
+  df = mul(s2(2.f), fma(mul(T, rq), inner, sub(mul(h, fma(dT, s2(-1.f), s2(1.f))), T)));
+}
+}  // namespace pk
+
 // Appendix A initial guess: hot (4/3) sqrt(A) above the Eq. (ColdHot)
 // threshold, else the positive root of the quadratic of Eq. (cold limit of
 // transcendental eq) in cancellation-free form.
@@ -149,17 +188,43 @@ __device__ __forceinline__ double A_of_cons(S D, S Mx, S My, S Mz, S Et, double&
   return eD * (eD + 2.0) - m2;
 }
 
-// Error-free transformations in float (Knuth's TwoSum; the FMA form of
-// Dekker's TwoProduct): a*b = p + e and a+b = s + e exactly. The _rn
-// intrinsics keep the compiler from contracting them into other FMAs.
-__device__ __forceinline__ void two_prod(float a, float b, float& p, float& e) {
-  p = __fmul_rn(a, b);
-  e = fmaf(a, b, -p);
+// Correctly rounded float operations on one lane (float) or two lanes
+// (float2, packed instructions); the _rn forms keep the compiler from
+// contracting them into other FMAs.
+__device__ __forceinline__ float vadd(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float vsub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float vmul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float vfma(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ float vneg(float a) { return -a; }
+__device__ __forceinline__ float vrcp(float a) { return qrcp(a); }
+__device__ __forceinline__ float2 vadd(float2 a, float2 b) { return pk::add(a, b); }
+__device__ __forceinline__ float2 vsub(float2 a, float2 b) { return pk::sub(a, b); }
+__device__ __forceinline__ float2 vmul(float2 a, float2 b) { return pk::mul(a, b); }
+__device__ __forceinline__ float2 vfma(float2 a, float2 b, float2 c) { return pk::fma(a, b, c); }
+__device__ __forceinline__ float2 vneg(float2 a) { return pk::neg(a); }
+__device__ __forceinline__ float2 vrcp(float2 a) { return pk::rcp(a); }
+template <class V> __device__ __forceinline__ V vsplat(float a);
+template <> __device__ __forceinline__ float vsplat<float>(float a) { return a; }
+template <> __device__ __forceinline__ float2 vsplat<float2>(float a) { return make_float2(a, a); }
+
+// Error-free transformations (Knuth's TwoSum; the FMA form of Dekker's
+// TwoProduct): a*b = p + e and a+b = s + e exactly, lane by lane.
+template <class V> __device__ __forceinline__ void two_prod(V a, V b, V& p, V& e) {
+  p = vmul(a, b);
+  e = vfma(a, b, vneg(p));
 }
-__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
-  s = __fadd_rn(a, b);
-  float bb = __fsub_rn(s, a);
-  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+template <class V> __device__ __forceinline__ void two_sum(V a, V b, V& s, V& e) {
+  s = vadd(a, b);
+  V bb = vsub(s, a);
+  e = vadd(vsub(a, vsub(s, bb)), vsub(b, bb));
+}
+
+// Power-of-two scale 2^(127 - ex) that brings D into [1, 2) (exact); false
+// for a non-positive, denormal-flushed, huge or NaN D.
+__device__ __forceinline__ bool comp_scale(float D, float& sc) {
+  const int ex = (__float_as_int(D) >> 23) & 0xff;
+  sc = __int_as_float((254 - (ex > 253 ? 253 : ex)) << 23);
+  return D > 0.0f && ex <= 253;
 }
 
 // A and m^2 from float conserved values without double arithmetic.
@@ -168,52 +233,73 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
 // cancellation between Et^2 + 2 Et D and |M|^2 (the source of the
 // (1 + Mach^2) error factor of Eq. ImprovedRelativeError) acts on a sum that
 // is accurate to about eps_float^2 of its terms instead of eps_float. The
-// inputs are first scaled by the power of two that brings D into [1, 2)
-// (exact), which keeps the products and their error parts clear of the float
-// overflow and underflow (flush-to-zero) ranges.
-__device__ __forceinline__ bool A_comp_float(float D, float Mx, float My, float Mz, float Et,
-                                             float& A, float& m2, int ori = 0) {
-  const int ex = (__float_as_int(D) >> 23) & 0xff;
-  if (!(D > 0.0f) || ex > 253) return false;  // non-positive, denormal-flushed, huge or NaN
-  const float sc = __int_as_float((254 - ex) << 23);   // 2^(127 - ex): D * sc in [1, 2)
-  const float d = __fmul_rn(D, sc), e = __fmul_rn(Et, sc);
-  const float mx = __fmul_rn(Mx, sc), my = __fmul_rn(My, sc), mz = __fmul_rn(Mz, sc);
-  float p1, e1, p2, e2, p3, e3, p4, e4, p5, e5;
+// inputs (d, e, mx, my, mz here) are first scaled by comp_scale, which keeps
+// the products and their error parts clear of the float overflow and
+// underflow (flush-to-zero) ranges. V = float or float2 (two states).
+template <class V>
+__device__ __forceinline__ void A_comp_scaled(V d, V e, V mx, V my, V mz, V& A, V& m2, int ori) {
+  V p1, e1, p2, e2, p3, e3, p4, e4, p5, e5;
   two_prod(e, e, p1, e1);
   if (ori) {  // original scheme: A D^2 = E^2 - D^2 - |M|^2
     two_prod(d, d, p2, e2);
-    p2 = -p2;
-    e2 = -e2;
+    p2 = vneg(p2);
+    e2 = vneg(e2);
   } else {    // A D^2 = Et^2 + 2 Et D - |M|^2
     two_prod(e, d, p2, e2);
-    p2 = __fmul_rn(p2, 2.0f);
-    e2 = __fmul_rn(e2, 2.0f);
+    p2 = vmul(p2, vsplat<V>(2.0f));
+    e2 = vmul(e2, vsplat<V>(2.0f));
   }
   two_prod(mx, mx, p3, e3);
   two_prod(my, my, p4, e4);
   two_prod(mz, mz, p5, e5);
-  float sa, ta, sb, tb, t2, ss, ts;
+  V sa, ta, sb, tb, t2, ss, ts;
   two_sum(p1, p2, sa, ta);
   two_sum(p3, p4, sb, tb);
   two_sum(sb, p5, sb, t2);
-  tb = __fadd_rn(tb, t2);
-  two_sum(sa, -sb, ss, ts);
-  const float low = __fadd_rn(__fsub_rn(__fadd_rn(e1, e2), __fadd_rn(__fadd_rn(e3, e4), e5)),
-                              __fadd_rn(__fsub_rn(ta, tb), ts));
-  const float ad2 = __fadd_rn(ss, low);
+  tb = vadd(tb, t2);
+  two_sum(sa, vneg(sb), ss, ts);
+  const V low = vadd(vsub(vadd(e1, e2), vadd(vadd(e3, e4), e5)), vadd(vsub(ta, tb), ts));
+  const V ad2 = vadd(ss, low);
   // A = ad2 / d^2 with d^2 = dh + dl exact (TwoProduct) and 1/dh from the
   // hardware reciprocal refined by one Newton-Raphson step; one residual
   // correction q += (ad2 - q dh - q dl) / dh then leaves A within about one
   // rounding of the exact quotient.
-  float dh, dl;
+  V dh, dl;
   two_prod(d, d, dh, dl);
-  float r = qrcp(dh);
-  r = fmaf(r, fmaf(-dh, r, 1.0f), r);
-  float q = __fmul_rn(ad2, r);
-  const float res = __fsub_rn(fmaf(-q, dh, ad2), __fmul_rn(q, dl));
-  A = fmaf(res, r, q);
-  m2 = __fmul_rn(__fadd_rn(sb, tb), r);
+  V r = vrcp(dh);
+  r = vfma(r, vfma(vneg(dh), r, vsplat<V>(1.0f)), r);
+  const V q = vmul(ad2, r);
+  const V res = vsub(vfma(vneg(q), dh, ad2), vmul(q, dl));
+  A = vfma(res, r, q);
+  m2 = vmul(vadd(sb, tb), r);
+}
+
+__device__ __forceinline__ bool A_comp_float(float D, float Mx, float My, float Mz, float Et,
+                                             float& A, float& m2, int ori = 0) {
+  float sc;
+  if (!comp_scale(D, sc)) return false;
+  A_comp_scaled(vmul(D, sc), vmul(Et, sc), vmul(Mx, sc), vmul(My, sc), vmul(Mz, sc), A, m2, ori);
   return true;
+}
+
+// A_comp_float of two states with packed arithmetic.
+__device__ __forceinline__ void A_comp_float_x2(const float (&Ua)[5], const float (&Ub)[5],
+                                                float& Aa, float& m2a, bool& oka, float& Ab,
+                                                float& m2b, bool& okb, int ori) {
+  float sa, sb;
+  oka = comp_scale(Ua[0], sa);
+  okb = comp_scale(Ub[0], sb);
+  const float2 sc = make_float2(sa, sb);
+  float2 A, m2;
+  A_comp_scaled(pk::mul(make_float2(Ua[0], Ub[0]), sc), pk::mul(make_float2(Ua[4], Ub[4]), sc),
+                pk::mul(make_float2(Ua[1], Ub[1]), sc), pk::mul(make_float2(Ua[2], Ub[2]), sc),
+                pk::mul(make_float2(Ua[3], Ub[3]), sc), A, m2, ori);
+  Aa = A.x;
+  Ab = A.y;
+  m2a = m2.x;
+  m2b = m2.y;
+  oka = oka && Aa > float(kEpsUnphysical);
+  okb = okb && Ab > float(kEpsUnphysical);
 }
 
 // A and m^2 of a conserved state in the precision of P; false when the
@@ -253,6 +339,35 @@ __device__ __forceinline__ void prims_from_htilde(S D, S Mx, S My, S Mz, R ht, P
   W.h = h;
   W.ht = ht;
   W.p = W.rho * W.T;
+}
+
+// prims_from_htilde of two float states with packed arithmetic.
+__device__ __forceinline__ void prims_from_htilde_x2(const float (&Ua)[5], const float (&Ub)[5],
+                                                     float ha, float hb, PrimX<float>& Wa,
+                                                     PrimX<float>& Wb) {
+  using namespace pk;
+  const float2 ht = make_float2(ha, hb);
+  const float2 D = make_float2(Ua[0], Ub[0]);
+  const float2 h = add(ht, s2(1.f));
+  const float2 Dh = mul(D, h);
+  const float2 rDh = make_float2(1.0f / Dh.x, 1.0f / Dh.y);
+  const float2 ux = mul(make_float2(Ua[1], Ub[1]), rDh);
+  const float2 uy = mul(make_float2(Ua[2], Ub[2]), rDh);
+  const float2 uz = mul(make_float2(Ua[3], Ub[3]), rDh);
+  const float2 g2 = fma(uz, uz, fma(uy, uy, fma(ux, ux, s2(1.f))));
+  const float2 rg = rsq(g2);
+  const float2 gamma = mul(g2, rg);
+  const float2 rho = mul(D, rg);
+  // T of htilde (Eq. T of h)
+  const float2 x = fma(fma(ht, s2(9.f), s2(18.f)), ht, s2(25.f));
+  const float2 num = mul(fma(ht, s2(2.f), s2(4.f)), ht);
+  const float2 den = add(fma(ht, s2(5.f), s2(5.f)), make_float2(sqrtf(x.x), sqrtf(x.y)));
+  const float2 T = make_float2(qdiv(num.x, den.x), qdiv(num.y, den.y));
+  const float2 p = mul(rho, T);
+  Wa.rho = rho.x; Wa.u[0] = ux.x; Wa.u[1] = uy.x; Wa.u[2] = uz.x; Wa.p = p.x;
+  Wa.T = T.x; Wa.h = h.x; Wa.gamma = gamma.x; Wa.rg = rg.x; Wa.ht = ha;
+  Wb.rho = rho.y; Wb.u[0] = ux.y; Wb.u[1] = uy.y; Wb.u[2] = uz.y; Wb.p = p.y;
+  Wb.T = T.y; Wb.h = h.y; Wb.gamma = gamma.y; Wb.rg = rg.y; Wb.ht = hb;
 }
 
 // Conserved -> primitive (Section 2.3). Returns 0 ok, 1 unphysical, 2 no
@@ -310,8 +425,13 @@ __device__ __forceinline__ void con2pri_x2(const typename P::S (&Ua)[5],
                                            typename P::S gb = typename P::S(0), int ori = 0) {
   using R = typename P::S;
   typename P::AT Aa_, ma_, Ab_, mb_;
-  const bool pa = A_and_m2<P>(Ua[0], Ua[1], Ua[2], Ua[3], Ua[4], Aa_, ma_, ori);
-  const bool pb = A_and_m2<P>(Ub[0], Ub[1], Ub[2], Ub[3], Ub[4], Ab_, mb_, ori);
+  bool pa, pb;
+  if constexpr (P::comp_a) {
+    A_comp_float_x2(Ua, Ub, Aa_, ma_, pa, Ab_, mb_, pb, ori);
+  } else {
+    pa = A_and_m2<P>(Ua[0], Ua[1], Ua[2], Ua[3], Ua[4], Aa_, ma_, ori);
+    pb = A_and_m2<P>(Ub[0], Ub[1], Ub[2], Ub[3], Ub[4], Ab_, mb_, ori);
+  }
   // an unphysical state iterates on a harmless stand-in and is discarded
   const R Aa = pa ? R(Aa_) : R(1), m2a = pa ? R(ma_) : R(0);
   const R Ab = pb ? R(Ab_) : R(1), m2b = pb ? R(mb_) : R(0);
@@ -322,13 +442,24 @@ __device__ __forceinline__ void con2pri_x2(const typename P::S (&Ua)[5],
   stb = 2;
   R preva = R(3.0e38), prevb = R(3.0e38);
   for (int k = 1; k <= maxit && !(da && db); ++k) {
-    R Ta, dTa, fa, dfa, Tb, dTb, fb, dfb;
-    T_dT_of_htilde(ha, Ta, dTa);
-    T_dT_of_htilde(hb, Tb, dTb);
-    f_df(ha, Ta, dTa, m2a, fa, dfa);
-    f_df(hb, Tb, dTb, m2b, fb, dfb);
-    R dha = qdiv(fa - Aa, dfa);
-    R dhb = qdiv(fb - Ab, dfb);
+    R dha, dhb;
+    if constexpr (sizeof(R) == 4) {
+      float2 T, dT, f, df;
+      const float2 h2 = make_float2(ha, hb);
+      pk::T_dT_of_htilde(h2, T, dT);
+      pk::f_df(h2, T, dT, make_float2(m2a, m2b), f, df);
+      const float2 dh = pk::mul(pk::sub(f, make_float2(Aa, Ab)), pk::rcp(df));
+      dha = dh.x;
+      dhb = dh.y;
+    } else {
+      R Ta, dTa, fa, dfa, Tb, dTb, fb, dfb;
+      T_dT_of_htilde(ha, Ta, dTa);
+      T_dT_of_htilde(hb, Tb, dTb);
+      f_df(ha, Ta, dTa, m2a, fa, dfa);
+      f_df(hb, Tb, dTb, m2b, fb, dfb);
+      dha = qdiv(fa - Aa, dfa);
+      dhb = qdiv(fb - Ab, dfb);
+    }
     if (!da) {
       R hn = ha - dha;
       if (!(hn > R(0))) hn = R(0.5) * ha;
@@ -354,8 +485,12 @@ __device__ __forceinline__ void con2pri_x2(const typename P::S (&Ua)[5],
       prevb = adh;
     }
   }
-  prims_from_htilde(Ua[0], Ua[1], Ua[2], Ua[3], ha, Wa);
-  prims_from_htilde(Ub[0], Ub[1], Ub[2], Ub[3], hb, Wb);
+  if constexpr (sizeof(R) == 4) {
+    prims_from_htilde_x2(Ua, Ub, ha, hb, Wa, Wb);
+  } else {
+    prims_from_htilde(Ua[0], Ua[1], Ua[2], Ua[3], ha, Wa);
+    prims_from_htilde(Ub[0], Ub[1], Ub[2], Ub[3], hb, Wb);
+  }
   const R nan = R(__longlong_as_double(0x7ff8000000000000ULL));
   if (!pa) {
     Wa.rho = Wa.u[0] = Wa.u[1] = Wa.u[2] = Wa.p = Wa.T = Wa.h = Wa.gamma = Wa.rg = Wa.ht = nan;
@@ -408,6 +543,52 @@ template <class R> __device__ __forceinline__ bool prim2con(PrimX<R>& W, R U[5],
   return true;
 }
 
+// prim2con and phys_flux<d> of two float states (lanes x, y of W[v]) with
+// packed arithmetic; a lane with rho <= 0 or p <= 0 gets NaN conserved
+// values and its ok flag false.
+template <int d>
+__device__ __forceinline__ void prim2con_flux_x2(const float2 (&W)[5], float2 (&U)[5],
+                                                 float2 (&F)[5], bool& okx, bool& oky,
+                                                 int ori) {
+  using namespace pk;
+  okx = W[0].x > 0.0f && W[4].x > 0.0f;
+  oky = W[0].y > 0.0f && W[4].y > 0.0f;
+  const float2 T = mul(W[4], rcp(W[0]));
+  const float2 a = mul(mul(s2(2.25f), T), T);
+  const float2 sq = add(s2(1.f), make_float2(sqrtf(a.x + 1.0f), sqrtf(a.y + 1.0f)));
+  const float2 t2 = mul(a, rcp(sq));                       // htilde - 2.5 T
+  const float2 ht = fma(s2(2.5f), T, t2);
+  const float2 u2 = fma(W[3], W[3], fma(W[2], W[2], mul(W[1], W[1])));
+  const float2 g2 = add(s2(1.f), u2);
+  const float2 rg = rsq(g2);
+  const float2 gamma = mul(g2, rg);
+  const float2 D = mul(W[0], gamma);
+  const float2 Dh = mul(D, add(s2(1.f), ht));
+  U[0] = D;
+  U[1] = mul(Dh, W[1]);
+  U[2] = mul(Dh, W[2]);
+  U[3] = mul(Dh, W[3]);
+  if (ori) {
+    U[4] = fma(Dh, gamma, neg(W[4]));  // original scheme: E = D h gamma - p
+  } else {  // Et = D [U^2 / (gamma + 1) + (1.5 T + t2 + htilde U^2) / gamma]
+    const float2 k1 = mul(u2, rcp(add(gamma, s2(1.f))));
+    U[4] = mul(D, fma(fma(ht, u2, fma(s2(1.5f), T, t2)), rg, k1));
+  }
+  const float2 v = mul(W[1 + d], rg);
+  F[0] = mul(U[0], v);
+  F[1] = mul(U[1], v);
+  F[2] = mul(U[2], v);
+  F[3] = mul(U[3], v);
+  F[1 + d] = add(F[1 + d], W[4]);
+  F[4] = ori ? U[1 + d] : mul(add(U[4], W[4]), v);
+  const float nan = __int_as_float(0x7fc00000);
+#pragma unroll
+  for (int q = 0; q < 5; ++q) {
+    if (!okx) U[q].x = nan;
+    if (!oky) U[q].y = nan;
+  }
+}
+
 // Physical flux along d (Eqs. D evolution, M evolution, ETilde evolution).
 template <int d, class R>
 __device__ __forceinline__ void phys_flux(const PrimX<R>& W, const R U[5], R F[5], int ori = 0) {
@@ -439,6 +620,53 @@ __device__ __forceinline__ void char_speeds(const PrimX<R>& W, R& lm, R& lp) {
   lp = (a + b) * rden;
 }
 
+// phys_flux<d> and char_speeds<d> of the left and right float states with
+// packed arithmetic (lane x left, lane y right).
+template <int d>
+__device__ __forceinline__ void outer_parts_x2(const PrimX<float>& WL, const float UL[5],
+                                               const PrimX<float>& WR, const float UR[5],
+                                               float FL[5], float FR[5], float& lmL, float& lpL,
+                                               float& lmR, float& lpR, int ori) {
+  using namespace pk;
+  constexpr int a0 = d == 0 ? 1 : 0, b0 = d == 2 ? 1 : 2;  // transverse components
+  const float2 ud = make_float2(WL.u[d], WR.u[d]);
+  const float2 v = mul(ud, make_float2(WL.rg, WR.rg));
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const float2 f = mul(make_float2(UL[q], UR[q]), v);
+    FL[q] = f.x;
+    FR[q] = f.y;
+  }
+  FL[1 + d] += WL.p;
+  FR[1 + d] += WR.p;
+  if (ori) {
+    FL[4] = UL[1 + d];
+    FR[4] = UR[1 + d];
+  } else {
+    const float2 f = mul(add(make_float2(UL[4], UR[4]), make_float2(WL.p, WR.p)), v);
+    FL[4] = f.x;
+    FR[4] = f.y;
+  }
+  // outer characteristic speeds (char_speeds)
+  const float2 T = make_float2(WL.T, WR.T), h = make_float2(WL.h, WR.h);
+  const float2 cnum = mul(T, fma(s2(-8.f), T, mul(s2(5.f), h)));
+  const float2 cden = mul(mul(s2(3.f), h), sub(h, T));
+  const float2 cs2 = make_float2(cnum.x / cden.x, cnum.y / cden.y);
+  const float2 omc = sub(s2(1.f), cs2);
+  const float2 ua = make_float2(WL.u[a0], WR.u[a0]), ub = make_float2(WL.u[b0], WR.u[b0]);
+  const float2 up2 = fma(ub, ub, mul(ua, ua));
+  const float2 u2 = fma(ud, ud, up2);
+  const float2 rden = rcp(fma(u2, omc, s2(1.f)));
+  const float2 a = mul(mul(make_float2(WL.gamma, WR.gamma), ud), omc);
+  const float2 bb = mul(cs2, fma(up2, omc, s2(1.f)));
+  const float2 b = make_float2(sqrtf(bb.x), sqrtf(bb.y));
+  const float2 lm = mul(sub(a, b), rden), lp = mul(add(a, b), rden);
+  lmL = lm.x;
+  lmR = lm.y;
+  lpL = lp.x;
+  lpR = lp.y;
+}
+
 // Relativistic HLLC of Mignone & Bodo (2005) with E = Etilde + D inside the
 // solver (Section 3.1), HLLE when requested or when the contact state is not
 // admissible (discriminant < 0, contact speed outside the outer speeds, or
@@ -447,11 +675,15 @@ template <int d, class R>
 __device__ __forceinline__ int riemann(int solver, const PrimX<R>& WL, const R UL[5],
                                        const PrimX<R>& WR, const R UR[5], R F[5], int ori = 0) {
   R FL[5], FR[5];
-  phys_flux<d>(WL, UL, FL, ori);
-  phys_flux<d>(WR, UR, FR, ori);
   R lmL, lpL, lmR, lpR;
-  char_speeds<d>(WL, lmL, lpL);
-  char_speeds<d>(WR, lmR, lpR);
+  if constexpr (sizeof(R) == 4) {
+    outer_parts_x2<d>(WL, UL, WR, UR, FL, FR, lmL, lpL, lmR, lpR, ori);
+  } else {
+    phys_flux<d>(WL, UL, FL, ori);
+    phys_flux<d>(WR, UR, FR, ori);
+    char_speeds<d>(WL, lmL, lpL);
+    char_speeds<d>(WR, lmR, lpR);
+  }
   R sL = fmin(lmL, lmR);
   R sR = fmax(lpL, lpR);
   if (sL >= R(0)) {

@@ -97,9 +97,15 @@ def test_advection_steps_parity_and_conservation(oracle, prec):
         assert r["status"] == 0
         R = r["out"]
     err = cons_rel_err(G, R)
-    # FP64: rounding only; float paths: the 1e-5 per-step target for smooth
-    # flows, accumulated over the steps at the measured ~3e-6 per step
-    assert err.max() <= (1e-11 if prec == "fp64" else nsteps * 5e-6), err.max()
+    # FP64: rounding only. Float storage: rounding the conserved state to
+    # float perturbs the conversion by (1 + Mach^2) eps_float
+    # (Eq. ImprovedRelativeError; Mach = |U| / U_s, U_s^2 = cs^2 / (1 - cs^2)),
+    # once per step. Here gamma = 10 at T ~ 1 gives Mach^2 ~ 200.
+    P0 = oracle.con2pri(C.reshape(5, -1))["prim"]
+    cs2 = oracle.cs2_of_T(P0[4] / P0[0])
+    mach2 = (P0[1] ** 2 + P0[2] ** 2 + P0[3] ** 2) * (1 - cs2) / cs2
+    tol32 = nsteps * (1 + mach2.max()) * 2.0 ** -24
+    assert err.max() <= (1e-11 if prec == "fp64" else tol32), (err.max(), tol32)
     tot0 = C.reshape(5, -1).sum(1)
     totg = G.reshape(5, -1).sum(1)
     scale = np.abs(G.reshape(5, -1)).sum(1)
