@@ -57,7 +57,7 @@ struct PatchArgs {
 template <class S> struct SmemLayout {  // S: storage type
   static constexpr size_t prim_elems = 5 * kGC;        // primitive tile
   static constexpr size_t face_elems = 3 * 2 * 5 * kNF; // predicted faces / fluxes
-  static constexpr size_t ht_elems = kGC;               // htilde of the tile cells
+  static constexpr size_t ht_elems = kGC;               // conic parameter tau of the tile cells
   static constexpr size_t bytes = (prim_elems + face_elems + ht_elems) * sizeof(S);
 };
 
@@ -171,36 +171,36 @@ __device__ __forceinline__ void recon_direction(const S* prim, int tc, const Pri
 #pragma unroll
       for (int v = 0; v < 5; ++v) face_slot(face, d, 0, v)[fi] = S(Uq[v].y);
     }
-    return;
-  }
-  PrimX<R> Wm, Wp;
-  R fm[5], fp[5];
+  } else {
+    PrimX<R> Wm, Wp;
+    R fm[5], fp[5];
 #pragma unroll
-  for (int v = 0; v < 5; ++v) {
-    R lo = R(prim[v * kGC + tc - off]);
-    R hi = R(prim[v * kGC + tc + off]);
-    R dW = limited_slope(wc[v] - lo, hi - wc[v], theta);
-    fm[v] = wc[v] - R(0.5) * dW;
-    fp[v] = wc[v] + R(0.5) * dW;
-  }
-  Wm.rho = fm[0]; Wm.u[0] = fm[1]; Wm.u[1] = fm[2]; Wm.u[2] = fm[3]; Wm.p = fm[4];
-  Wp.rho = fp[0]; Wp.u[0] = fp[1]; Wp.u[1] = fp[2]; Wp.u[2] = fp[3]; Wp.p = fp[4];
-  R Um[5], Up[5], Fm[5], Fp[5];
-  if (!prim2con(Wm, Um, ori)) bad = 1;
-  if (!prim2con(Wp, Up, ori)) bad = 1;
-  phys_flux<d>(Wm, Um, Fm, ori);
-  phys_flux<d>(Wp, Up, Fp, ori);
+    for (int v = 0; v < 5; ++v) {
+      R lo = R(prim[v * kGC + tc - off]);
+      R hi = R(prim[v * kGC + tc + off]);
+      R dW = limited_slope(wc[v] - lo, hi - wc[v], theta);
+      fm[v] = wc[v] - R(0.5) * dW;
+      fp[v] = wc[v] + R(0.5) * dW;
+    }
+    Wm.rho = fm[0]; Wm.u[0] = fm[1]; Wm.u[1] = fm[2]; Wm.u[2] = fm[3]; Wm.p = fm[4];
+    Wp.rho = fp[0]; Wp.u[0] = fp[1]; Wp.u[1] = fp[2]; Wp.u[2] = fp[3]; Wp.p = fp[4];
+    R Um[5], Up[5], Fm[5], Fp[5];
+    if (!prim2con(Wm, Um, ori)) bad = 1;
+    if (!prim2con(Wp, Up, ori)) bad = 1;
+    phys_flux<d>(Wm, Um, Fm, ori);
+    phys_flux<d>(Wp, Up, Fp, ori);
 #pragma unroll
-  for (int v = 0; v < 5; ++v) dF[v] = dF[v] + (Fp[v] - Fm[v]);
-  if (trans && cd >= 0) {
-    int fi = face_index<d>(i, j, k, cd);
+    for (int v = 0; v < 5; ++v) dF[v] = dF[v] + (Fp[v] - Fm[v]);
+    if (trans && cd >= 0) {
+      int fi = face_index<d>(i, j, k, cd);
 #pragma unroll
-    for (int v = 0; v < 5; ++v) face_slot(face, d, 1, v)[fi] = S(Um[v]);
-  }
-  if (trans && cd <= 7) {
-    int fi = face_index<d>(i, j, k, cd + 1);
+      for (int v = 0; v < 5; ++v) face_slot(face, d, 1, v)[fi] = S(Um[v]);
+    }
+    if (trans && cd <= 7) {
+      int fi = face_index<d>(i, j, k, cd + 1);
 #pragma unroll
-    for (int v = 0; v < 5; ++v) face_slot(face, d, 0, v)[fi] = S(Up[v]);
+      for (int v = 0; v < 5; ++v) face_slot(face, d, 0, v)[fi] = S(Up[v]);
+    }
   }
 }
 
@@ -238,7 +238,7 @@ template <int d> __device__ __forceinline__ int face_owner(int fi, int side) {
 }
 
 // Riemann flux of face fi along d from the two predicted states in its
-// slots; their Newton solves start from the converged htilde of the cells
+// slots; their Newton solves start from the converged tau of the cells
 // they belong to (a warm start: the predicted state differs from the cell
 // state by half a limited slope and half a time step).
 template <int d, class P, bool PAIR>
@@ -317,8 +317,8 @@ __global__ void __launch_bounds__(NT, MINB) patch_kernel(PatchArgs a) {
         prim[2 * kGC + ca] = S(Wa.u[1]);
         prim[3 * kGC + ca] = S(Wa.u[2]);
         prim[4 * kGC + ca] = S(Wa.p);
-        hts[ca] = S(Wa.ht);
-        hts[cb] = S(Wb.ht);
+        hts[ca] = S(Wa.tau);
+        hts[cb] = S(Wb.tau);
         prim[cb] = S(Wb.rho);
         prim[kGC + cb] = S(Wb.u[0]);
         prim[2 * kGC + cb] = S(Wb.u[1]);
@@ -338,7 +338,7 @@ __global__ void __launch_bounds__(NT, MINB) patch_kernel(PatchArgs a) {
         prim[2 * kGC + c] = S(W.u[1]);
         prim[3 * kGC + c] = S(W.u[2]);
         prim[4 * kGC + c] = S(W.p);
-        hts[c] = S(W.ht);
+        hts[c] = S(W.tau);
       }
     }
     const int bad_input = __syncthreads_or(code & CODE_BAD_INPUT);
@@ -407,7 +407,7 @@ __global__ void __launch_bounds__(NT, MINB) patch_kernel(PatchArgs a) {
           const bool signal = a.partial_dt && a.cfl_mode != 1;
           for (int c0 = tid; c0 < kItems; c0 += NT) {
             S Un[NPC][5];
-            S g0[NPC];  // htilde of the cell before the step: warm start of the CFL solve
+            S g0[NPC];  // tau of the cell before the step: warm start of the CFL solve
             if constexpr (PAIR && sizeof(R) == 4) {
               // both cells' divergences in packed arithmetic
               int tcq[2], fq[2][6];

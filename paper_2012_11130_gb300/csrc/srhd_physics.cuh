@@ -20,14 +20,16 @@ namespace srhd {
 // A is formed in double in both precisions, so both use the double value.
 constexpr double kEpsUnphysical = 2e-16;
 
-// Newton stopping rule. Near the root the iteration converges
-// quadratically, e_{k+1} <= C e_k^2 in relative terms, with C <= 0.56 over
-// the whole range of states (measured with the oracle: rho 1e-6..1e2,
-// T 1e-8..1e4, gamma 1..1e4). Once a step satisfies |dh| <= tol htilde the
-// error left after applying it is at most C tol^2: 3e-17 for tol = 2^-27 in
-// double and 8e-9 for tol = 2^-13 in float, below the rounding of either
-// precision, so the iteration stops there instead of taking one more step.
-// A step that stops contracting at the rounding floor also ends it.
+// Newton stopping rule (for the conic-parameter iteration of the
+// conversions below). Near the root the iteration converges quadratically,
+// e_{k+1} <= C e_k^2 in relative terms, with C <= 0.56 over the whole range
+// of states (measured in double: rho 1e-6..1e2, T 1e-10..1e6, gamma 1..1e6;
+// largest 0.557). Once a step satisfies |dtau| <= tol tau the error left
+// after applying it is at most C tol^2: 3e-17 for tol = 2^-27 in double and
+// 8e-9 for tol = 2^-13 in float, below the rounding of either precision, so
+// the iteration stops there instead of taking one more step. (htilde and T
+// inherit the relative error of tau up to a factor below 2.) A step that
+// stops contracting at the rounding floor also ends it.
 template <class R> struct NewtonCfg;
 template <> struct NewtonCfg<double> {
   static constexpr double tol = 7.450580596923828e-09;  // 2^-27
@@ -59,6 +61,7 @@ template <class R> struct PrimX {
   R T, h, gamma;    // T = p/rho, h = 1 + htilde, gamma = sqrt(1 + U.U)
   R rg;             // 1 / gamma (three-velocity v = U rg)
   R ht;             // htilde (set by the conversions from conserved variables)
+  R tau;            // conic parameter h - T - 1 (set by the same conversions)
 };
 
 // Eq. (T_to_HTilde): htilde(T) without subtraction.
@@ -67,49 +70,16 @@ template <class R> __device__ __forceinline__ R htilde_of_T(R T) {
   return R(2.5) * T + qdiv(a, R(1) + sqrt(a + R(1)));
 }
 
-// Eq. (T of h) and its derivative Eq. (dT_dh), sharing one reciprocal square
-// root and one division: with x = 9 ht^2 + 18 ht + 25, s = sqrt(x),
-// den = 5 ht + 5 + s: T = (2 ht^2 + 4 ht)/den and
-// dT = [(4 ht + 4) - T ((9 ht + 9)/s + 5)] / den.
-template <class R> __device__ __forceinline__ void T_dT_of_htilde(R ht, R& T, R& dT) {
-  R x = (R(9) * ht + R(18)) * ht + R(25);
-  R rs = rsqrt_r(x);
-  R den = R(5) * ht + R(5) + x * rs;
-  R rden = qrcp(den);
-  T = (R(2) * ht + R(4)) * ht * rden;
-  dT = ((R(4) * ht + R(4)) - T * ((R(9) * ht + R(9)) * rs + R(5))) * rden;
-}
-
-template <class R> __device__ __forceinline__ R T_of_htilde(R ht) {
-  R x = (R(9) * ht + R(18)) * ht + R(25);
-  return qdiv((R(2) * ht + R(4)) * ht, R(5) * ht + R(5) + sqrt(x));
-}
-
 // Eq. (sound_speed): c_s^2 = T (5h - 8T) / (3h (h - T)).
 template <class R> __device__ __forceinline__ R cs2_of(R T, R h) {
   return T * (R(5) * h - R(8) * T) / (R(3) * h * (h - T));
 }
 
-// Eq. (transcendental equation) f(htilde) and Appendix A df/dhtilde, in a
-// form that cannot overflow float for m^2 up to ~1e30:
-// f  = ht (ht + 2) - 2 T h + T^2 hh/q,                 q = hh + m2
-// f' = 2h - 2T - 2h T' + 2T/q [T' hh (hh/q) + h (h T' + T) (m2/q)].
-template <class R>
-__device__ __forceinline__ void f_df(R ht, R T, R dT, R m2, R& f, R& df) {
-  R h = ht + R(1);
-  R hh = h * h;
-  R rq = qrcp(hh + m2);
-  R a1 = hh * rq, a2 = m2 * rq;
-  f = ht * (ht + R(2)) - R(2) * T * h + T * T * a1;
-  df = R(2) * h - R(2) * T - R(2) * h * dT +
-       R(2) * T * rq * (dT * hh * a1 + h * (h * dT + T) * a2);
-}
-
 // Packed FP32: the sm_100 family executes an add, a multiply or a fused
 // multiply-add on both lanes of a float2 as one instruction (each lane
-// rounded as its scalar counterpart). The paired Newton solves evaluate the
-// polynomial part of both states' iterations this way; reciprocals and
-// square roots stay per lane.
+// rounded as its scalar counterpart). Paired work (two Newton solves, the
+// two face states of a cell, the two sides of a face) is evaluated this
+// way; reciprocals and square roots stay per lane.
 namespace pk {
 __device__ __forceinline__ float2 s2(float a) { return make_float2(a, a); }
 // negation and subtraction as one packed instruction each (exact: x (-1))
@@ -120,39 +90,79 @@ __device__ __forceinline__ float2 mul(float2 a, float2 b) { return __fmul2_rn(a,
 __device__ __forceinline__ float2 fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 __device__ __forceinline__ float2 rcp(float2 a) { return make_float2(qrcp(a.x), qrcp(a.y)); }
 __device__ __forceinline__ float2 rsq(float2 a) { return make_float2(rsqrtf(a.x), rsqrtf(a.y)); }
-
-// T_dT_of_htilde and f_df on two lanes.
-__device__ __forceinline__ void T_dT_of_htilde(float2 ht, float2& T, float2& dT) {
-  const float2 x = fma(fma(ht, s2(9.f), s2(18.f)), ht, s2(25.f));
-  const float2 rs = rsq(x);
-  const float2 rden = rcp(fma(x, rs, fma(ht, s2(5.f), s2(5.f))));
-  T = mul(mul(fma(ht, s2(2.f), s2(4.f)), ht), rden);
-  // dT = [(4 ht + 4) + T ((-9 ht - 9) rs - 5)] rden
-  dT = mul(fma(T, fma(fma(ht, s2(-9.f), s2(-9.f)), rs, s2(-5.f)), fma(ht, s2(4.f), s2(4.f))),
-           rden);
-}
-__device__ __forceinline__ void f_df(float2 ht, float2 T, float2 dT, float2 m2, float2& f,
-                                     float2& df) {
-  const float2 h = add(ht, s2(1.f));
-  const float2 hh = mul(h, h);
-  const float2 rq = rcp(add(hh, m2));
-  const float2 a1 = mul(hh, rq), a2 = mul(m2, rq);
-  f = fma(mul(T, T), a1, fma(mul(s2(-2.f), T), h, mul(ht, add(ht, s2(2.f)))));
-  const float2 inner = fma(dT, mul(hh, a1), mul(mul(h, fma(h, dT, T)), a2));
-  // df = 2 [h (1 - dT) - T + T rq inner]
-  df = mul(s2(2.f), fma(mul(T, rq), inner, sub(mul(h, fma(dT, s2(-1.f), s2(1.f))), T)));
-}
+__device__ __forceinline__ float2 sqr(float2 a) { return make_float2(sqrtf(a.x), sqrtf(a.y)); }
 }  // namespace pk
 
-// Appendix A initial guess: hot (4/3) sqrt(A) above the Eq. (ColdHot)
-// threshold, else the positive root of the quadratic of Eq. (cold limit of
-// transcendental eq) in cancellation-free form.
-template <class R> __device__ __forceinline__ R newton_guess(R A, R m2) {
-  R P = R(1) + m2;
-  R tb = qdiv(R(1800) * P, R(437) * m2 + R(117));
-  if (A > tb * tb) return R(4.0 / 3.0) * sqrt(A);
-  R a = qdiv(R(43) * m2 + R(63), R(125) * P);
-  return qdiv(R(2) * A, R(1.2) + sqrt(R(1.44) + R(4) * a * A));
+// The same operations on one float, one double or a packed float2, for code
+// written once for all three (scalar forms may be contracted into FMAs).
+namespace ar {
+template <class V> __device__ __forceinline__ V c(double x) { return V(x); }
+template <> __device__ __forceinline__ float2 c<float2>(double x) { return pk::s2(float(x)); }
+__device__ __forceinline__ float add(float a, float b) { return a + b; }
+__device__ __forceinline__ double add(double a, double b) { return a + b; }
+__device__ __forceinline__ float2 add(float2 a, float2 b) { return pk::add(a, b); }
+__device__ __forceinline__ float mul(float a, float b) { return a * b; }
+__device__ __forceinline__ double mul(double a, double b) { return a * b; }
+__device__ __forceinline__ float2 mul(float2 a, float2 b) { return pk::mul(a, b); }
+__device__ __forceinline__ float fma(float a, float b, float d) { return fmaf(a, b, d); }
+__device__ __forceinline__ double fma(double a, double b, double d) { return ::fma(a, b, d); }
+__device__ __forceinline__ float2 fma(float2 a, float2 b, float2 d) { return pk::fma(a, b, d); }
+__device__ __forceinline__ float neg(float a) { return -a; }
+__device__ __forceinline__ double neg(double a) { return -a; }
+__device__ __forceinline__ float2 neg(float2 a) { return pk::neg(a); }
+__device__ __forceinline__ float rcp(float a) { return qrcp(a); }
+__device__ __forceinline__ double rcp(double a) { return qrcp(a); }
+__device__ __forceinline__ float2 rcp(float2 a) { return pk::rcp(a); }
+__device__ __forceinline__ float sqr(float a) { return sqrtf(a); }
+__device__ __forceinline__ double sqr(double a) { return sqrt(a); }
+__device__ __forceinline__ float2 sqr(float2 a) { return pk::sqr(a); }
+}  // namespace ar
+
+// ---- conserved -> primitive: Newton-Raphson on the conic parameter --------
+// The Taub-Mathews relation (h - 4T)(h - T) = 1 (Eq. TM EOS) is a hyperbola
+// in (T, h) with the rational parametrisation t = h - T >= 1,
+//   T = (t^2 - 1) / (3t),  h = (4t^2 - 1) / (3t).
+// With tau = t - 1 and the identity h^2 - 1 - 2Th + T^2 h^2/(h^2 + m^2) =
+// (h - T)^2 - 1 - T^2 m^2/(h^2 + m^2), the function f(htilde) of
+// Eq. (transcendental equation) becomes
+//   f = P N / Dn,  P = tau (2 + tau),  Q = (1 + 2 tau)(3 + 2 tau) = 4t^2 - 1,
+//   N = Q^2 + m^2 (8t^2 + 1),  Dn = Q^2 + 9 t^2 m^2,
+// where every term is positive (no cancellation, no square root). The
+// conversions solve P N / Dn = A for tau by Newton-Raphson and then take
+// htilde = tau (5 + 4 tau) / (3t) and T = tau (2 + tau) / (3t); the root is
+// the htilde of Eq. (transcendental equation). The start
+// tau0 = A / (1 + sqrt(1 + A)) is the exact root for m = 0 (there N = Dn)
+// and within 7 % of the root elsewhere. N and Dn are multiplied by
+// lam = 1 / (1 + tau0)^2, which leaves their ratio unchanged and keeps both
+// of order t^2 + m^2 (float range) instead of t^2 m^2.
+
+// Start of the iteration (V = float, double or float2).
+template <class V> __device__ __forceinline__ V tau_start(V A) {
+  using namespace ar;
+  return mul(A, rcp(add(c<V>(1.0), sqr(add(c<V>(1.0), A)))));
+}
+
+// Newton step delta = (P N/Dn - A) / (d/dtau)(P N/Dn) at tau. ml = m^2 lam,
+// ml9 = 9 m^2 lam, nA = -A (fixed per solve).
+template <class V>
+__device__ __forceinline__ V tau_step(V tau, V ml, V ml9, V nA, V lam) {
+  using namespace ar;
+  const V t = add(tau, c<V>(1.0));
+  const V t2 = add(t, t);
+  const V s = mul(t, t);
+  const V P = mul(tau, add(tau, c<V>(2.0)));
+  const V Q = mul(fma(tau, c<V>(2.0), c<V>(1.0)), fma(tau, c<V>(2.0), c<V>(3.0)));
+  const V Ql = mul(Q, lam);
+  const V QQl = mul(Q, Ql);
+  const V N = fma(ml, fma(s, c<V>(8.0), c<V>(1.0)), QQl);  // lam N
+  const V Dn = fma(ml9, s, QQl);                              // lam Dn
+  const V rD = rcp(Dn);
+  const V r = mul(N, rD);                                      // N / Dn
+  const V dN = mul(mul(t2, c<V>(8.0)), add(Ql, ml));          // lam dN/dtau = 16 t (Q + m^2) lam
+  const V dD = mul(t2, fma(Ql, c<V>(8.0), ml9));              // lam dDn/dtau = 2t (8Q + 9 m^2) lam
+  const V dr = mul(fma(neg(r), dD, dN), rD);                  // dr/dtau
+  const V dG = fma(t2, r, mul(P, dr));                        // d(P r)/dtau, P' = 2t
+  return mul(fma(P, r, nA), rcp(dG));
 }
 
 // Precision tags. S is the storage and arithmetic type; AT is the type in
@@ -321,32 +331,38 @@ __device__ __forceinline__ bool A_and_m2(typename P::S D, typename P::S Mx, type
   }
 }
 
-// Primitives from a converged htilde (Eq. four-velocity, Eq. new expression
-// of Lorentz factor, Eq. density, Eq. T of h, Eq. p=rhoT).
+// Primitives from the converged conic parameter tau (Eq. four-velocity,
+// Eq. new expression of Lorentz factor, Eq. density, Eq. p=rhoT):
+// htilde = tau (5 + 4 tau) / (3t), T = tau (2 + tau) / (3t), t = 1 + tau.
 template <class R, class S>
-__device__ __forceinline__ void prims_from_htilde(S D, S Mx, S My, S Mz, R ht, PrimX<R>& W) {
-  R h = R(1) + ht;
-  R rDh = R(1) / (R(D) * h);
+__device__ __forceinline__ void prims_from_tau(S D, S Mx, S My, S Mz, R tau, PrimX<R>& W) {
+  const R r3t = qrcp(R(3) * (R(1) + tau));
+  const R ht = tau * (R(5) + R(4) * tau) * r3t;
+  const R h = R(1) + ht;
+  const R rDh = R(1) / (R(D) * h);
   W.u[0] = R(Mx) * rDh;
   W.u[1] = R(My) * rDh;
   W.u[2] = R(Mz) * rDh;
-  R g2 = R(1) + (W.u[0] * W.u[0] + W.u[1] * W.u[1] + W.u[2] * W.u[2]);
-  R rg = rsqrt_r(g2);
+  const R g2 = R(1) + (W.u[0] * W.u[0] + W.u[1] * W.u[1] + W.u[2] * W.u[2]);
+  const R rg = rsqrt_r(g2);
   W.gamma = g2 * rg;
   W.rg = rg;
   W.rho = R(D) * rg;
-  W.T = T_of_htilde(ht);
+  W.T = tau * (R(2) + tau) * r3t;
   W.h = h;
   W.ht = ht;
+  W.tau = tau;
   W.p = W.rho * W.T;
 }
 
-// prims_from_htilde of two float states with packed arithmetic.
-__device__ __forceinline__ void prims_from_htilde_x2(const float (&Ua)[5], const float (&Ub)[5],
-                                                     float ha, float hb, PrimX<float>& Wa,
-                                                     PrimX<float>& Wb) {
+// prims_from_tau of two float states with packed arithmetic.
+__device__ __forceinline__ void prims_from_tau_x2(const float (&Ua)[5], const float (&Ub)[5],
+                                                  float2 tau, PrimX<float>& Wa,
+                                                  PrimX<float>& Wb) {
   using namespace pk;
-  const float2 ht = make_float2(ha, hb);
+  const float2 r3t = rcp(fma(tau, s2(3.f), s2(3.f)));
+  const float2 ht = mul(mul(tau, fma(tau, s2(4.f), s2(5.f))), r3t);
+  const float2 T = mul(mul(tau, add(tau, s2(2.f))), r3t);
   const float2 D = make_float2(Ua[0], Ub[0]);
   const float2 h = add(ht, s2(1.f));
   const float2 Dh = mul(D, h);
@@ -358,26 +374,33 @@ __device__ __forceinline__ void prims_from_htilde_x2(const float (&Ua)[5], const
   const float2 rg = rsq(g2);
   const float2 gamma = mul(g2, rg);
   const float2 rho = mul(D, rg);
-  // T of htilde (Eq. T of h)
-  const float2 x = fma(fma(ht, s2(9.f), s2(18.f)), ht, s2(25.f));
-  const float2 num = mul(fma(ht, s2(2.f), s2(4.f)), ht);
-  const float2 den = add(fma(ht, s2(5.f), s2(5.f)), make_float2(sqrtf(x.x), sqrtf(x.y)));
-  const float2 T = make_float2(qdiv(num.x, den.x), qdiv(num.y, den.y));
   const float2 p = mul(rho, T);
   Wa.rho = rho.x; Wa.u[0] = ux.x; Wa.u[1] = uy.x; Wa.u[2] = uz.x; Wa.p = p.x;
-  Wa.T = T.x; Wa.h = h.x; Wa.gamma = gamma.x; Wa.rg = rg.x; Wa.ht = ha;
+  Wa.T = T.x; Wa.h = h.x; Wa.gamma = gamma.x; Wa.rg = rg.x; Wa.ht = ht.x; Wa.tau = tau.x;
   Wb.rho = rho.y; Wb.u[0] = ux.y; Wb.u[1] = uy.y; Wb.u[2] = uz.y; Wb.p = p.y;
-  Wb.T = T.y; Wb.h = h.y; Wb.gamma = gamma.y; Wb.rg = rg.y; Wb.ht = hb;
+  Wb.T = T.y; Wb.h = h.y; Wb.gamma = gamma.y; Wb.rg = rg.y; Wb.ht = ht.y; Wb.tau = tau.y;
+}
+
+template <class R> __device__ __forceinline__ void set_nan(PrimX<R>& W) {
+  const R nan = R(__longlong_as_double(0x7ff8000000000000ULL));
+  W.rho = W.u[0] = W.u[1] = W.u[2] = W.p = W.T = W.h = W.gamma = W.rg = W.ht = W.tau = nan;
+}
+
+// Stopping rule of the Newton iterations (per state): the step just applied
+// was at most tol of tau, or it stopped contracting at the rounding floor.
+template <class R>
+__device__ __forceinline__ bool newton_done(R adh, R tau, R prev, int k) {
+  return adh <= NewtonCfg<R>::tol * tau ||
+         (k >= 3 && adh >= prev && adh <= NewtonCfg<R>::floor * tau);
 }
 
 // Conserved -> primitive (Section 2.3). Returns 0 ok, 1 unphysical, 2 no
-// convergence. Newton-Raphson on f(htilde) = A (monotone f), then
-// Eq. (four-velocity), Eq. (new expression of Lorentz factor), Eq. (density),
-// Eq. (T of h), Eq. (p=rhoT). A step that would make htilde non-positive
-// halves htilde instead. Stops when |dh| <= tol htilde, or when the step no
-// longer contracts at the rounding floor, or after maxit steps (status 2).
-// guess > 0 starts the iteration there (a warm start from a nearby state);
-// otherwise the Appendix A guess is used. The root does not depend on it.
+// convergence. A and m^2 as in Eq. (transcendental equation) and
+// Eq. (Unphysical result), then Newton-Raphson for the conic parameter tau
+// (see above); a step that would make tau non-positive halves tau instead.
+// Stops by newton_done or after maxit steps (status 2). guess > 0 is a tau
+// to start from (a warm start from a nearby state); otherwise tau_start(A).
+// The root does not depend on the start.
 template <class P>
 __device__ __forceinline__ int con2pri(typename P::S D, typename P::S Mx, typename P::S My,
                                        typename P::S Mz, typename P::S Et,
@@ -386,36 +409,35 @@ __device__ __forceinline__ int con2pri(typename P::S D, typename P::S Mx, typena
   using R = typename P::S;
   typename P::AT Aa, m2a;
   if (!A_and_m2<P>(D, Mx, My, Mz, Et, Aa, m2a, ori)) {
-    R nan = R(__longlong_as_double(0x7ff8000000000000ULL));
-    W.rho = W.u[0] = W.u[1] = W.u[2] = W.p = W.T = W.h = W.gamma = W.rg = W.ht = nan;
+    set_nan(W);
     return 1;
   }
   const R A = R(Aa), m2 = R(m2a);
-  R ht = guess > R(0) ? guess : newton_guess(A, m2);
+  const R t0 = tau_start(A);
+  R tau = guess > R(0) ? guess : t0;
+  const R t1 = R(1) + t0;
+  const R lam = qrcp(t1 * t1);
+  const R ml = m2 * lam, ml9 = R(9) * ml, nA = -A;
   int status = 2;
   R prev = R(3.0e38);
   for (int k = 1; k <= maxit; ++k) {
-    R T, dT, f, df;
-    T_dT_of_htilde(ht, T, dT);
-    f_df(ht, T, dT, m2, f, df);
-    R dh = qdiv(f - A, df);
-    R hn = ht - dh;
-    if (!(hn > R(0))) hn = R(0.5) * ht;
-    R adh = fabs(dh);
-    ht = hn;
-    if (adh <= NewtonCfg<R>::tol * ht) { status = 0; break; }
-    if (k >= 3 && adh >= prev && adh <= NewtonCfg<R>::floor * ht) { status = 0; break; }
+    const R dh = tau_step(tau, ml, ml9, nA, lam);
+    R tn = tau - dh;
+    if (!(tn > R(0))) tn = R(0.5) * tau;
+    const R adh = fabs(dh);
+    tau = tn;
+    if (newton_done(adh, tau, prev, k)) { status = 0; break; }
     prev = adh;
   }
-  prims_from_htilde(D, Mx, My, Mz, ht, W);
+  prims_from_tau(D, Mx, My, Mz, tau, W);
   return status;
 }
 
 // Two conserved -> primitive conversions advanced in lockstep: the same
-// Newton-Raphson iteration and stopping rule as con2pri, applied to two
-// independent states so that their dependency chains interleave (the
-// single solve is a chain of dependent square roots and divisions). The loop
-// runs until both have stopped; a state that has stopped is not updated.
+// iteration and stopping rule as con2pri, applied to two independent states
+// so that their dependency chains interleave (in float, both lanes of each
+// step are one packed instruction). The loop runs until both have stopped;
+// a state that has stopped is not updated.
 template <class P>
 __device__ __forceinline__ void con2pri_x2(const typename P::S (&Ua)[5],
                                            const typename P::S (&Ub)[5],
@@ -435,69 +457,74 @@ __device__ __forceinline__ void con2pri_x2(const typename P::S (&Ua)[5],
   // an unphysical state iterates on a harmless stand-in and is discarded
   const R Aa = pa ? R(Aa_) : R(1), m2a = pa ? R(ma_) : R(0);
   const R Ab = pb ? R(Ab_) : R(1), m2b = pb ? R(mb_) : R(0);
-  R ha = ga > R(0) ? ga : newton_guess(Aa, m2a);
-  R hb = gb > R(0) ? gb : newton_guess(Ab, m2b);
   bool da = false, db = false;
   sta = 2;
   stb = 2;
   R preva = R(3.0e38), prevb = R(3.0e38);
-  for (int k = 1; k <= maxit && !(da && db); ++k) {
-    R dha, dhb;
-    if constexpr (sizeof(R) == 4) {
-      float2 T, dT, f, df;
-      const float2 h2 = make_float2(ha, hb);
-      pk::T_dT_of_htilde(h2, T, dT);
-      pk::f_df(h2, T, dT, make_float2(m2a, m2b), f, df);
-      const float2 dh = pk::mul(pk::sub(f, make_float2(Aa, Ab)), pk::rcp(df));
-      dha = dh.x;
-      dhb = dh.y;
-    } else {
-      R Ta, dTa, fa, dfa, Tb, dTb, fb, dfb;
-      T_dT_of_htilde(ha, Ta, dTa);
-      T_dT_of_htilde(hb, Tb, dTb);
-      f_df(ha, Ta, dTa, m2a, fa, dfa);
-      f_df(hb, Tb, dTb, m2b, fb, dfb);
-      dha = qdiv(fa - Aa, dfa);
-      dhb = qdiv(fb - Ab, dfb);
-    }
-    if (!da) {
-      R hn = ha - dha;
-      if (!(hn > R(0))) hn = R(0.5) * ha;
-      R adh = fabs(dha);
-      ha = hn;
-      if (adh <= NewtonCfg<R>::tol * ha ||
-          (k >= 3 && adh >= preva && adh <= NewtonCfg<R>::floor * ha)) {
-        da = true;
-        sta = 0;
-      }
-      preva = adh;
-    }
-    if (!db) {
-      R hn = hb - dhb;
-      if (!(hn > R(0))) hn = R(0.5) * hb;
-      R adh = fabs(dhb);
-      hb = hn;
-      if (adh <= NewtonCfg<R>::tol * hb ||
-          (k >= 3 && adh >= prevb && adh <= NewtonCfg<R>::floor * hb)) {
-        db = true;
-        stb = 0;
-      }
-      prevb = adh;
-    }
-  }
   if constexpr (sizeof(R) == 4) {
-    prims_from_htilde_x2(Ua, Ub, ha, hb, Wa, Wb);
+    using namespace pk;
+    const float2 A2 = make_float2(Aa, Ab);
+    const float2 t0 = tau_start(A2);
+    float2 tau = make_float2(ga > 0.0f ? ga : t0.x, gb > 0.0f ? gb : t0.y);
+    const float2 t1 = add(t0, s2(1.f));
+    const float2 lam = rcp(mul(t1, t1));
+    const float2 ml = mul(make_float2(m2a, m2b), lam), ml9 = mul(ml, s2(9.f));
+    const float2 nA = neg(A2);
+    for (int k = 1; k <= maxit && !(da && db); ++k) {
+      const float2 dh = tau_step(tau, ml, ml9, nA, lam);
+      if (!da) {
+        float tn = tau.x - dh.x;
+        if (!(tn > 0.0f)) tn = 0.5f * tau.x;
+        const float adh = fabsf(dh.x);
+        tau.x = tn;
+        if (newton_done(adh, tn, preva, k)) { da = true; sta = 0; }
+        preva = adh;
+      }
+      if (!db) {
+        float tn = tau.y - dh.y;
+        if (!(tn > 0.0f)) tn = 0.5f * tau.y;
+        const float adh = fabsf(dh.y);
+        tau.y = tn;
+        if (newton_done(adh, tn, prevb, k)) { db = true; stb = 0; }
+        prevb = adh;
+      }
+    }
+    prims_from_tau_x2(Ua, Ub, tau, Wa, Wb);
   } else {
-    prims_from_htilde(Ua[0], Ua[1], Ua[2], Ua[3], ha, Wa);
-    prims_from_htilde(Ub[0], Ub[1], Ub[2], Ub[3], hb, Wb);
+    const R t0a = tau_start(Aa), t0b = tau_start(Ab);
+    R ta = ga > R(0) ? ga : t0a, tb = gb > R(0) ? gb : t0b;
+    const R t1a = R(1) + t0a, t1b = R(1) + t0b;
+    const R lama = qrcp(t1a * t1a), lamb = qrcp(t1b * t1b);
+    const R mla = m2a * lama, mlb = m2b * lamb;
+    for (int k = 1; k <= maxit && !(da && db); ++k) {
+      const R dha = tau_step(ta, mla, R(9) * mla, -Aa, lama);
+      const R dhb = tau_step(tb, mlb, R(9) * mlb, -Ab, lamb);
+      if (!da) {
+        R tn = ta - dha;
+        if (!(tn > R(0))) tn = R(0.5) * ta;
+        const R adh = fabs(dha);
+        ta = tn;
+        if (newton_done(adh, tn, preva, k)) { da = true; sta = 0; }
+        preva = adh;
+      }
+      if (!db) {
+        R tn = tb - dhb;
+        if (!(tn > R(0))) tn = R(0.5) * tb;
+        const R adh = fabs(dhb);
+        tb = tn;
+        if (newton_done(adh, tn, prevb, k)) { db = true; stb = 0; }
+        prevb = adh;
+      }
+    }
+    prims_from_tau(Ua[0], Ua[1], Ua[2], Ua[3], ta, Wa);
+    prims_from_tau(Ub[0], Ub[1], Ub[2], Ub[3], tb, Wb);
   }
-  const R nan = R(__longlong_as_double(0x7ff8000000000000ULL));
   if (!pa) {
-    Wa.rho = Wa.u[0] = Wa.u[1] = Wa.u[2] = Wa.p = Wa.T = Wa.h = Wa.gamma = Wa.rg = Wa.ht = nan;
+    set_nan(Wa);
     sta = 1;
   }
   if (!pb) {
-    Wb.rho = Wb.u[0] = Wb.u[1] = Wb.u[2] = Wb.p = Wb.T = Wb.h = Wb.gamma = Wb.rg = Wb.ht = nan;
+    set_nan(Wb);
     stb = 1;
   }
 }
