@@ -61,10 +61,10 @@ PEAK_FP64_TFLOPS = 1.25
 # only for the kernel sources with the recorded hash.
 # Captured at 128^3 (4096 patches) and scaled by 8 to the 32768-patch launch
 # (profiles/patch_kernel_advection128.md).
-NCU_TRAFFIC = {"sources_sha": "c34452f24989e938",
-               "mixed_cf": 8 * (142.862336e6 + 25.040384e6),
-               "mixed": 8 * (141.856512e6 + 23.923456e6),
-               "fp64": 8 * (273.881600e6 + 67.597568e6)}
+NCU_TRAFFIC = {"sources_sha": "6453d0c260cab094",
+               "mixed_cf": 8 * (141.691392e6 + 23.852800e6),
+               "mixed": 8 * (141.719296e6 + 24.104192e6),
+               "fp64": 8 * (273.167360e6 + 67.307776e6)}
 
 
 def kernel_sources_sha() -> str:
