@@ -211,6 +211,73 @@ srhd_status srhd_fill_ghosts_uniform(srhd_ctx* ctx, srhd_prec prec, const void* 
                                      void* ghosted, int32_t npx, int32_t npy, int32_t npz,
                                      const int32_t* bc, void* stream);
 
+/* ---- AMR: the steps around the per-patch update in a patch hierarchy ----
+ * Section 3.1: data live in 8^3 patches on levels l = 0, 1, ... (level l has
+ * a cell 2^l times finer than level 0) and level l takes two substeps per
+ * step of level l-1. The calls below work on one array of all patches of
+ * all levels, [ntotal][5][8^3] (a patch is an index into it); the caller
+ * builds the maps from its hierarchy (paper_2012_11130_gb300/amr.py does).
+ * They move data only and are HBM-bound. Map entries are range checked on
+ * the device: an invalid entry gives NaN (fill) or is skipped. */
+
+/* Ghost-zone fill of the patches p0 .. p0+n-1 (all cells of their 12^3
+ * tiles, interior included), from a source map. The paper fills the ghost
+ * zones of a fine patch from its own level where that level covers them and
+ * otherwise from the coarser level; here the coarse value is the
+ * coarse cell containing the ghost cell (piecewise-constant prolongation,
+ * conservative and physical whenever the coarse state is), interpolated
+ * linearly in time between the coarse level's states before and after its
+ * step. Boundary conditions are encoded in the map (a copy of an edge cell
+ * for outflow, a wrapped cell for periodic, a fixed state for inflow).
+ *   cur, prev [ntotal][5][8^3]: the latest interior states of all patches,
+ *       and those before each level's latest step;
+ *   ghosted [ntotal][5][12^3] output (rows p0 .. p0+n-1 written);
+ *   map [ntotal][12^3] int32 (row p for patch p), per tile cell:
+ *       q >= 0, bit 30 clear: copy of cur cell q (q = patch * 512 + cell,
+ *             cell = (k*8 + j)*8 + i);
+ *       q >= 0, bit 30 set (SRHD_AMR_COARSE): (1-w) prev[q'] + w cur[q'],
+ *             q' = q without bit 30;
+ *       q < 0: special state -1-q of `special` [nspecial][5] (device, may
+ *             be NULL when nspecial == 0);
+ *   ntotal >= 1, 0 <= p0, n >= 0, p0 + n <= ntotal, 0 <= w <= 1. */
+#define SRHD_AMR_COARSE (1 << 30)
+srhd_status srhd_amr_fill_ghosts(srhd_ctx* ctx, srhd_prec prec, const void* cur,
+                                 const void* prev, void* ghosted, const int32_t* map,
+                                 int32_t ntotal, int32_t p0, int32_t n, double w,
+                                 const void* special, int32_t nspecial, void* stream);
+
+/* Restriction: each listed parent patch takes, in every cell, the mean of
+ * the 2x2x2 cells of its child covering that cell (volume average, so the
+ * mass, momentum and energy of the coarse level equal those of the fine one
+ * where it is refined).
+ *   cur [ntotal][5][8^3] in/out;
+ *   children [nparent][9] int32: parent index, then the children of octants
+ *       cx + 2 cy + 4 cz (cx = 1 for the child of larger x). */
+srhd_status srhd_amr_restrict(srhd_ctx* ctx, srhd_prec prec, void* cur,
+                              const int32_t* children, int32_t nparent, int32_t ntotal,
+                              void* stream);
+
+/* Coarse-fine flux correction (the correction that keeps the
+ * composite grid conservative): the coarse cells on a patch face bordering
+ * the finer level are corrected by U += s (dt/dh) (F_coarse - <F_fine>),
+ * s = +1 on a high face and -1 on a low one, with F_coarse the patch-face
+ * flux of the coarse step and <F_fine> the mean of the fine patch-face fluxes
+ * over the 2x2 fine faces covering the coarse face and over the two fine
+ * substeps.
+ *   cur [ntotal][5][8^3] in/out;
+ *   flux_coarse, flux_fine0, flux_fine1 [ntotal][6][5][64]: patch-face
+ *       fluxes (srhd_advance_patches' patch_face_flux) of the coarse step and
+ *       of the two fine substeps;
+ *   faces [nrows][25] int32: coarse patch, then for faces -x,+x,-y,+y,-z,+z
+ *       the four fine patches across it, ordered qa + 2 qb by quadrant (qa
+ *       along the lower transverse axis), or -1 for a face that does not
+ *       border the finer level; a coarse patch appears in one row only;
+ *   dt_dh [ntotal][2] device doubles (the coarse patch's dt, dh). */
+srhd_status srhd_amr_flux_correct(srhd_ctx* ctx, srhd_prec prec, void* cur,
+                                  const void* flux_coarse, const void* flux_fine0,
+                                  const void* flux_fine1, const int32_t* faces, int32_t nrows,
+                                  const double* dt_dh, int32_t ntotal, void* stream);
+
 /* CFL time step of a batch of interior patches, like srhd_cfl_dt, for
  * callers that cannot allocate device memory. (The paper has no counterpart:
  * this is a deployment variant of srhd_cfl_dt.) Some callers cannot call

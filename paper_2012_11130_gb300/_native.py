@@ -24,7 +24,9 @@ PATCH_UNPHYSICAL, PATCH_BAD_INPUT, PATCH_NOCONV = 1, 2, 4
 # Every symbol declared in include/srhd.h.
 EXPORTS = ("srhd_default_params", "srhd_create", "srhd_destroy", "srhd_last_error",
            "srhd_prim2con", "srhd_con2pri", "srhd_flux_patches", "srhd_advance_patches",
-           "srhd_cfl_dt", "srhd_fill_ghosts_uniform", "srhd_cfl_dt_noalloc")
+           "srhd_cfl_dt", "srhd_fill_ghosts_uniform", "srhd_cfl_dt_noalloc",
+           "srhd_amr_fill_ghosts", "srhd_amr_restrict", "srhd_amr_flux_correct")
+SRHD_AMR_COARSE = 1 << 30
 
 
 class Params(ctypes.Structure):
@@ -73,6 +75,13 @@ def load(path: str = LIB_PATH):
     L.srhd_cfl_dt.argtypes = [vp, ctypes.c_int, vp, i32, d, vp, vp]
     L.srhd_fill_ghosts_uniform.restype = st
     L.srhd_fill_ghosts_uniform.argtypes = [vp, ctypes.c_int, vp, vp, i32, i32, i32, i32p, vp]
+    L.srhd_amr_fill_ghosts.restype = st
+    L.srhd_amr_fill_ghosts.argtypes = [vp, ctypes.c_int, vp, vp, vp, vp, i32, i32, i32, d, vp,
+                                       i32, vp]
+    L.srhd_amr_restrict.restype = st
+    L.srhd_amr_restrict.argtypes = [vp, ctypes.c_int, vp, vp, i32, i32, vp]
+    L.srhd_amr_flux_correct.restype = st
+    L.srhd_amr_flux_correct.argtypes = [vp, ctypes.c_int, vp, vp, vp, vp, vp, i32, vp, i32, vp]
     _lib = L
     return L
 

@@ -1,0 +1,159 @@
+// AMR kernels of libsrhd (sm_103a): the steps on either side of the
+// per-patch update in a hierarchy of 8^3 patches (Section 3.1 of
+// arXiv 2012.11130 and its flux-correction and ghost-zone passage):
+//   amr_fill_kernel            ghost zones from a precomputed source map:
+//                              same-level copies, piecewise-constant
+//                              prolongation from the coarser level (linear in
+//                              time between its old and new states),
+//                              boundary states;
+//   amr_restrict_kernel        fine -> coarse averaging (2x2x2 children);
+//   amr_flux_correct_kernel    coarse-fine flux correction with the patch-face
+//                              fluxes of the coarse step and of the two fine
+//                              substeps.
+// All three move data: they are bound by HBM bandwidth. Every index that
+// comes from a map is range checked on the device; an invalid entry gives
+// NaN (fill) or is skipped (restriction, correction), never an access out of
+// bounds.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace srhd {
+
+constexpr int kAmrTile = 12 * 12 * 12;   // ghosted tile cells
+constexpr int kAmrInt = 8 * 8 * 8;       // interior cells
+constexpr int32_t kAmrCoarseBit = 1 << 30;
+
+// ghosted[p][v][c] for p in [p0, p0 + n), c in the 12^3 tile, from
+// map[p][c]: >= 0 without kAmrCoarseBit -> cur[q] (q = patch * 512 + cell);
+// with kAmrCoarseBit -> (1 - w) prev[q] + w cur[q]; < 0 -> special[-1 - m].
+template <class S>
+__global__ void amr_fill_kernel(const S* __restrict__ cur, const S* __restrict__ prev,
+                                S* __restrict__ ghosted, const int32_t* __restrict__ map,
+                                int64_t p0, int64_t n, int64_t ncells, S w,
+                                const S* __restrict__ special, int nspecial) {
+  const int64_t total = n * kAmrTile;
+  const S nan = S(__longlong_as_double(0x7ff8000000000000ULL));
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t pl = q / kAmrTile;
+    const int c = int(q - pl * kAmrTile);
+    const int64_t p = p0 + pl;
+    const int32_t m = map[p * kAmrTile + c];
+    S* g = ghosted + p * 5 * kAmrTile + c;
+    if (m < 0) {
+      const int k = -1 - m;
+      const bool ok = k < nspecial;
+#pragma unroll
+      for (int v = 0; v < 5; ++v) g[v * kAmrTile] = ok ? special[k * 5 + v] : nan;
+      continue;
+    }
+    const bool coarse = (m & kAmrCoarseBit) != 0;
+    const int64_t src = m & ~kAmrCoarseBit;
+    if (src >= ncells) {
+#pragma unroll
+      for (int v = 0; v < 5; ++v) g[v * kAmrTile] = nan;
+      continue;
+    }
+    const int64_t sp = src / kAmrInt, sc = src - sp * kAmrInt;
+    const S* a = cur + sp * 5 * kAmrInt + sc;
+    if (coarse) {
+      const S* b = prev + sp * 5 * kAmrInt + sc;
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        const S x = b[v * kAmrInt], y = a[v * kAmrInt];
+        g[v * kAmrTile] = x + w * (y - x);
+      }
+    } else {
+#pragma unroll
+      for (int v = 0; v < 5; ++v) g[v * kAmrTile] = a[v * kAmrInt];
+    }
+  }
+}
+
+// Every cell of the listed parent patches becomes the mean of the 2x2x2
+// cells of the child that covers it. children[r] = {parent, child of octant
+// 0..7} (octant = cx + 2 cy + 4 cz). The eight values are summed pairwise in
+// a fixed order, then scaled by 1/8 (exact).
+template <class S>
+__global__ void amr_restrict_kernel(S* __restrict__ cur, const int32_t* __restrict__ children,
+                                    int64_t nparent, int64_t npatch_total) {
+  const int64_t total = nparent * kAmrInt;
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = q / kAmrInt;
+    const int c = int(q - r * kAmrInt);
+    const int i = c & 7, j = (c >> 3) & 7, k = c >> 6;
+    const int32_t par = children[r * 9];
+    const int32_t ch = children[r * 9 + 1 + (i >> 2) + 2 * (j >> 2) + 4 * (k >> 2)];
+    if (par < 0 || par >= npatch_total || ch < 0 || ch >= npatch_total) continue;
+    const int fi = 2 * (i & 3), fj = 2 * (j & 3), fk = 2 * (k & 3);
+    const int f0 = (fk * 8 + fj) * 8 + fi;
+    const S* fsrc = cur + (int64_t)ch * 5 * kAmrInt;
+    S* dst = cur + (int64_t)par * 5 * kAmrInt + c;
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+      const S* f = fsrc + v * kAmrInt + f0;
+      const S s0 = f[0] + f[1], s1 = f[8] + f[9], s2 = f[64] + f[65], s3 = f[72] + f[73];
+      dst[v * kAmrInt] = ((s0 + s1) + (s2 + s3)) * S(0.125);
+    }
+  }
+}
+
+// Flux correction of unrefined coarse patches. faces[r] = {coarse patch,
+// then for each patch face f = 0..5 (-x, +x, -y, +y, -z, +z) the four fine
+// patches across it, ordered qa + 2 qb by the quadrant of the face
+// (qa along the lower transverse axis), or -1 where the face does not border
+// the finer level}. flux_* are patch-face fluxes [patch][6][5][64]
+// (face cell t = a + 8 b, a along the lower transverse axis). For a coarse
+// cell on face f: U += s (dt/dh) (F_coarse - <F_fine>), s = +1 on a high face,
+// -1 on a low one, <F_fine> the mean over the 2x2 fine faces and the two fine
+// substeps. One block per listed coarse patch; the faces of a patch are done
+// one after another (a corner cell borders several).
+template <class S>
+__global__ void amr_flux_correct_kernel(S* __restrict__ cur, const S* __restrict__ flux_c,
+                                        const S* __restrict__ flux_f0,
+                                        const S* __restrict__ flux_f1,
+                                        const int32_t* __restrict__ faces, int64_t nface_rows,
+                                        const double* __restrict__ dt_dh,
+                                        int64_t npatch_total) {
+  constexpr int kF = 6 * 5 * 64;
+  for (int64_t r = blockIdx.x; r < nface_rows; r += gridDim.x) {
+    const int32_t cp = faces[r * 25];
+    if (cp < 0 || cp >= npatch_total) continue;  // uniform per block
+    const S coef = S(dt_dh[2 * cp] / dt_dh[2 * cp + 1]);
+    for (int f = 0; f < 6; ++f) {
+      const int32_t* fp = faces + r * 25 + 1 + 4 * f;
+      const bool active = fp[0] >= 0;
+      if (active) {
+        const int d = f >> 1, high = f & 1;
+        for (int q = threadIdx.x; q < 5 * 64; q += blockDim.x) {
+          const int v = q >> 6, t = q & 63, a = t & 7, b = t >> 3;
+          const int32_t fine = fp[(a >> 2) + 2 * (b >> 2)];
+          if (fine < 0 || fine >= npatch_total) continue;
+          // fine face cells covering coarse face cell (a, b)
+          const int fa = 2 * (a & 3), fb = 2 * (b & 3);
+          const int fside = 2 * d + (1 - high);
+          const S* F0 = flux_f0 + (int64_t)fine * kF + (fside * 5 + v) * 64;
+          const S* F1 = flux_f1 + (int64_t)fine * kF + (fside * 5 + v) * 64;
+          const int t0 = fb * 8 + fa;
+          const S fsum = ((F0[t0] + F0[t0 + 1]) + (F0[t0 + 8] + F0[t0 + 9])) +
+                         ((F1[t0] + F1[t0 + 1]) + (F1[t0 + 8] + F1[t0 + 9]));
+          const S fc = flux_c[(int64_t)cp * kF + (f * 5 + v) * 64 + t];
+          const S du = coef * (fc - S(0.125) * fsum);
+          const int e = high ? 7 : 0;
+          int i, j, k;
+          if (d == 0) { i = e; j = a; k = b; }
+          else if (d == 1) { i = a; j = e; k = b; }
+          else { i = a; j = b; k = e; }
+          S* u = cur + (int64_t)cp * 5 * kAmrInt + v * kAmrInt + (k * 8 + j) * 8 + i;
+          *u = high ? *u + du : *u - du;
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+}  // namespace srhd

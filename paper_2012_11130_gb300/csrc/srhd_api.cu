@@ -8,6 +8,7 @@
 #include <new>
 
 #include "srhd.h"
+#include "srhd_amr.cuh"
 #include "srhd_kernels.cuh"
 
 namespace srhd {
@@ -372,6 +373,89 @@ srhd_status srhd_fill_ghosts_uniform(srhd_ctx* c, srhd_prec prec, const void* in
     return decltype(L)::fill_ghosts(interior, ghosted, npx, npy, npz, bc, grid, s);
   });
   return e == cudaSuccess ? SRHD_OK : cuda_fail(e, "fill_ghosts launch");
+}
+
+// ---- AMR ---------------------------------------------------------------------
+namespace {
+bool is_double(srhd_prec prec) { return prec == SRHD_FP64; }
+}  // namespace
+
+srhd_status srhd_amr_fill_ghosts(srhd_ctx* c, srhd_prec prec, const void* cur, const void* prev,
+                                 void* ghosted, const int32_t* map, int32_t ntotal, int32_t p0,
+                                 int32_t n, double w, const void* special, int32_t nspecial,
+                                 void* stream) {
+  srhd_status st = check_ctx(c);
+  if (st != SRHD_OK) return st;
+  if (!valid_prec(prec)) return fail(SRHD_ERR_ARG, "invalid precision %d", int(prec));
+  if (ntotal < 1 || p0 < 0 || n < 0 || (int64_t)p0 + n > ntotal)
+    return fail(SRHD_ERR_ARG, "patch range [%d, %d) outside [0, %d)", p0, p0 + n, ntotal);
+  if (!(w >= 0.0 && w <= 1.0)) return fail(SRHD_ERR_ARG, "time weight w must be in [0, 1]");
+  if (nspecial < 0 || (nspecial > 0 && !special))
+    return fail(SRHD_ERR_ARG, "special states: nspecial < 0 or NULL array");
+  if (n == 0) return SRHD_OK;
+  if (!cur || !prev || !ghosted || !map) return fail(SRHD_ERR_ARG, "cur/prev/ghosted/map is NULL");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int grid = grid_for(c, (int64_t)n * srhd::kAmrTile, 16);
+  const int64_t ncells = (int64_t)ntotal * srhd::kAmrInt;
+  if (is_double(prec))
+    srhd::amr_fill_kernel<double><<<grid, 256, 0, s>>>(
+        static_cast<const double*>(cur), static_cast<const double*>(prev),
+        static_cast<double*>(ghosted), map, p0, n, ncells, w, static_cast<const double*>(special),
+        nspecial);
+  else
+    srhd::amr_fill_kernel<float><<<grid, 256, 0, s>>>(
+        static_cast<const float*>(cur), static_cast<const float*>(prev),
+        static_cast<float*>(ghosted), map, p0, n, ncells, float(w),
+        static_cast<const float*>(special), nspecial);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? SRHD_OK : cuda_fail(e, "amr_fill launch");
+}
+
+srhd_status srhd_amr_restrict(srhd_ctx* c, srhd_prec prec, void* cur, const int32_t* children,
+                              int32_t nparent, int32_t ntotal, void* stream) {
+  srhd_status st = check_ctx(c);
+  if (st != SRHD_OK) return st;
+  if (!valid_prec(prec)) return fail(SRHD_ERR_ARG, "invalid precision %d", int(prec));
+  if (nparent < 0 || ntotal < 1) return fail(SRHD_ERR_ARG, "nparent < 0 or ntotal < 1");
+  if (nparent == 0) return SRHD_OK;
+  if (!cur || !children) return fail(SRHD_ERR_ARG, "cur/children is NULL");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int grid = grid_for(c, (int64_t)nparent * srhd::kAmrInt, 16);
+  if (is_double(prec))
+    srhd::amr_restrict_kernel<double><<<grid, 256, 0, s>>>(static_cast<double*>(cur), children,
+                                                          nparent, ntotal);
+  else
+    srhd::amr_restrict_kernel<float><<<grid, 256, 0, s>>>(static_cast<float*>(cur), children,
+                                                         nparent, ntotal);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? SRHD_OK : cuda_fail(e, "amr_restrict launch");
+}
+
+srhd_status srhd_amr_flux_correct(srhd_ctx* c, srhd_prec prec, void* cur, const void* flux_coarse,
+                                  const void* flux_fine0, const void* flux_fine1,
+                                  const int32_t* faces, int32_t nrows, const double* dt_dh,
+                                  int32_t ntotal, void* stream) {
+  srhd_status st = check_ctx(c);
+  if (st != SRHD_OK) return st;
+  if (!valid_prec(prec)) return fail(SRHD_ERR_ARG, "invalid precision %d", int(prec));
+  if (nrows < 0 || ntotal < 1) return fail(SRHD_ERR_ARG, "nrows < 0 or ntotal < 1");
+  if (nrows == 0) return SRHD_OK;
+  if (!cur || !flux_coarse || !flux_fine0 || !flux_fine1 || !faces || !dt_dh)
+    return fail(SRHD_ERR_ARG, "a pointer argument is NULL");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int grid = nrows < c->num_sms * 8 ? nrows : c->num_sms * 8;
+  if (is_double(prec))
+    srhd::amr_flux_correct_kernel<double><<<grid, 320, 0, s>>>(
+        static_cast<double*>(cur), static_cast<const double*>(flux_coarse),
+        static_cast<const double*>(flux_fine0), static_cast<const double*>(flux_fine1), faces,
+        nrows, dt_dh, ntotal);
+  else
+    srhd::amr_flux_correct_kernel<float><<<grid, 320, 0, s>>>(
+        static_cast<float*>(cur), static_cast<const float*>(flux_coarse),
+        static_cast<const float*>(flux_fine0), static_cast<const float*>(flux_fine1), faces,
+        nrows, dt_dh, ntotal);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? SRHD_OK : cuda_fail(e, "amr_flux_correct launch");
 }
 
 }  // extern "C"

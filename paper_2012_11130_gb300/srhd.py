@@ -25,7 +25,8 @@ import torch
 from . import _native as N
 
 __all__ = ["Params", "Context", "prim2con", "con2pri", "flux_patches", "advance_patches",
-           "cfl_dt", "fill_ghosts_uniform", "default_context"]
+           "cfl_dt", "fill_ghosts_uniform", "amr_fill_ghosts", "amr_restrict",
+           "amr_flux_correct", "default_context"]
 
 
 @dataclass
@@ -271,6 +272,50 @@ class Context:
                                                  _stream(stream)), "srhd_fill_ghosts_uniform")
         return ghosted
 
+    # ---- AMR (include/srhd.h: srhd_amr_*) -------------------------------------
+    def amr_fill_ghosts(self, cur, prev, ghosted, amr_map, p0, n, w=0.0, special=None,
+                        stream=None, prec=None):
+        """Ghost-zone fill of patches p0..p0+n-1 from the source map
+        [ntotal][12^3] (int32); cur/prev [ntotal][5][8][8][8]."""
+        _need_cuda(cur, "cur")
+        _need_cuda(prev, "prev", cur.dtype)
+        _need_cuda(ghosted, "ghosted", cur.dtype)
+        _need_cuda(amr_map, "map", torch.int32)
+        nsp = 0 if special is None else special.shape[0]
+        if special is not None:
+            _need_cuda(special, "special", cur.dtype)
+        N.check(self._L.srhd_amr_fill_ghosts(self._h, _prec(cur, prec), _ptr(cur), _ptr(prev),
+                                             _ptr(ghosted), _ptr(amr_map), cur.shape[0], p0, n,
+                                             float(w), _ptr(special), nsp, _stream(stream)),
+                "srhd_amr_fill_ghosts")
+        return ghosted
+
+    def amr_restrict(self, cur, children, stream=None, prec=None):
+        """Fine -> coarse averaging; children [nparent][9] int32."""
+        _need_cuda(cur, "cur")
+        _need_cuda(children, "children", torch.int32)
+        N.check(self._L.srhd_amr_restrict(self._h, _prec(cur, prec), _ptr(cur), _ptr(children),
+                                          children.shape[0], cur.shape[0], _stream(stream)),
+                "srhd_amr_restrict")
+        return cur
+
+    def amr_flux_correct(self, cur, flux_coarse, flux_fine0, flux_fine1, faces, dt_dh,
+                         stream=None, prec=None):
+        """Coarse-fine flux correction; faces [nrows][25] int32; patch-face
+        fluxes [ntotal][6][5][64]; dt_dh [ntotal][2] float64."""
+        _need_cuda(cur, "cur")
+        for t, nm in ((flux_coarse, "flux_coarse"), (flux_fine0, "flux_fine0"),
+                      (flux_fine1, "flux_fine1")):
+            _need_cuda(t, nm, cur.dtype)
+        _need_cuda(faces, "faces", torch.int32)
+        _need_cuda(dt_dh, "dt_dh", torch.float64)
+        N.check(self._L.srhd_amr_flux_correct(self._h, _prec(cur, prec), _ptr(cur),
+                                              _ptr(flux_coarse), _ptr(flux_fine0),
+                                              _ptr(flux_fine1), _ptr(faces), faces.shape[0],
+                                              _ptr(dt_dh), cur.shape[0], _stream(stream)),
+                "srhd_amr_flux_correct")
+        return cur
+
 
 _default = {}
 
@@ -306,3 +351,19 @@ def cfl_dt(cons, dh, dt_out=None, stream=None, prec=None):
 
 def fill_ghosts_uniform(interior, npx, npy, npz, bc=("periodic",) * 3, ghosted=None, stream=None):
     return default_context().fill_ghosts_uniform(interior, npx, npy, npz, bc, ghosted, stream)
+
+
+def amr_fill_ghosts(cur, prev, ghosted, amr_map, p0, n, w=0.0, special=None, stream=None,
+                    prec=None):
+    return default_context().amr_fill_ghosts(cur, prev, ghosted, amr_map, p0, n, w, special,
+                                             stream, prec)
+
+
+def amr_restrict(cur, children, stream=None, prec=None):
+    return default_context().amr_restrict(cur, children, stream, prec)
+
+
+def amr_flux_correct(cur, flux_coarse, flux_fine0, flux_fine1, faces, dt_dh, stream=None,
+                     prec=None):
+    return default_context().amr_flux_correct(cur, flux_coarse, flux_fine0, flux_fine1, faces,
+                                              dt_dh, stream, prec)

@@ -242,3 +242,96 @@ def amr_patch_prims(coords, level: int, base: int = 64, xp=np, device=None, **bl
     Z = z[:, :, None, None]
     W = blast_prims_at(X + 0 * Y + 0 * Z, Y + 0 * X + 0 * Z, Z + 0 * X + 0 * Y, xp=xp, **blast)
     return W.transpose(0, 1) if xp is not np else W.transpose(1, 0, 2, 3, 4)
+
+
+# ---- AMR hierarchies with data exchange (Hierarchy / AmrRun) -----------------
+
+def nested_hierarchy(base=(4, 4, 4), nlev=3):
+    """Test hierarchy: level 0 covers the base patches; level l + 1 refines
+    the central 2x2x2 patches of level l (a block of 4x4x4 patches at every
+    level), so every level's ghost zones lie on its own level or the next
+    coarser one. Returns per-level (n_l, 3) patch coordinates."""
+    px, py, pz = base
+    lev = [np.array([(x, y, z) for z in range(pz) for y in range(py) for x in range(px)])]
+    for l in range(1, nlev):
+        P = [b << (l - 1) for b in base]
+        c = [p // 2 - 1 for p in P]
+        lev.append(np.array([(2 * X + cx, 2 * Y + cy, 2 * Z + cz)
+                             for Z in (c[2], c[2] + 1) for Y in (c[1], c[1] + 1)
+                             for X in (c[0], c[0] + 1)
+                             for cz in (0, 1) for cy in (0, 1) for cx in (0, 1)]))
+    return lev
+
+
+def level_prims(coords, level, fn, dh0, xp=np, device=None):
+    """[n][5][8][8][8] primitive states of level-`level` patches at `coords`,
+    fn(x, y, z) -> (rho, Ux, Uy, Uz, p) evaluated at the cell centres
+    (physical coordinates, level-0 cell size dh0)."""
+    c = xp.asarray(np.asarray(coords), dtype=xp.float64)
+    if device is not None:
+        c = c.to(device)
+    dh = dh0 / 2 ** level
+    g = (xp.arange(8, dtype=xp.float64) + 0.5) * dh
+    if device is not None:
+        g = g.to(device)
+    x = 8 * dh * c[:, 0, None, None, None] + g[None, None, None, :]
+    y = 8 * dh * c[:, 1, None, None, None] + g[None, None, :, None]
+    z = 8 * dh * c[:, 2, None, None, None] + g[None, :, None, None]
+    x, y, z = xp.broadcast_arrays(x, y, z) if xp is np else xp.broadcast_tensors(x, y, z)
+    W = fn(x, y, z)
+    return xp.stack([xp.asarray(w) * xp.ones_like(x) for w in W], 1) if xp is np else \
+        xp.stack([w * xp.ones_like(x) for w in W], 1)
+
+
+def bump_prims(x, y, z, xp=np):
+    """Smooth test state for AMR runs: a density and pressure bump moving
+    diagonally through the refined block (rho 1..3, p 0.5..1.5, U 0.3)."""
+    r2 = (x - 0.45) ** 2 + (y - 0.5) ** 2 + (z - 0.55) ** 2
+    e = xp.exp(-r2 / 0.01)
+    return (1.0 + 2.0 * e, 0.3 + 0 * x, -0.2 + 0 * x, 0.1 + 0 * x, 0.5 + e)
+
+
+def jet_hierarchy(base=(8, 8, 16), radii=(0.25, 0.125, 0.0625), heights=(1.0, 0.75, 0.5)):
+    """Static hierarchy of the relativistic-jet configuration: level 0 covers
+    the base patches ([0,1] x [0,1] x [0,2] in units of the x width); level
+    l = 1, 2, 3 refines, in groups of eight, every level-(l-1) patch whose
+    box comes within radii[l-1] of the jet axis (x = y = 0.5) and starts
+    below heights[l-1] (the cocoon region around the beam), and that is
+    surrounded by refined-or-refinable neighbours so that proper nesting
+    holds. Returns per-level (n_l, 3) patch coordinates."""
+    lev = [np.array([(x, y, z) for z in range(base[2]) for y in range(base[1])
+                     for x in range(base[0])])]
+    Lx = 1.0
+    for l in range(1, len(radii) + 1):
+        P = [b << (l - 1) for b in base]
+        w = Lx / P[0]  # patch width at level l - 1
+        parents = []
+        have = set(map(tuple, lev[l - 1]))
+        for (X, Y, Z) in lev[l - 1]:
+            # distance from the axis to the patch box, and its bottom
+            dx = max(abs((X + 0.5) * w - 0.5) - 0.5 * w, 0.0)
+            dy = max(abs((Y + 0.5) * w - 0.5) - 0.5 * w, 0.0)
+            if np.hypot(dx, dy) <= radii[l - 1] and Z * w < heights[l - 1] * 2 * Lx:
+                # proper nesting: all 26 neighbours must exist on level l - 1
+                ok = True
+                for oz in (-1, 0, 1):
+                    for oy in (-1, 0, 1):
+                        for ox in (-1, 0, 1):
+                            q = (X + ox, Y + oy, Z + oz)
+                            inside = all(0 <= q[a] < P[a] for a in range(3))
+                            if inside and q not in have:
+                                ok = False
+                if ok:
+                    parents.append((X, Y, Z))
+        lev.append(np.array([(2 * X + cx, 2 * Y + cy, 2 * Z + cz) for (X, Y, Z) in parents
+                             for cz in (0, 1) for cy in (0, 1) for cx in (0, 1)]).reshape(-1, 3))
+    return lev
+
+
+def jet_states(gamma_jet=10.0, rho_amb=1.0, T_amb=1e-6, density_contrast=1e-3, T_jet=10.0):
+    """Primitive states (rho, Ux, Uy, Uz, p) of the cold static ambient and
+    of the hot jet beam moving along +z with Lorentz factor gamma_jet."""
+    amb = (rho_amb, 0.0, 0.0, 0.0, rho_amb * T_amb)
+    rj = rho_amb * density_contrast
+    jet = (rj, 0.0, 0.0, float(np.sqrt(gamma_jet ** 2 - 1.0)), rj * T_jet)
+    return amb, jet

@@ -1,0 +1,188 @@
+"""GPU parity of the AMR exchange (srhd_amr_fill_ghosts, srhd_amr_restrict,
+srhd_amr_flux_correct) and of whole subcycled AMR steps (amr.AmrRun) against
+the CPU oracle (oracle/amr_oracle.py), through the C ABI."""
+import numpy as np
+import pytest
+
+from gpu_common import cons_rel_err, require_gpu, to_dev, to_np, torch_dtype
+from oracle import amr_oracle
+from paper_2012_11130_gb300 import workloads as Wk
+
+pytestmark = pytest.mark.gpu
+
+DH0 = 1.0 / 32
+
+
+def _setup(oracle, nlev, fn, bc=("periodic",) * 3, inflow=None):
+    from paper_2012_11130_gb300.amr import Hierarchy
+    lev = Wk.nested_hierarchy(base=(4, 4, 4), nlev=nlev)
+    h = Hierarchy((4, 4, 4), lev, bc=bc, inflow=inflow)
+    levs = [[tuple(c) for c in l] for l in lev]
+    data = []
+    for l, coords in enumerate(lev):
+        W = Wk.level_prims(coords, l, fn, DH0)
+        C, st = oracle.prim2con(W.transpose(1, 0, 2, 3, 4).reshape(5, -1))
+        assert np.all(st == 0)
+        data.append({tuple(c): C.reshape(5, len(coords), 8, 8, 8)[:, n].copy()
+                     for n, c in enumerate(coords)})
+    return h, levs, data
+
+
+def _stack(h, levs, d):
+    return np.stack([d[l][c] for l in range(h.nlev) for c in levs[l]])
+
+
+def _consistent(amr):
+    for l in range(len(amr.levels) - 2, -1, -1):
+        amr.restrict(l)
+    for l, d in enumerate(amr.data):
+        amr.old[l] = {c: v.copy() for c, v in d.items()}
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed_cf"])
+def test_fill_and_restrict_match_oracle(oracle, prec):
+    torch, srhd = require_gpu()
+    special = [[7.0, 0.1, 0.2, 0.3, 9.0]]
+    inflow = dict(axis=2, side=0, center=(16.0, 16.0), radius=5.0, index=0)
+    h, levs, _ = _setup(oracle, 3, Wk.bump_prims, bc=("outflow", "periodic", "outflow"),
+                        inflow=inflow)
+    rng = np.random.default_rng(7)
+    cur = rng.uniform(1, 2, (h.ntotal, 5, 8, 8, 8))
+    prev = rng.uniform(1, 2, (h.ntotal, 5, 8, 8, 8))
+    if prec != "fp64":
+        cur = cur.astype(np.float32).astype(np.float64)
+        prev = prev.astype(np.float32).astype(np.float64)
+    dt = torch_dtype(torch, prec)
+    ctx = srhd.Context()
+    cg, pg = to_dev(torch, cur, dt), to_dev(torch, prev, dt)
+    G = torch.full((h.ntotal, 5, 12, 12, 12), -1.0, dtype=dt, device="cuda")
+    mp = torch.from_numpy(h.map).cuda()
+    sp = to_dev(torch, np.asarray(special), dt)
+    data = [{c: cur[h.offsets[l] + n] for n, c in enumerate(levs[l])} for l in range(3)]
+    amr = amr_oracle.OracleAmr((4, 4, 4), levs, data, DH0, bc=("outflow", "periodic", "outflow"),
+                               inflow=dict(inflow, state=special[0]))
+    amr.old = [{c: prev[h.offsets[l] + n] for n, c in enumerate(levs[l])} for l in range(3)]
+    tol = 1e-15 if prec == "fp64" else 2e-7
+    for l, w in ((0, 0.0), (1, 0.0), (2, 0.5)):
+        o, n = h.offsets[l], h.counts[l]
+        ctx.amr_fill_ghosts(cg, pg, G, mp, o, n, w, sp, prec=prec)
+        Gn = to_np(G)
+        for q in range(0, n, 7):
+            ref = amr.ghosted(l, levs[l][q], w)
+            assert np.allclose(Gn[o + q], ref, rtol=tol, atol=0), (l, q)
+    # restriction of level 2 onto level 1 and of level 1 onto level 0
+    for l in (1, 0):
+        ctx.amr_restrict(cg, torch.from_numpy(h.children[l]).cuda(), prec=prec)
+        amr.restrict(l)
+    got = to_np(cg)
+    ref = _stack(h, levs, amr.data)
+    assert np.allclose(got, ref, rtol=tol, atol=0)
+
+
+def test_bad_map_entries_give_nan_and_args_are_checked(oracle):
+    torch, srhd = require_gpu()
+    ctx = srhd.Context()
+    cur = torch.ones((2, 5, 8, 8, 8), dtype=torch.float64, device="cuda")
+    G = torch.zeros((2, 5, 12, 12, 12), dtype=torch.float64, device="cuda")
+    mp = torch.zeros((2, 1728), dtype=torch.int32, device="cuda")
+    mp[0, 5] = 2 * 512          # past the last cell
+    mp[0, 6] = -3               # special state 2 of 1
+    sp = torch.zeros((1, 5), dtype=torch.float64, device="cuda")
+    ctx.amr_fill_ghosts(cur, cur, G, mp, 0, 2, 0.0, sp)
+    g = to_np(G)
+    assert np.isnan(g[0, :, 0, 0, 5]).all() and np.isnan(g[0, :, 0, 0, 6]).all()
+    assert (g[0, :, 0, 0, 7] == 1).all() and (g[1] == 1).all()
+    with pytest.raises(Exception, match="outside"):
+        ctx.amr_fill_ghosts(cur, cur, G, mp, 1, 2, 0.0, sp)
+    with pytest.raises(Exception, match="time weight"):
+        ctx.amr_fill_ghosts(cur, cur, G, mp, 0, 2, 1.5, sp)
+
+
+def _gpu_run(torch, srhd, h, levs, data, prec, steps, graph=False):
+    from paper_2012_11130_gb300.amr import AmrRun
+    dt = torch_dtype(torch, prec)
+    C0 = to_dev(torch, _stack(h, levs, data), dt)
+    ctx = srhd.Context(srhd.Params(cfl_mode="light"))
+    run = AmrRun(ctx, h, C0, DH0, prec=prec)
+    for l in range(h.nlev - 2, -1, -1):    # consistent t = 0 state
+        ctx.amr_restrict(run.cur, run.children[l], prec=prec)
+    run.prev.copy_(run.cur)
+    if graph:
+        run.capture()
+    for _ in range(steps):
+        run.replay() if graph else run.step()
+    torch.cuda.synchronize()
+    return run
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed_cf"])
+def test_amr_step_matches_oracle(oracle, prec):
+    torch, srhd = require_gpu()
+    h, levs, data = _setup(oracle, 3, Wk.bump_prims)
+    if prec != "fp64":
+        data = [{c: v.astype(np.float32).astype(np.float64) for c, v in d.items()} for d in data]
+    run = _gpu_run(torch, srhd, h, levs, data, prec, 1)
+    assert int(run.status.abs().max()) == 0
+    amr = amr_oracle.OracleAmr((4, 4, 4), levs, data, DH0)
+    _consistent(amr)
+    amr.step()
+    got = to_np(run.cur)
+    ref = _stack(h, levs, amr.data)
+    err = cons_rel_err(got.transpose(1, 0, 2, 3, 4), ref.transpose(1, 0, 2, 3, 4))
+    assert err.max() <= (1e-12 if prec == "fp64" else 1e-5), err.max()
+
+
+def test_amr_composite_conservation_and_graph_replay(oracle):
+    torch, srhd = require_gpu()
+    h, levs, data = _setup(oracle, 3, Wk.bump_prims)
+    a = _gpu_run(torch, srhd, h, levs, data, "fp64", 3)
+    b = _gpu_run(torch, srhd, h, levs, data, "fp64", 3, graph=True)
+    assert torch.equal(a.cur, b.cur)
+    o, n = h.offsets[0], h.counts[0]
+    C0 = _stack(h, levs, data)[o:o + n]
+    # the t = 0 level-0 totals are those of the consistent (restricted) state
+    r = _gpu_run(torch, srhd, h, levs, data, "fp64", 0)
+    t0 = to_np(r.cur[o:o + n]).reshape(n, 5, -1).sum(axis=(0, 2))
+    t1 = to_np(a.cur[o:o + n]).reshape(n, 5, -1).sum(axis=(0, 2))
+    scale = np.abs(C0).reshape(n, 5, -1).sum(axis=(0, 2))
+    assert np.all(np.abs(t1 - t0) <= 1e-13 * scale), (t1 - t0) / scale
+
+
+def test_jet_inflow_small_hierarchy(oracle):
+    # a two-level jet hierarchy on a 4x4x8 base (level 1 refines the 2x2
+    # patch columns around the axis up to half the height): the beam enters
+    # through the z = 0 face; FP64 matches the oracle after one coarse step
+    # and the float path keeps every patch physical for several steps
+    torch, srhd = require_gpu()
+    from paper_2012_11130_gb300.amr import AmrRun, Hierarchy
+    lev = Wk.jet_hierarchy(base=(4, 4, 8), radii=(0.1,), heights=(0.5,))
+    assert [len(l) for l in lev] == [128, 128]
+    inflow = dict(axis=2, side=0, center=(16.0, 16.0), radius=2.0, index=0)
+    h = Hierarchy((4, 4, 8), lev, bc=("outflow",) * 3, inflow=inflow)
+    amb, jet = Wk.jet_states(gamma_jet=10.0)
+    Camb, _ = oracle.prim2con(np.asarray(amb, float).reshape(5, 1))
+    Cjet, _ = oracle.prim2con(np.asarray(jet, float).reshape(5, 1))
+    levs = [[tuple(c) for c in l] for l in lev]
+    data = [{c: np.broadcast_to(Camb[:, 0, None, None, None], (5, 8, 8, 8)).copy()
+             for c in levs[l]} for l in range(len(lev))]
+    dh0 = 1.0 / 32
+    for prec, steps in (("fp64", 1), ("mixed_cf", 6)):
+        dt = torch_dtype(torch, prec)
+        C0 = to_dev(torch, _stack(h, levs, data), dt)
+        ctx = srhd.Context(srhd.Params(cfl_mode="light"))
+        run = AmrRun(ctx, h, C0, dh0, prec=prec, special=to_dev(torch, Cjet.T, dt))
+        for _ in range(steps):
+            run.step()
+        torch.cuda.synchronize()
+        assert int(run.status.abs().max()) >> 8 == 0
+        got = to_np(run.cur)
+        assert np.isfinite(got).all()
+        if prec == "fp64":
+            amr = amr_oracle.OracleAmr((4, 4, 8), levs, data, dh0, bc=("outflow",) * 3,
+                                       inflow=dict(inflow, state=Cjet[:, 0]))
+            amr.step()
+            ref = _stack(h, levs, amr.data)
+            err = cons_rel_err(got.transpose(1, 0, 2, 3, 4), ref.transpose(1, 0, 2, 3, 4))
+            assert err.max() <= 1e-11, err.max()
+            # the beam has entered: D in the bottom cells on the axis changed
+            assert not np.allclose(got, _stack(h, levs, data))
