@@ -329,6 +329,98 @@ def bench_amr(torch, srhd, steps: int, warmup: int, prec: str = "mixed_cf"):
     return out
 
 
+def bench_jet(torch, srhd, steps: int, gammas=(10.0, 20.0, 50.0, 100.0),
+              precs=("mixed_cf", "fp64"), variants=None):
+    """Relativistic jet on a static 4-level AMR hierarchy (configuration 5):
+    [0,1] x [0,1] x [0,2], base 64 x 64 x 128 cells (8 x 8 x 16 patches),
+    levels 1-3 refined around the beam and cocoon, finest-equivalent
+    512 x 512 x 1024; beam radius 16 finest cells injected through z = 0
+    with Lorentz factor gamma, density contrast 1e-3, T_jet = 10 into a cold
+    static ambient (T = 1e-6); outflow elsewhere; dt_l = 0.4 dh_l. Every
+    coarse step: per level substep ghost fill + update, then restriction and
+    coarse-fine flux correction (amr.AmrRun), as one CUDA graph. Reports
+    cell updates/s of the update launches alone (CUDA events around them,
+    eager steps) and of the whole step (graph replay), and the L1 difference
+    of rho between each float run and the FP64 run after `steps` steps."""
+    from paper_2012_11130_gb300 import amr, workloads
+    base, dh0 = (8, 8, 16), 1.0 / 64
+    lev = workloads.jet_hierarchy(base=base)
+    inflow = dict(axis=2, side=0, center=(32.0, 32.0), radius=2.0, index=0)
+    h = amr.Hierarchy(base, lev, bc=("outflow",) * 3, inflow=inflow)
+    c64 = srhd.Context(srhd.Params())
+    out = {"workload": ("relativistic jet, [0,1]x[0,1]x[0,2], base 64x64x128, 4 levels of 8^3 "
+                        "patches (finest-equivalent 512x512x1024) refined around beam and "
+                        "cocoon; beam radius 16 finest cells through z = 0, density contrast "
+                        "1e-3, T_jet = 10, ambient T = 1e-6; ghost fill, restriction and "
+                        "flux correction on the GPU; one CUDA graph per coarse step"),
+           "patches_per_level": h.counts, "patches": h.ntotal,
+           "cell_updates_per_coarse_step": None, "coarse_steps": steps, "runs": {}}
+    dev = torch.device("cuda")
+    for g in gammas:
+        amb, jet = workloads.jet_states(gamma_jet=g)
+        Ca = c64.prim2con(torch.tensor(amb, dtype=torch.float64, device=dev).reshape(5, 1))
+        Cj = c64.prim2con(torch.tensor(jet, dtype=torch.float64, device=dev).reshape(5, 1))
+        finals = {}
+        for prec in precs:
+            dt = torch.float64 if prec == "fp64" else torch.float32
+            C0 = Ca[:, 0].reshape(1, 5, 1, 1, 1).expand(h.ntotal, 5, 8, 8, 8).to(dt).contiguous()
+            v = (variants or {}).get(prec, 0)
+            ctx = srhd.Context(srhd.Params(patch_variant=v))
+            run = amr.AmrRun(ctx, h, C0, dh0, prec=prec, special=Cj.t().to(dt))
+            out["cell_updates_per_coarse_step"] = run.cell_updates_per_step
+            run.step()                      # warm-up (one coarse step)
+            torch.cuda.synchronize()
+            ne = min(4, max(1, steps - 1))
+            run.timer = []
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(ne):
+                run.step()
+            e1.record()
+            torch.cuda.synchronize()
+            upd_ms = sum(a.elapsed_time(b) for a, b in run.timer) / ne
+            eager_ms = e0.elapsed_time(e1) / ne
+            run.timer = None
+            nr = steps - 1 - ne
+            graph_ms = None
+            if nr > 0:
+                run.capture(warmup=0)
+                e0.record()
+                for _ in range(nr):
+                    run.replay()
+                e1.record()
+                torch.cuda.synchronize()
+                graph_ms = e0.elapsed_time(e1) / nr
+            st = run.status.cpu()
+            upd = run.cell_updates_per_step
+            out["runs"][f"{prec}_gamma{g:g}"] = {
+                "cell_updates_per_s_update_only": upd / (upd_ms * 1e-3),
+                "cell_updates_per_s_whole_step": upd / (graph_ms * 1e-3) if graph_ms else None,
+                "ms_update_per_coarse_step": upd_ms, "ms_whole_step_graph": graph_ms,
+                "ms_whole_step_eager": eager_ms,
+                "patches_unphysical": int(((st >> 8) & 1).sum()),
+                "patches_retried_last_step": int(((st & 255) > 0).sum()),
+            }
+            o, n = h.offsets[0], h.counts[0]
+            lo, ln = h.offsets[-1], h.counts[-1]
+            finals[prec] = (run.cur[o:o + n].to(torch.float64).clone(),
+                            run.cur[lo:lo + ln].to(torch.float64).clone())
+            del run, C0
+            torch.cuda.empty_cache()
+        if "fp64" in finals:
+            def rho(C):
+                return c64.con2pri(C.permute(1, 0, 2, 3, 4).reshape(5, -1).contiguous())[0]
+            r0, r3 = rho(finals["fp64"][0]), rho(finals["fp64"][1])
+            for prec in precs:
+                if prec == "fp64":
+                    continue
+                q0, q3 = rho(finals[prec][0]), rho(finals[prec][1])
+                out["runs"][f"{prec}_gamma{g:g}"]["l1_rho_vs_fp64"] = {
+                    "level0": float((1 - q0 / r0).abs().mean()),
+                    "finest": float((1 - q3 / r3).abs().mean())}
+    return out
+
+
 def bench_con2pri_stress(torch, srhd, prec: str, log2n: int = 26, reps: int = 5):
     """The con2pri stress batch (2^26 cells; rho 1e-6..1e2, T 1e-8..1e4,
     gamma 1..1e6, random direction): cells/s of srhd_con2pri and the
@@ -578,6 +670,13 @@ def run_ours(args):
         amr_res = bench_amr(torch, srhd, max(3, args.steps // 4), 2, precs[0] if precs[0] != "fp64"
                             else "mixed_cf")
 
+    jet_res = None
+    if not args.no_jet and args.grid == N_GRID and rank == 0:
+        vs = {q: results[q]["autotune"]["chosen_variant"] for q in precs
+              if results[q].get("autotune")}
+        jet_res = bench_jet(torch, srhd, args.jet_steps, variants=vs,
+                            precs=tuple(q for q in ("mixed_cf", "fp64") if q in precs))
+
     l1 = {}
     stress = {}
     if not args.no_l1 and rank == 0:
@@ -642,6 +741,7 @@ def run_ours(args):
         "l1_shock_tube": st_l1,
         "con2pri_stress": stress or None,
         "amr_blast": amr_res,
+        "amr_jet": jet_res,
         "kernel_sources_sha": sha,
     }
     print(json.dumps(line))
@@ -661,6 +761,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-l1", action="store_true")
     ap.add_argument("--no-amr", action="store_true")
+    ap.add_argument("--no-jet", action="store_true", help="skip the AMR jet (configuration 5)")
+    ap.add_argument("--jet-steps", type=int, default=100, help="coarse steps of each jet run")
     ap.add_argument("--no-tune", action="store_true", help="skip the launch-variant autotuner")
     ap.add_argument("--variant", type=int, default=None,
                     help="use this launch variant of the patch kernel (no autotuning)")
