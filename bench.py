@@ -675,6 +675,7 @@ def run_ours(args):
         vs = {q: results[q]["autotune"]["chosen_variant"] for q in precs
               if results[q].get("autotune")}
         jet_res = bench_jet(torch, srhd, args.jet_steps, variants=vs,
+                            gammas=tuple(float(g) for g in args.jet_gammas.split(",")),
                             precs=tuple(q for q in ("mixed_cf", "fp64") if q in precs))
 
     l1 = {}
@@ -763,6 +764,8 @@ def main():
     ap.add_argument("--no-amr", action="store_true")
     ap.add_argument("--no-jet", action="store_true", help="skip the AMR jet (configuration 5)")
     ap.add_argument("--jet-steps", type=int, default=100, help="coarse steps of each jet run")
+    ap.add_argument("--jet-gammas", default="10,20,50,100",
+                    help="comma-separated beam Lorentz factors of the jet runs")
     ap.add_argument("--no-tune", action="store_true", help="skip the launch-variant autotuner")
     ap.add_argument("--variant", type=int, default=None,
                     help="use this launch variant of the patch kernel (no autotuning)")

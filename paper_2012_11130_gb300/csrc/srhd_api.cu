@@ -395,18 +395,23 @@ srhd_status srhd_amr_fill_ghosts(srhd_ctx* c, srhd_prec prec, const void* cur, c
   if (n == 0) return SRHD_OK;
   if (!cur || !prev || !ghosted || !map) return fail(SRHD_ERR_ARG, "cur/prev/ghosted/map is NULL");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  const int grid = grid_for(c, (int64_t)n * srhd::kAmrTile, 16);
   const int64_t ncells = (int64_t)ntotal * srhd::kAmrInt;
-  if (is_double(prec))
-    srhd::amr_fill_kernel<double><<<grid, 256, 0, s>>>(
-        static_cast<const double*>(cur), static_cast<const double*>(prev),
-        static_cast<double*>(ghosted), map, p0, n, ncells, w, static_cast<const double*>(special),
-        nspecial);
-  else
-    srhd::amr_fill_kernel<float><<<grid, 256, 0, s>>>(
-        static_cast<const float*>(cur), static_cast<const float*>(prev),
-        static_cast<float*>(ghosted), map, p0, n, ncells, float(w),
-        static_cast<const float*>(special), nspecial);
+  // four cells per thread when the map and ghosted rows are 16-byte aligned
+  // (every row is: 1728 elements of 4 or 8 bytes), else one
+  const bool wide = (reinterpret_cast<uintptr_t>(map) % 16 == 0) &&
+                    (reinterpret_cast<uintptr_t>(ghosted) % 16 == 0);
+  const int grid = grid_for(c, (int64_t)n * srhd::kAmrTile / (wide ? 4 : 1), 16);
+  if (is_double(prec)) {
+    auto k = wide ? srhd::amr_fill4_kernel<double> : srhd::amr_fill_kernel<double>;
+    k<<<grid, 256, 0, s>>>(static_cast<const double*>(cur), static_cast<const double*>(prev),
+                           static_cast<double*>(ghosted), map, p0, n, ncells, w,
+                           static_cast<const double*>(special), nspecial);
+  } else {
+    auto k = wide ? srhd::amr_fill4_kernel<float> : srhd::amr_fill_kernel<float>;
+    k<<<grid, 256, 0, s>>>(static_cast<const float*>(cur), static_cast<const float*>(prev),
+                           static_cast<float*>(ghosted), map, p0, n, ncells, float(w),
+                           static_cast<const float*>(special), nspecial);
+  }
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? SRHD_OK : cuda_fail(e, "amr_fill launch");
 }
