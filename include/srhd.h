@@ -97,6 +97,11 @@ enum {
 };
 
 /* Run-time parameters (Sections 3.1-3.3). */
+/* Equation of state (Section 2.2): the Taub-Mathews EoS of the paper, or the
+ * polytropic EoS h = 1 + Gamma/(Gamma-1) T that the paper keeps for pure
+ * non-relativistic (Gamma = 5/3) or ultra-relativistic (Gamma = 4/3) gas. */
+typedef enum srhd_eos { SRHD_EOS_TM = 0, SRHD_EOS_POLYTROPIC = 1 } srhd_eos;
+
 typedef struct srhd_params {
   double cfl;             /* C_CFL of Eq. (time_step_sound_speed); default 0.5 */
   double theta;           /* minmod coefficient of the PLM limiter; default 1.5 */
@@ -116,6 +121,12 @@ typedef struct srhd_params {
   int32_t scheme;         /* srhd_scheme; default SRHD_SCHEME_REDUCED. Applies to
                              every call of the context: the fifth conserved
                              variable of all arrays is then E instead of Etilde */
+  int32_t eos;            /* srhd_eos; default SRHD_EOS_TM. Applies to every call
+                             of the context. SRHD_EOS_POLYTROPIC runs one fixed
+                             launch configuration of the patch kernel
+                             (patch_variant is then ignored). */
+  double gamma;           /* Gamma of SRHD_EOS_POLYTROPIC, 1 < gamma <= 5/3;
+                             default 5/3 (ignored for SRHD_EOS_TM) */
 } srhd_params;
 
 typedef struct srhd_ctx srhd_ctx;

@@ -15,6 +15,7 @@ repository's design notes; none here is "parity unpinned".
 """
 from __future__ import annotations
 
+import contextlib
 import ctypes
 import os
 import subprocess
@@ -64,6 +65,8 @@ def lib():
                          "or_rapidity_integral"):
                 getattr(L, name).restype = d
                 getattr(L, name).argtypes = [d, d]
+            L.or_set_eos.restype = i32
+            L.or_set_eos.argtypes = [i32, d]
             L.or_limited_slope.restype = d
             L.or_limited_slope.argtypes = [d, d, d]
             L.or_prim2con.restype = None
@@ -105,6 +108,28 @@ def _f64(a):
 
 
 # --- Section 2.2: TM equation of state ------------------------------------
+# --- equation of state selection (Section 2.2) ---------------------------------
+EOS_TM, EOS_POLYTROPIC = 0, 1
+
+
+def set_eos(kind=EOS_TM, gamma=5.0 / 3.0):
+    """Select the EoS of every following oracle call on this thread: the
+    Taub-Mathews EoS (default) or the polytropic h = 1 + Gamma/(Gamma-1) T
+    with 1 < Gamma <= 5/3."""
+    if lib().or_set_eos(int(kind), float(gamma)) != 0:
+        raise ValueError(f"invalid EoS selection kind={kind} gamma={gamma}")
+
+
+@contextlib.contextmanager
+def eos(kind=EOS_TM, gamma=5.0 / 3.0):
+    """Context in which the oracle uses the given EoS (restores TM after)."""
+    set_eos(kind, gamma)
+    try:
+        yield
+    finally:
+        set_eos(EOS_TM)
+
+
 def htilde_of_T(T):
     """Eq. (T_to_HTilde)."""
     return np.vectorize(lib().or_htilde_of_T, otypes=[float])(T)

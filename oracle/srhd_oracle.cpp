@@ -78,25 +78,34 @@ constexpr double kEpsUnphysical = 2e-16;  // Section 3.3: eps_machine, double pr
 constexpr int kNewtonMaxIter = 50;
 
 // ----------------------------------------------------------------------------
-// Taub-Mathews equation of state (Section 2.2)
+// Equations of state (Section 2.2): Taub-Mathews (the paper's) or, selected by
+// or_set_eos, the polytropic (constant-Gamma) EoS the paper keeps for pure
+// non-relativistic or ultra-relativistic gas: h = 1 + Gamma/(Gamma-1) T.
 // ----------------------------------------------------------------------------
+struct EosSel { int gamma_law = 0; double gam = 5.0 / 3.0; };
+thread_local EosSel g_eos;
 
 // Eq. (T_to_HTilde): htilde(T) = 2.5 T + 2.25 T^2 / (1 + sqrt(2.25 T^2 + 1)),
 // the TM enthalpy (Eq. TM EOS) minus one, written without a subtraction.
+// Polytropic: htilde = Gamma/(Gamma-1) T.
 template <class R> R htilde_of_T(R T) {
+  if (g_eos.gamma_law) return R(g_eos.gam / (g_eos.gam - 1.0)) * T;
   R a = R(2.25) * T * T;
   return R(2.5) * T + a / (R(1.0) + sqrt(a + R(1.0)));
 }
 
-// Eq. (T of h): inverse of the TM EoS in terms of htilde.
+// Eq. (T of h): inverse of the TM EoS in terms of htilde (polytropic:
+// T = (Gamma-1)/Gamma htilde).
 template <class R> R T_of_htilde(R ht) {
+  if (g_eos.gamma_law) return R((g_eos.gam - 1.0) / g_eos.gam) * ht;
   R num = R(2.0) * ht * ht + R(4.0) * ht;
   R den = R(5.0) * ht + R(5.0) + sqrt(R(9.0) * ht * ht + R(18.0) * ht + R(25.0));
   return num / den;
 }
 
-// Eq. (dT_dh), Appendix A: derivative of Eq. (T of h).
+// Eq. (dT_dh), Appendix A: derivative of Eq. (T of h) (polytropic: constant).
 template <class R> R dT_dhtilde(R ht) {
+  if (g_eos.gamma_law) return R((g_eos.gam - 1.0) / g_eos.gam);
   R s = sqrt(R(9.0) * ht * ht + R(18.0) * ht + R(25.0));
   R den = R(5.0) * ht + R(5.0) + s;
   R num = R(2.0) * ht * ht + R(4.0) * ht;
@@ -106,8 +115,10 @@ template <class R> R dT_dhtilde(R ht) {
 }
 
 // Eq. (sound_speed): squared TM sound speed c_s^2 as a function of T.
+// Polytropic: c_s^2 = Gamma p / (rho h) = Gamma T / h.
 template <class R> R cs2_of_T(R T) {
   R h = R(1.0) + htilde_of_T(T);
+  if (g_eos.gamma_law) return R(g_eos.gam) * T / h;
   return (T / (R(3.0) * h)) * ((R(5.0) * h - R(8.0) * T) / (h - T));
 }
 
@@ -186,6 +197,12 @@ template <class R> R A_of_cons(const R U[5], R* m2_out, int ori = 0) {
 // the quadratic is used instead. Its crossing with the hot guess is exactly
 // the threshold of Eq. ColdHot, which confirms this reading.)
 template <class R> R newton_guess(R A, R m2) {
+  if (g_eos.gamma_law) {
+    // Polytropic EoS: the root for m = 0, where f = ((1-k) htilde + 1)^2 - 1
+    // with k = (Gamma-1)/Gamma, i.e. htilde = A / ((1-k)(1 + sqrt(1 + A))).
+    R omk = R(1.0 / g_eos.gam);
+    return A / (omk * (R(1.0) + sqrt(R(1.0) + A)));
+  }
   R P = R(1.0) + m2;
   R thr_base = R(1800.0) * P / (R(437.0) * m2 + R(117.0));
   R thr = thr_base * thr_base;
@@ -650,9 +667,11 @@ const GaussLegendre& gauss_legendre() { static GaussLegendre g; return g; }
 // isentrope of the TM gas, d ln rho = (1.5/T + 2.25/sqrt(1 + 2.25 T^2)) dT
 // (from dh = dp/rho with p = rho T, i.e. Eq. entropy), and the Riemann
 // invariant Eq. (Riemann invariant) gives d asinh(U) = +/- c_s d ln rho.
+// Polytropic EoS: p/rho^Gamma = const, d ln rho = dT / ((Gamma-1) T).
 double rapidity_integrand(double u) {
   double T = std::exp(u);
   double cs = std::sqrt(cs2_of_T(T));
+  if (g_eos.gamma_law) return cs / (g_eos.gam - 1.0);
   return cs * (1.5 + 2.25 * T / std::sqrt(1.0 + 2.25 * T * T));
 }
 
@@ -706,6 +725,7 @@ RState make_state(double rho, double U, double p) {
 // p (h - T) / rho^{5/3} = const with p = rho T): rho = rho_K [T (h-T) /
 // (T_K (h_K - T_K))]^{3/2}.
 double isentrope_rho(const RState& K, double T) {
+  if (g_eos.gamma_law) return K.rho * std::pow(T / K.T, 1.0 / (g_eos.gam - 1.0));
   double h = 1.0 + htilde_of_T(T);
   return K.rho * std::pow(T * (h - T) / (K.T * (K.h - K.T)), 1.5);
 }
@@ -893,6 +913,16 @@ void sample_exact(const ExactSolution& S, double xi, double* rho, double* U, dou
 // ============================================================================
 extern "C" {
 
+// EoS selection for the calls that follow on this thread: kind 0 = TM,
+// kind 1 = polytropic with the given Gamma (1 < Gamma <= 5/3). Returns 0, or
+// BADARG.
+int or_set_eos(int kind, double gam) {
+  if (kind == 0) { g_eos.gamma_law = 0; return OK; }
+  if (kind != 1 || !(gam > 1.0) || !(gam <= 5.0 / 3.0 + 1e-12)) return BADARG;
+  g_eos.gamma_law = 1;
+  g_eos.gam = gam;
+  return OK;
+}
 double or_htilde_of_T(double T) { return htilde_of_T(T); }
 double or_T_of_htilde(double ht) { return T_of_htilde(ht); }
 double or_dT_dhtilde(double ht) { return dT_dhtilde(ht); }

@@ -18,6 +18,7 @@ SRHD_HLLC, SRHD_HLLE = 0, 1
 SRHD_CFL_SIGNAL, SRHD_CFL_LIGHT = 0, 1
 SRHD_BC_PERIODIC, SRHD_BC_OUTFLOW = 0, 1
 SRHD_SCHEME_REDUCED, SRHD_SCHEME_TOTAL = 0, 1
+SRHD_EOS_TM, SRHD_EOS_POLYTROPIC = 0, 1
 CELL_OK, CELL_UNPHYSICAL, CELL_NOCONV = 0, 1, 2
 PATCH_UNPHYSICAL, PATCH_BAD_INPUT, PATCH_NOCONV = 1, 2, 4
 
@@ -34,7 +35,8 @@ class Params(ctypes.Structure):
                 ("retry_factor", ctypes.c_double), ("theta_floor", ctypes.c_double),
                 ("riemann", ctypes.c_int32), ("cfl_mode", ctypes.c_int32),
                 ("ndim", ctypes.c_int32), ("newton_max_iter", ctypes.c_int32),
-                ("patch_variant", ctypes.c_int32), ("scheme", ctypes.c_int32)]
+                ("patch_variant", ctypes.c_int32), ("scheme", ctypes.c_int32),
+                ("eos", ctypes.c_int32), ("gamma", ctypes.c_double)]
 
 
 class SrhdError(RuntimeError):
@@ -75,6 +77,8 @@ def load(path: str = LIB_PATH):
     L.srhd_cfl_dt.argtypes = [vp, ctypes.c_int, vp, i32, d, vp, vp]
     L.srhd_fill_ghosts_uniform.restype = st
     L.srhd_fill_ghosts_uniform.argtypes = [vp, ctypes.c_int, vp, vp, i32, i32, i32, i32p, vp]
+    L.srhd_cfl_dt_noalloc.restype = st
+    L.srhd_cfl_dt_noalloc.argtypes = [ctypes.c_int, vp, i32, d, ctypes.POINTER(Params), vp, vp]
     L.srhd_amr_fill_ghosts.restype = st
     L.srhd_amr_fill_ghosts.argtypes = [vp, ctypes.c_int, vp, vp, vp, vp, i32, i32, i32, d, vp,
                                        i32, vp]

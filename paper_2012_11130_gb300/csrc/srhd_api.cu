@@ -48,6 +48,7 @@ struct srhd_ctx {
   int device;
   int num_sms;
   int patch_grid[3][srhd::kPatchVariants];  // persistent grid per precision and variant
+  int poly_grid[3];                         // persistent grid of the polytropic kernels
   int scratch_slots;      // capacity of the partial-minimum arrays
   double* partial_dt;     // scratch [scratch_slots]
   int32_t* partial_bad;   // scratch [scratch_slots]
@@ -110,7 +111,15 @@ srhd_status check_params(const srhd_params* p) {
     return fail(SRHD_ERR_ARG, "scheme must be SRHD_SCHEME_REDUCED or SRHD_SCHEME_TOTAL");
   if (p->patch_variant < 0 || p->patch_variant >= srhd::kPatchVariants)
     return fail(SRHD_ERR_ARG, "patch_variant must be in [0, %d)", srhd::kPatchVariants);
+  if (p->eos != SRHD_EOS_TM && p->eos != SRHD_EOS_POLYTROPIC)
+    return fail(SRHD_ERR_ARG, "eos must be SRHD_EOS_TM or SRHD_EOS_POLYTROPIC");
+  if (p->eos == SRHD_EOS_POLYTROPIC && !(p->gamma > 1.0 && p->gamma <= 5.0 / 3.0 + 1e-12))
+    return fail(SRHD_ERR_ARG, "gamma of the polytropic EoS must be in (1, 5/3]");
   return SRHD_OK;
+}
+
+srhd::EosArg eos_arg(const srhd_params& p) {
+  return srhd::EosArg{p.eos == SRHD_EOS_POLYTROPIC ? 1 : 0, p.gamma};
 }
 
 srhd_status check_ctx(const srhd_ctx* c) {
@@ -144,6 +153,8 @@ srhd_status srhd_default_params(srhd_params* p) {
   p->newton_max_iter = 0;
   p->patch_variant = 0;
   p->scheme = SRHD_SCHEME_REDUCED;
+  p->eos = SRHD_EOS_TM;
+  p->gamma = 5.0 / 3.0;
   return SRHD_OK;
 }
 
@@ -183,6 +194,18 @@ srhd_status srhd_create(srhd_ctx** out, const srhd_params* p) {
     c->patch_grid[SRHD_MIXED][v] = nsm * b32;
     c->patch_grid[SRHD_MIXED_CF][v] = nsm * bcf;
   }
+  {
+    int b64 = srhd::Launch<srhd::PrecFP64>::poly_blocks_per_sm();
+    int b32 = srhd::Launch<srhd::PrecMixed>::poly_blocks_per_sm();
+    int bcf = srhd::Launch<srhd::PrecMixedCF>::poly_blocks_per_sm();
+    if (b64 < 1 || b32 < 1 || bcf < 1) {
+      delete c;
+      return fail(SRHD_ERR_CUDA, "polytropic patch kernel does not fit on an SM");
+    }
+    c->poly_grid[SRHD_FP64] = nsm * b64;
+    c->poly_grid[SRHD_MIXED] = nsm * b32;
+    c->poly_grid[SRHD_MIXED_CF] = nsm * bcf;
+  }
   c->scratch_slots = nsm * 8;
   c->partial_dt = nullptr;
   c->partial_bad = nullptr;
@@ -217,7 +240,8 @@ srhd_status srhd_prim2con(srhd_ctx* c, srhd_prec prec, const void* prim, void* c
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   int grid = grid_for(c, n, 16);
   cudaError_t e = dispatch(prec, [&](auto L) {
-    return decltype(L)::prim2con(prim, cons, n, var_stride, c->params.scheme, grid, s);
+    return decltype(L)::prim2con(prim, cons, n, var_stride, c->params.scheme,
+                                 eos_arg(c->params), grid, s);
   });
   return e == cudaSuccess ? SRHD_OK : cuda_fail(e, "prim2con launch");
 }
@@ -235,7 +259,7 @@ srhd_status srhd_con2pri(srhd_ctx* c, srhd_prec prec, const void* cons, void* pr
   int maxit = newton_maxit(c, prec);
   cudaError_t e = dispatch(prec, [&](auto L) {
     return decltype(L)::con2pri(cons, prim, n, var_stride, cell_status, maxit, c->params.scheme,
-                                grid, s);
+                                eos_arg(c->params), grid, s);
   });
   return e == cudaSuccess ? SRHD_OK : cuda_fail(e, "con2pri launch");
 }
@@ -243,7 +267,8 @@ srhd_status srhd_con2pri(srhd_ctx* c, srhd_prec prec, const void* cons, void* pr
 static srhd_status launch_patches(srhd_ctx* c, srhd_prec prec, srhd::PatchArgs& a,
                                   double* dt_next, cudaStream_t s) {
   const int variant = c->params.patch_variant;
-  int grid = c->patch_grid[prec][variant];
+  const int poly = c->params.eos == SRHD_EOS_POLYTROPIC ? 1 : 0;
+  int grid = poly ? c->poly_grid[prec] : c->patch_grid[prec][variant];
   if (grid > a.npatch) grid = a.npatch;
   if (dt_next) {
     a.partial_dt = c->partial_dt;
@@ -251,7 +276,7 @@ static srhd_status launch_patches(srhd_ctx* c, srhd_prec prec, srhd::PatchArgs& 
   }
   cudaError_t e = cudaSuccess;
   if (a.npatch > 0) {
-    e = dispatch(prec, [&](auto L) { return decltype(L)::patches(a, variant, grid, s); });
+    e = dispatch(prec, [&](auto L) { return decltype(L)::patches(a, variant, poly, grid, s); });
     if (e != cudaSuccess) return cuda_fail(e, "patch kernel launch");
   } else {
     grid = 0;
@@ -273,6 +298,7 @@ static void fill_common(const srhd_ctx* c, srhd_prec prec, srhd::PatchArgs& a) {
   a.cfl_mode = c->params.cfl_mode;
   a.ndim = c->params.ndim;
   a.maxit = newton_maxit(c, prec);
+  a.eos_gamma = c->params.gamma;
   a.ori = c->params.scheme == SRHD_SCHEME_TOTAL ? 1 : 0;
   a.partial_dt = nullptr;
   a.partial_bad = nullptr;
@@ -346,7 +372,8 @@ srhd_status srhd_cfl_dt(srhd_ctx* c, srhd_prec prec, const void* cons, int32_t n
     int maxit = newton_maxit(c, prec);
     e = dispatch(prec, [&](auto L) {
       return decltype(L)::cfl(cons, ncell, dh, c->params.cfl, c->params.ndim, c->params.cfl_mode,
-                              maxit, c->params.scheme, c->partial_dt, c->partial_bad, grid, s);
+                              maxit, c->params.scheme, eos_arg(c->params), c->partial_dt,
+                              c->partial_bad, grid, s);
     });
     if (e != cudaSuccess) return cuda_fail(e, "cfl launch");
   }

@@ -52,7 +52,16 @@ struct PatchArgs {
   int riemann, cfl_mode, ndim, maxit;
   int flux_only;
   int ori;                // 1: original scheme (total energy E, flux M)
+  double eos_gamma;       // Gamma of the polytropic EoS (used by the EosPoly kernels)
 };
+
+// EoS object of a launch: the TM tag, or the polytropic EoS with the
+// launch's Gamma.
+template <class E> __device__ __forceinline__ E make_eos(const PatchArgs& a);
+template <> __device__ __forceinline__ EosTM make_eos<EosTM>(const PatchArgs&) { return EosTM{}; }
+template <> __device__ __forceinline__ EosPoly make_eos<EosPoly>(const PatchArgs& a) {
+  return EosPoly{a.eos_gamma};
+}
 
 template <class S> struct SmemLayout {  // S: storage type
   static constexpr size_t prim_elems = 5 * kGC;        // primitive tile
@@ -136,10 +145,10 @@ template <class S> __device__ __forceinline__ S* face_slot(S* face, int d, int s
   return face + ((d * 2 + side) * 5 + v) * kNF;
 }
 
-template <int d, class R, class S>
+template <int d, class R, class S, class E>
 __device__ __forceinline__ void recon_direction(const S* prim, int tc, const PrimX<R>& W, R theta,
                                                 int i, int j, int k, bool interior, S* face,
-                                                R dF[5], int& bad, int ori) {
+                                                R dF[5], int& bad, int ori, const E& eos) {
   constexpr int off = (d == 0) ? 1 : ((d == 1) ? kG : kG * kG);
   R wc[5] = {W.rho, W.u[0], W.u[1], W.u[2], W.p};
   const int cd = (d == 0) ? i : ((d == 1) ? j : k);
@@ -157,7 +166,7 @@ __device__ __forceinline__ void recon_direction(const S* prim, int tc, const Pri
       Wq[v] = pk::fma(pk::s2(dW), make_float2(-0.5f, 0.5f), pk::s2(wc[v]));
     }
     bool okm, okp;
-    prim2con_flux_x2<d>(Wq, Uq, Fq, okm, okp, ori);
+    prim2con_flux_x2<d>(Wq, Uq, Fq, okm, okp, ori, eos);
     if (!okm || !okp) bad = 1;
 #pragma unroll
     for (int v = 0; v < 5; ++v) dF[v] = dF[v] + (Fq[v].y - Fq[v].x);
@@ -185,8 +194,8 @@ __device__ __forceinline__ void recon_direction(const S* prim, int tc, const Pri
     Wm.rho = fm[0]; Wm.u[0] = fm[1]; Wm.u[1] = fm[2]; Wm.u[2] = fm[3]; Wm.p = fm[4];
     Wp.rho = fp[0]; Wp.u[0] = fp[1]; Wp.u[1] = fp[2]; Wp.u[2] = fp[3]; Wp.p = fp[4];
     R Um[5], Up[5], Fm[5], Fp[5];
-    if (!prim2con(Wm, Um, ori)) bad = 1;
-    if (!prim2con(Wp, Up, ori)) bad = 1;
+    if (!prim2con(Wm, Um, ori, eos)) bad = 1;
+    if (!prim2con(Wp, Up, ori, eos)) bad = 1;
     phys_flux<d>(Wm, Um, Fm, ori);
     phys_flux<d>(Wp, Up, Fp, ori);
 #pragma unroll
@@ -241,9 +250,10 @@ template <int d> __device__ __forceinline__ int face_owner(int fi, int side) {
 // slots; their Newton solves start from the converged tau of the cells
 // they belong to (a warm start: the predicted state differs from the cell
 // state by half a limited slope and half a time step).
-template <int d, class P, bool PAIR>
+template <int d, class P, bool PAIR, class E>
 __device__ __forceinline__ int face_flux(typename P::S* face, const typename P::S* hts, int fi,
-                                         int solver, int maxit, int& code, int ori) {
+                                         int solver, int maxit, int& code, int ori,
+                                         const E& eos) {
   using S = typename P::S;
   using R = S;
   const S gL = hts[face_owner<d>(fi, 0)], gR = hts[face_owner<d>(fi, 1)];
@@ -256,23 +266,23 @@ __device__ __forceinline__ int face_flux(typename P::S* face, const typename P::
   PrimX<R> WL, WR;
   int sl, sr;
   if constexpr (PAIR) {
-    con2pri_x2<P>(UL, UR, WL, WR, maxit, sl, sr, gL, gR, ori);
+    con2pri_x2<P>(UL, UR, WL, WR, maxit, sl, sr, gL, gR, ori, eos);
   } else {
-    sl = con2pri<P>(UL[0], UL[1], UL[2], UL[3], UL[4], WL, maxit, gL, ori);
-    sr = con2pri<P>(UR[0], UR[1], UR[2], UR[3], UR[4], WR, maxit, gR, ori);
+    sl = con2pri<P>(UL[0], UL[1], UL[2], UL[3], UL[4], WL, maxit, gL, ori, eos);
+    sr = con2pri<P>(UR[0], UR[1], UR[2], UR[3], UR[4], WR, maxit, gR, ori, eos);
   }
   if (sl == 2 || sr == 2) code |= CODE_NOCONV;
   int fail = (sl == 1 || sr == 1);
   R FL_[5] = {R(UL[0]), R(UL[1]), R(UL[2]), R(UL[3]), R(UL[4])};
   R FR_[5] = {R(UR[0]), R(UR[1]), R(UR[2]), R(UR[3]), R(UR[4])};
   R F[5];
-  riemann<d>(solver, WL, FL_, WR, FR_, F, ori);
+  riemann<d>(solver, WL, FL_, WR, FR_, F, ori, eos);
 #pragma unroll
   for (int v = 0; v < 5; ++v) face_slot(face, d, 0, v)[fi] = S(F[v]);
   return fail;
 }
 
-template <class P, int NT, int MINB, bool PAIR>
+template <class P, int NT, int MINB, bool PAIR, class E = EosTM>
 __global__ void __launch_bounds__(NT, MINB) patch_kernel(PatchArgs a) {
   static_assert(NT % 32 == 0 && NT >= 64 && NT <= 1024, "block size");
   using S = typename P::S;
@@ -286,6 +296,7 @@ __global__ void __launch_bounds__(NT, MINB) patch_kernel(PatchArgs a) {
   const int tid = threadIdx.x;
   const int maxit = a.maxit;
   const int ori = a.ori;
+  const E eos = make_eos<E>(a);
 
   double dt_min = DBL_MAX;
   int cfl_bad = 0;
@@ -309,7 +320,7 @@ __global__ void __launch_bounds__(NT, MINB) patch_kernel(PatchArgs a) {
         }
         PrimX<R> Wa, Wb;
         int sa, sb;
-        con2pri_x2<P>(Ua, Ub, Wa, Wb, maxit, sa, sb, S(0), S(0), ori);
+        con2pri_x2<P>(Ua, Ub, Wa, Wb, maxit, sa, sb, S(0), S(0), ori, eos);
         if (sa == 1 || sb == 1) code |= CODE_BAD_INPUT;
         if (sa == 2 || sb == 2) code |= CODE_NOCONV;
         prim[ca] = S(Wa.rho);
@@ -330,7 +341,7 @@ __global__ void __launch_bounds__(NT, MINB) patch_kernel(PatchArgs a) {
         const int c = needed_tile_cell(r);
         PrimX<R> W;
         int st = con2pri<P>(in[c], in[kGC + c], in[2 * kGC + c], in[3 * kGC + c],
-                            in[4 * kGC + c], W, maxit, S(0), ori);
+                            in[4 * kGC + c], W, maxit, S(0), ori, eos);
         if (st == 1) code |= CODE_BAD_INPUT;
         if (st == 2) code |= CODE_NOCONV;
         prim[c] = S(W.rho);
@@ -369,9 +380,9 @@ __global__ void __launch_bounds__(NT, MINB) patch_kernel(PatchArgs a) {
           W.u[2] = R(prim[3 * kGC + tc]);
           W.p = R(prim[4 * kGC + tc]);
           R dF[5] = {R(0), R(0), R(0), R(0), R(0)};
-          recon_direction<0>(prim, tc, W, theta, i, j, k, interior, face, dF, fail, ori);
-          recon_direction<1>(prim, tc, W, theta, i, j, k, interior, face, dF, fail, ori);
-          recon_direction<2>(prim, tc, W, theta, i, j, k, interior, face, dF, fail, ori);
+          recon_direction<0>(prim, tc, W, theta, i, j, k, interior, face, dF, fail, ori, eos);
+          recon_direction<1>(prim, tc, W, theta, i, j, k, interior, face, dF, fail, ori, eos);
+          recon_direction<2>(prim, tc, W, theta, i, j, k, interior, face, dF, fail, ori, eos);
           halfstep_direction<0>(i, j, k, interior, face, dF, half);
           halfstep_direction<1>(i, j, k, interior, face, dF, half);
           halfstep_direction<2>(i, j, k, interior, face, dF, half);
@@ -380,10 +391,11 @@ __global__ void __launch_bounds__(NT, MINB) patch_kernel(PatchArgs a) {
         // ---- phase 3: Riemann fluxes ----------------------------------------
         for (int f = tid; f < 3 * kNF; f += NT) {
           const int d = f / kNF, fi = f - d * kNF;
-          if (d == 0) fail |= face_flux<0, P, PAIR>(face, hts, fi, a.riemann, maxit, code, ori);
+          if (d == 0)
+            fail |= face_flux<0, P, PAIR>(face, hts, fi, a.riemann, maxit, code, ori, eos);
           else if (d == 1)
-            fail |= face_flux<1, P, PAIR>(face, hts, fi, a.riemann, maxit, code, ori);
-          else fail |= face_flux<2, P, PAIR>(face, hts, fi, a.riemann, maxit, code, ori);
+            fail |= face_flux<1, P, PAIR>(face, hts, fi, a.riemann, maxit, code, ori, eos);
+          else fail |= face_flux<2, P, PAIR>(face, hts, fi, a.riemann, maxit, code, ori, eos);
         }
         fail = __syncthreads_or(fail);
         if (a.flux_only) {
@@ -467,16 +479,16 @@ __global__ void __launch_bounds__(NT, MINB) patch_kernel(PatchArgs a) {
               int st[NPC];
               if constexpr (PAIR) {
                 con2pri_x2<P>(Un[0], Un[1], W[0], W[1], maxit, st[0], st[1], g0[0], g0[NPC - 1],
-                              ori);
+                              ori, eos);
               } else {
                 st[0] = con2pri<P>(Un[0][0], Un[0][1], Un[0][2], Un[0][3], Un[0][4], W[0], maxit,
-                                   g0[0], ori);
+                                   g0[0], ori, eos);
               }
 #pragma unroll
               for (int q = 0; q < NPC; ++q) {
                 // the largest signal speed of the patch; dt = C dh / S_max once
                 if (st[q] != 1) {
-                  att_smax = fmax(att_smax, smax_of(W[q], a.ndim));
+                  att_smax = fmax(att_smax, smax_of(W[q], a.ndim, eos));
                 } else {
                   att_bad = 1;
                   fail4 = 1;
@@ -560,8 +572,9 @@ __global__ void cfl_finalize_kernel(const double* partial, const int32_t* bad, i
                                     double* dt_out);
 
 // ---- batched conversions ----------------------------------------------------
-template <class S>
-__global__ void prim2con_kernel(const S* prim, S* cons, int64_t n, int64_t stride, int ori) {
+template <class S, class E = EosTM>
+__global__ void prim2con_kernel(const S* prim, S* cons, int64_t n, int64_t stride, int ori,
+                                E eos) {
   using R = S;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
@@ -572,22 +585,22 @@ __global__ void prim2con_kernel(const S* prim, S* cons, int64_t n, int64_t strid
     W.u[2] = prim[3 * stride + i];
     W.p = prim[4 * stride + i];
     R U[5];
-    prim2con(W, U, ori);
+    prim2con(W, U, ori, eos);
 #pragma unroll
     for (int v = 0; v < 5; ++v) cons[v * stride + i] = U[v];
   }
 }
 
-template <class P>
+template <class P, class E = EosTM>
 __global__ void con2pri_kernel(const typename P::S* cons, typename P::S* prim, int64_t n,
-                               int64_t stride, int32_t* status, int maxit, int ori) {
+                               int64_t stride, int32_t* status, int maxit, int ori, E eos) {
   using S = typename P::S;
   using R = S;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     PrimX<R> W;
     int st = con2pri<P>(cons[i], cons[stride + i], cons[2 * stride + i], cons[3 * stride + i],
-                        cons[4 * stride + i], W, maxit, S(0), ori);
+                        cons[4 * stride + i], W, maxit, S(0), ori, eos);
     prim[i] = W.rho;
     prim[stride + i] = W.u[0];
     prim[2 * stride + i] = W.u[1];
@@ -598,11 +611,11 @@ __global__ void con2pri_kernel(const typename P::S* cons, typename P::S* prim, i
 }
 
 // CFL bound over interior patches [np][5][8^3]; per-block partial minima.
-template <class P, int NT>
+template <class P, int NT, class E = EosTM>
 __global__ void __launch_bounds__(NT) cfl_kernel(const typename P::S* cons, int64_t ncell,
                                                  double dh, double cfl, int ndim, int mode,
                                                  int maxit, double* partial, int32_t* bad_out,
-                                                 int ori) {
+                                                 int ori, E eos) {
   using S = typename P::S;
   using R = S;
   __shared__ double s_red[NT / 32];
@@ -614,10 +627,11 @@ __global__ void __launch_bounds__(NT) cfl_kernel(const typename P::S* cons, int6
     const int64_t p = q / kNC, c = q - p * kNC;
     const S* b = cons + p * 5 * kNC + c;
     PrimX<R> W;
-    int st = con2pri<P>(b[0], b[kNC], b[2 * kNC], b[3 * kNC], b[4 * kNC], W, maxit, S(0), ori);
+    int st = con2pri<P>(b[0], b[kNC], b[2 * kNC], b[3 * kNC], b[4 * kNC], W, maxit, S(0), ori,
+                        eos);
     if (st == 1) { bad = 1; continue; }
     if (mode == 1) m = fmin(m, cfl * dh);
-    else m = fmin(m, cfl * dh / double(smax_of(W, ndim)));
+    else m = fmin(m, cfl * dh / double(smax_of(W, ndim, eos)));
   }
   for (int o = 16; o > 0; o >>= 1) {
     m = fmin(m, __shfl_xor_sync(0xffffffffu, m, o));
@@ -665,16 +679,27 @@ __global__ void fill_ghosts_kernel(const S* interior, S* ghosted, int npx, int n
 // srhd_mixed.cu and srhd_mixed_cf.cu for the tags of srhd_physics.cuh).
 constexpr int kPatchVariants = 4;  // launch variants of patch_kernel per precision
 
+// EoS of a launch: poly = 0 selects the Taub-Mathews kernels, 1 the
+// polytropic ones with the given Gamma.
+struct EosArg {
+  int poly;
+  double gam;
+};
+
 template <class P> struct Launch {
   static cudaError_t setup();
   static int patch_blocks_per_sm(int variant);
-  static cudaError_t patches(const PatchArgs& a, int variant, int grid, cudaStream_t s);
+  // a.eos_gamma and `poly` select the EoS; the polytropic EoS runs one
+  // launch configuration (PolyVariant) whatever the variant
+  static cudaError_t patches(const PatchArgs& a, int variant, int poly, int grid, cudaStream_t s);
+  static int poly_blocks_per_sm();
   static cudaError_t prim2con(const void* prim, void* cons, int64_t n, int64_t stride, int ori,
-                              int grid, cudaStream_t s);
+                              EosArg eos, int grid, cudaStream_t s);
   static cudaError_t con2pri(const void* cons, void* prim, int64_t n, int64_t stride,
-                             int32_t* status, int maxit, int ori, int grid, cudaStream_t s);
+                             int32_t* status, int maxit, int ori, EosArg eos, int grid,
+                             cudaStream_t s);
   static cudaError_t cfl(const void* cons, int64_t ncell, double dh, double cfl, int ndim, int mode,
-                         int maxit, int ori, double* partial, int32_t* bad, int grid,
+                         int maxit, int ori, EosArg eos, double* partial, int32_t* bad, int grid,
                          cudaStream_t s);
   static cudaError_t fill_ghosts(const void* interior, void* ghosted, int npx, int npy, int npz,
                                  const int32_t* bc, int grid, cudaStream_t s);

@@ -24,6 +24,16 @@ template <> struct PatchVariant<float, 1> { static constexpr int nt = 448, minb 
 template <> struct PatchVariant<float, 2> { static constexpr int nt = 320, minb = 2; static constexpr bool pair = true; };
 template <> struct PatchVariant<float, 3> { static constexpr int nt = 384, minb = 2; static constexpr bool pair = true; };
 
+// The polytropic-EoS kernel runs one configuration per storage type.
+template <class S> struct PolyVariant;
+template <> struct PolyVariant<double> { static constexpr int nt = 512, minb = 1; static constexpr bool pair = false; };
+template <> struct PolyVariant<float> { static constexpr int nt = 448, minb = 2; static constexpr bool pair = true; };
+
+template <class P> struct PolyKernel {
+  using Cfg = PolyVariant<typename P::S>;
+  static constexpr auto fn = patch_kernel<P, Cfg::nt, Cfg::minb, Cfg::pair, EosPoly>;
+};
+
 template <class P, int V> struct PatchKernel {
   using S = typename P::S;
   using Cfg = PatchVariant<S, V>;
@@ -40,7 +50,19 @@ template <class P> cudaError_t Launch<P>::setup() {
   if (e == cudaSuccess) e = setup_variant<P, 1>();
   if (e == cudaSuccess) e = setup_variant<P, 2>();
   if (e == cudaSuccess) e = setup_variant<P, 3>();
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(PolyKernel<P>::fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             int(SmemLayout<typename P::S>::bytes));
   return e;
+}
+
+template <class P> int Launch<P>::poly_blocks_per_sm() {
+  int nb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, PolyKernel<P>::fn,
+                                                    PolyKernel<P>::Cfg::nt,
+                                                    SmemLayout<typename P::S>::bytes) != cudaSuccess)
+    return 0;
+  return nb;
 }
 
 template <class P, int V> static int blocks_variant() {
@@ -68,7 +90,12 @@ static cudaError_t launch_variant(const PatchArgs& a, int grid, cudaStream_t s) 
 }
 
 template <class P>
-cudaError_t Launch<P>::patches(const PatchArgs& a, int variant, int grid, cudaStream_t s) {
+cudaError_t Launch<P>::patches(const PatchArgs& a, int variant, int poly, int grid,
+                               cudaStream_t s) {
+  if (poly) {
+    PolyKernel<P>::fn<<<grid, PolyKernel<P>::Cfg::nt, SmemLayout<typename P::S>::bytes, s>>>(a);
+    return cudaGetLastError();
+  }
   switch (variant) {
     case 0: return launch_variant<P, 0>(a, grid, s);
     case 1: return launch_variant<P, 1>(a, grid, s);
@@ -79,30 +106,46 @@ cudaError_t Launch<P>::patches(const PatchArgs& a, int variant, int grid, cudaSt
 
 template <class P>
 cudaError_t Launch<P>::prim2con(const void* prim, void* cons, int64_t n, int64_t stride, int ori,
-                                int grid, cudaStream_t s) {
+                                EosArg eos, int grid, cudaStream_t s) {
   using S = typename P::S;
-  prim2con_kernel<S><<<grid, 256, 0, s>>>(static_cast<const S*>(prim), static_cast<S*>(cons), n,
-                                          stride, ori);
+  if (eos.poly)
+    prim2con_kernel<S, EosPoly><<<grid, 256, 0, s>>>(
+        static_cast<const S*>(prim), static_cast<S*>(cons), n, stride, ori, EosPoly{eos.gam});
+  else
+    prim2con_kernel<S, EosTM><<<grid, 256, 0, s>>>(static_cast<const S*>(prim),
+                                                   static_cast<S*>(cons), n, stride, ori, EosTM{});
   return cudaGetLastError();
 }
 
 template <class P>
 cudaError_t Launch<P>::con2pri(const void* cons, void* prim, int64_t n, int64_t stride,
-                               int32_t* status, int maxit, int ori, int grid, cudaStream_t s) {
+                               int32_t* status, int maxit, int ori, EosArg eos, int grid,
+                               cudaStream_t s) {
   using S = typename P::S;
-  con2pri_kernel<P><<<grid, 256, 0, s>>>(static_cast<const S*>(cons), static_cast<S*>(prim), n,
-                                         stride, status, maxit, ori);
+  if (eos.poly)
+    con2pri_kernel<P, EosPoly><<<grid, 256, 0, s>>>(static_cast<const S*>(cons),
+                                                    static_cast<S*>(prim), n, stride, status,
+                                                    maxit, ori, EosPoly{eos.gam});
+  else
+    con2pri_kernel<P, EosTM><<<grid, 256, 0, s>>>(static_cast<const S*>(cons),
+                                                  static_cast<S*>(prim), n, stride, status, maxit,
+                                                  ori, EosTM{});
   return cudaGetLastError();
 }
 
 template <class P>
 cudaError_t Launch<P>::cfl(const void* cons, int64_t ncell, double dh, double cfl, int ndim,
-                           int mode, int maxit, int ori, double* partial, int32_t* bad, int grid,
-                           cudaStream_t s) {
+                           int mode, int maxit, int ori, EosArg eos, double* partial, int32_t* bad,
+                           int grid, cudaStream_t s) {
   using S = typename P::S;
-  cfl_kernel<P, kCflThreads><<<grid, kCflThreads, 0, s>>>(static_cast<const S*>(cons), ncell, dh,
-                                                          cfl, ndim, mode, maxit, partial, bad,
-                                                          ori);
+  if (eos.poly)
+    cfl_kernel<P, kCflThreads, EosPoly><<<grid, kCflThreads, 0, s>>>(
+        static_cast<const S*>(cons), ncell, dh, cfl, ndim, mode, maxit, partial, bad, ori,
+        EosPoly{eos.gam});
+  else
+    cfl_kernel<P, kCflThreads, EosTM><<<grid, kCflThreads, 0, s>>>(
+        static_cast<const S*>(cons), ncell, dh, cfl, ndim, mode, maxit, partial, bad, ori,
+        EosTM{});
   return cudaGetLastError();
 }
 

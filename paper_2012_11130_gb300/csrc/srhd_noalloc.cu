@@ -49,11 +49,11 @@ int32_t* g_bad_addr[kMaxDevices] = {};
 
 // One block per patch: the minimum of C dh / S_max over its 512 cells (or
 // C dh in light-speed mode) and a flag for unphysical cells.
-template <class P>
+template <class P, class E>
 __global__ void __launch_bounds__(kThreads) patch_cfl_kernel(const typename P::S* cons, double dh,
                                                              double cfl, int ndim, int mode,
                                                              int maxit, double* patch_dt,
-                                                             int32_t* patch_bad, int ori) {
+                                                             int32_t* patch_bad, int ori, E eos) {
   using S = typename P::S;
   using R = S;
   __shared__ double s_m[kThreads / 32];
@@ -65,9 +65,10 @@ __global__ void __launch_bounds__(kThreads) patch_cfl_kernel(const typename P::S
     srhd::PrimX<R> W;
     int st = srhd::con2pri<P>(base[c], base[kCells + c], base[2 * kCells + c],
                               base[3 * kCells + c], base[4 * kCells + c], W, maxit,
-                              S(0), ori);
+                              S(0), ori, eos);
     if (st == 1) { bad = 1; continue; }
-    m = (mode == 1) ? fmin(m, cfl * dh) : fmin(m, cfl * dh / double(srhd::smax_of(W, ndim)));
+    m = (mode == 1) ? fmin(m, cfl * dh)
+                    : fmin(m, cfl * dh / double(srhd::smax_of(W, ndim, eos)));
   }
   for (int o = 16; o > 0; o >>= 1) {
     m = fmin(m, __shfl_xor_sync(0xffffffffu, m, o));
@@ -111,6 +112,24 @@ __global__ void __launch_bounds__(kThreads) patch_cfl_reduce_kernel(const double
     else if (mm == DBL_MAX) mm = __longlong_as_double(0x7ff0000000000000ULL);
     dt_out[0] = mm;
   }
+}
+
+template <class P, class E>
+void launch_patch_cfl(const void* cons, int32_t npatch, double dh, const srhd_params& p, int maxit,
+                      double* patch_dt, int32_t* patch_bad, int ori, E eos, cudaStream_t s) {
+  patch_cfl_kernel<P, E><<<npatch, kThreads, 0, s>>>(
+      static_cast<const typename P::S*>(cons), dh, p.cfl, p.ndim, p.cfl_mode, maxit, patch_dt,
+      patch_bad, ori, eos);
+}
+
+template <class P>
+void launch_patch_cfl(const void* cons, int32_t npatch, double dh, const srhd_params& p, int maxit,
+                      double* patch_dt, int32_t* patch_bad, int ori, cudaStream_t s) {
+  if (p.eos == SRHD_EOS_POLYTROPIC)
+    launch_patch_cfl<P>(cons, npatch, dh, p, maxit, patch_dt, patch_bad, ori,
+                        srhd::EosPoly{p.gamma}, s);
+  else
+    launch_patch_cfl<P>(cons, npatch, dh, p, maxit, patch_dt, patch_bad, ori, srhd::EosTM{}, s);
 }
 
 srhd_status noalloc_fail(srhd_status st, const char* msg) {
@@ -167,6 +186,10 @@ extern "C" srhd_status srhd_cfl_dt_noalloc(srhd_prec prec, const void* cons, int
     return noalloc_fail(SRHD_ERR_ARG, "newton_max_iter must be in [0, 1000]");
   if (p.scheme != SRHD_SCHEME_REDUCED && p.scheme != SRHD_SCHEME_TOTAL)
     return noalloc_fail(SRHD_ERR_ARG, "invalid scheme");
+  if (p.eos != SRHD_EOS_TM && p.eos != SRHD_EOS_POLYTROPIC)
+    return noalloc_fail(SRHD_ERR_ARG, "invalid eos");
+  if (p.eos == SRHD_EOS_POLYTROPIC && !(p.gamma > 1.0 && p.gamma <= 5.0 / 3.0 + 1e-12))
+    return noalloc_fail(SRHD_ERR_ARG, "gamma of the polytropic EoS must be in (1, 5/3]");
   const int ori = p.scheme == SRHD_SCHEME_TOTAL ? 1 : 0;
   double* patch_dt = nullptr;
   int32_t* patch_bad = nullptr;
@@ -176,17 +199,11 @@ extern "C" srhd_status srhd_cfl_dt_noalloc(srhd_prec prec, const void* cons, int
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (npatch > 0) {
     if (prec == SRHD_FP64)
-      patch_cfl_kernel<srhd::PrecFP64><<<npatch, kThreads, 0, s>>>(
-          static_cast<const double*>(cons), dh, p.cfl, p.ndim, p.cfl_mode, maxit, patch_dt,
-          patch_bad, ori);
+      launch_patch_cfl<srhd::PrecFP64>(cons, npatch, dh, p, maxit, patch_dt, patch_bad, ori, s);
     else if (prec == SRHD_MIXED)
-      patch_cfl_kernel<srhd::PrecMixed><<<npatch, kThreads, 0, s>>>(
-          static_cast<const float*>(cons), dh, p.cfl, p.ndim, p.cfl_mode, maxit, patch_dt,
-          patch_bad, ori);
+      launch_patch_cfl<srhd::PrecMixed>(cons, npatch, dh, p, maxit, patch_dt, patch_bad, ori, s);
     else
-      patch_cfl_kernel<srhd::PrecMixedCF><<<npatch, kThreads, 0, s>>>(
-          static_cast<const float*>(cons), dh, p.cfl, p.ndim, p.cfl_mode, maxit, patch_dt,
-          patch_bad, ori);
+      launch_patch_cfl<srhd::PrecMixedCF>(cons, npatch, dh, p, maxit, patch_dt, patch_bad, ori, s);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return noalloc_fail(SRHD_ERR_CUDA, cudaGetErrorString(e));
   }

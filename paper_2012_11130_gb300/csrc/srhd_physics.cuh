@@ -12,6 +12,7 @@
 #pragma once
 
 #include <cstdint>
+#include <type_traits>
 #include <cuda_runtime.h>
 
 namespace srhd {
@@ -61,18 +62,43 @@ template <class R> struct PrimX {
   R T, h, gamma;    // T = p/rho, h = 1 + htilde, gamma = sqrt(1 + U.U)
   R rg;             // 1 / gamma (three-velocity v = U rg)
   R ht;             // htilde (set by the conversions from conserved variables)
-  R tau;            // conic parameter h - T - 1 (set by the same conversions)
+  R tau;            // solver variable: conic parameter h - T - 1 (TM) or htilde
+                    // (polytropic), set by the same conversions
 };
 
-// Eq. (T_to_HTilde): htilde(T) without subtraction.
-template <class R> __device__ __forceinline__ R htilde_of_T(R T) {
-  R a = R(2.25) * T * T;
-  return R(2.5) * T + qdiv(a, R(1) + sqrt(a + R(1)));
+// Equation of state, selected at compile time by a tag:
+//   EosTM    the Taub-Mathews EoS (Eq. TM EOS), the paper's;
+//   EosPoly  the polytropic EoS h = 1 + Gamma/(Gamma-1) T (Section 2.2; kept
+//            by the paper for pure non-relativistic or ultra-relativistic
+//            gas), with Gamma (1 < Gamma <= 5/3) given at run time.
+struct EosTM {};
+struct EosPoly {
+  double gam;
+};
+
+// htilde(T) and htilde - T. TM: Eq. (T_to_HTilde) without subtraction,
+// htilde - T = 1.5 T + 2.25 T^2/(1 + sqrt(1 + 2.25 T^2)). Polytropic:
+// Gamma/(Gamma-1) T and T/(Gamma-1).
+template <class R>
+__device__ __forceinline__ void eos_ht(const EosTM&, R T, R& ht, R& hmT) {
+  const R a = R(2.25) * T * T;
+  const R t2 = qdiv(a, R(1) + sqrt(a + R(1)));
+  ht = R(2.5) * T + t2;
+  hmT = R(1.5) * T + t2;
+}
+template <class R>
+__device__ __forceinline__ void eos_ht(const EosPoly& e, R T, R& ht, R& hmT) {
+  hmT = T * R(1.0 / (e.gam - 1.0));
+  ht = T + hmT;
 }
 
-// Eq. (sound_speed): c_s^2 = T (5h - 8T) / (3h (h - T)).
-template <class R> __device__ __forceinline__ R cs2_of(R T, R h) {
+// Sound speed squared. TM: Eq. (sound_speed), c_s^2 = T (5h - 8T) / (3h (h - T)).
+// Polytropic: Gamma T / h.
+template <class R> __device__ __forceinline__ R cs2_of(const EosTM&, R T, R h) {
   return T * (R(5) * h - R(8) * T) / (R(3) * h * (h - T));
+}
+template <class R> __device__ __forceinline__ R cs2_of(const EosPoly& e, R T, R h) {
+  return R(e.gam) * T / h;
 }
 
 // Packed FP32: the sm_100 family executes an add, a multiply or a fused
@@ -163,6 +189,34 @@ __device__ __forceinline__ V tau_step(V tau, V ml, V ml9, V nA, V lam) {
   const V dr = mul(fma(neg(r), dD, dN), rD);                  // dr/dtau
   const V dG = fma(t2, r, mul(P, dr));                        // d(P r)/dtau, P' = 2t
   return mul(fma(P, r, nA), rcp(dG));
+}
+
+// ---- conserved -> primitive for the polytropic EoS --------------------------
+// With T = k htilde (k = (Gamma-1)/Gamma) and (h - T) = 1 + (1-k) htilde, the
+// same identity gives f = (1-k) htilde (2 + (1-k) htilde)
+// - k^2 htilde^2 m^2/(h^2 + m^2), rational in htilde; Newton-Raphson on
+// htilde from the m = 0 root htilde0 = A / ((1-k)(1 + sqrt(1 + A))). Its
+// quadratic constant is <= 0.67 for 1 < Gamma <= 5/3 (measured over
+// T 1e-10..1e6, gamma 1..1e6), so the stopping rule of NewtonCfg holds.
+template <class V> __device__ __forceinline__ V poly_start(V A, V omk) {
+  using namespace ar;
+  return mul(A, rcp(mul(omk, add(c<V>(1.0), sqr(add(c<V>(1.0), A))))));
+}
+
+// Newton step (f - A)/f' at htilde = x; omk = 1 - k, k2 = k^2, nA = -A.
+template <class V>
+__device__ __forceinline__ V poly_step(V x, V m2, V omk, V k2, V nA) {
+  using namespace ar;
+  const V h = add(x, c<V>(1.0));
+  const V q = fma(h, h, m2);
+  const V rq = rcp(q);
+  const V ox = mul(omk, x);
+  const V km = mul(mul(k2, m2), rq);                      // k^2 m^2 / q
+  const V G = fma(neg(mul(km, x)), x, fma(ox, add(ox, c<V>(2.0)), nA));   // f - A
+  // f' = 2 (1-k)(1 + (1-k) x) - 2 k^2 x m^2 (q - x h) / q^2
+  const V dG = mul(c<V>(2.0), fma(neg(mul(km, x)), mul(fma(neg(x), h, q), rq),
+                                  mul(omk, add(ox, c<V>(1.0)))));
+  return mul(G, rcp(dG));
 }
 
 // Precision tags. S is the storage and arithmetic type; AT is the type in
@@ -381,6 +435,71 @@ __device__ __forceinline__ void prims_from_tau_x2(const float (&Ua)[5], const fl
   Wb.T = T.y; Wb.h = h.y; Wb.gamma = gamma.y; Wb.rg = rg.y; Wb.ht = ht.y; Wb.tau = tau.y;
 }
 
+// Primitives from the converged htilde of the polytropic EoS (T = k htilde).
+template <class R, class S>
+__device__ __forceinline__ void prims_from_ht_poly(S D, S Mx, S My, S Mz, R ht, R k,
+                                                   PrimX<R>& W) {
+  const R h = R(1) + ht;
+  const R rDh = R(1) / (R(D) * h);
+  W.u[0] = R(Mx) * rDh;
+  W.u[1] = R(My) * rDh;
+  W.u[2] = R(Mz) * rDh;
+  const R g2 = R(1) + (W.u[0] * W.u[0] + W.u[1] * W.u[1] + W.u[2] * W.u[2]);
+  const R rg = rsqrt_r(g2);
+  W.gamma = g2 * rg;
+  W.rg = rg;
+  W.rho = R(D) * rg;
+  W.T = k * ht;
+  W.h = h;
+  W.ht = ht;
+  W.tau = ht;
+  W.p = W.rho * W.T;
+}
+
+// Solver of Eq. (transcendental equation) per EoS, in the variable x that
+// the warm starts carry (tau for TM, htilde for the polytropic EoS):
+// init(A, m2) fixes the per-state constants, start() gives x0, step(x) the
+// Newton step, prims() the primitives from the converged x.
+template <class E, class V> struct Solver;
+template <class V> struct Solver<EosTM, V> {
+  V ml, ml9, nA, lam;
+  __device__ __forceinline__ V init(const EosTM&, V A, V m2) {
+    using namespace ar;
+    const V t0 = tau_start(A);
+    const V t1 = add(t0, c<V>(1.0));
+    lam = rcp(mul(t1, t1));
+    ml = mul(m2, lam);
+    ml9 = mul(ml, c<V>(9.0));
+    nA = neg(A);
+    return t0;
+  }
+  __device__ __forceinline__ V step(V x) const { return tau_step(x, ml, ml9, nA, lam); }
+};
+template <class V> struct Solver<EosPoly, V> {
+  V m2, omk, k2, nA;
+  __device__ __forceinline__ V init(const EosPoly& e, V A, V m2_) {
+    using namespace ar;
+    const double k = (e.gam - 1.0) / e.gam;
+    m2 = m2_;
+    omk = c<V>(1.0 - k);
+    k2 = c<V>(k * k);
+    nA = neg(A);
+    return poly_start(A, omk);
+  }
+  __device__ __forceinline__ V step(V x) const { return poly_step(x, m2, omk, k2, nA); }
+};
+
+template <class R, class S>
+__device__ __forceinline__ void prims_from_x(const EosTM&, S D, S Mx, S My, S Mz, R x,
+                                             PrimX<R>& W) {
+  prims_from_tau(D, Mx, My, Mz, x, W);
+}
+template <class R, class S>
+__device__ __forceinline__ void prims_from_x(const EosPoly& e, S D, S Mx, S My, S Mz, R x,
+                                             PrimX<R>& W) {
+  prims_from_ht_poly(D, Mx, My, Mz, x, R((e.gam - 1.0) / e.gam), W);
+}
+
 template <class R> __device__ __forceinline__ void set_nan(PrimX<R>& W) {
   const R nan = R(__longlong_as_double(0x7ff8000000000000ULL));
   W.rho = W.u[0] = W.u[1] = W.u[2] = W.p = W.T = W.h = W.gamma = W.rg = W.ht = W.tau = nan;
@@ -401,11 +520,12 @@ __device__ __forceinline__ bool newton_done(R adh, R tau, R prev, int k) {
 // Stops by newton_done or after maxit steps (status 2). guess > 0 is a tau
 // to start from (a warm start from a nearby state); otherwise tau_start(A).
 // The root does not depend on the start.
-template <class P>
+template <class P, class E = EosTM>
 __device__ __forceinline__ int con2pri(typename P::S D, typename P::S Mx, typename P::S My,
                                        typename P::S Mz, typename P::S Et,
                                        PrimX<typename P::S>& W, int maxit,
-                                       typename P::S guess = typename P::S(0), int ori = 0) {
+                                       typename P::S guess = typename P::S(0), int ori = 0,
+                                       const E& eos = E()) {
   using R = typename P::S;
   typename P::AT Aa, m2a;
   if (!A_and_m2<P>(D, Mx, My, Mz, Et, Aa, m2a, ori)) {
@@ -413,15 +533,13 @@ __device__ __forceinline__ int con2pri(typename P::S D, typename P::S Mx, typena
     return 1;
   }
   const R A = R(Aa), m2 = R(m2a);
-  const R t0 = tau_start(A);
+  Solver<E, R> sv;
+  const R t0 = sv.init(eos, A, m2);
   R tau = guess > R(0) ? guess : t0;
-  const R t1 = R(1) + t0;
-  const R lam = qrcp(t1 * t1);
-  const R ml = m2 * lam, ml9 = R(9) * ml, nA = -A;
   int status = 2;
   R prev = R(3.0e38);
   for (int k = 1; k <= maxit; ++k) {
-    const R dh = tau_step(tau, ml, ml9, nA, lam);
+    const R dh = sv.step(tau);
     R tn = tau - dh;
     if (!(tn > R(0))) tn = R(0.5) * tau;
     const R adh = fabs(dh);
@@ -429,7 +547,7 @@ __device__ __forceinline__ int con2pri(typename P::S D, typename P::S Mx, typena
     if (newton_done(adh, tau, prev, k)) { status = 0; break; }
     prev = adh;
   }
-  prims_from_tau(D, Mx, My, Mz, tau, W);
+  prims_from_x(eos, D, Mx, My, Mz, tau, W);
   return status;
 }
 
@@ -438,13 +556,14 @@ __device__ __forceinline__ int con2pri(typename P::S D, typename P::S Mx, typena
 // so that their dependency chains interleave (in float, both lanes of each
 // step are one packed instruction). The loop runs until both have stopped;
 // a state that has stopped is not updated.
-template <class P>
+template <class P, class E = EosTM>
 __device__ __forceinline__ void con2pri_x2(const typename P::S (&Ua)[5],
                                            const typename P::S (&Ub)[5],
                                            PrimX<typename P::S>& Wa, PrimX<typename P::S>& Wb,
                                            int maxit, int& sta, int& stb,
                                            typename P::S ga = typename P::S(0),
-                                           typename P::S gb = typename P::S(0), int ori = 0) {
+                                           typename P::S gb = typename P::S(0), int ori = 0,
+                                           const E& eos = E()) {
   using R = typename P::S;
   typename P::AT Aa_, ma_, Ab_, mb_;
   bool pa, pb;
@@ -463,15 +582,11 @@ __device__ __forceinline__ void con2pri_x2(const typename P::S (&Ua)[5],
   R preva = R(3.0e38), prevb = R(3.0e38);
   if constexpr (sizeof(R) == 4) {
     using namespace pk;
-    const float2 A2 = make_float2(Aa, Ab);
-    const float2 t0 = tau_start(A2);
+    Solver<E, float2> sv;
+    const float2 t0 = sv.init(eos, make_float2(Aa, Ab), make_float2(m2a, m2b));
     float2 tau = make_float2(ga > 0.0f ? ga : t0.x, gb > 0.0f ? gb : t0.y);
-    const float2 t1 = add(t0, s2(1.f));
-    const float2 lam = rcp(mul(t1, t1));
-    const float2 ml = mul(make_float2(m2a, m2b), lam), ml9 = mul(ml, s2(9.f));
-    const float2 nA = neg(A2);
     for (int k = 1; k <= maxit && !(da && db); ++k) {
-      const float2 dh = tau_step(tau, ml, ml9, nA, lam);
+      const float2 dh = sv.step(tau);
       if (!da) {
         float tn = tau.x - dh.x;
         if (!(tn > 0.0f)) tn = 0.5f * tau.x;
@@ -489,16 +604,19 @@ __device__ __forceinline__ void con2pri_x2(const typename P::S (&Ua)[5],
         prevb = adh;
       }
     }
-    prims_from_tau_x2(Ua, Ub, tau, Wa, Wb);
+    if constexpr (std::is_same<E, EosTM>::value) {
+      prims_from_tau_x2(Ua, Ub, tau, Wa, Wb);
+    } else {
+      prims_from_x(eos, Ua[0], Ua[1], Ua[2], Ua[3], tau.x, Wa);
+      prims_from_x(eos, Ub[0], Ub[1], Ub[2], Ub[3], tau.y, Wb);
+    }
   } else {
-    const R t0a = tau_start(Aa), t0b = tau_start(Ab);
+    Solver<E, R> sva, svb;
+    const R t0a = sva.init(eos, Aa, m2a), t0b = svb.init(eos, Ab, m2b);
     R ta = ga > R(0) ? ga : t0a, tb = gb > R(0) ? gb : t0b;
-    const R t1a = R(1) + t0a, t1b = R(1) + t0b;
-    const R lama = qrcp(t1a * t1a), lamb = qrcp(t1b * t1b);
-    const R mla = m2a * lama, mlb = m2b * lamb;
     for (int k = 1; k <= maxit && !(da && db); ++k) {
-      const R dha = tau_step(ta, mla, R(9) * mla, -Aa, lama);
-      const R dhb = tau_step(tb, mlb, R(9) * mlb, -Ab, lamb);
+      const R dha = sva.step(ta);
+      const R dhb = svb.step(tb);
       if (!da) {
         R tn = ta - dha;
         if (!(tn > R(0))) tn = R(0.5) * ta;
@@ -516,8 +634,8 @@ __device__ __forceinline__ void con2pri_x2(const typename P::S (&Ua)[5],
         prevb = adh;
       }
     }
-    prims_from_tau(Ua[0], Ua[1], Ua[2], Ua[3], ta, Wa);
-    prims_from_tau(Ub[0], Ub[1], Ub[2], Ub[3], tb, Wb);
+    prims_from_x(eos, Ua[0], Ua[1], Ua[2], Ua[3], ta, Wa);
+    prims_from_x(eos, Ub[0], Ub[1], Ub[2], Ub[3], tb, Wb);
   }
   if (!pa) {
     set_nan(Wa);
@@ -537,16 +655,16 @@ __device__ __forceinline__ void con2pri_x2(const typename P::S (&Ua)[5],
 // (gamma - 1 = U^2 / (gamma + 1); htilde - T = 1.5 T + 2.25 T^2 / (1 + sqrt(1 + 2.25 T^2))),
 // which shares 1/gamma with the flux and needs one division and no square
 // root beyond those of htilde and gamma.
-template <class R> __device__ __forceinline__ bool prim2con(PrimX<R>& W, R U[5], int ori = 0) {
+template <class R, class E = EosTM>
+__device__ __forceinline__ bool prim2con(PrimX<R>& W, R U[5], int ori = 0, const E& eos = E()) {
   if (!(W.rho > R(0)) || !(W.p > R(0))) {
     R nan = R(__longlong_as_double(0x7ff8000000000000ULL));
     for (int v = 0; v < 5; ++v) U[v] = nan;
     return false;
   }
   const R T = qdiv(W.p, W.rho);
-  const R a = R(2.25) * T * T;
-  const R t2 = qdiv(a, R(1) + sqrt(a + R(1)));  // htilde - 2.5 T
-  const R ht = R(2.5) * T + t2;
+  R ht, hmT;                                     // htilde and htilde - T
+  eos_ht(eos, T, ht, hmT);
   const R u2 = W.u[0] * W.u[0] + W.u[1] * W.u[1] + W.u[2] * W.u[2];
   const R g2 = R(1) + u2;
   const R rg = rsqrt_r(g2);
@@ -561,7 +679,7 @@ template <class R> __device__ __forceinline__ bool prim2con(PrimX<R>& W, R U[5],
   if (ori) {
     U[4] = Dh * gamma - W.p;  // original scheme: E = D h gamma - p
   } else {
-    U[4] = D * (qdiv(u2, gamma + R(1)) + (R(1.5) * T + t2 + ht * u2) * rg);
+    U[4] = D * (qdiv(u2, gamma + R(1)) + (hmT + ht * u2) * rg);
   }
   W.T = T;
   W.h = h;
@@ -573,18 +691,25 @@ template <class R> __device__ __forceinline__ bool prim2con(PrimX<R>& W, R U[5],
 // prim2con and phys_flux<d> of two float states (lanes x, y of W[v]) with
 // packed arithmetic; a lane with rho <= 0 or p <= 0 gets NaN conserved
 // values and its ok flag false.
-template <int d>
+template <int d, class E = EosTM>
 __device__ __forceinline__ void prim2con_flux_x2(const float2 (&W)[5], float2 (&U)[5],
                                                  float2 (&F)[5], bool& okx, bool& oky,
-                                                 int ori) {
+                                                 int ori, const E& eos = E()) {
   using namespace pk;
   okx = W[0].x > 0.0f && W[4].x > 0.0f;
   oky = W[0].y > 0.0f && W[4].y > 0.0f;
   const float2 T = mul(W[4], rcp(W[0]));
-  const float2 a = mul(mul(s2(2.25f), T), T);
-  const float2 sq = add(s2(1.f), make_float2(sqrtf(a.x + 1.0f), sqrtf(a.y + 1.0f)));
-  const float2 t2 = mul(a, rcp(sq));                       // htilde - 2.5 T
-  const float2 ht = fma(s2(2.5f), T, t2);
+  float2 ht, hmT;                                          // htilde and htilde - T
+  if constexpr (std::is_same<E, EosTM>::value) {
+    const float2 a = mul(mul(s2(2.25f), T), T);
+    const float2 sq = add(s2(1.f), make_float2(sqrtf(a.x + 1.0f), sqrtf(a.y + 1.0f)));
+    const float2 t2 = mul(a, rcp(sq));                     // htilde - 2.5 T
+    ht = fma(s2(2.5f), T, t2);
+    hmT = fma(s2(1.5f), T, t2);
+  } else {
+    hmT = mul(T, s2(float(1.0 / (eos.gam - 1.0))));
+    ht = add(T, hmT);
+  }
   const float2 u2 = fma(W[3], W[3], fma(W[2], W[2], mul(W[1], W[1])));
   const float2 g2 = add(s2(1.f), u2);
   const float2 rg = rsq(g2);
@@ -599,7 +724,7 @@ __device__ __forceinline__ void prim2con_flux_x2(const float2 (&W)[5], float2 (&
     U[4] = fma(Dh, gamma, neg(W[4]));  // original scheme: E = D h gamma - p
   } else {  // Et = D [U^2 / (gamma + 1) + (1.5 T + t2 + htilde U^2) / gamma]
     const float2 k1 = mul(u2, rcp(add(gamma, s2(1.f))));
-    U[4] = mul(D, fma(fma(ht, u2, fma(s2(1.5f), T, t2)), rg, k1));
+    U[4] = mul(D, fma(fma(ht, u2, hmT), rg, k1));
   }
   const float2 v = mul(W[1 + d], rg);
   F[0] = mul(U[0], v);
@@ -631,9 +756,9 @@ __device__ __forceinline__ void phys_flux(const PrimX<R>& W, const R U[5], R F[5
 // Outer characteristic speeds along d with the TM sound speed, in the
 // four-velocity form [gamma U_d (1-cs2) -/+ sqrt(cs2 (1 + U_perp^2 (1-cs2)))]
 // / [1 + U^2 (1-cs2)].
-template <int d, class R>
-__device__ __forceinline__ void char_speeds(const PrimX<R>& W, R& lm, R& lp) {
-  R cs2 = cs2_of(W.T, W.h);
+template <int d, class R, class E = EosTM>
+__device__ __forceinline__ void char_speeds(const PrimX<R>& W, R& lm, R& lp, const E& eos = E()) {
+  R cs2 = cs2_of(eos, W.T, W.h);
   R omc = R(1) - cs2;
   R ud = W.u[d];
   // transverse part summed directly (no u2 - ud^2 cancellation)
@@ -649,11 +774,12 @@ __device__ __forceinline__ void char_speeds(const PrimX<R>& W, R& lm, R& lp) {
 
 // phys_flux<d> and char_speeds<d> of the left and right float states with
 // packed arithmetic (lane x left, lane y right).
-template <int d>
+template <int d, class E = EosTM>
 __device__ __forceinline__ void outer_parts_x2(const PrimX<float>& WL, const float UL[5],
                                                const PrimX<float>& WR, const float UR[5],
                                                float FL[5], float FR[5], float& lmL, float& lpL,
-                                               float& lmR, float& lpR, int ori) {
+                                               float& lmR, float& lpR, int ori,
+                                               const E& eos = E()) {
   using namespace pk;
   constexpr int a0 = d == 0 ? 1 : 0, b0 = d == 2 ? 1 : 2;  // transverse components
   const float2 ud = make_float2(WL.u[d], WR.u[d]);
@@ -676,9 +802,14 @@ __device__ __forceinline__ void outer_parts_x2(const PrimX<float>& WL, const flo
   }
   // outer characteristic speeds (char_speeds)
   const float2 T = make_float2(WL.T, WR.T), h = make_float2(WL.h, WR.h);
-  const float2 cnum = mul(T, fma(s2(-8.f), T, mul(s2(5.f), h)));
-  const float2 cden = mul(mul(s2(3.f), h), sub(h, T));
-  const float2 cs2 = make_float2(cnum.x / cden.x, cnum.y / cden.y);
+  float2 cs2;
+  if constexpr (std::is_same<E, EosTM>::value) {
+    const float2 cnum = mul(T, fma(s2(-8.f), T, mul(s2(5.f), h)));
+    const float2 cden = mul(mul(s2(3.f), h), sub(h, T));
+    cs2 = make_float2(cnum.x / cden.x, cnum.y / cden.y);
+  } else {
+    cs2 = mul(mul(s2(float(eos.gam)), T), rcp(h));
+  }
   const float2 omc = sub(s2(1.f), cs2);
   const float2 ua = make_float2(WL.u[a0], WR.u[a0]), ub = make_float2(WL.u[b0], WR.u[b0]);
   const float2 up2 = fma(ub, ub, mul(ua, ua));
@@ -698,18 +829,19 @@ __device__ __forceinline__ void outer_parts_x2(const PrimX<float>& WL, const flo
 // solver (Section 3.1), HLLE when requested or when the contact state is not
 // admissible (discriminant < 0, contact speed outside the outer speeds, or
 // non-positive contact pressure). Returns 1 on fallback.
-template <int d, class R>
+template <int d, class R, class E = EosTM>
 __device__ __forceinline__ int riemann(int solver, const PrimX<R>& WL, const R UL[5],
-                                       const PrimX<R>& WR, const R UR[5], R F[5], int ori = 0) {
+                                       const PrimX<R>& WR, const R UR[5], R F[5], int ori = 0,
+                                       const E& eos = E()) {
   R FL[5], FR[5];
   R lmL, lpL, lmR, lpR;
   if constexpr (sizeof(R) == 4) {
-    outer_parts_x2<d>(WL, UL, WR, UR, FL, FR, lmL, lpL, lmR, lpR, ori);
+    outer_parts_x2<d>(WL, UL, WR, UR, FL, FR, lmL, lpL, lmR, lpR, ori, eos);
   } else {
     phys_flux<d>(WL, UL, FL, ori);
     phys_flux<d>(WR, UR, FR, ori);
-    char_speeds<d>(WL, lmL, lpL);
-    char_speeds<d>(WR, lmR, lpR);
+    char_speeds<d>(WL, lmL, lpL, eos);
+    char_speeds<d>(WR, lmR, lpR, eos);
   }
   R sL = fmin(lmL, lmR);
   R sR = fmax(lpL, lpR);
@@ -778,8 +910,9 @@ template <class R> __device__ __forceinline__ R limited_slope(R dl, R dr, R thet
 
 // Signal speed bound S_max of one cell (Section 3.2, Eqs. time_step_U_max
 // and SMax; |U_x|+|U_y|+|U_z| and ndim gamma U_s).
-template <class R> __device__ __forceinline__ R smax_of(const PrimX<R>& W, int ndim) {
-  R cs2 = cs2_of(W.T, W.h);
+template <class R, class E = EosTM>
+__device__ __forceinline__ R smax_of(const PrimX<R>& W, int ndim, const E& eos = E()) {
+  R cs2 = cs2_of(eos, W.T, W.h);
   R omc = R(1) - cs2;
   R us = sqrt(qdiv(cs2, omc));      // U_s = c_s / sqrt(1 - c_s^2)
   R gs = rsqrt_r(omc);              // gamma_s = 1 / sqrt(1 - c_s^2)

@@ -25,7 +25,7 @@ import torch
 from . import _native as N
 
 __all__ = ["Params", "Context", "prim2con", "con2pri", "flux_patches", "advance_patches",
-           "cfl_dt", "fill_ghosts_uniform", "amr_fill_ghosts", "amr_restrict",
+           "cfl_dt", "cfl_dt_noalloc", "fill_ghosts_uniform", "amr_fill_ghosts", "amr_restrict",
            "amr_flux_correct", "default_context"]
 
 
@@ -42,13 +42,17 @@ class Params:
     newton_max_iter: int = 0
     patch_variant: int = 0       # launch variant of the fused kernel (autotune.py)
     scheme: str = "reduced"      # "reduced" (Etilde, the paper's) | "total" (original, E)
+    eos: str = "tm"              # "tm" (Taub-Mathews, the paper's) | "polytropic"
+    gamma: float = 5.0 / 3.0     # Gamma of the polytropic EoS, 1 < gamma <= 5/3
 
     def to_c(self) -> N.Params:
         return N.Params(self.cfl, self.theta, self.retry_factor, self.theta_floor,
                         {"hllc": N.SRHD_HLLC, "hlle": N.SRHD_HLLE}[self.riemann],
                         {"signal": N.SRHD_CFL_SIGNAL, "light": N.SRHD_CFL_LIGHT}[self.cfl_mode],
                         self.ndim, self.newton_max_iter, self.patch_variant,
-                        {"reduced": N.SRHD_SCHEME_REDUCED, "total": N.SRHD_SCHEME_TOTAL}[self.scheme])
+                        {"reduced": N.SRHD_SCHEME_REDUCED, "total": N.SRHD_SCHEME_TOTAL}[self.scheme],
+                        {"tm": N.SRHD_EOS_TM, "polytropic": N.SRHD_EOS_POLYTROPIC}[self.eos],
+                        self.gamma)
 
 
 _PREC = {"fp64": (N.SRHD_FP64, torch.float64), "mixed": (N.SRHD_MIXED, torch.float32),
@@ -347,6 +351,21 @@ def advance_patches(cons_ghosted, dt_dh, **kw):
 
 def cfl_dt(cons, dh, dt_out=None, stream=None, prec=None):
     return default_context().cfl_dt(cons, dh, dt_out, stream, prec)
+
+
+def cfl_dt_noalloc(cons, dh, dt_out=None, params: Params | None = None, stream=None, prec=None):
+    """srhd_cfl_dt_noalloc: the CFL bound of interior patches [np][5][8][8][8]
+    without a context (no device allocation by the library)."""
+    _need_cuda(cons, "cons")
+    if dt_out is None:
+        dt_out = torch.empty(1, dtype=torch.float64, device=cons.device)
+    _need_cuda(dt_out, "dt_out", torch.float64)
+    L = N.load()
+    p = (params or Params()).to_c()
+    N.check(L.srhd_cfl_dt_noalloc(_prec(cons, prec), _ptr(cons), cons.shape[0], float(dh),
+                                  ctypes.byref(p), _ptr(dt_out), _stream(stream)),
+            "srhd_cfl_dt_noalloc")
+    return dt_out
 
 
 def fill_ghosts_uniform(interior, npx, npy, npz, bc=("periodic",) * 3, ghosted=None, stream=None):
