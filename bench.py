@@ -242,12 +242,13 @@ def time_e2e(torch, ctx, G, dt_dh, steps, warmup, prec):
     return secs, h2d, d2h
 
 
-def l1_one_period(torch, srhd, prec, n=64):
+def l1_one_period(torch, srhd, prec, n=64, params=None):
     """L1 error of rho (Eq. relative L1 error) after one period of the
-    diagonal wave at n^3, evolved on the GPU with the fused CFL."""
+    diagonal wave at n^3, evolved on the GPU with the fused CFL (uniform p
+    and velocity: the wave is translated exactly, whatever the EoS)."""
     import numpy as np
     from paper_2012_11130_gb300 import workloads
-    ctx = srhd.Context(srhd.Params())
+    ctx = srhd.Context(params or srhd.Params())
     W = torch.from_numpy(workloads.advection_prims(n)).to("cuda")
     C = ctx.prim2con(W.reshape(5, -1)).reshape(5, n, n, n)
     npx = n // 8
@@ -326,6 +327,32 @@ def bench_amr(torch, srhd, steps: int, warmup: int, prec: str = "mixed_cf"):
     }
     del batch
     torch.cuda.empty_cache()
+    return out
+
+
+def bench_polytropic(torch, srhd, steps: int, warmup: int, precs=("mixed_cf", "fp64"),
+                     gamma=4.0 / 3.0, variants=None):
+    """The 256^3 advection batch with the polytropic EoS (Gamma = 4/3, the
+    ultra-relativistic gas the paper keeps it for), HLLC and the HLLE-only
+    path: cell updates/s of the fused step and the one-period L1 of rho at
+    64^3 (the same exact translation as for TM)."""
+    out = {"workload": "256^3 periodic advection (as the headline) with the polytropic EoS, "
+                       f"Gamma = {gamma:g}", "gamma": gamma, "runs": {}}
+    for prec in precs:
+        for riemann in ("hllc", "hlle"):
+            ctx = srhd.Context(srhd.Params(eos="polytropic", gamma=gamma, riemann=riemann))
+            G, dt_dh = build_workload(torch, srhd, ctx, prec)
+            total_ms, per, dt_next, smax = time_device(torch, ctx, G, dt_dh, steps, warmup,
+                                                       lambda: None, prec)
+            cells = G.shape[0] * CELLS_PER_PATCH
+            r = {"value": cells * steps / (total_ms * 1e-3), "unit": UNIT,
+                 "ms_per_step": total_ms / steps, "patch_status_max": smax}
+            if riemann == "hllc":
+                r["l1_rho_64"], _ = l1_one_period(torch, srhd, prec, params=srhd.Params(
+                    eos="polytropic", gamma=gamma))
+            out["runs"][f"{prec}_{riemann}"] = r
+            del G, dt_dh
+            torch.cuda.empty_cache()
     return out
 
 
@@ -670,6 +697,11 @@ def run_ours(args):
         amr_res = bench_amr(torch, srhd, max(3, args.steps // 4), 2, precs[0] if precs[0] != "fp64"
                             else "mixed_cf")
 
+    poly_res = None
+    if not args.no_poly and args.grid == N_GRID and rank == 0:
+        poly_res = bench_polytropic(torch, srhd, max(3, args.steps // 2), 3,
+                                    precs=tuple(q for q in ("mixed_cf", "fp64") if q in precs))
+
     jet_res = None
     if not args.no_jet and args.grid == N_GRID and rank == 0:
         vs = {q: results[q]["autotune"]["chosen_variant"] for q in precs
@@ -743,6 +775,7 @@ def run_ours(args):
         "con2pri_stress": stress or None,
         "amr_blast": amr_res,
         "amr_jet": jet_res,
+        "polytropic": poly_res,
         "kernel_sources_sha": sha,
     }
     print(json.dumps(line))
@@ -763,6 +796,7 @@ def main():
     ap.add_argument("--no-l1", action="store_true")
     ap.add_argument("--no-amr", action="store_true")
     ap.add_argument("--no-jet", action="store_true", help="skip the AMR jet (configuration 5)")
+    ap.add_argument("--no-poly", action="store_true", help="skip the polytropic-EoS workload")
     ap.add_argument("--jet-steps", type=int, default=100, help="coarse steps of each jet run")
     ap.add_argument("--jet-gammas", default="10,20,50,100",
                     help="comma-separated beam Lorentz factors of the jet runs")
