@@ -86,6 +86,10 @@ def lib():
                                            d, d, i32, _ip, i32]
             L.or_advance_patches.restype = None
             L.or_advance_patches.argtypes = [_dp, _dp, i64, _dp, d, d, d, i32, _ip, _ip, _dp, i32]
+            L.or_advance_block_vl.restype = i32
+            L.or_advance_block_vl.argtypes = L.or_advance_block.argtypes
+            L.or_advance_patches_vl.restype = None
+            L.or_advance_patches_vl.argtypes = L.or_advance_patches.argtypes
             L.or_cfl_dt.restype = d
             L.or_cfl_dt.argtypes = [_dp, i64, d, d, i32, i32, i32]
             L.or_count_advance_block.restype = None
@@ -281,6 +285,41 @@ def advance_patches(cons, dt_dh, theta=DEFAULT_THETA, riemann=0, want_flux=False
     return dict(out=out, status=st, retries=rt, flux=flux)
 
 
+def advance_block_vl(cons, n, act, dt, dh, theta=DEFAULT_THETA, riemann=0, want_flux=False,
+                     retry_factor=RETRY_FACTOR, theta_floor=THETA_FLOOR, scheme=NEW):
+    """One VL (predictor-corrector) step of a block with 3 ghost cells on
+    active dims: cons [5][Nz][Ny][Nx], N_d = n_d + 6 on active dims."""
+    cons = _f64(cons)
+    nx, ny, nz = n
+    out = np.empty((5, nz, ny, nx))
+    flux = None
+    if want_flux:
+        nf = sum(((nx * ny * nz) // n[d]) * (n[d] + 1) for d in range(3) if act[d])
+        flux = np.empty(5 * nf)
+    r = np.zeros(1, np.int32)
+    st = lib().or_advance_block_vl(_p(cons), _p(out), _p(flux), nx, ny, nz, int(act[0]),
+                                   int(act[1]), int(act[2]), dt, dh, theta, retry_factor,
+                                   theta_floor, riemann, _p(r, _ip), scheme)
+    return dict(out=out, status=st, retries=int(r[0]), flux=flux)
+
+
+def advance_patches_vl(cons, dt_dh, theta=DEFAULT_THETA, riemann=0, want_flux=False,
+                       scheme=NEW):
+    """Batched VL step of independent 8^3 patches with 3-cell ghosts:
+    cons [np][5][14][14][14] -> dict(out [np][5][8][8][8], status, retries,
+    flux [np][3][5][576] if requested)."""
+    cons = _f64(cons)
+    npatch = cons.shape[0]
+    out = np.empty((npatch, 5, 8, 8, 8))
+    st = np.empty(npatch, np.int32)
+    rt = np.empty(npatch, np.int32)
+    flux = np.empty((npatch, 3, 5, 576)) if want_flux else None
+    dt_dh = _f64(dt_dh).reshape(npatch, 2)
+    lib().or_advance_patches_vl(_p(cons), _p(out), npatch, _p(dt_dh), theta, RETRY_FACTOR,
+                                THETA_FLOOR, riemann, _p(st, _ip), _p(rt, _ip), _p(flux), scheme)
+    return dict(out=out, status=st, retries=rt, flux=flux)
+
+
 def cfl_dt(cons, dh, cfl=0.5, ndim=3, cfl_mode=0, scheme=NEW):
     """Eq. (time_step_sound_speed): min over cells cons [5][n]."""
     cons = _f64(cons).reshape(5, -1)
@@ -323,20 +362,22 @@ def rapidity_integral(T1, T2):
 
 
 # --- whole-domain driver (plain Python loop over oracle steps) -------------
-def fill_ghosts(interior, act, bc):
-    """Pad [5][nz][ny][nx] with 2 ghost cells on active dims.
+def fill_ghosts(interior, act, bc, width=2):
+    """Pad [5][nz][ny][nx] with `width` ghost cells on active dims (2 for
+    MUSCL-Hancock, 3 for VL).
 
     bc: 'periodic' (wrap) or 'outflow' (zero-gradient copy of the edge cell)."""
     mode = "wrap" if bc == "periodic" else "edge"
-    pads = [(0, 0)] + [((2, 2) if act[d] else (0, 0)) for d in (2, 1, 0)]
+    pads = [(0, 0)] + [((width, width) if act[d] else (0, 0)) for d in (2, 1, 0)]
     return np.pad(interior, pads, mode=mode)
 
 
 def evolve(cons, act, dh, t_end, bc, cfl=0.5, theta=DEFAULT_THETA, riemann=0, max_steps=10**7,
-           scheme=NEW):
+           scheme=NEW, integrator="mh"):
     """Advance the whole domain to t_end: each step takes the CFL time step
     of the current state (clipped to reach t_end exactly), fills ghosts and
-    applies one block step. Returns dict(cons, t, steps, retries)."""
+    applies one block step (integrator "mh": MUSCL-Hancock, "vl": VL).
+    Returns dict(cons, t, steps, retries)."""
     cons = _f64(cons).copy()
     nz, ny, nx = cons.shape[1:]
     n = (nx, ny, nz)
@@ -350,8 +391,12 @@ def evolve(cons, act, dh, t_end, bc, cfl=0.5, theta=DEFAULT_THETA, riemann=0, ma
             raise RuntimeError("unphysical state in CFL")
         if t + dt > t_end:
             dt = t_end - t
-        r = advance_block(fill_ghosts(cons, act, bc), n, act, dt, dh, theta=theta,
-                          riemann=riemann, scheme=scheme)
+        if integrator == "vl":
+            r = advance_block_vl(fill_ghosts(cons, act, bc, 3), n, act, dt, dh, theta=theta,
+                                 riemann=riemann, scheme=scheme)
+        else:
+            r = advance_block(fill_ghosts(cons, act, bc), n, act, dt, dh, theta=theta,
+                              riemann=riemann, scheme=scheme)
         if r["status"] not in (BLK_OK, BLK_NOCONV):
             raise RuntimeError(f"block step failed with status {r['status']}")
         retries += r["retries"]

@@ -631,6 +631,212 @@ int advance_block(const R* in, R* out, R* flux_out, const int n[3], const int ac
 
 
 // ----------------------------------------------------------------------------
+// VL integrator (Section 3.1: "MUSCL-Hancock and VL"; van Leer 2006, Falle
+// 1991): a predictor-corrector step.
+//   predictor  U*(c) = U^n(c) - dt/(2 dh) sum_d [F1(c, c+e_d) - F1(c-e_d, c)]
+//              with F1 the Riemann flux between the piecewise-constant cell
+//              states (first order, unsplit), then W* = con2pri(U*);
+//   corrector  PLM slopes of W* (the limiter with coefficient theta), face
+//              states W* -/+ dW/2 (no Hancock evolution), their conserved
+//              form, the Riemann flux, and
+//              U^{n+1} = U^n - dt/dh sum_d [F(face+) - F(face-)].
+// The corrector's PLM stencil reaches two cells beyond the face and the
+// predictor one more, so the block carries 3 ghost cells per active side.
+// The limiter retry (Section 3.3) redoes the corrector with a smaller theta;
+// the predictor does not depend on theta. If a predicted state is
+// unphysical the corrector cannot run: the block returns BLK_UNPHYSICAL with
+// NaN outputs.
+// ----------------------------------------------------------------------------
+template <class R> struct VlBlock {
+  int n[3], g[3], N[3], act[3];
+  int ori, riemann;
+  R dt, dh;
+  const R* in;
+  std::vector<R> W;          // W^n [5][Ncells]
+  std::vector<int8_t> Wst;   // -1 not computed, else con2pri status
+  std::vector<R> Wh;         // W* [5][Ncells]
+  std::vector<int8_t> Whst;  // -1 not computed, else status (1 = unphysical)
+  int ncell() const { return N[0] * N[1] * N[2]; }
+  int idx(int i, int j, int k) const {
+    return ((k + g[2]) * N[1] + (j + g[1])) * N[0] + (i + g[0]);
+  }
+};
+
+template <class R> int vl_prim_n(VlBlock<R>& B, int c, R W[5]) {
+  const int nc = B.ncell();
+  if (B.Wst[c] < 0) {
+    R U[5], Wc[5];
+    for (int v = 0; v < 5; ++v) U[v] = B.in[(size_t)v * nc + c];
+    B.Wst[c] = (int8_t)con2pri(U, Wc, (R*)nullptr, (Con2PriInfo*)nullptr, B.ori);
+    for (int v = 0; v < 5; ++v) B.W[(size_t)v * nc + c] = Wc[v];
+  }
+  for (int v = 0; v < 5; ++v) W[v] = B.W[(size_t)v * nc + c];
+  return B.Wst[c];
+}
+
+// Predicted primitive state W* of cell (i,j,k); returns 0 ok, 1 unphysical
+// predicted state, 2 unphysical input in its stencil.
+template <class R> int vl_half(VlBlock<R>& B, int i, int j, int k, R out[5]) {
+  const int nc = B.ncell();
+  const int c = B.idx(i, j, k);
+  if (B.Whst[c] < 0) {
+    R Wc[5], Uc[5];
+    int st = vl_prim_n(B, c, Wc);
+    for (int v = 0; v < 5; ++v) Uc[v] = B.in[(size_t)v * nc + c];
+    R div[5] = {R(0.0), R(0.0), R(0.0), R(0.0), R(0.0)};
+    for (int d = 0; d < 3 && st != UNPHYSICAL; ++d) {
+      if (!B.act[d]) continue;
+      int e[3] = {0, 0, 0};
+      e[d] = 1;
+      const int cm = B.idx(i - e[0], j - e[1], k - e[2]);
+      const int cp = B.idx(i + e[0], j + e[1], k + e[2]);
+      R Wm[5], Wp[5], Um[5], Up[5], Fm[5], Fp[5];
+      int sm = vl_prim_n(B, cm, Wm), sp = vl_prim_n(B, cp, Wp);
+      if (sm == UNPHYSICAL || sp == UNPHYSICAL) { st = UNPHYSICAL; break; }
+      for (int v = 0; v < 5; ++v) {
+        Um[v] = B.in[(size_t)v * nc + cm];
+        Up[v] = B.in[(size_t)v * nc + cp];
+      }
+      riemann_flux(d, B.riemann, Wm, Um, Wc, Uc, Fm, B.ori);
+      riemann_flux(d, B.riemann, Wc, Uc, Wp, Up, Fp, B.ori);
+      for (int v = 0; v < 5; ++v) div[v] = div[v] + (Fp[v] - Fm[v]);
+    }
+    if (st == UNPHYSICAL) {
+      B.Whst[c] = 2;
+    } else {
+      R half = R(0.5) * B.dt / B.dh;
+      R Uh[5], Wh[5];
+      for (int v = 0; v < 5; ++v) Uh[v] = Uc[v] - half * div[v];
+      int s2 = con2pri(Uh, Wh, (R*)nullptr, (Con2PriInfo*)nullptr, B.ori);
+      B.Whst[c] = (int8_t)(s2 == UNPHYSICAL ? 1 : 0);
+      for (int v = 0; v < 5; ++v) B.Wh[(size_t)v * nc + c] = Wh[v];
+    }
+  }
+  for (int v = 0; v < 5; ++v) out[v] = B.Wh[(size_t)v * nc + c];
+  return B.Whst[c];
+}
+
+template <class R>
+int advance_block_vl(const R* in, R* out, R* flux_out, const int n[3], const int act[3], R dt,
+                     R dh, const Params& P, int* retries_out) {
+  VlBlock<R> B;
+  for (int d = 0; d < 3; ++d) {
+    B.n[d] = n[d];
+    B.act[d] = act[d];
+    B.g[d] = act[d] ? 3 : 0;
+    B.N[d] = n[d] + 2 * B.g[d];
+  }
+  B.in = in;
+  B.ori = P.ori;
+  B.riemann = P.riemann;
+  B.dt = dt;
+  B.dh = dh;
+  const int nc = B.ncell();
+  B.W.assign((size_t)5 * nc, R(0.0));
+  B.Wst.assign(nc, -1);
+  B.Wh.assign((size_t)5 * nc, R(0.0));
+  B.Whst.assign(nc, -1);
+  const int nint = n[0] * n[1] * n[2];
+  int nf[3];
+  for (int d = 0; d < 3; ++d) nf[d] = act[d] ? (nint / n[d]) * (n[d] + 1) : 0;
+  std::vector<R> Fd[3];
+  for (int d = 0; d < 3; ++d) Fd[d].assign((size_t)5 * nf[d], R(0.0));
+  const double theta0 = P.theta;
+  double theta = theta0;
+  int attempt = 0;
+  int result = BLK_OK;
+  int predicted_bad = 0, badin = 0;
+  for (;;) {
+    int fail = 0;
+    for (int d = 0; d < 3 && !fail && !predicted_bad && !badin; ++d) {
+      if (!act[d]) continue;
+      int ext[3] = {n[0], n[1], n[2]};
+      ext[d] = n[d] + 1;
+      int e[3] = {0, 0, 0};
+      e[d] = 1;
+      for (int kk = 0; kk < ext[2] && !fail && !predicted_bad && !badin; ++kk)
+        for (int jj = 0; jj < ext[1] && !fail && !predicted_bad && !badin; ++jj)
+          for (int ii = 0; ii < ext[0]; ++ii) {
+            // face between cl = (ii,jj,kk) - e_d and cr = (ii,jj,kk)
+            const int il = ii - e[0], jl = jj - e[1], kl = kk - e[2];
+            R Wl[5], Wll[5], Wr[5], Wrr[5], Wlm[5], Wrp[5];
+            int s[4];
+            s[0] = vl_half(B, il - e[0], jl - e[1], kl - e[2], Wll);
+            s[1] = vl_half(B, il, jl, kl, Wl);
+            s[2] = vl_half(B, ii, jj, kk, Wr);
+            s[3] = vl_half(B, ii + e[0], jj + e[1], kk + e[2], Wrr);
+            if (s[0] == 2 || s[1] == 2 || s[2] == 2 || s[3] == 2) { badin = 1; break; }
+            if (s[0] || s[1] || s[2] || s[3]) { predicted_bad = 1; break; }
+            for (int v = 0; v < 5; ++v) {
+              R dWl = limited_slope(Wl[v] - Wll[v], Wr[v] - Wl[v], R(theta));
+              R dWr = limited_slope(Wr[v] - Wl[v], Wrr[v] - Wr[v], R(theta));
+              Wlm[v] = Wl[v] + R(0.5) * dWl;   // left state: + face of cl
+              Wrp[v] = Wr[v] - R(0.5) * dWr;   // right state: - face of cr
+            }
+            R UL[5], UR[5], F[5];
+            if (prim2con(Wlm, UL, B.ori) != OK || prim2con(Wrp, UR, B.ori) != OK) {
+              fail = 1;
+              break;
+            }
+            riemann_flux(d, P.riemann, Wlm, UL, Wrp, UR, F, B.ori);
+            const int fi = (kk * ext[1] + jj) * ext[0] + ii;
+            for (int v = 0; v < 5; ++v) Fd[d][(size_t)v * nf[d] + fi] = F[v];
+          }
+    }
+    if (badin) { result = BLK_BAD_INPUT; break; }
+    if (predicted_bad) { result = BLK_UNPHYSICAL; break; }
+    if (!fail) {
+      R coef = dt / dh;
+      for (int k = 0; k < n[2]; ++k)
+        for (int j = 0; j < n[1]; ++j)
+          for (int i = 0; i < n[0]; ++i) {
+            R div[5];
+            for (int v = 0; v < 5; ++v) div[v] = R(0.0);
+            for (int d = 0; d < 3; ++d) {
+              if (!act[d]) continue;
+              int ext[3] = {n[0], n[1], n[2]};
+              ext[d] = n[d] + 1;
+              int p0[3] = {i, j, k};
+              int p1[3] = {i, j, k};
+              p1[d] += 1;
+              int f0 = (p0[2] * ext[1] + p0[1]) * ext[0] + p0[0];
+              int f1 = (p1[2] * ext[1] + p1[1]) * ext[0] + p1[0];
+              for (int v = 0; v < 5; ++v)
+                div[v] = div[v] + (Fd[d][(size_t)v * nf[d] + f1] - Fd[d][(size_t)v * nf[d] + f0]);
+            }
+            const int c = B.idx(i, j, k);
+            const int o = (k * n[1] + j) * n[0] + i;
+            R Un[5];
+            for (int v = 0; v < 5; ++v) {
+              Un[v] = in[(size_t)v * nc + c] - coef * div[v];
+              out[(size_t)v * nint + o] = Un[v];
+            }
+            R m2;
+            R A = A_of_cons(Un, &m2, P.ori);
+            if (!(val(Un[0]) > 0.0) || !(val(A) > kEpsUnphysical)) fail = 1;
+          }
+    }
+    if (!fail) break;
+    if (theta == 0.0) { result = BLK_UNPHYSICAL; break; }
+    ++attempt;
+    theta = theta * P.retry_factor;
+    if (theta < P.theta_floor * theta0) theta = 0.0;
+  }
+  if (badin || predicted_bad)
+    for (size_t q = 0; q < (size_t)5 * nint; ++q) out[q] = R(NAN);
+  if (retries_out) *retries_out = attempt;
+  if (flux_out) {
+    size_t off = 0;
+    for (int d = 0; d < 3; ++d) {
+      for (size_t q = 0; q < (size_t)5 * nf[d]; ++q) flux_out[off + q] = Fd[d][q];
+      off += (size_t)5 * nf[d];
+    }
+  }
+  return result;
+}
+
+
+// ----------------------------------------------------------------------------
 // Exact solution of the 1-D relativistic Riemann problem with the TM EoS
 // (Appendix C). Double precision only; this is not on the hot path.
 // ----------------------------------------------------------------------------
@@ -1004,6 +1210,38 @@ void or_advance_patches(const double* in, double* out, int64_t npatch, const dou
     int st = advance_block(in + (size_t)p * 5 * 1728, out + (size_t)p * 5 * 512,
                            flux_out ? flux_out + (size_t)p * nflux : (double*)nullptr, n, act,
                            dt_dh[2 * p], dt_dh[2 * p + 1], P, &r);
+    if (status) status[p] = st;
+    if (retries) retries[p] = r;
+  }
+}
+
+// VL block step (3 ghost cells on active sides), arguments as or_advance_block.
+int or_advance_block_vl(const double* in, double* out, double* flux_out, int nx, int ny, int nz,
+                        int actx, int acty, int actz, double dt, double dh, double theta,
+                        double retry_factor, double theta_floor, int riemann, int32_t* retries,
+                        int scheme) {
+  int n[3] = {nx, ny, nz};
+  int act[3] = {actx, acty, actz};
+  Params P{theta, retry_factor, theta_floor, riemann, actx + acty + actz, 0.5, 0, scheme};
+  int r = 0;
+  int st = advance_block_vl(in, out, flux_out, n, act, dt, dh, P, &r);
+  if (retries) *retries = r;
+  return st;
+}
+
+// Batched VL advance of 8^3 patches with 3-cell ghosts, cons_in [np][5][14^3].
+void or_advance_patches_vl(const double* in, double* out, int64_t npatch, const double* dt_dh,
+                           double theta, double retry_factor, double theta_floor, int riemann,
+                           int32_t* status, int32_t* retries, double* flux_out, int scheme) {
+  const int n[3] = {8, 8, 8};
+  const int act[3] = {1, 1, 1};
+  Params P{theta, retry_factor, theta_floor, riemann, 3, 0.5, 0, scheme};
+  const size_t nflux = (size_t)3 * 5 * 9 * 64;
+  for (int64_t p = 0; p < npatch; ++p) {
+    int r = 0;
+    int st = advance_block_vl(in + (size_t)p * 5 * 2744, out + (size_t)p * 5 * 512,
+                              flux_out ? flux_out + (size_t)p * nflux : (double*)nullptr, n, act,
+                              dt_dh[2 * p], dt_dh[2 * p + 1], P, &r);
     if (status) status[p] = st;
     if (retries) retries[p] = r;
   }
