@@ -170,7 +170,7 @@ def job_throughput(local_ms: float, units_per_rank: int, steps: int, device=None
 # ---------------------------------------------------------------------------
 # workload on the device
 # ---------------------------------------------------------------------------
-def build_workload(torch, srhd, ctx, prec, n=N_GRID):
+def build_workload(torch, srhd, ctx, prec, n=N_GRID, ghost=2):
     from paper_2012_11130_gb300 import workloads
     W = workloads.advection_prims(n)                       # float64 [5][n][n][n]
     Wd = torch.from_numpy(W).to("cuda")
@@ -182,7 +182,7 @@ def build_workload(torch, srhd, ctx, prec, n=N_GRID):
     dtype = torch.float64 if prec == "fp64" else torch.float32
     P = P.to(dtype).contiguous()
     del C
-    G = ctx.fill_ghosts_uniform(P, npx, npx, npx)
+    G = (ctx.fill_ghosts_uniform3 if ghost == 3 else ctx.fill_ghosts_uniform)(P, npx, npx, npx)
     del P
     npatch = G.shape[0]
     dh = 1.0 / n
@@ -190,14 +190,15 @@ def build_workload(torch, srhd, ctx, prec, n=N_GRID):
     return G, dt_dh
 
 
-def time_device(torch, ctx, G, dt_dh, steps, warmup, barrier, prec):
+def time_device(torch, ctx, G, dt_dh, steps, warmup, barrier, prec, vl=False):
     npatch = G.shape[0]
+    step = ctx.advance_patches_vl if vl else ctx.advance_patches
     out = torch.empty((npatch, 5, 8, 8, 8), dtype=G.dtype, device="cuda")
     dn = torch.empty(1, dtype=torch.float64, device="cuda")
     st = torch.empty(npatch, dtype=torch.int32, device="cuda")
     stream = torch.cuda.current_stream()
     for _ in range(warmup):
-        ctx.advance_patches(G, dt_dh, cons_out=out, dt_next=dn, patch_status=st, prec=prec)
+        step(G, dt_dh, cons_out=out, dt_next=dn, patch_status=st, prec=prec)
     torch.cuda.synchronize()
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
            for _ in range(steps)]
@@ -208,7 +209,7 @@ def time_device(torch, ctx, G, dt_dh, steps, warmup, barrier, prec):
     t0.record(stream)
     for e0, e1 in evs:
         e0.record(stream)
-        ctx.advance_patches(G, dt_dh, cons_out=out, dt_next=dn, patch_status=st, prec=prec)
+        step(G, dt_dh, cons_out=out, dt_next=dn, patch_status=st, prec=prec)
         e1.record(stream)
     t1.record(stream)
     torch.cuda.synchronize()
@@ -242,7 +243,7 @@ def time_e2e(torch, ctx, G, dt_dh, steps, warmup, prec):
     return secs, h2d, d2h
 
 
-def l1_one_period(torch, srhd, prec, n=64, params=None):
+def l1_one_period(torch, srhd, prec, n=64, params=None, vl=False):
     """L1 error of rho (Eq. relative L1 error) after one period of the
     diagonal wave at n^3, evolved on the GPU with the fused CFL (uniform p
     and velocity: the wave is translated exactly, whatever the EoS)."""
@@ -268,8 +269,12 @@ def l1_one_period(torch, srhd, prec, n=64, params=None):
         dt = min(dt, t_end - t)
         dd[:, 0] = dt
         dd[:, 1] = dh
-        G = ctx.fill_ghosts_uniform(U, npx, npx, npx)
-        ctx.advance_patches(G, dd, cons_out=out, dt_next=dn, prec=prec)
+        if vl:
+            G = ctx.fill_ghosts_uniform3(U, npx, npx, npx)
+            ctx.advance_patches_vl(G, dd, cons_out=out, dt_next=dn, prec=prec)
+        else:
+            G = ctx.fill_ghosts_uniform(U, npx, npx, npx)
+            ctx.advance_patches(G, dd, cons_out=out, dt_next=dn, prec=prec)
         U, out = out, U
         t += dt
         steps += 1
@@ -353,6 +358,27 @@ def bench_polytropic(torch, srhd, steps: int, warmup: int, precs=("mixed_cf", "f
             out["runs"][f"{prec}_{riemann}"] = r
             del G, dt_dh
             torch.cuda.empty_cache()
+    return out
+
+
+def bench_vl(torch, srhd, steps: int, warmup: int, precs=("mixed_cf", "fp64")):
+    """The 256^3 advection batch advanced with the VL integrator (14^3 tiles,
+    three ghost cells): cell updates/s of srhd_advance_patches_vl and the
+    one-period L1 of rho at 64^3."""
+    out = {"workload": "256^3 periodic advection (as the headline), VL integrator, "
+                       "32768 patches of 8^3 + 3 ghost cells", "runs": {}}
+    for prec in precs:
+        ctx = srhd.Context(srhd.Params())
+        G, dt_dh = build_workload(torch, srhd, ctx, prec, ghost=3)
+        total_ms, per, dt_next, smax = time_device(torch, ctx, G, dt_dh, steps, warmup,
+                                                   lambda: None, prec, vl=True)
+        cells = G.shape[0] * CELLS_PER_PATCH
+        r = {"value": cells * steps / (total_ms * 1e-3), "unit": UNIT,
+             "ms_per_step": total_ms / steps, "patch_status_max": smax}
+        r["l1_rho_64"], _ = l1_one_period(torch, srhd, prec, vl=True)
+        out["runs"][prec] = r
+        del G, dt_dh
+        torch.cuda.empty_cache()
     return out
 
 
@@ -702,6 +728,11 @@ def run_ours(args):
         poly_res = bench_polytropic(torch, srhd, max(3, args.steps // 2), 3,
                                     precs=tuple(q for q in ("mixed_cf", "fp64") if q in precs))
 
+    vl_res = None
+    if not args.no_vl and args.grid == N_GRID and rank == 0:
+        vl_res = bench_vl(torch, srhd, max(3, args.steps // 2), 3,
+                          precs=tuple(q for q in ("mixed_cf", "fp64") if q in precs))
+
     jet_res = None
     if not args.no_jet and args.grid == N_GRID and rank == 0:
         vs = {q: results[q]["autotune"]["chosen_variant"] for q in precs
@@ -776,6 +807,7 @@ def run_ours(args):
         "amr_blast": amr_res,
         "amr_jet": jet_res,
         "polytropic": poly_res,
+        "vl": vl_res,
         "kernel_sources_sha": sha,
     }
     print(json.dumps(line))
@@ -797,6 +829,7 @@ def main():
     ap.add_argument("--no-amr", action="store_true")
     ap.add_argument("--no-jet", action="store_true", help="skip the AMR jet (configuration 5)")
     ap.add_argument("--no-poly", action="store_true", help="skip the polytropic-EoS workload")
+    ap.add_argument("--no-vl", action="store_true", help="skip the VL-integrator workload")
     ap.add_argument("--jet-steps", type=int, default=100, help="coarse steps of each jet run")
     ap.add_argument("--jet-gammas", default="10,20,50,100",
                     help="comma-separated beam Lorentz factors of the jet runs")

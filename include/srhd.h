@@ -205,6 +205,24 @@ srhd_status srhd_advance_patches(srhd_ctx* ctx, srhd_prec prec, const void* cons
                                  const double* dt_dh, const int32_t* worklist, double* dt_next,
                                  int32_t* patch_status, void* stream);
 
+/* One VL step (the predictor-corrector integrator GAMER-SR offers beside
+ * MUSCL-Hancock, Section 3.1) of a batch of independent patches with THREE
+ * ghost cells per side: a first-order unsplit predictor to the half step
+ * (Riemann fluxes between the piecewise-constant cell states), con2pri of
+ * the predicted state, then PLM reconstruction of it (no Hancock step),
+ * conserved face states, Riemann flux and the conservative update, with the
+ * Eq. (Unphysical result) check and the limiter retry of the corrector
+ * (Section 3.3) and the optional CFL bound, as srhd_advance_patches. An
+ * unphysical predicted state marks the patch SRHD_PATCH_UNPHYSICAL and its
+ * output NaN (the predictor does not depend on the limiter).
+ *   cons_ghosted [npatch][5][14^3] input (8^3 interior, 3 ghost cells per
+ *   side, x fastest); every other argument as srhd_advance_patches (the
+ *   patch_variant parameter does not apply; eos and scheme do). */
+srhd_status srhd_advance_patches_vl(srhd_ctx* ctx, srhd_prec prec, const void* cons_ghosted,
+                                    void* cons_out, void* patch_face_flux, int32_t npatch,
+                                    const double* dt_dh, const int32_t* worklist,
+                                    double* dt_next, int32_t* patch_status, void* stream);
+
 /* CFL time step (Section 3.2) of a batch of interior patches:
  * dt_out = min over all cells of C_CFL dh / S_max (signal mode) or
  * C_CFL dh (light mode); NaN if some cell is unphysical.
@@ -288,6 +306,12 @@ srhd_status srhd_amr_flux_correct(srhd_ctx* ctx, srhd_prec prec, void* cur,
                                   const void* flux_coarse, const void* flux_fine0,
                                   const void* flux_fine1, const int32_t* faces, int32_t nrows,
                                   const double* dt_dh, int32_t ntotal, void* stream);
+
+/* srhd_fill_ghosts_uniform with three ghost cells per side: ghosted
+ * [np][5][14^3] for srhd_advance_patches_vl. */
+srhd_status srhd_fill_ghosts_uniform3(srhd_ctx* ctx, srhd_prec prec, const void* interior,
+                                      void* ghosted, int32_t npx, int32_t npy, int32_t npz,
+                                      const int32_t* bc, void* stream);
 
 /* CFL time step of a batch of interior patches, like srhd_cfl_dt, for
  * callers that cannot allocate device memory. (The paper has no counterpart:

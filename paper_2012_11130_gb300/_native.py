@@ -26,7 +26,8 @@ PATCH_UNPHYSICAL, PATCH_BAD_INPUT, PATCH_NOCONV = 1, 2, 4
 EXPORTS = ("srhd_default_params", "srhd_create", "srhd_destroy", "srhd_last_error",
            "srhd_prim2con", "srhd_con2pri", "srhd_flux_patches", "srhd_advance_patches",
            "srhd_cfl_dt", "srhd_fill_ghosts_uniform", "srhd_cfl_dt_noalloc",
-           "srhd_amr_fill_ghosts", "srhd_amr_restrict", "srhd_amr_flux_correct")
+           "srhd_amr_fill_ghosts", "srhd_amr_restrict", "srhd_amr_flux_correct",
+           "srhd_advance_patches_vl", "srhd_fill_ghosts_uniform3")
 SRHD_AMR_COARSE = 1 << 30
 
 
@@ -77,6 +78,10 @@ def load(path: str = LIB_PATH):
     L.srhd_cfl_dt.argtypes = [vp, ctypes.c_int, vp, i32, d, vp, vp]
     L.srhd_fill_ghosts_uniform.restype = st
     L.srhd_fill_ghosts_uniform.argtypes = [vp, ctypes.c_int, vp, vp, i32, i32, i32, i32p, vp]
+    L.srhd_advance_patches_vl.restype = st
+    L.srhd_advance_patches_vl.argtypes = L.srhd_advance_patches.argtypes
+    L.srhd_fill_ghosts_uniform3.restype = st
+    L.srhd_fill_ghosts_uniform3.argtypes = L.srhd_fill_ghosts_uniform.argtypes
     L.srhd_cfl_dt_noalloc.restype = st
     L.srhd_cfl_dt_noalloc.argtypes = [ctypes.c_int, vp, i32, d, ctypes.POINTER(Params), vp, vp]
     L.srhd_amr_fill_ghosts.restype = st

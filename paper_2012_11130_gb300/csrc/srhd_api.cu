@@ -49,6 +49,7 @@ struct srhd_ctx {
   int num_sms;
   int patch_grid[3][srhd::kPatchVariants];  // persistent grid per precision and variant
   int poly_grid[3];                         // persistent grid of the polytropic kernels
+  int vl_grid[3][2];                        // persistent grid of the VL kernels [prec][poly]
   int scratch_slots;      // capacity of the partial-minimum arrays
   double* partial_dt;     // scratch [scratch_slots]
   int32_t* partial_bad;   // scratch [scratch_slots]
@@ -205,6 +206,18 @@ srhd_status srhd_create(srhd_ctx** out, const srhd_params* p) {
     c->poly_grid[SRHD_FP64] = nsm * b64;
     c->poly_grid[SRHD_MIXED] = nsm * b32;
     c->poly_grid[SRHD_MIXED_CF] = nsm * bcf;
+    for (int poly = 0; poly < 2; ++poly) {
+      int v64 = srhd::Launch<srhd::PrecFP64>::vl_blocks_per_sm(poly);
+      int v32 = srhd::Launch<srhd::PrecMixed>::vl_blocks_per_sm(poly);
+      int vcf = srhd::Launch<srhd::PrecMixedCF>::vl_blocks_per_sm(poly);
+      if (v64 < 1 || v32 < 1 || vcf < 1) {
+        delete c;
+        return fail(SRHD_ERR_CUDA, "VL patch kernel does not fit on an SM");
+      }
+      c->vl_grid[SRHD_FP64][poly] = nsm * v64;
+      c->vl_grid[SRHD_MIXED][poly] = nsm * v32;
+      c->vl_grid[SRHD_MIXED_CF][poly] = nsm * vcf;
+    }
   }
   c->scratch_slots = nsm * 8;
   c->partial_dt = nullptr;
@@ -265,10 +278,11 @@ srhd_status srhd_con2pri(srhd_ctx* c, srhd_prec prec, const void* cons, void* pr
 }
 
 static srhd_status launch_patches(srhd_ctx* c, srhd_prec prec, srhd::PatchArgs& a,
-                                  double* dt_next, cudaStream_t s) {
+                                  double* dt_next, cudaStream_t s, bool vl = false) {
   const int variant = c->params.patch_variant;
   const int poly = c->params.eos == SRHD_EOS_POLYTROPIC ? 1 : 0;
-  int grid = poly ? c->poly_grid[prec] : c->patch_grid[prec][variant];
+  int grid = vl ? c->vl_grid[prec][poly]
+                : (poly ? c->poly_grid[prec] : c->patch_grid[prec][variant]);
   if (grid > a.npatch) grid = a.npatch;
   if (dt_next) {
     a.partial_dt = c->partial_dt;
@@ -276,7 +290,10 @@ static srhd_status launch_patches(srhd_ctx* c, srhd_prec prec, srhd::PatchArgs& 
   }
   cudaError_t e = cudaSuccess;
   if (a.npatch > 0) {
-    e = dispatch(prec, [&](auto L) { return decltype(L)::patches(a, variant, poly, grid, s); });
+    e = dispatch(prec, [&](auto L) {
+      return vl ? decltype(L)::patches_vl(a, poly, grid, s)
+                : decltype(L)::patches(a, variant, poly, grid, s);
+    });
     if (e != cudaSuccess) return cuda_fail(e, "patch kernel launch");
   } else {
     grid = 0;
@@ -353,6 +370,31 @@ srhd_status srhd_advance_patches(srhd_ctx* c, srhd_prec prec, const void* cons_g
   return launch_patches(c, prec, a, dt_next, static_cast<cudaStream_t>(stream));
 }
 
+srhd_status srhd_advance_patches_vl(srhd_ctx* c, srhd_prec prec, const void* cons_ghosted,
+                                    void* cons_out, void* patch_face_flux, int32_t npatch,
+                                    const double* dt_dh, const int32_t* worklist,
+                                    double* dt_next, int32_t* patch_status, void* stream) {
+  srhd_status st = check_ctx(c);
+  if (st != SRHD_OK) return st;
+  if (!valid_prec(prec)) return fail(SRHD_ERR_ARG, "invalid precision %d", int(prec));
+  if (npatch < 0) return fail(SRHD_ERR_ARG, "npatch < 0");
+  if (npatch > 0 && (!cons_ghosted || !cons_out || !dt_dh))
+    return fail(SRHD_ERR_ARG, "cons_ghosted/cons_out/dt_dh is NULL");
+  if (npatch == 0 && !dt_next) return SRHD_OK;
+  srhd::PatchArgs a;
+  fill_common(c, prec, a);
+  a.in = cons_ghosted;
+  a.out = cons_out;
+  a.pflux = patch_face_flux;
+  a.face_flux = nullptr;
+  a.npatch = npatch;
+  a.dt_dh = dt_dh;
+  a.worklist = worklist;
+  a.status = patch_status;
+  a.flux_only = 0;
+  return launch_patches(c, prec, a, dt_next, static_cast<cudaStream_t>(stream), true);
+}
+
 srhd_status srhd_cfl_dt(srhd_ctx* c, srhd_prec prec, const void* cons, int32_t npatch, double dh,
                         double* dt_out, void* stream) {
   srhd_status st = check_ctx(c);
@@ -400,6 +442,26 @@ srhd_status srhd_fill_ghosts_uniform(srhd_ctx* c, srhd_prec prec, const void* in
     return decltype(L)::fill_ghosts(interior, ghosted, npx, npy, npz, bc, grid, s);
   });
   return e == cudaSuccess ? SRHD_OK : cuda_fail(e, "fill_ghosts launch");
+}
+
+srhd_status srhd_fill_ghosts_uniform3(srhd_ctx* c, srhd_prec prec, const void* interior,
+                                      void* ghosted, int32_t npx, int32_t npy, int32_t npz,
+                                      const int32_t* bc, void* stream) {
+  srhd_status st = check_ctx(c);
+  if (st != SRHD_OK) return st;
+  if (!valid_prec(prec)) return fail(SRHD_ERR_ARG, "invalid precision %d", int(prec));
+  if (npx < 1 || npy < 1 || npz < 1) return fail(SRHD_ERR_ARG, "patch counts must be >= 1");
+  if (!interior || !ghosted || !bc) return fail(SRHD_ERR_ARG, "interior/ghosted/bc is NULL");
+  for (int d = 0; d < 3; ++d)
+    if (bc[d] != SRHD_BC_PERIODIC && bc[d] != SRHD_BC_OUTFLOW)
+      return fail(SRHD_ERR_ARG, "bc[%d] must be SRHD_BC_PERIODIC or SRHD_BC_OUTFLOW", d);
+  int64_t total = (int64_t)npx * npy * npz * 5 * (14 * 14 * 14);  // 14^3 tiles
+  int grid = grid_for(c, total, 16);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t e = dispatch(prec, [&](auto L) {
+    return decltype(L)::fill_ghosts3(interior, ghosted, npx, npy, npz, bc, grid, s);
+  });
+  return e == cudaSuccess ? SRHD_OK : cuda_fail(e, "fill_ghosts3 launch");
 }
 
 // ---- AMR ---------------------------------------------------------------------

@@ -648,20 +648,23 @@ __global__ void __launch_bounds__(NT) cfl_kernel(const typename P::S* cons, int6
   }
 }
 
-// Ghost fill of a uniform grid of patches (periodic or outflow per axis).
-template <class S>
+// Ghost fill of a uniform grid of patches (periodic or outflow per axis),
+// GH ghost cells per side (2 for the MUSCL-Hancock tiles, 3 for VL).
+template <class S, int GH = 2>
 __global__ void fill_ghosts_kernel(const S* interior, S* ghosted, int npx, int npy, int npz,
                                    int bcx, int bcy, int bcz) {
+  constexpr int TE = kN + 2 * GH, TC = TE * TE * TE;
   const int64_t np = (int64_t)npx * npy * npz;
-  const int64_t total = np * 5 * kGC;
+  const int64_t total = np * 5 * TC;
   const int nx = npx * kN, ny = npy * kN, nz = npz * kN;
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total;
        q += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t p = q / (5 * kGC);
-    const int rem = int(q - p * 5 * kGC);
-    const int v = rem / kGC, c = rem - v * kGC;
+    const int64_t p = q / (5 * TC);
+    const int rem = int(q - p * 5 * TC);
+    const int v = rem / TC, c = rem - v * TC;
     const int px = int(p % npx), py = int((p / npx) % npy), pz = int(p / ((int64_t)npx * npy));
-    int x = px * kN + (c % kG) - 2, y = py * kN + ((c / kG) % kG) - 2, z = pz * kN + c / (kG * kG) - 2;
+    int x = px * kN + (c % TE) - GH, y = py * kN + ((c / TE) % TE) - GH;
+    int z = pz * kN + c / (TE * TE) - GH;
     auto wrap = [](int g, int n, int bc) {
       if (bc == 0) return ((g % n) + n) % n;
       return g < 0 ? 0 : (g >= n ? n - 1 : g);
@@ -701,6 +704,11 @@ template <class P> struct Launch {
   static cudaError_t cfl(const void* cons, int64_t ncell, double dh, double cfl, int ndim, int mode,
                          int maxit, int ori, EosArg eos, double* partial, int32_t* bad, int grid,
                          cudaStream_t s);
+  // the VL integrator (srhd_vl.cuh) on 14^3 tiles
+  static cudaError_t patches_vl(const PatchArgs& a, int poly, int grid, cudaStream_t s);
+  static int vl_blocks_per_sm(int poly);
+  static cudaError_t fill_ghosts3(const void* interior, void* ghosted, int npx, int npy, int npz,
+                                  const int32_t* bc, int grid, cudaStream_t s);
   static cudaError_t fill_ghosts(const void* interior, void* ghosted, int npx, int npy, int npz,
                                  const int32_t* bc, int grid, cudaStream_t s);
 };

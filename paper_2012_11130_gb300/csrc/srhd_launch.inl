@@ -5,6 +5,7 @@
 #pragma once
 
 #include "srhd_kernels.cuh"
+#include "srhd_vl.cuh"
 
 namespace srhd {
 
@@ -34,6 +35,17 @@ template <class P> struct PolyKernel {
   static constexpr auto fn = patch_kernel<P, Cfg::nt, Cfg::minb, Cfg::pair, EosPoly>;
 };
 
+// The VL kernel: one configuration per storage type (its shared memory,
+// 227 KB double / 114 KB float, allows one / two CTAs per SM).
+template <class S> struct VlVariant;
+template <> struct VlVariant<double> { static constexpr int nt = 512, minb = 1; };
+template <> struct VlVariant<float> { static constexpr int nt = 384, minb = 2; };
+
+template <class P, class E> struct VlKernel {
+  using Cfg = VlVariant<typename P::S>;
+  static constexpr auto fn = vl_patch_kernel<P, Cfg::nt, Cfg::minb, E>;
+};
+
 template <class P, int V> struct PatchKernel {
   using S = typename P::S;
   using Cfg = PatchVariant<S, V>;
@@ -53,7 +65,45 @@ template <class P> cudaError_t Launch<P>::setup() {
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(PolyKernel<P>::fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              int(SmemLayout<typename P::S>::bytes));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(VlKernel<P, EosTM>::fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             int(VlSmem<typename P::S>::bytes));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(VlKernel<P, EosPoly>::fn,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             int(VlSmem<typename P::S>::bytes));
   return e;
+}
+
+template <class P> int Launch<P>::vl_blocks_per_sm(int poly) {
+  int nb = 0;
+  cudaError_t e = poly ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                             &nb, VlKernel<P, EosPoly>::fn, VlKernel<P, EosPoly>::Cfg::nt,
+                             VlSmem<typename P::S>::bytes)
+                       : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                             &nb, VlKernel<P, EosTM>::fn, VlKernel<P, EosTM>::Cfg::nt,
+                             VlSmem<typename P::S>::bytes);
+  return e == cudaSuccess ? nb : 0;
+}
+
+template <class P>
+cudaError_t Launch<P>::patches_vl(const PatchArgs& a, int poly, int grid, cudaStream_t s) {
+  constexpr size_t smem = VlSmem<typename P::S>::bytes;
+  if (poly)
+    VlKernel<P, EosPoly>::fn<<<grid, VlKernel<P, EosPoly>::Cfg::nt, smem, s>>>(a);
+  else
+    VlKernel<P, EosTM>::fn<<<grid, VlKernel<P, EosTM>::Cfg::nt, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <class P>
+cudaError_t Launch<P>::fill_ghosts3(const void* interior, void* ghosted, int npx, int npy,
+                                    int npz, const int32_t* bc, int grid, cudaStream_t s) {
+  using S = typename P::S;
+  fill_ghosts_kernel<S, 3><<<grid, 256, 0, s>>>(static_cast<const S*>(interior),
+                                                static_cast<S*>(ghosted), npx, npy, npz, bc[0],
+                                                bc[1], bc[2]);
+  return cudaGetLastError();
 }
 
 template <class P> int Launch<P>::poly_blocks_per_sm() {

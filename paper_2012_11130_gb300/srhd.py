@@ -25,7 +25,8 @@ import torch
 from . import _native as N
 
 __all__ = ["Params", "Context", "prim2con", "con2pri", "flux_patches", "advance_patches",
-           "cfl_dt", "cfl_dt_noalloc", "fill_ghosts_uniform", "amr_fill_ghosts", "amr_restrict",
+           "cfl_dt", "cfl_dt_noalloc", "fill_ghosts_uniform", "fill_ghosts_uniform3",
+           "advance_patches_vl", "amr_fill_ghosts", "amr_restrict",
            "amr_flux_correct", "default_context"]
 
 
@@ -276,6 +277,46 @@ class Context:
                                                  _stream(stream)), "srhd_fill_ghosts_uniform")
         return ghosted
 
+    # ---- VL integrator (include/srhd.h: srhd_advance_patches_vl) ---------------
+    def advance_patches_vl(self, cons_ghosted, dt_dh, cons_out=None, patch_face_flux=None,
+                           worklist=None, dt_next=None, patch_status=None, npatch=None,
+                           stream=None, prec=None):
+        """One VL step of device patches with three ghost cells,
+        [npatch][5][14][14][14] -> [npatch][5][8][8][8]."""
+        _need_cuda(cons_ghosted, "cons_ghosted")
+        if npatch is None:
+            npatch = worklist.numel() if worklist is not None else cons_ghosted.shape[0]
+        if cons_out is None:
+            cons_out = torch.empty((cons_ghosted.shape[0], 5, 8, 8, 8), dtype=cons_ghosted.dtype,
+                                   device=cons_ghosted.device)
+        _need_cuda(cons_out, "cons_out", cons_ghosted.dtype)
+        _need_cuda(dt_dh, "dt_dh", torch.float64)
+        for name, t, dt in (("patch_face_flux", patch_face_flux, cons_ghosted.dtype),
+                            ("worklist", worklist, torch.int32), ("dt_next", dt_next, torch.float64),
+                            ("patch_status", patch_status, torch.int32)):
+            if t is not None:
+                _need_cuda(t, name, dt)
+        N.check(self._L.srhd_advance_patches_vl(
+            self._h, _prec(cons_ghosted, prec), _ptr(cons_ghosted), _ptr(cons_out),
+            _ptr(patch_face_flux), npatch, _ptr(dt_dh), _ptr(worklist), _ptr(dt_next),
+            _ptr(patch_status), _stream(stream)), "srhd_advance_patches_vl")
+        return cons_out
+
+    def fill_ghosts_uniform3(self, interior, npx, npy, npz, bc=("periodic",) * 3, ghosted=None,
+                             stream=None):
+        """Uniform-grid ghost fill with three ghost cells ([np][5][14^3])."""
+        _need_cuda(interior, "interior")
+        if ghosted is None:
+            ghosted = torch.empty((interior.shape[0], 5, 14, 14, 14), dtype=interior.dtype,
+                                  device=interior.device)
+        _need_cuda(ghosted, "ghosted", interior.dtype)
+        code = {"periodic": N.SRHD_BC_PERIODIC, "outflow": N.SRHD_BC_OUTFLOW}
+        bcs = (ctypes.c_int32 * 3)(*[code[b] for b in bc])
+        N.check(self._L.srhd_fill_ghosts_uniform3(self._h, _prec(interior), _ptr(interior),
+                                                  _ptr(ghosted), npx, npy, npz, bcs,
+                                                  _stream(stream)), "srhd_fill_ghosts_uniform3")
+        return ghosted
+
     # ---- AMR (include/srhd.h: srhd_amr_*) -------------------------------------
     def amr_fill_ghosts(self, cur, prev, ghosted, amr_map, p0, n, w=0.0, special=None,
                         stream=None, prec=None):
@@ -386,3 +427,12 @@ def amr_flux_correct(cur, flux_coarse, flux_fine0, flux_fine1, faces, dt_dh, str
                      prec=None):
     return default_context().amr_flux_correct(cur, flux_coarse, flux_fine0, flux_fine1, faces,
                                               dt_dh, stream, prec)
+
+
+def advance_patches_vl(cons_ghosted, dt_dh, **kw):
+    return default_context().advance_patches_vl(cons_ghosted, dt_dh, **kw)
+
+
+def fill_ghosts_uniform3(interior, npx, npy, npz, bc=("periodic",) * 3, ghosted=None,
+                         stream=None):
+    return default_context().fill_ghosts_uniform3(interior, npx, npy, npz, bc, ghosted, stream)

@@ -103,8 +103,9 @@ def advection_ghosted_patch_prims(n: int, patches, amp: float = 0.5,
 
 
 def rough_patch_prims(npatch: int, seed: int = 0, spread: float = 1.0,
-                      lg_gamma_max: float = 1.5) -> np.ndarray:
-    """[np][5][12][12][12] uncorrelated ghosted patches."""
+                      lg_gamma_max: float = 1.5, edge: int = GP) -> np.ndarray:
+    """[np][5][edge]^3 uncorrelated ghosted patches (edge 12, or 14 for VL)."""
+    GP = edge  # noqa: N806
     rng = np.random.default_rng(seed)
     n = npatch * GP ** 3
     rho = 10.0 ** rng.uniform(-spread, spread, n)
@@ -118,8 +119,10 @@ def rough_patch_prims(npatch: int, seed: int = 0, spread: float = 1.0,
 
 
 def smooth_patch_prims(npatch: int, seed: int = 0, amp: float = 0.3,
-                       Umax: float = 0.5) -> np.ndarray:
-    """[np][5][12][12][12] patches of smooth random waves (no retry expected)."""
+                       Umax: float = 0.5, edge: int = GP) -> np.ndarray:
+    """[np][5][edge]^3 patches of smooth random waves (no retry expected;
+    edge 12, or 14 for the VL integrator's three ghost cells)."""
+    GP = edge  # noqa: N806
     rng = np.random.default_rng(seed)
     c = np.arange(GP) / GP
     z, y, x = np.meshgrid(c, c, c, indexing="ij")
