@@ -23,9 +23,11 @@
  * Ownership and execution
  *   Every data pointer is a caller-owned DEVICE pointer on the context's
  *   device unless stated otherwise. The library allocates device memory only
- *   in srhd_create (the context's scratch) and frees it in srhd_destroy.
+ *   in srhd_create (the context's scratch) and in srhd_advance_uniform_host
+ *   (its stage), and frees it in srhd_destroy.
  *   Calls are asynchronous on the given stream (a cudaStream_t passed as
- *   void*, NULL = legacy default stream) and never synchronise the device.
+ *   void*, NULL = legacy default stream) and never synchronise the device;
+ *   srhd_advance_uniform_host alone waits, for its own work only.
  *   A context must not be used by two streams at once: its scratch is
  *   shared by the calls that use it (srhd_advance_patches with dt_next,
  *   srhd_cfl_dt).
@@ -205,6 +207,23 @@ srhd_status srhd_advance_patches(srhd_ctx* ctx, srhd_prec prec, const void* cons
                                  const double* dt_dh, const int32_t* worklist, double* dt_next,
                                  int32_t* patch_status, void* stream);
 
+/* srhd_advance_patches on patches p0 .. p0+n-1 of a uniform grid resident on
+ * the device, tiled as in srhd_fill_ghosts_uniform, without a ghosted copy:
+ * the kernel reads each patch's 12^3 tile (two ghost cells, periodic or
+ * outflow per axis) from the patch and its neighbours in `interior` while
+ * it loads the tile (the same values srhd_fill_ghosts_uniform writes, so
+ * the results are identical to fill + srhd_advance_patches).
+ *   interior [npx*npy*npz][5][8^3]; bc[3] host srhd_bc of x, y, z;
+ *   0 <= p0, n >= 0, p0 + n <= npx*npy*npz;
+ *   cons_out [n][5][8^3] (row i: patch p0+i) must not overlap interior;
+ *   patch_face_flux (nullable) [n][6][5][64], dt_dh [n][2], patch_status
+ *   (nullable) [n] and dt_next (nullable) as srhd_advance_patches. */
+srhd_status srhd_advance_uniform(srhd_ctx* ctx, srhd_prec prec, const void* interior,
+                                 int32_t npx, int32_t npy, int32_t npz, const int32_t* bc,
+                                 int32_t p0, int32_t n, void* cons_out, void* patch_face_flux,
+                                 const double* dt_dh, double* dt_next, int32_t* patch_status,
+                                 void* stream);
+
 /* One VL step (the predictor-corrector integrator GAMER-SR offers beside
  * MUSCL-Hancock, Section 3.1) of a batch of independent patches with THREE
  * ghost cells per side: a first-order unsplit predictor to the half step
@@ -307,11 +326,53 @@ srhd_status srhd_amr_flux_correct(srhd_ctx* ctx, srhd_prec prec, void* cur,
                                   const void* flux_fine1, const int32_t* faces, int32_t nrows,
                                   const double* dt_dh, int32_t ntotal, void* stream);
 
+/* srhd_fill_ghosts_uniform restricted to the patches p0 .. p0+n-1, so that a
+ * caller can fill and advance part of a grid while the rest is in transit:
+ * ghosted [n][5][12^3] receives patch p0+i in row i; interior [np][5][8^3]
+ * is the whole grid (read wherever the ghost zones reach);
+ * 0 <= p0, n >= 0, p0 + n <= npx*npy*npz. */
+srhd_status srhd_fill_ghosts_uniform_range(srhd_ctx* ctx, srhd_prec prec, const void* interior,
+                                           void* ghosted, int32_t npx, int32_t npy, int32_t npz,
+                                           const int32_t* bc, int32_t p0, int32_t n,
+                                           void* stream);
+
 /* srhd_fill_ghosts_uniform with three ghost cells per side: ghosted
  * [np][5][14^3] for srhd_advance_patches_vl. */
 srhd_status srhd_fill_ghosts_uniform3(srhd_ctx* ctx, srhd_prec prec, const void* interior,
                                       void* ghosted, int32_t npx, int32_t npy, int32_t npz,
                                       const int32_t* bc, void* stream);
+
+/* One MUSCL-Hancock step (the fused update of srhd_advance_patches, with
+ * the CFL bound of the result) of a uniform grid whose state lives in HOST
+ * memory, tiled as in srhd_fill_ghosts_uniform. Only interiors cross the
+ * host link: the grid is cut into chunks of whole z slabs of patches; the
+ * copies in, the step of each chunk (srhd_advance_uniform, which gathers
+ * the ghost zones from the copied slabs) and the copies out run on streams
+ * of the context (one for each copy direction, two for the chunks' steps,
+ * taken in turn), so the copies of one chunk overlap the step of another. (Not part of the paper's solver: the host-resident
+ * driver of a uniform-grid run.) The call is synchronous: it starts after
+ * the work already queued on `stream` and returns when the outputs are
+ * written; work queued on `stream` afterwards follows it.
+ *   host_in  [np][5][8^3] host array, the state at t^n (np = npx*npy*npz);
+ *   host_out [np][5][8^3] host array, the state at t^n + dt; it may be
+ *            host_in itself, otherwise it must not overlap it. Page-locked
+ *            (pinned) host memory lets the copies overlap; pageable memory
+ *            gives the same result, serialised;
+ *   bc[3]: srhd_bc of x, y, z; dt >= 0 and dh > 0 for every patch;
+ *   dt_next (nullable, HOST double): min over all cells of C_CFL dh / S_max
+ *            of the result, NaN if some updated cell is unphysical;
+ *   patch_status (nullable) [np] HOST int32, see SRHD_PATCH_*;
+ *   chunks in [1, 64]: chunk k holds slabs npz*k/K .. npz*(k+1)/K - 1,
+ *            K = min(chunks, npz); one slab per chunk overlaps best.
+ * Device memory: the first call allocates the stage (two interior copies of
+ * the grid, per-patch scratch) and keeps it
+ * in the context for later calls; a larger grid or a wider storage type
+ * reallocates it. On an error the call waits for its queued work and
+ * returns the status; host_out is then undefined. */
+srhd_status srhd_advance_uniform_host(srhd_ctx* ctx, srhd_prec prec, const void* host_in,
+                                      void* host_out, int32_t npx, int32_t npy, int32_t npz,
+                                      const int32_t* bc, double dt, double dh, double* dt_next,
+                                      int32_t* patch_status, int32_t chunks, void* stream);
 
 /* CFL time step of a batch of interior patches, like srhd_cfl_dt, for
  * callers that cannot allocate device memory. (The paper has no counterpart:

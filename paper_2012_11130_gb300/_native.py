@@ -27,7 +27,9 @@ EXPORTS = ("srhd_default_params", "srhd_create", "srhd_destroy", "srhd_last_erro
            "srhd_prim2con", "srhd_con2pri", "srhd_flux_patches", "srhd_advance_patches",
            "srhd_cfl_dt", "srhd_fill_ghosts_uniform", "srhd_cfl_dt_noalloc",
            "srhd_amr_fill_ghosts", "srhd_amr_restrict", "srhd_amr_flux_correct",
-           "srhd_advance_patches_vl", "srhd_fill_ghosts_uniform3")
+           "srhd_advance_patches_vl", "srhd_fill_ghosts_uniform3",
+           "srhd_fill_ghosts_uniform_range", "srhd_advance_uniform_host",
+           "srhd_advance_uniform")
 SRHD_AMR_COARSE = 1 << 30
 
 
@@ -80,6 +82,16 @@ def load(path: str = LIB_PATH):
     L.srhd_fill_ghosts_uniform.argtypes = [vp, ctypes.c_int, vp, vp, i32, i32, i32, i32p, vp]
     L.srhd_advance_patches_vl.restype = st
     L.srhd_advance_patches_vl.argtypes = L.srhd_advance_patches.argtypes
+    L.srhd_fill_ghosts_uniform_range.restype = st
+    L.srhd_fill_ghosts_uniform_range.argtypes = [vp, ctypes.c_int, vp, vp, i32, i32, i32, i32p,
+                                                 i32, i32, vp]
+    L.srhd_advance_uniform.restype = st
+    L.srhd_advance_uniform.argtypes = [vp, ctypes.c_int, vp, i32, i32, i32, i32p, i32, i32, vp,
+                                       vp, vp, vp, vp, vp]
+    L.srhd_advance_uniform_host.restype = st
+    L.srhd_advance_uniform_host.argtypes = [vp, ctypes.c_int, vp, vp, i32, i32, i32, i32p,
+                                            ctypes.c_double, ctypes.c_double,
+                                            ctypes.POINTER(ctypes.c_double), i32p, i32, vp]
     L.srhd_fill_ghosts_uniform3.restype = st
     L.srhd_fill_ghosts_uniform3.argtypes = L.srhd_fill_ghosts_uniform.argtypes
     L.srhd_cfl_dt_noalloc.restype = st

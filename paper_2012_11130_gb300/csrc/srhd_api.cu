@@ -1,5 +1,6 @@
 // C ABI of libsrhd (declared in include/srhd.h): context management,
 // argument validation and launches. Device work is in srhd_kernels.cuh.
+#include <algorithm>
 #include <cfloat>
 #include <cmath>
 #include <cstdarg>
@@ -41,7 +42,76 @@ __global__ void cfl_finalize_kernel(const double* partial, const int32_t* bad, i
     dt_out[0] = mm;
   }
 }
+
+// (dt, dh) of every patch of a uniform step.
+__global__ void set_dt_dh_kernel(double* dt_dh, int64_t n, double dt, double dh) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    dt_dh[2 * i] = dt;
+    dt_dh[2 * i + 1] = dh;
+  }
+}
+
+// Minimum of n per-chunk CFL bounds: NaN if one is NaN (an unphysical cell).
+__global__ void min_dt_kernel(const double* v, int n, double* out) {
+  double m = __longlong_as_double(0x7ff0000000000000ULL);
+  bool bad = false;
+  for (int i = 0; i < n; ++i) {
+    bad |= isnan(v[i]);
+    m = fmin(m, v[i]);
+  }
+  out[0] = bad ? __longlong_as_double(0x7ff8000000000000ULL) : m;
+}
 }  // namespace srhd
+
+// Device buffers, streams and events of srhd_advance_uniform_host: made on
+// its first call, grown when a larger grid or a wider storage type arrives,
+// freed by srhd_destroy.
+struct UniformStage {
+  static constexpr int kMaxChunks = 64;
+  int64_t cap_cells = 0;  // bytes of in and of out
+  int64_t cap_patches = 0;
+  void* in = nullptr;       // interior state at t^n, [np][5][8^3]
+  void* out = nullptr;      // interior state at t^n+1
+  double* dt_dh = nullptr;  // [np][2]
+  int32_t* status = nullptr;
+  double* dn = nullptr;       // per-chunk CFL bounds, then their minimum
+  double* host_dn = nullptr;  // pinned copy of the minimum
+  double* part_dt = nullptr;  // CFL partial minima of the two compute streams, [2][slots]
+  int32_t* part_bad = nullptr;
+  // host-to-device, two compute streams (even and odd chunks), device-to-host
+  cudaStream_t s[4] = {};
+  cudaEvent_t copied[kMaxChunks] = {}, stepped[kMaxChunks] = {}, start = nullptr,
+              fin = nullptr;
+  bool have_streams = false;
+
+  void free_buffers() {
+    cudaFree(in);
+    cudaFree(out);
+    cudaFree(dt_dh);
+    cudaFree(status);
+    in = out = nullptr;
+    dt_dh = nullptr;
+    status = nullptr;
+    cap_cells = cap_patches = 0;
+  }
+  ~UniformStage() {
+    free_buffers();
+    cudaFree(dn);
+    cudaFree(part_dt);
+    cudaFree(part_bad);
+    cudaFreeHost(host_dn);
+    if (have_streams) {
+      for (auto& x : s) cudaStreamDestroy(x);
+      for (int k = 0; k < kMaxChunks; ++k) {
+        cudaEventDestroy(copied[k]);
+        cudaEventDestroy(stepped[k]);
+      }
+      cudaEventDestroy(start);
+      cudaEventDestroy(fin);
+    }
+  }
+};
 
 struct srhd_ctx {
   srhd_params params;
@@ -53,6 +123,7 @@ struct srhd_ctx {
   int scratch_slots;      // capacity of the partial-minimum arrays
   double* partial_dt;     // scratch [scratch_slots]
   int32_t* partial_bad;   // scratch [scratch_slots]
+  UniformStage* uniform;  // srhd_advance_uniform_host's state (NULL until its first call)
 };
 
 namespace {
@@ -91,6 +162,12 @@ int grid_for(const srhd_ctx* c, int64_t n, int per_sm) {
   int64_t g = (n + 255) / 256;
   int64_t cap = (int64_t)c->num_sms * per_sm;
   if (g > cap) g = cap;
+  return g < 1 ? 1 : int(g);
+}
+
+// Blocks of the ghost fill: one per patch, at most eight per SM (grid-stride).
+int ghost_grid(const srhd_ctx* c, int64_t npatch) {
+  int64_t g = std::min<int64_t>(npatch, (int64_t)c->num_sms * 8);
   return g < 1 ? 1 : int(g);
 }
 
@@ -220,6 +297,7 @@ srhd_status srhd_create(srhd_ctx** out, const srhd_params* p) {
     }
   }
   c->scratch_slots = nsm * 8;
+  c->uniform = nullptr;
   c->partial_dt = nullptr;
   c->partial_bad = nullptr;
   e = cudaMalloc(&c->partial_dt, sizeof(double) * c->scratch_slots);
@@ -238,6 +316,7 @@ srhd_status srhd_destroy(srhd_ctx* c) {
   if (!c) return SRHD_OK;
   cudaFree(c->partial_dt);
   cudaFree(c->partial_bad);
+  delete c->uniform;
   delete c;
   return SRHD_OK;
 }
@@ -278,15 +357,20 @@ srhd_status srhd_con2pri(srhd_ctx* c, srhd_prec prec, const void* cons, void* pr
 }
 
 static srhd_status launch_patches(srhd_ctx* c, srhd_prec prec, srhd::PatchArgs& a,
-                                  double* dt_next, cudaStream_t s, bool vl = false) {
+                                  double* dt_next, cudaStream_t s, bool vl = false,
+                                  double* scratch_dt = nullptr, int32_t* scratch_bad = nullptr) {
+  if (!scratch_dt) {
+    scratch_dt = c->partial_dt;
+    scratch_bad = c->partial_bad;
+  }
   const int variant = c->params.patch_variant;
   const int poly = c->params.eos == SRHD_EOS_POLYTROPIC ? 1 : 0;
   int grid = vl ? c->vl_grid[prec][poly]
                 : (poly ? c->poly_grid[prec] : c->patch_grid[prec][variant]);
   if (grid > a.npatch) grid = a.npatch;
   if (dt_next) {
-    a.partial_dt = c->partial_dt;
-    a.partial_bad = c->partial_bad;
+    a.partial_dt = scratch_dt;
+    a.partial_bad = scratch_bad;
   }
   cudaError_t e = cudaSuccess;
   if (a.npatch > 0) {
@@ -299,7 +383,7 @@ static srhd_status launch_patches(srhd_ctx* c, srhd_prec prec, srhd::PatchArgs& 
     grid = 0;
   }
   if (dt_next) {
-    srhd::cfl_finalize_kernel<<<1, 256, 0, s>>>(c->partial_dt, c->partial_bad, grid, dt_next);
+    srhd::cfl_finalize_kernel<<<1, 256, 0, s>>>(scratch_dt, scratch_bad, grid, dt_next);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "cfl finalize launch");
   }
@@ -319,6 +403,10 @@ static void fill_common(const srhd_ctx* c, srhd_prec prec, srhd::PatchArgs& a) {
   a.ori = c->params.scheme == SRHD_SCHEME_TOTAL ? 1 : 0;
   a.partial_dt = nullptr;
   a.partial_bad = nullptr;
+  a.gather = 0;
+  a.gnx = a.gny = a.gnz = 1;
+  a.gbcx = a.gbcy = a.gbcz = 0;
+  a.gp0 = 0;
 }
 
 srhd_status srhd_flux_patches(srhd_ctx* c, srhd_prec prec, const void* cons_ghosted,
@@ -367,6 +455,61 @@ srhd_status srhd_advance_patches(srhd_ctx* c, srhd_prec prec, const void* cons_g
   a.worklist = worklist;
   a.status = patch_status;
   a.flux_only = 0;
+  return launch_patches(c, prec, a, dt_next, static_cast<cudaStream_t>(stream));
+}
+
+static srhd_status check_bc(const int32_t* bc) {
+  if (!bc) return fail(SRHD_ERR_ARG, "bc is NULL");
+  for (int d = 0; d < 3; ++d)
+    if (bc[d] != SRHD_BC_PERIODIC && bc[d] != SRHD_BC_OUTFLOW)
+      return fail(SRHD_ERR_ARG, "bc[%d] must be SRHD_BC_PERIODIC or SRHD_BC_OUTFLOW", d);
+  return SRHD_OK;
+}
+
+// The fused step of srhd_advance_patches on patches p0 .. p0+n-1 of a uniform
+// grid, reading each 12^3 tile from the grid (gather mode of patch_kernel).
+static void gather_args(const srhd_ctx* c, srhd_prec prec, srhd::PatchArgs& a,
+                        const void* interior, int32_t npx, int32_t npy, int32_t npz,
+                        const int32_t* bc, int64_t p0) {
+  fill_common(c, prec, a);
+  a.in = interior;
+  a.gather = 1;
+  a.gnx = npx;
+  a.gny = npy;
+  a.gnz = npz;
+  a.gbcx = bc[0];
+  a.gbcy = bc[1];
+  a.gbcz = bc[2];
+  a.gp0 = p0;
+  a.face_flux = nullptr;
+  a.worklist = nullptr;
+  a.flux_only = 0;
+}
+
+srhd_status srhd_advance_uniform(srhd_ctx* c, srhd_prec prec, const void* interior, int32_t npx,
+                                 int32_t npy, int32_t npz, const int32_t* bc, int32_t p0,
+                                 int32_t n, void* cons_out, void* patch_face_flux,
+                                 const double* dt_dh, double* dt_next, int32_t* patch_status,
+                                 void* stream) {
+  srhd_status st = check_ctx(c);
+  if (st != SRHD_OK) return st;
+  if (!valid_prec(prec)) return fail(SRHD_ERR_ARG, "invalid precision %d", int(prec));
+  if (npx < 1 || npy < 1 || npz < 1) return fail(SRHD_ERR_ARG, "patch counts must be >= 1");
+  const int64_t np = (int64_t)npx * npy * npz;
+  if (np > INT32_MAX) return fail(SRHD_ERR_ARG, "more than 2^31-1 patches");
+  if (p0 < 0 || n < 0 || p0 + (int64_t)n > np)
+    return fail(SRHD_ERR_ARG, "patch range [%d, %d) outside the grid", p0, p0 + n);
+  if ((st = check_bc(bc)) != SRHD_OK) return st;
+  if (n > 0 && (!interior || !cons_out || !dt_dh))
+    return fail(SRHD_ERR_ARG, "interior/cons_out/dt_dh is NULL");
+  if (n == 0 && !dt_next) return SRHD_OK;
+  srhd::PatchArgs a;
+  gather_args(c, prec, a, interior, npx, npy, npz, bc, p0);
+  a.out = cons_out;
+  a.pflux = patch_face_flux;
+  a.npatch = n;
+  a.dt_dh = dt_dh;
+  a.status = patch_status;
   return launch_patches(c, prec, a, dt_next, static_cast<cudaStream_t>(stream));
 }
 
@@ -435,11 +578,34 @@ srhd_status srhd_fill_ghosts_uniform(srhd_ctx* c, srhd_prec prec, const void* in
   for (int d = 0; d < 3; ++d)
     if (bc[d] != SRHD_BC_PERIODIC && bc[d] != SRHD_BC_OUTFLOW)
       return fail(SRHD_ERR_ARG, "bc[%d] must be SRHD_BC_PERIODIC or SRHD_BC_OUTFLOW", d);
-  int64_t total = (int64_t)npx * npy * npz * 5 * srhd::kGC;
-  int grid = grid_for(c, total, 16);
+  const int64_t np = (int64_t)npx * npy * npz;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   cudaError_t e = dispatch(prec, [&](auto L) {
-    return decltype(L)::fill_ghosts(interior, ghosted, npx, npy, npz, bc, grid, s);
+    return decltype(L)::fill_ghosts(interior, ghosted, npx, npy, npz, bc, 2, 0, np,
+                                    ghost_grid(c, np), s);
+  });
+  return e == cudaSuccess ? SRHD_OK : cuda_fail(e, "fill_ghosts launch");
+}
+
+srhd_status srhd_fill_ghosts_uniform_range(srhd_ctx* c, srhd_prec prec, const void* interior,
+                                           void* ghosted, int32_t npx, int32_t npy, int32_t npz,
+                                           const int32_t* bc, int32_t p0, int32_t n, void* stream) {
+  srhd_status st = check_ctx(c);
+  if (st != SRHD_OK) return st;
+  if (!valid_prec(prec)) return fail(SRHD_ERR_ARG, "invalid precision %d", int(prec));
+  if (npx < 1 || npy < 1 || npz < 1) return fail(SRHD_ERR_ARG, "patch counts must be >= 1");
+  const int64_t np = (int64_t)npx * npy * npz;
+  if (p0 < 0 || n < 0 || p0 + (int64_t)n > np)
+    return fail(SRHD_ERR_ARG, "patch range [%d, %d) outside the grid", p0, p0 + n);
+  if (n == 0) return SRHD_OK;
+  if (!interior || !ghosted || !bc) return fail(SRHD_ERR_ARG, "interior/ghosted/bc is NULL");
+  for (int d = 0; d < 3; ++d)
+    if (bc[d] != SRHD_BC_PERIODIC && bc[d] != SRHD_BC_OUTFLOW)
+      return fail(SRHD_ERR_ARG, "bc[%d] must be SRHD_BC_PERIODIC or SRHD_BC_OUTFLOW", d);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t e = dispatch(prec, [&](auto L) {
+    return decltype(L)::fill_ghosts(interior, ghosted, npx, npy, npz, bc, 2, p0, n,
+                                    ghost_grid(c, n), s);
   });
   return e == cudaSuccess ? SRHD_OK : cuda_fail(e, "fill_ghosts launch");
 }
@@ -455,11 +621,11 @@ srhd_status srhd_fill_ghosts_uniform3(srhd_ctx* c, srhd_prec prec, const void* i
   for (int d = 0; d < 3; ++d)
     if (bc[d] != SRHD_BC_PERIODIC && bc[d] != SRHD_BC_OUTFLOW)
       return fail(SRHD_ERR_ARG, "bc[%d] must be SRHD_BC_PERIODIC or SRHD_BC_OUTFLOW", d);
-  int64_t total = (int64_t)npx * npy * npz * 5 * (14 * 14 * 14);  // 14^3 tiles
-  int grid = grid_for(c, total, 16);
+  const int64_t np = (int64_t)npx * npy * npz;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   cudaError_t e = dispatch(prec, [&](auto L) {
-    return decltype(L)::fill_ghosts3(interior, ghosted, npx, npy, npz, bc, grid, s);
+    return decltype(L)::fill_ghosts(interior, ghosted, npx, npy, npz, bc, 3, 0, np,
+                                    ghost_grid(c, np), s);
   });
   return e == cudaSuccess ? SRHD_OK : cuda_fail(e, "fill_ghosts3 launch");
 }
@@ -553,3 +719,191 @@ srhd_status srhd_amr_flux_correct(srhd_ctx* c, srhd_prec prec, void* cur, const 
 }
 
 }  // extern "C"
+
+// ---- uniform grid resident in host memory ----------------------------------
+namespace {
+
+// Makes the stage's streams and events and sizes its buffers for np patches,
+// esz bytes per value.
+srhd_status uniform_stage(srhd_ctx* c, int64_t np, int64_t esz) {
+  if (!c->uniform) {
+    c->uniform = new (std::nothrow) UniformStage;
+    if (!c->uniform) return fail(SRHD_ERR_ARG, "out of host memory");
+  }
+  UniformStage& u = *c->uniform;
+  cudaError_t e = cudaSuccess;
+  if (!u.have_streams) {
+    for (auto& x : u.s)
+      if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&x, cudaStreamNonBlocking);
+    for (int k = 0; k < UniformStage::kMaxChunks && e == cudaSuccess; ++k) {
+      e = cudaEventCreateWithFlags(&u.copied[k], cudaEventDisableTiming);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&u.stepped[k], cudaEventDisableTiming);
+    }
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&u.start, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&u.fin, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaMalloc(&u.dn, sizeof(double) * (UniformStage::kMaxChunks + 1));
+    if (e == cudaSuccess) e = cudaMalloc(&u.part_dt, sizeof(double) * 2 * c->scratch_slots);
+    if (e == cudaSuccess) e = cudaMalloc(&u.part_bad, sizeof(int32_t) * 2 * c->scratch_slots);
+    if (e == cudaSuccess) e = cudaMallocHost(&u.host_dn, sizeof(double));
+    if (e != cudaSuccess) {
+      // a partly made stage is destroyed whole and made again on the next call
+      u.have_streams = true;
+      delete c->uniform;
+      c->uniform = nullptr;
+      return cuda_fail(e, "uniform stage streams/events");
+    }
+    u.have_streams = true;
+  }
+  const int64_t cells = np * 5 * srhd::kNC * esz;
+  if (cells > u.cap_cells || np > u.cap_patches) {
+    u.free_buffers();
+    e = cudaMalloc(&u.in, cells);
+    if (e == cudaSuccess) e = cudaMalloc(&u.out, cells);
+    if (e == cudaSuccess) e = cudaMalloc(&u.dt_dh, sizeof(double) * 2 * np);
+    if (e == cudaSuccess) e = cudaMalloc(&u.status, sizeof(int32_t) * np);
+    if (e != cudaSuccess) {
+      u.free_buffers();
+      return cuda_fail(e, "cudaMalloc uniform stage");
+    }
+    u.cap_cells = cells;
+    u.cap_patches = np;
+  }
+  return SRHD_OK;
+}
+
+}  // namespace
+
+srhd_status srhd_advance_uniform_host(srhd_ctx* c, srhd_prec prec, const void* host_in,
+                                      void* host_out, int32_t npx, int32_t npy, int32_t npz,
+                                      const int32_t* bc, double dt, double dh, double* dt_next,
+                                      int32_t* patch_status, int32_t chunks, void* stream) {
+  srhd_status st = check_ctx(c);
+  if (st != SRHD_OK) return st;
+  if (!valid_prec(prec)) return fail(SRHD_ERR_ARG, "invalid precision %d", int(prec));
+  if (npx < 1 || npy < 1 || npz < 1) return fail(SRHD_ERR_ARG, "patch counts must be >= 1");
+  const int64_t np = (int64_t)npx * npy * npz;
+  if (np > INT32_MAX) return fail(SRHD_ERR_ARG, "more than 2^31-1 patches");
+  if (!host_in || !host_out) return fail(SRHD_ERR_ARG, "host_in/host_out is NULL");
+  if ((st = check_bc(bc)) != SRHD_OK) return st;
+  if (!(dt >= 0.0) || !std::isfinite(dt)) return fail(SRHD_ERR_ARG, "dt must be finite and >= 0");
+  if (!(dh > 0.0) || !std::isfinite(dh)) return fail(SRHD_ERR_ARG, "dh must be positive");
+  if (chunks < 1 || chunks > UniformStage::kMaxChunks)
+    return fail(SRHD_ERR_ARG, "chunks must be in [1, %d]", UniformStage::kMaxChunks);
+  // chunk k holds the z slabs z0[k] .. z0[k+1]-1 (a slab is npx*npy patches)
+  const int K = chunks < npz ? chunks : npz;
+  const int64_t slab = (int64_t)npx * npy;
+  int z0[UniformStage::kMaxChunks + 1];
+  for (int k = 0; k <= K; ++k) z0[k] = int((int64_t)npz * k / K);
+  const int64_t esz = prec == SRHD_FP64 ? 8 : 4;
+  const int64_t pbytes = 5 * srhd::kNC * esz;
+  st = uniform_stage(c, np, esz);
+  if (st != SRHD_OK) return st;
+  UniformStage& u = *c->uniform;
+  cudaStream_t user = static_cast<cudaStream_t>(stream);
+  cudaStream_t h2d = u.s[0], d2h = u.s[3];
+  const char* what = "uniform step";
+  srhd::set_dt_dh_kernel<<<grid_for(c, np, 4), 256, 0, user>>>(u.dt_dh, np, dt, dh);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaEventRecord(u.start, user);
+  for (cudaStream_t x : u.s)
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(x, u.start, 0);
+  // Copies in: with periodic z the first chunk also needs the last one, so
+  // that is copied second.
+  int order[UniformStage::kMaxChunks];
+  const bool zper = bc[2] == SRHD_BC_PERIODIC;
+  for (int k = 0, n = 0; k < K; ++k) {
+    if (zper && K > 1 && k == 1) order[n++] = K - 1;
+    if (!(zper && K > 1 && k == K - 1)) order[n++] = k;
+  }
+  // The copies are enqueued in that order, each only when a chunk about to
+  // be enqueued needs it (one chunk ahead), so that the first step is queued
+  // without waiting for the host to queue every copy.
+  int ncopied = 0;
+  bool issued[UniformStage::kMaxChunks] = {};
+  auto issue_through = [&](int k) {
+    while (!issued[k] && e == cudaSuccess) {
+      const int j = order[ncopied++];
+      const int64_t a = z0[j] * slab, n = (z0[j + 1] - z0[j]) * slab;
+      e = cudaMemcpyAsync(static_cast<char*>(u.in) + a * pbytes,
+                          static_cast<const char*>(host_in) + a * pbytes, n * pbytes,
+                          cudaMemcpyHostToDevice, h2d);
+      if (e == cudaSuccess) e = cudaEventRecord(u.copied[j], h2d);
+      issued[j] = true;
+    }
+  };
+  auto chunk_of = [&](int z) {
+    int k = 0;
+    while (z >= z0[k + 1]) ++k;
+    return k;
+  };
+  // the chunks whose copies the step of chunk k reads (the ghost zones,
+  // two cells deep, reach one slab below and one above)
+  auto for_needed = [&](int k, auto&& f) {
+    for (int z = z0[k] - 1; z <= z0[k + 1]; ++z) {
+      int zz = z;
+      if (zz < 0 || zz >= npz) {
+        if (!zper) continue;
+        zz = (zz + npz) % npz;
+      }
+      f(chunk_of(zz));
+    }
+  };
+  // Chunk k steps on compute stream k % 2 with CFL scratch k % 2 (its tiles
+  // gathered from the grid copy), so that a launch's last partly filled wave
+  // overlaps the next chunk's launch.
+  for (int k = 0; k < K && e == cudaSuccess; ++k) {
+    const int par = k & 1;
+    cudaStream_t comp = u.s[1 + par];
+    for_needed(k, issue_through);
+    if (k + 1 < K) for_needed(k + 1, issue_through);
+    for_needed(k, [&](int j) {
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(comp, u.copied[j], 0);
+    });
+    if (e != cudaSuccess) break;
+    const int64_t a = z0[k] * slab, n = (z0[k + 1] - z0[k]) * slab;
+    srhd::PatchArgs pa;
+    gather_args(c, prec, pa, u.in, npx, npy, npz, bc, a);
+    pa.out = static_cast<char*>(u.out) + a * pbytes;
+    pa.pflux = nullptr;
+    pa.npatch = int32_t(n);
+    pa.dt_dh = u.dt_dh + 2 * a;
+    pa.status = u.status + a;
+    st = launch_patches(c, prec, pa, dt_next ? u.dn + k : nullptr, comp, false,
+                        u.part_dt + par * c->scratch_slots, u.part_bad + par * c->scratch_slots);
+    if (st != SRHD_OK) break;
+    e = cudaEventRecord(u.stepped[k], comp);
+    if (e != cudaSuccess) break;
+    e = cudaStreamWaitEvent(d2h, u.stepped[k], 0);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(static_cast<char*>(host_out) + a * pbytes,
+                          static_cast<const char*>(u.out) + a * pbytes, n * pbytes,
+                          cudaMemcpyDeviceToHost, d2h);
+    if (e == cudaSuccess && patch_status)
+      e = cudaMemcpyAsync(patch_status + a, u.status + a, n * sizeof(int32_t),
+                          cudaMemcpyDeviceToHost, d2h);
+  }
+  if (st != SRHD_OK || e != cudaSuccess) {
+    // nothing may still be copying into the caller's buffers after the return
+    for (cudaStream_t x : u.s) cudaStreamSynchronize(x);
+    return st != SRHD_OK ? st : cuda_fail(e, what);
+  }
+  if (dt_next) {
+    // the device-to-host stream has waited for every chunk's step
+    srhd::min_dt_kernel<<<1, 1, 0, d2h>>>(u.dn, K, u.dn + UniformStage::kMaxChunks);
+    e = cudaGetLastError();
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(u.host_dn, u.dn + UniformStage::kMaxChunks, sizeof(double),
+                          cudaMemcpyDeviceToHost, d2h);
+  }
+  // Every stream's work precedes fin: the device-to-host stream waited for
+  // each chunk's step, and each step for its copies in.
+  if (e == cudaSuccess) e = cudaEventRecord(u.fin, d2h);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(user, u.fin, 0);
+  if (e == cudaSuccess) e = cudaEventSynchronize(u.fin);
+  if (e != cudaSuccess) {
+    for (cudaStream_t x : u.s) cudaStreamSynchronize(x);
+    return cuda_fail(e, what);
+  }
+  if (dt_next) *dt_next = *u.host_dn;
+  return SRHD_OK;
+}

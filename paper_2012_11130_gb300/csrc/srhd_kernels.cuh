@@ -38,7 +38,7 @@ constexpr int kRC = 512 + 6 * 64;   // 896 reconstructed cells
 enum { CODE_UNPHYSICAL = 1, CODE_BAD_INPUT = 2, CODE_NOCONV = 4 };
 
 struct PatchArgs {
-  const void* in;         // [np][5][12^3]
+  const void* in;         // [np][5][12^3], or the interior array of a gathered grid
   void* out;              // [np][5][8^3] (advance) or nullptr
   void* pflux;            // [np][6][5][64] (nullable)
   void* face_flux;        // [np][3][5][576] (flux mode)
@@ -53,6 +53,12 @@ struct PatchArgs {
   int flux_only;
   int ori;                // 1: original scheme (total energy E, flux M)
   double eos_gamma;       // Gamma of the polytropic EoS (used by the EosPoly kernels)
+  // Uniform-grid gather (gather = 1): `in` is the interior array [.][5][8^3]
+  // of a grid of gnx*gny*gnz patches (patch (ix,iy,iz) at (iz*gny + iy)*gnx
+  // + ix); item p is grid patch gp0 + p, whose 12^3 tile the kernel reads
+  // from that patch and its neighbours (gbc*: 0 periodic, 1 outflow).
+  int gather, gnx, gny, gnz, gbcx, gbcy, gbcz;
+  int64_t gp0;
 };
 
 // EoS object of a launch: the TM tag, or the polytropic EoS with the
@@ -126,6 +132,24 @@ __device__ __forceinline__ void recon_cell(int r, int& i, int& j, int& k) {
     case 0: i = side; j = a; k = b; break;
     case 1: i = a; j = side; k = b; break;
     default: i = a; j = b; k = side; break;
+  }
+}
+
+// Source of a ghosted coordinate g in [-GH, kN+GH) of the patch at pc along an
+// axis of n patches: the patch q holding it and the cell l in that patch.
+// Periodic boundaries (bc 0) wrap the patch index, outflow ones (bc 1) take
+// the edge cell of the patch itself.
+__device__ __forceinline__ void ghost_src(int g, int pc, int n, int bc, int& q, int& l) {
+  const int o = g < 0 ? -1 : (g >= kN ? 1 : 0);
+  q = pc + o;
+  l = g - kN * o;
+  if (q < 0 || q >= n) {
+    if (bc == 0) {
+      q = q < 0 ? q + n : q - n;
+    } else {
+      q = pc;
+      l = o < 0 ? 0 : kN - 1;
+    }
   }
 }
 
@@ -303,7 +327,32 @@ __global__ void __launch_bounds__(NT, MINB) patch_kernel(PatchArgs a) {
 
   for (int w = blockIdx.x; w < a.npatch; w += gridDim.x) {
     const int p = a.worklist ? a.worklist[w] : w;
-    const S* in = static_cast<const S*>(a.in) + (size_t)p * 5 * kGC;
+    const S* base = static_cast<const S*>(a.in);
+    // Offset of this patch's own data in `base` (its ghosted tile, or its
+    // interior in a gathered grid) and the stride between variables.
+    int64_t self;
+    int vs, gpx = 0, gpy = 0, gpz = 0;
+    if (a.gather) {
+      const int64_t q = a.gp0 + p;
+      gpx = int(q % a.gnx);
+      gpy = int((q / a.gnx) % a.gny);
+      gpz = int(q / ((int64_t)a.gnx * a.gny));
+      self = q * 5 * kNC;
+      vs = kNC;
+    } else {
+      self = (int64_t)p * 5 * kGC;
+      vs = kGC;
+    }
+    // offset of variable 0 of tile cell c (12^3 index)
+    auto tile_src = [&](int c) -> int64_t {
+      if (!a.gather) return self + c;
+      const int gz = c / (kG * kG), gy = (c / kG) % kG, gx = c % kG;
+      int qx, lx, qy, ly, qz, lz;
+      ghost_src(gx - 2, gpx, a.gnx, a.gbcx, qx, lx);
+      ghost_src(gy - 2, gpy, a.gny, a.gbcy, qy, ly);
+      ghost_src(gz - 2, gpz, a.gnz, a.gbcz, qz, lz);
+      return ((int64_t)(qz * a.gny + qy) * a.gnx + qx) * (5 * kNC) + (lz * kN + ly) * kN + lx;
+    };
     const double dt = a.dt_dh[2 * p], dh = a.dt_dh[2 * p + 1];
     int code = 0;
 
@@ -312,11 +361,12 @@ __global__ void __launch_bounds__(NT, MINB) patch_kernel(PatchArgs a) {
     if constexpr (PAIR) {
       for (int r = tid; r < kTileNeeded / 2; r += NT) {
         const int ca = needed_tile_cell(r), cb = needed_tile_cell(r + kTileNeeded / 2);
+        const int64_t oa = tile_src(ca), ob = tile_src(cb);
         S Ua[5], Ub[5];
 #pragma unroll
         for (int v = 0; v < 5; ++v) {
-          Ua[v] = in[v * kGC + ca];
-          Ub[v] = in[v * kGC + cb];
+          Ua[v] = base[oa + v * vs];
+          Ub[v] = base[ob + v * vs];
         }
         PrimX<R> Wa, Wb;
         int sa, sb;
@@ -339,9 +389,10 @@ __global__ void __launch_bounds__(NT, MINB) patch_kernel(PatchArgs a) {
     } else {
       for (int r = tid; r < kTileNeeded; r += NT) {
         const int c = needed_tile_cell(r);
+        const int64_t o = tile_src(c);
         PrimX<R> W;
-        int st = con2pri<P>(in[c], in[kGC + c], in[2 * kGC + c], in[3 * kGC + c],
-                            in[4 * kGC + c], W, maxit, S(0), ori, eos);
+        int st = con2pri<P>(base[o], base[o + vs], base[o + 2 * vs], base[o + 3 * vs],
+                            base[o + 4 * vs], W, maxit, S(0), ori, eos);
         if (st == 1) code |= CODE_BAD_INPUT;
         if (st == 2) code |= CODE_NOCONV;
         prim[c] = S(W.rho);
@@ -423,11 +474,13 @@ __global__ void __launch_bounds__(NT, MINB) patch_kernel(PatchArgs a) {
             if constexpr (PAIR && sizeof(R) == 4) {
               // both cells' divergences in packed arithmetic
               int tcq[2], fq[2][6];
+              int64_t own[2];  // offsets of the cells' old states
 #pragma unroll
               for (int q = 0; q < 2; ++q) {
                 const int c = c0 + q * kItems;
                 const int i = c & 7, j = (c >> 3) & 7, k = c >> 6;
                 tcq[q] = tile_index(i, j, k);
+                own[q] = self + (a.gather ? c : tcq[q]);
                 g0[q] = hts[tcq[q]];
                 fq[q][0] = face_index<0>(i, j, k, i);
                 fq[q][1] = face_index<0>(i, j, k, i + 1);
@@ -446,8 +499,8 @@ __global__ void __launch_bounds__(NT, MINB) patch_kernel(PatchArgs a) {
                 const float2 div = pk::add(pk::add(pk::sub(ld(0, 1), ld(0, 0)),
                                                    pk::sub(ld(1, 3), ld(1, 2))),
                                            pk::sub(ld(2, 5), ld(2, 4)));
-                const float2 un = pk::fma(mcoef, div, make_float2(in[v * kGC + tcq[0]],
-                                                                  in[v * kGC + tcq[1]]));
+                const float2 un = pk::fma(mcoef, div, make_float2(base[own[0] + v * vs],
+                                                                  base[own[1] + v * vs]));
                 Un[0][v] = un.x;
                 Un[1][v] = un.y;
                 out[v * kNC + c0] = un.x;
@@ -459,6 +512,7 @@ __global__ void __launch_bounds__(NT, MINB) patch_kernel(PatchArgs a) {
                 const int c = c0 + q * kItems;
                 const int i = c & 7, j = (c >> 3) & 7, k = c >> 6;
                 const int tc = tile_index(i, j, k);
+                const int64_t own = self + (a.gather ? c : tc);
                 g0[q] = hts[tc];
                 const int fx0 = face_index<0>(i, j, k, i), fx1 = face_index<0>(i, j, k, i + 1);
                 const int fy0 = face_index<1>(i, j, k, j), fy1 = face_index<1>(i, j, k, j + 1);
@@ -469,7 +523,7 @@ __global__ void __launch_bounds__(NT, MINB) patch_kernel(PatchArgs a) {
                   div = div + (R(face_slot(face, 0, 0, v)[fx1]) - R(face_slot(face, 0, 0, v)[fx0]));
                   div = div + (R(face_slot(face, 1, 0, v)[fy1]) - R(face_slot(face, 1, 0, v)[fy0]));
                   div = div + (R(face_slot(face, 2, 0, v)[fz1]) - R(face_slot(face, 2, 0, v)[fz0]));
-                  Un[q][v] = S(R(in[v * kGC + tc]) - coef * div);
+                  Un[q][v] = S(R(base[own + v * vs]) - coef * div);
                   out[v * kNC + c] = Un[q][v];
                 }
               }
@@ -649,32 +703,78 @@ __global__ void __launch_bounds__(NT) cfl_kernel(const typename P::S* cons, int6
 }
 
 // Ghost fill of a uniform grid of patches (periodic or outflow per axis),
-// GH ghost cells per side (2 for the MUSCL-Hancock tiles, 3 for VL).
-template <class S, int GH = 2>
-__global__ void fill_ghosts_kernel(const S* interior, S* ghosted, int npx, int npy, int npz,
-                                   int bcx, int bcy, int bcz) {
-  constexpr int TE = kN + 2 * GH, TC = TE * TE * TE;
-  const int64_t np = (int64_t)npx * npy * npz;
-  const int64_t total = np * 5 * TC;
-  const int nx = npx * kN, ny = npy * kN, nz = npz * kN;
-  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total;
-       q += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t p = q / (5 * TC);
-    const int rem = int(q - p * 5 * TC);
-    const int v = rem / TC, c = rem - v * TC;
-    const int px = int(p % npx), py = int((p / npx) % npy), pz = int(p / ((int64_t)npx * npy));
-    int x = px * kN + (c % TE) - GH, y = py * kN + ((c / TE) % TE) - GH;
-    int z = pz * kN + c / (TE * TE) - GH;
-    auto wrap = [](int g, int n, int bc) {
-      if (bc == 0) return ((g % n) + n) % n;
-      return g < 0 ? 0 : (g >= n ? n - 1 : g);
-    };
-    x = wrap(x, nx, bcx);
-    y = wrap(y, ny, bcy);
-    z = wrap(z, nz, bcz);
-    const int64_t sp = ((int64_t)(z / kN) * npy + (y / kN)) * npx + (x / kN);
-    const int sc = ((z % kN) * kN + (y % kN)) * kN + (x % kN);
-    ghosted[q] = interior[sp * 5 * kNC + v * kNC + sc];
+// GH ghost cells per side (2 for the MUSCL-Hancock tiles, 3 for VL), for the
+// patches p0 .. p0+nfill-1 (row pl of ghosted holds patch p0+pl). One block
+// per patch (grid-stride), one thread per tile row (variable, z, y): the row
+// takes its z and y source from the patch or a neighbour, gathers its TE
+// cells along x from the rows of the patch and of its two x neighbours, and
+// writes them with vector stores when `wide` (ghosted aligned to the store).
+// Periodic boundaries wrap the patch index; outflow ones take the edge cell.
+template <class S, int TE>
+__device__ __forceinline__ void store_row(S* o, const S (&v)[TE], bool wide) {
+  if (wide) {
+    if constexpr (sizeof(S) == 4 && TE % 4 == 0) {
+#pragma unroll
+      for (int i = 0; i < TE; i += 4)
+        reinterpret_cast<float4*>(o)[i / 4] = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
+    } else if constexpr (sizeof(S) == 4) {
+#pragma unroll
+      for (int i = 0; i < TE; i += 2)
+        reinterpret_cast<float2*>(o)[i / 2] = make_float2(v[i], v[i + 1]);
+    } else {
+#pragma unroll
+      for (int i = 0; i < TE; i += 2)
+        reinterpret_cast<double2*>(o)[i / 2] = make_double2(v[i], v[i + 1]);
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < TE; ++i) o[i] = v[i];
+  }
+}
+
+// Byte alignment the vector stores of store_row need.
+template <class S, int GH> constexpr int ghost_store_align() {
+  return (sizeof(S) == 4 && (kN + 2 * GH) % 4 != 0) ? 8 : 16;
+}
+
+template <class S, int GH>
+__global__ void __launch_bounds__(256)
+    fill_ghosts_kernel(const S* __restrict__ interior, S* __restrict__ ghosted, int npx, int npy,
+                       int npz, int bcx, int bcy, int bcz, int64_t p0, int64_t nfill, int wide) {
+  constexpr int TE = kN + 2 * GH, TC = TE * TE * TE, ROWS = 5 * TE * TE;
+  for (int64_t pl = blockIdx.x; pl < nfill; pl += gridDim.x) {
+    const int64_t p = p0 + pl;
+    const int px = int(p % npx), py = int((p / npx) % npy);
+    const int pz = int(p / ((int64_t)npx * npy));
+    int qxl = px - 1, qxr = px + 1;
+    bool cl = false, cr = false;
+    if (qxl < 0) {
+      if (bcx == 0) qxl += npx; else { qxl = px; cl = true; }
+    }
+    if (qxr >= npx) {
+      if (bcx == 0) qxr -= npx; else { qxr = px; cr = true; }
+    }
+    S* out = ghosted + pl * (5 * TC);
+    for (int r = threadIdx.x; r < ROWS; r += blockDim.x) {
+      const int v = r / (TE * TE), rem = r - v * (TE * TE);
+      const int tz = rem / TE, ty = rem - tz * TE;
+      int qz, lz, qy, ly;
+      ghost_src(tz - GH, pz, npz, bcz, qz, lz);
+      ghost_src(ty - GH, py, npy, bcy, qy, ly);
+      const int64_t plane = ((int64_t)qz * npy + qy) * npx;
+      const int cell = (lz * kN + ly) * kN;
+      const S* rl = interior + ((plane + qxl) * 5 + v) * kNC + cell;
+      const S* rc = interior + ((plane + px) * 5 + v) * kNC + cell;
+      const S* rr = interior + ((plane + qxr) * 5 + v) * kNC + cell;
+      S val[TE];
+#pragma unroll
+      for (int i = 0; i < GH; ++i) val[i] = rl[cl ? 0 : kN - GH + i];
+#pragma unroll
+      for (int i = 0; i < kN; ++i) val[GH + i] = rc[i];
+#pragma unroll
+      for (int i = 0; i < GH; ++i) val[GH + kN + i] = rr[cr ? kN - 1 : i];
+      store_row<S, TE>(out + r * TE, val, wide != 0);
+    }
   }
 }
 
@@ -707,10 +807,10 @@ template <class P> struct Launch {
   // the VL integrator (srhd_vl.cuh) on 14^3 tiles
   static cudaError_t patches_vl(const PatchArgs& a, int poly, int grid, cudaStream_t s);
   static int vl_blocks_per_sm(int poly);
-  static cudaError_t fill_ghosts3(const void* interior, void* ghosted, int npx, int npy, int npz,
-                                  const int32_t* bc, int grid, cudaStream_t s);
+  // uniform-grid ghost fill with gh = 2 or 3 ghost cells, patches p0 .. p0+n-1
   static cudaError_t fill_ghosts(const void* interior, void* ghosted, int npx, int npy, int npz,
-                                 const int32_t* bc, int grid, cudaStream_t s);
+                                 const int32_t* bc, int gh, int64_t p0, int64_t n, int grid,
+                                 cudaStream_t s);
 };
 
 constexpr int kCflThreads = 256;

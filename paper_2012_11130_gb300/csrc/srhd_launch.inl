@@ -96,16 +96,6 @@ cudaError_t Launch<P>::patches_vl(const PatchArgs& a, int poly, int grid, cudaSt
   return cudaGetLastError();
 }
 
-template <class P>
-cudaError_t Launch<P>::fill_ghosts3(const void* interior, void* ghosted, int npx, int npy,
-                                    int npz, const int32_t* bc, int grid, cudaStream_t s) {
-  using S = typename P::S;
-  fill_ghosts_kernel<S, 3><<<grid, 256, 0, s>>>(static_cast<const S*>(interior),
-                                                static_cast<S*>(ghosted), npx, npy, npz, bc[0],
-                                                bc[1], bc[2]);
-  return cudaGetLastError();
-}
-
 template <class P> int Launch<P>::poly_blocks_per_sm() {
   int nb = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, PolyKernel<P>::fn,
@@ -201,11 +191,21 @@ cudaError_t Launch<P>::cfl(const void* cons, int64_t ncell, double dh, double cf
 
 template <class P>
 cudaError_t Launch<P>::fill_ghosts(const void* interior, void* ghosted, int npx, int npy, int npz,
-                                   const int32_t* bc, int grid, cudaStream_t s) {
+                                   const int32_t* bc, int gh, int64_t p0, int64_t n, int grid,
+                                   cudaStream_t s) {
   using S = typename P::S;
-  fill_ghosts_kernel<S><<<grid, 256, 0, s>>>(static_cast<const S*>(interior),
-                                             static_cast<S*>(ghosted), npx, npy, npz, bc[0], bc[1],
-                                             bc[2]);
+  const auto addr = reinterpret_cast<uintptr_t>(ghosted);
+  if (gh == 3) {
+    const int wide = addr % ghost_store_align<S, 3>() == 0;
+    fill_ghosts_kernel<S, 3><<<grid, 256, 0, s>>>(static_cast<const S*>(interior),
+                                                  static_cast<S*>(ghosted), npx, npy, npz, bc[0],
+                                                  bc[1], bc[2], p0, n, wide);
+  } else {
+    const int wide = addr % ghost_store_align<S, 2>() == 0;
+    fill_ghosts_kernel<S, 2><<<grid, 256, 0, s>>>(static_cast<const S*>(interior),
+                                                  static_cast<S*>(ghosted), npx, npy, npz, bc[0],
+                                                  bc[1], bc[2], p0, n, wide);
+  }
   return cudaGetLastError();
 }
 

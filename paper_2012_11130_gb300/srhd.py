@@ -277,6 +277,69 @@ class Context:
                                                  _stream(stream)), "srhd_fill_ghosts_uniform")
         return ghosted
 
+    def advance_uniform(self, interior, npx, npy, npz, dt_dh, bc=("periodic",) * 3, p0=0,
+                        n=None, cons_out=None, patch_face_flux=None, dt_next=None,
+                        patch_status=None, stream=None, prec=None):
+        """One fused step of patches p0 .. p0+n-1 of a device-resident
+        uniform grid (srhd_advance_uniform): the ghost zones are read from
+        the neighbouring patches of `interior` [np][5][8][8][8] (patch
+        (ix, iy, iz) at (iz*npy + iy)*npx + ix); no ghosted copy is made.
+        Returns cons_out [n][5][8][8][8]."""
+        _need_cuda(interior, "interior")
+        npatch = npx * npy * npz
+        if n is None:
+            n = npatch - p0
+        if interior.shape[0] != npatch:
+            raise ValueError(f"interior holds {interior.shape[0]} patches, grid has {npatch}")
+        if cons_out is None:
+            cons_out = torch.empty((n, 5, 8, 8, 8), dtype=interior.dtype, device=interior.device)
+        _need_cuda(cons_out, "cons_out", interior.dtype)
+        _need_cuda(dt_dh, "dt_dh", torch.float64)
+        for name, t, dt in (("patch_face_flux", patch_face_flux, interior.dtype),
+                            ("dt_next", dt_next, torch.float64),
+                            ("patch_status", patch_status, torch.int32)):
+            if t is not None:
+                _need_cuda(t, name, dt)
+        code = {"periodic": N.SRHD_BC_PERIODIC, "outflow": N.SRHD_BC_OUTFLOW}
+        bcs = (ctypes.c_int32 * 3)(*[code[b] for b in bc])
+        N.check(self._L.srhd_advance_uniform(
+            self._h, _prec(interior, prec), _ptr(interior), npx, npy, npz, bcs, p0, n,
+            _ptr(cons_out), _ptr(patch_face_flux), _ptr(dt_dh), _ptr(dt_next),
+            _ptr(patch_status), _stream(stream)), "srhd_advance_uniform")
+        return cons_out
+
+    def advance_uniform_host(self, interior, npx, npy, npz, dt, dh, bc=("periodic",) * 3,
+                             cons_out=None, patch_status=None, chunks=32, stream=None, prec=None):
+        """One step of a uniform grid held in host memory
+        (srhd_advance_uniform_host): interior [np][5][8][8][8] CPU tensor
+        (pinned for overlapped copies), patch (ix, iy, iz) at index
+        (iz*npy + iy)*npx + ix. Returns (cons_out, dt_next); cons_out may be
+        `interior` itself."""
+        if interior.device.type != "cpu" or not interior.is_contiguous():
+            raise ValueError("interior must be a contiguous host tensor")
+        n = npx * npy * npz
+        if tuple(interior.shape) != (n, 5, 8, 8, 8):
+            raise ValueError(f"interior must be [{n}][5][8][8][8], got {tuple(interior.shape)}")
+        if cons_out is None:
+            cons_out = torch.empty_like(interior, pin_memory=interior.is_pinned())
+        if (cons_out.device.type != "cpu" or cons_out.dtype != interior.dtype
+                or cons_out.shape != interior.shape or not cons_out.is_contiguous()):
+            raise ValueError("cons_out must be a contiguous host tensor like interior")
+        if patch_status is not None and (patch_status.device.type != "cpu"
+                                         or patch_status.dtype != torch.int32
+                                         or patch_status.numel() < n):
+            raise ValueError("patch_status must be a host int32 tensor of npatch entries")
+        code = {"periodic": N.SRHD_BC_PERIODIC, "outflow": N.SRHD_BC_OUTFLOW}
+        bcs = (ctypes.c_int32 * 3)(*[code[b] for b in bc])
+        dn = ctypes.c_double(0.0)
+        st = (ctypes.cast(patch_status.data_ptr(), ctypes.POINTER(ctypes.c_int32))
+              if patch_status is not None else None)
+        N.check(self._L.srhd_advance_uniform_host(
+            self._h, _prec(interior, prec), _ptr(interior), _ptr(cons_out), npx, npy, npz, bcs,
+            float(dt), float(dh), ctypes.byref(dn), st, int(chunks), _stream(stream)),
+            "srhd_advance_uniform_host")
+        return cons_out, dn.value
+
     # ---- VL integrator (include/srhd.h: srhd_advance_patches_vl) ---------------
     def advance_patches_vl(self, cons_ghosted, dt_dh, cons_out=None, patch_face_flux=None,
                            worklist=None, dt_next=None, patch_status=None, npatch=None,

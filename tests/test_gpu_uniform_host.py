@@ -1,0 +1,171 @@
+"""GPU parity of the uniform-grid steps. srhd_advance_uniform (the patch
+kernel gathering its tiles from the grid) is bit-identical to the ghost
+fill followed by srhd_advance_patches, for whole grids and patch ranges.
+The host-resident step (srhd_advance_uniform_host): the chunked pipeline (copies in, ghost fill,
+fused step, copies out on four streams) equals the oracle's MUSCL-Hancock
+step of the whole periodic or mixed-boundary grid, is bit-identical for
+every chunk count, in place, with pageable memory and to the device-resident
+path (fill + srhd_advance_patches), and reports unphysical cells and bad
+arguments."""
+import numpy as np
+import pytest
+import torch as _torch
+
+from gpu_common import cons_rel_err, require_gpu
+from paper_2012_11130_gb300 import workloads
+
+pytestmark = pytest.mark.gpu
+
+NPX, NPY, NPZ = 3, 2, 4
+
+
+def _field(oracle, seed):
+    rng = np.random.default_rng(seed)
+    nz, ny, nx = 8 * NPZ, 8 * NPY, 8 * NPX
+    z, y, x = np.meshgrid(np.arange(nz) / nz, np.arange(ny) / ny, np.arange(nx) / nx,
+                          indexing="ij")
+    ph = rng.uniform(0, 2 * np.pi, 5)
+    W = np.stack([1 + 0.3 * np.sin(2 * np.pi * (x + 2 * y) + ph[0]),
+                  0.6 * np.sin(2 * np.pi * (x + z) + ph[2]),
+                  0.6 * np.cos(2 * np.pi * (x - y) + ph[3]),
+                  0.6 * np.sin(2 * np.pi * z + ph[4]),
+                  1 + 0.3 * np.sin(2 * np.pi * (y - z) + ph[1])]).reshape(5, -1)
+    C, st = oracle.prim2con(W)
+    assert np.all(st == 0)
+    return C.reshape(5, nz, ny, nx)
+
+
+def _pad(C, bc):
+    mode = {"periodic": "wrap", "outflow": "edge"}
+    for ax, b in zip((3, 2, 1), bc):
+        pads = [(0, 0)] * 4
+        pads[ax] = (2, 2)
+        C = np.pad(C, pads, mode=mode[b])
+    return C
+
+
+def _same_bits(a, b):
+    """Bitwise equality (NaN included)."""
+    it = {8: _torch.int64, 4: _torch.int32}[a.element_size()]
+    return a.dtype == b.dtype and _torch.equal(a.view(it), b.view(it))
+
+
+def _host(a, dtype, pinned=True):
+    t = _torch.from_numpy(np.ascontiguousarray(a)).to(dtype)
+    return t.pin_memory() if pinned else t
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed", "mixed_cf"])
+@pytest.mark.parametrize("bc", [("periodic",) * 3, ("outflow", "periodic", "outflow")])
+def test_gather_equals_fill_and_advance(oracle, prec, bc):
+    torch, srhd = require_gpu()
+    dtype = torch.float64 if prec == "fp64" else torch.float32
+    # a rough field, so that some patches retry with a smaller limiter
+    Wp = workloads.rough_patch_prims(NPX * NPY * NPZ, seed=2, spread=0.5, lg_gamma_max=0.7,
+                                     edge=8)
+    C, st = oracle.prim2con(Wp.transpose(1, 0, 2, 3, 4).reshape(5, -1))
+    assert np.all(st == 0)
+    P = C.reshape(5, -1, 8, 8, 8).transpose(1, 0, 2, 3, 4)
+    U = torch.from_numpy(np.ascontiguousarray(P)).to(dtype).cuda()
+    npatch = NPX * NPY * NPZ
+    ctx = srhd.Context()
+    dd = torch.tensor([[0.004 + 1e-4 * i, 1 / 32] for i in range(npatch)], dtype=torch.float64,
+                      device="cuda")
+    G = ctx.fill_ghosts_uniform(U, NPX, NPY, NPZ, bc=bc)
+
+    def run(step, rows):
+        n = len(rows)
+        pf = torch.zeros((n, 6, 5, 64), dtype=dtype, device="cuda")
+        dn = torch.empty(1, dtype=torch.float64, device="cuda")
+        stt = torch.full((n,), -1, dtype=torch.int32, device="cuda")
+        out = step(pf, dn, stt)
+        return out.cpu(), pf.cpu(), dn.item(), stt.cpu()
+
+    for p0, n in ((0, npatch), (5, 9), (npatch - 7, 7)):
+        rows = list(range(p0, p0 + n))
+        wl = torch.tensor(rows, dtype=torch.int32, device="cuda")
+        want = run(lambda pf, dn, stt: ctx.advance_patches(
+            G[p0:p0 + n].contiguous(), dd[p0:p0 + n].contiguous(), patch_face_flux=pf,
+            dt_next=dn, patch_status=stt, prec=prec), rows)
+        got = run(lambda pf, dn, stt: ctx.advance_uniform(
+            U, NPX, NPY, NPZ, dd[p0:p0 + n].contiguous(), bc=bc, p0=p0, n=n, patch_face_flux=pf,
+            dt_next=dn, patch_status=stt, prec=prec), rows)
+        assert _same_bits(got[0], want[0]) and _same_bits(got[1], want[1])
+        assert _same_bits(torch.tensor(got[2]), torch.tensor(want[2]))
+        assert torch.equal(got[3], want[3])
+        del wl
+    # the rough field exercises the limiter retry
+    assert int((want[3] & 255).max()) > 0
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed_cf"])
+@pytest.mark.parametrize("bc", [("periodic",) * 3, ("outflow", "periodic", "outflow")])
+def test_matches_oracle_and_every_chunking(oracle, prec, bc):
+    torch, srhd = require_gpu()
+    dtype = torch.float64 if prec == "fp64" else torch.float32
+    C = _field(oracle, seed=3)
+    if prec != "fp64":
+        C = C.astype(np.float32).astype(np.float64)
+    dh, dt = 1.0 / 32, 0.4 / 32
+    ref = oracle.advance_block(_pad(C, bc), (8 * NPX, 8 * NPY, 8 * NPZ), (1, 1, 1), dt, dh)
+    assert ref["status"] == 0 and ref["retries"] == 0
+    want_dt = oracle.cfl_dt(ref["out"], dh)
+    ctx = srhd.Context()
+    U = _host(workloads.patchify(C), dtype)
+    npatch = NPX * NPY * NPZ
+    outs = []
+    for chunks in (1, 2, 3, 4, 9, 32):
+        st = torch.full((npatch,), -1, dtype=torch.int32)
+        out, dn = ctx.advance_uniform_host(U, NPX, NPY, NPZ, dt, dh, bc=bc, patch_status=st,
+                                           chunks=chunks, prec=prec)
+        assert int(st.abs().max()) == 0
+        outs.append((out.clone(), dn))
+    for out, dn in outs[1:]:
+        assert torch.equal(out, outs[0][0]) and dn == outs[0][1]
+    got = workloads.unpatchify(outs[0][0].double().numpy(), NPX, NPY, NPZ)
+    tol = 1e-12 if prec == "fp64" else 1e-5
+    err = cons_rel_err(got.reshape(5, -1), ref["out"].reshape(5, -1))
+    assert err.max() <= tol, err.max()
+    assert abs(outs[0][1] / want_dt - 1) <= tol
+    # the device-resident path gives the same bits
+    Ud = U.cuda()
+    G = ctx.fill_ghosts_uniform(Ud, NPX, NPY, NPZ, bc=bc)
+    dd = torch.tensor([[dt, dh]] * npatch, dtype=torch.float64, device="cuda")
+    dnd = torch.empty(1, dtype=torch.float64, device="cuda")
+    outd = ctx.advance_patches(G, dd, dt_next=dnd, prec=prec)
+    assert torch.equal(outd.cpu(), outs[0][0]) and dnd.item() == outs[0][1]
+    # in place, and from pageable memory
+    V = U.clone()
+    out, dn = ctx.advance_uniform_host(V, NPX, NPY, NPZ, dt, dh, bc=bc, cons_out=V, chunks=3,
+                                       prec=prec)
+    assert out is V and torch.equal(V, outs[0][0]) and dn == outs[0][1]
+    Up = _host(workloads.patchify(C), dtype, pinned=False)
+    out, dn = ctx.advance_uniform_host(Up, NPX, NPY, NPZ, dt, dh, bc=bc, chunks=2, prec=prec)
+    assert torch.equal(out, outs[0][0]) and dn == outs[0][1]
+
+
+def test_unphysical_cell_and_bad_arguments(oracle):
+    torch, srhd = require_gpu()
+    C = _field(oracle, seed=5)
+    P = workloads.patchify(C)
+    P[7, 0, 3, 3, 3] = -1.0  # negative D in patch 7
+    U = _host(P, torch.float64)
+    ctx = srhd.Context()
+    st = torch.zeros(NPX * NPY * NPZ, dtype=torch.int32)
+    out, dn = ctx.advance_uniform_host(U, NPX, NPY, NPZ, 1e-3, 1.0 / 32, patch_status=st)
+    assert np.isnan(dn)
+    s = st.numpy()
+    assert s[7] >> 8 == 2 and (np.delete(s, 7) == 0).all()
+    assert torch.isnan(out[7]).all() and not torch.isnan(out[:7]).any()
+    # a grid larger than the first allocates a larger stage
+    big = _host(np.concatenate([P, P]), torch.float64)
+    out, dn = ctx.advance_uniform_host(big, NPX, NPY, 2 * NPZ, 1e-3, 1.0 / 32)
+    assert np.isnan(dn)
+    for kw in (dict(chunks=0), dict(chunks=65), dict(dt=-1.0), dict(dh=0.0)):
+        args = dict(dt=1e-3, dh=1.0 / 32, chunks=4)
+        args.update(kw)
+        with pytest.raises(Exception):
+            ctx.advance_uniform_host(U, NPX, NPY, NPZ, args["dt"], args["dh"],
+                                     chunks=args["chunks"])
+    with pytest.raises(ValueError):
+        ctx.advance_uniform_host(U.cuda(), NPX, NPY, NPZ, 1e-3, 1.0 / 32)

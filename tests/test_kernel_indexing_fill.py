@@ -1,0 +1,137 @@
+"""CPU check of the index arithmetic of the uniform ghost-fill kernel
+(fill_ghosts_kernel in srhd_kernels.cuh), restated here: every source index
+lies in the interior array, every destination in the ghosted rows of the
+range, the rows tile each ghosted patch exactly once, the vector stores are
+aligned, and the gathered values equal a wrap/edge padding of the field."""
+import numpy as np
+import pytest
+
+KN = 8
+
+
+def ghost_src(g, pc, n, bc):
+    o = -1 if g < 0 else (1 if g >= KN else 0)
+    q, l = pc + o, g - KN * o
+    if q < 0 or q >= n:
+        if bc == 0:
+            q = q + n if q < 0 else q - n
+        else:
+            q, l = pc, (0 if o < 0 else KN - 1)
+    return q, l
+
+
+def kernel_fill(interior, npx, npy, npz, bc, gh, p0, nfill):
+    """The kernel's loops with its index arithmetic; returns the ghosted rows
+    and checks every index against its array."""
+    te = KN + 2 * gh
+    tc, rows = te ** 3, 5 * te * te
+    flat = interior.reshape(-1)
+    out = np.full(nfill * 5 * tc, np.nan)
+    written = np.zeros(out.size, int)
+    for pl in range(nfill):
+        p = p0 + pl
+        px, py, pz = p % npx, (p // npx) % npy, p // (npx * npy)
+        qxl, qxr, cl, cr = px - 1, px + 1, False, False
+        if qxl < 0:
+            if bc[0] == 0:
+                qxl += npx
+            else:
+                qxl, cl = px, True
+        if qxr >= npx:
+            if bc[0] == 0:
+                qxr -= npx
+            else:
+                qxr, cr = px, True
+        for r in range(rows):
+            v, rem = r // (te * te), r % (te * te)
+            tz, ty = rem // te, rem % te
+            qz, lz = ghost_src(tz - gh, pz, npz, bc[2])
+            qy, ly = ghost_src(ty - gh, py, npy, bc[1])
+            plane = (qz * npy + qy) * npx
+            cell = (lz * KN + ly) * KN
+            src = []
+            for i in range(gh):
+                src.append(((plane + qxl) * 5 + v) * 512 + cell + (0 if cl else KN - gh + i))
+            for i in range(KN):
+                src.append(((plane + px) * 5 + v) * 512 + cell + i)
+            for i in range(gh):
+                src.append(((plane + qxr) * 5 + v) * 512 + cell + (KN - 1 if cr else i))
+            dst = pl * 5 * tc + r * te
+            assert all(0 <= s < flat.size for s in src)
+            assert 0 <= dst and dst + te <= out.size
+            out[dst:dst + te] = flat[src]
+            written[dst:dst + te] += 1
+    assert (written == 1).all()
+    return out.reshape(nfill, 5, te, te, te)
+
+
+@pytest.mark.parametrize("gh", [2, 3])
+@pytest.mark.parametrize("dims,bc", [((3, 2, 4), (0, 0, 0)), ((3, 2, 4), (1, 0, 1)),
+                                     ((1, 1, 2), (0, 1, 0)), ((2, 1, 1), (1, 1, 1))])
+def test_fill_matches_padding(gh, dims, bc):
+    npx, npy, npz = dims
+    rng = np.random.default_rng(7)
+    field = rng.normal(size=(5, 8 * npz, 8 * npy, 8 * npx))
+    patches = field.reshape(5, npz, 8, npy, 8, npx, 8).transpose(1, 3, 5, 0, 2, 4, 6)
+    patches = patches.reshape(-1, 5, 8, 8, 8)
+    padded = field
+    for ax, b in zip((3, 2, 1), bc):
+        pads = [(0, 0)] * 4
+        pads[ax] = (gh, gh)
+        padded = np.pad(padded, pads, mode="wrap" if b == 0 else "edge")
+    te = KN + 2 * gh
+    n = npx * npy * npz
+    for p0, nf in ((0, n), (n // 2, n - n // 2)):
+        G = kernel_fill(patches, npx, npy, npz, bc, gh, p0, nf)
+        for pl in range(nf):
+            p = p0 + pl
+            px, py, pz = p % npx, (p // npx) % npy, p // (npx * npy)
+            want = padded[:, 8 * pz:8 * pz + te, 8 * py:8 * py + te, 8 * px:8 * px + te]
+            assert np.array_equal(G[pl], want)
+
+
+@pytest.mark.parametrize("esz", [4, 8])
+@pytest.mark.parametrize("gh", [2, 3])
+def test_vector_stores_aligned(esz, gh):
+    te = KN + 2 * gh
+    align = 8 if (esz == 4 and te % 4 != 0) else 16
+    width = 4 if (esz == 4 and te % 4 == 0) else 2     # elements per store
+    assert te % width == 0 and width * esz == align
+    tile = 5 * te ** 3 * esz
+    assert tile % align == 0 and (te * esz) % align == 0
+
+
+def tile_src(c, gp, dims, bc):
+    """The patch kernel's gather offset of 12^3 tile cell c of grid patch gp."""
+    npx, npy, npz = dims
+    gpx, gpy, gpz = gp % npx, (gp // npx) % npy, gp // (npx * npy)
+    gz, gy, gx = c // 144, (c // 12) % 12, c % 12
+    qx, lx = ghost_src(gx - 2, gpx, npx, bc[0])
+    qy, ly = ghost_src(gy - 2, gpy, npy, bc[1])
+    qz, lz = ghost_src(gz - 2, gpz, npz, bc[2])
+    return ((qz * npy + qy) * npx + qx) * 2560 + (lz * 8 + ly) * 8 + lx
+
+
+@pytest.mark.parametrize("dims,bc", [((3, 2, 4), (0, 0, 0)), ((3, 2, 4), (1, 0, 1)),
+                                     ((1, 1, 1), (0, 1, 0))])
+def test_gather_offsets_match_padding(dims, bc):
+    npx, npy, npz = dims
+    rng = np.random.default_rng(3)
+    field = rng.normal(size=(5, 8 * npz, 8 * npy, 8 * npx))
+    flat = field.reshape(5, npz, 8, npy, 8, npx, 8).transpose(1, 3, 5, 0, 2, 4, 6).reshape(-1)
+    padded = field
+    for ax, b in zip((3, 2, 1), bc):
+        pads = [(0, 0)] * 4
+        pads[ax] = (2, 2)
+        padded = np.pad(padded, pads, mode="wrap" if b == 0 else "edge")
+    for gp in range(npx * npy * npz):
+        px, py, pz = gp % npx, (gp // npx) % npy, gp // (npx * npy)
+        want = padded[:, 8 * pz:8 * pz + 12, 8 * py:8 * py + 12, 8 * px:8 * px + 12]
+        off = np.array([tile_src(c, gp, dims, bc) for c in range(1728)])
+        assert off.min() >= 0 and off.max() + 4 * 512 < flat.size
+        for v in range(5):
+            assert np.array_equal(flat[off + v * 512], want[v].reshape(-1))
+        # the interior cells' own offsets (phase 4) are gp*2560 + c
+        for c in (0, 7, 63, 511):
+            i, j, k = c & 7, (c >> 3) & 7, c >> 6
+            assert tile_src(((k + 2) * 12 + j + 2) * 12 + i + 2, gp, dims, bc) == gp * 2560 + c

@@ -50,9 +50,22 @@ MUTANTS = [
      "test_oracle_scheme.py::test_riemann_consistency_and_upwinding"),
     ("half_step_factor", "R half = R(0.5) * dt / dh;", "R half = dt / dh;",
      "test_oracle_scheme.py::test_shock_tube_converges_to_exact"),
-    ("update_sign", "Un[v] = in[(size_t)v * nc + c] - coef * div[v];",
-     "Un[v] = in[(size_t)v * nc + c] + coef * div[v];",
+    ("update_sign",
+     "            int o = (k * n[1] + j) * n[0] + i;\n            R Un[5];\n"
+     "            for (int v = 0; v < 5; ++v) {\n"
+     "              Un[v] = in[(size_t)v * nc + c] - coef * div[v];",
+     "            int o = (k * n[1] + j) * n[0] + i;\n            R Un[5];\n"
+     "            for (int v = 0; v < 5; ++v) {\n"
+     "              Un[v] = in[(size_t)v * nc + c] + coef * div[v];",
      "test_oracle_scheme.py::test_periodic_conservation"),
+    ("vl_update_sign",
+     "            const int o = (k * n[1] + j) * n[0] + i;\n            R Un[5];\n"
+     "            for (int v = 0; v < 5; ++v) {\n"
+     "              Un[v] = in[(size_t)v * nc + c] - coef * div[v];",
+     "            const int o = (k * n[1] + j) * n[0] + i;\n            R Un[5];\n"
+     "            for (int v = 0; v < 5; ++v) {\n"
+     "              Un[v] = in[(size_t)v * nc + c] + coef * div[v];",
+     "test_oracle_vl.py::test_mirror_symmetry_and_periodic_conservation"),
     ("cfl_sound_term", "R umax = gs * su + R(double(ndim)) * gamma * us;",
      "R umax = gs * su + gamma * us;", "test_oracle_scheme.py::test_cfl_limits"),
     ("taub_adiabat_sign", "(hd / rhod + K.h / K.rho) * (K.p - ps);",
