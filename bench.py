@@ -61,10 +61,10 @@ PEAK_FP64_TFLOPS = 1.25
 # only for the kernel sources with the recorded hash.
 # Captured at 128^3 (4096 patches) and scaled by 8 to the 32768-patch launch
 # (profiles/patch_kernel_advection128.md).
-NCU_TRAFFIC = {"sources_sha": "6453d0c260cab094",
-               "mixed_cf": 8 * (141.691392e6 + 23.852800e6),
-               "mixed": 8 * (141.719296e6 + 24.104192e6),
-               "fp64": 8 * (273.167360e6 + 67.307776e6)}
+NCU_TRAFFIC = {"sources_sha": "a11dc006f1abc8d2",
+               "mixed_cf": 8 * (141.704192e6 + 23.876096e6),
+               "mixed": 8 * (141.704448e6 + 24.325888e6),
+               "fp64": 8 * (273.109504e6 + 67.365632e6)}
 
 
 def kernel_sources_sha() -> str:

@@ -306,7 +306,9 @@ __device__ __forceinline__ int face_flux(typename P::S* face, const typename P::
   return fail;
 }
 
-template <class P, int NT, int MINB, bool PAIR, class E = EosTM>
+// GATHER: the uniform-grid gather mode of PatchArgs (a.gather must be 1);
+// otherwise a.in is a ghosted batch.
+template <class P, int NT, int MINB, bool PAIR, class E = EosTM, bool GATHER = false>
 __global__ void __launch_bounds__(NT, MINB) patch_kernel(PatchArgs a) {
   static_assert(NT % 32 == 0 && NT >= 64 && NT <= 1024, "block size");
   using S = typename P::S;
@@ -328,30 +330,39 @@ __global__ void __launch_bounds__(NT, MINB) patch_kernel(PatchArgs a) {
   for (int w = blockIdx.x; w < a.npatch; w += gridDim.x) {
     const int p = a.worklist ? a.worklist[w] : w;
     const S* base = static_cast<const S*>(a.in);
-    // Offset of this patch's own data in `base` (its ghosted tile, or its
-    // interior in a gathered grid) and the stride between variables.
-    int64_t self;
-    int vs, gpx = 0, gpy = 0, gpz = 0;
-    if (a.gather) {
+    // ghosted batch: this patch's tile; gathered grid: this patch's interior
+    int gpx = 0, gpy = 0, gpz = 0;
+    const S* in;
+    if constexpr (GATHER) {
       const int64_t q = a.gp0 + p;
       gpx = int(q % a.gnx);
       gpy = int((q / a.gnx) % a.gny);
       gpz = int(q / ((int64_t)a.gnx * a.gny));
-      self = q * 5 * kNC;
-      vs = kNC;
+      in = base + q * 5 * kNC;
     } else {
-      self = (int64_t)p * 5 * kGC;
-      vs = kGC;
+      in = base + (size_t)p * 5 * kGC;
     }
-    // offset of variable 0 of tile cell c (12^3 index)
-    auto tile_src = [&](int c) -> int64_t {
-      if (!a.gather) return self + c;
-      const int gz = c / (kG * kG), gy = (c / kG) % kG, gx = c % kG;
-      int qx, lx, qy, ly, qz, lz;
-      ghost_src(gx - 2, gpx, a.gnx, a.gbcx, qx, lx);
-      ghost_src(gy - 2, gpy, a.gny, a.gbcy, qy, ly);
-      ghost_src(gz - 2, gpz, a.gnz, a.gbcz, qz, lz);
-      return ((int64_t)(qz * a.gny + qy) * a.gnx + qx) * (5 * kNC) + (lz * kN + ly) * kN + lx;
+    // the five conserved variables of tile cell c (12^3 index)
+    auto load_tile = [&](int c, S (&U)[5]) {
+      if constexpr (GATHER) {
+        const int gz = c / (kG * kG), gy = (c / kG) % kG, gx = c % kG;
+        int qx, lx, qy, ly, qz, lz;
+        ghost_src(gx - 2, gpx, a.gnx, a.gbcx, qx, lx);
+        ghost_src(gy - 2, gpy, a.gny, a.gbcy, qy, ly);
+        ghost_src(gz - 2, gpz, a.gnz, a.gbcz, qz, lz);
+        const S* src = base + ((int64_t)(qz * a.gny + qy) * a.gnx + qx) * (5 * kNC) +
+                       ((lz * kN + ly) * kN + lx);
+#pragma unroll
+        for (int v = 0; v < 5; ++v) U[v] = src[v * kNC];
+      } else {
+#pragma unroll
+        for (int v = 0; v < 5; ++v) U[v] = in[v * kGC + c];
+      }
+    };
+    // old state of interior cell c (8^3 index; tc its tile index), variable v
+    auto old_state = [&](int v, int c, int tc) -> S {
+      if constexpr (GATHER) return in[v * kNC + c];
+      else return in[v * kGC + tc];
     };
     const double dt = a.dt_dh[2 * p], dh = a.dt_dh[2 * p + 1];
     int code = 0;
@@ -361,13 +372,9 @@ __global__ void __launch_bounds__(NT, MINB) patch_kernel(PatchArgs a) {
     if constexpr (PAIR) {
       for (int r = tid; r < kTileNeeded / 2; r += NT) {
         const int ca = needed_tile_cell(r), cb = needed_tile_cell(r + kTileNeeded / 2);
-        const int64_t oa = tile_src(ca), ob = tile_src(cb);
         S Ua[5], Ub[5];
-#pragma unroll
-        for (int v = 0; v < 5; ++v) {
-          Ua[v] = base[oa + v * vs];
-          Ub[v] = base[ob + v * vs];
-        }
+        load_tile(ca, Ua);
+        load_tile(cb, Ub);
         PrimX<R> Wa, Wb;
         int sa, sb;
         con2pri_x2<P>(Ua, Ub, Wa, Wb, maxit, sa, sb, S(0), S(0), ori, eos);
@@ -389,10 +396,10 @@ __global__ void __launch_bounds__(NT, MINB) patch_kernel(PatchArgs a) {
     } else {
       for (int r = tid; r < kTileNeeded; r += NT) {
         const int c = needed_tile_cell(r);
-        const int64_t o = tile_src(c);
+        S U[5];
+        load_tile(c, U);
         PrimX<R> W;
-        int st = con2pri<P>(base[o], base[o + vs], base[o + 2 * vs], base[o + 3 * vs],
-                            base[o + 4 * vs], W, maxit, S(0), ori, eos);
+        int st = con2pri<P>(U[0], U[1], U[2], U[3], U[4], W, maxit, S(0), ori, eos);
         if (st == 1) code |= CODE_BAD_INPUT;
         if (st == 2) code |= CODE_NOCONV;
         prim[c] = S(W.rho);
@@ -473,14 +480,13 @@ __global__ void __launch_bounds__(NT, MINB) patch_kernel(PatchArgs a) {
             S g0[NPC];  // tau of the cell before the step: warm start of the CFL solve
             if constexpr (PAIR && sizeof(R) == 4) {
               // both cells' divergences in packed arithmetic
-              int tcq[2], fq[2][6];
-              int64_t own[2];  // offsets of the cells' old states
+              int tcq[2], cq[2], fq[2][6];
 #pragma unroll
               for (int q = 0; q < 2; ++q) {
                 const int c = c0 + q * kItems;
                 const int i = c & 7, j = (c >> 3) & 7, k = c >> 6;
+                cq[q] = c;
                 tcq[q] = tile_index(i, j, k);
-                own[q] = self + (a.gather ? c : tcq[q]);
                 g0[q] = hts[tcq[q]];
                 fq[q][0] = face_index<0>(i, j, k, i);
                 fq[q][1] = face_index<0>(i, j, k, i + 1);
@@ -499,8 +505,8 @@ __global__ void __launch_bounds__(NT, MINB) patch_kernel(PatchArgs a) {
                 const float2 div = pk::add(pk::add(pk::sub(ld(0, 1), ld(0, 0)),
                                                    pk::sub(ld(1, 3), ld(1, 2))),
                                            pk::sub(ld(2, 5), ld(2, 4)));
-                const float2 un = pk::fma(mcoef, div, make_float2(base[own[0] + v * vs],
-                                                                  base[own[1] + v * vs]));
+                const float2 un = pk::fma(mcoef, div, make_float2(old_state(v, cq[0], tcq[0]),
+                                                                  old_state(v, cq[1], tcq[1])));
                 Un[0][v] = un.x;
                 Un[1][v] = un.y;
                 out[v * kNC + c0] = un.x;
@@ -512,7 +518,6 @@ __global__ void __launch_bounds__(NT, MINB) patch_kernel(PatchArgs a) {
                 const int c = c0 + q * kItems;
                 const int i = c & 7, j = (c >> 3) & 7, k = c >> 6;
                 const int tc = tile_index(i, j, k);
-                const int64_t own = self + (a.gather ? c : tc);
                 g0[q] = hts[tc];
                 const int fx0 = face_index<0>(i, j, k, i), fx1 = face_index<0>(i, j, k, i + 1);
                 const int fy0 = face_index<1>(i, j, k, j), fy1 = face_index<1>(i, j, k, j + 1);
@@ -523,7 +528,7 @@ __global__ void __launch_bounds__(NT, MINB) patch_kernel(PatchArgs a) {
                   div = div + (R(face_slot(face, 0, 0, v)[fx1]) - R(face_slot(face, 0, 0, v)[fx0]));
                   div = div + (R(face_slot(face, 1, 0, v)[fy1]) - R(face_slot(face, 1, 0, v)[fy0]));
                   div = div + (R(face_slot(face, 2, 0, v)[fz1]) - R(face_slot(face, 2, 0, v)[fz0]));
-                  Un[q][v] = S(R(base[own + v * vs]) - coef * div);
+                  Un[q][v] = S(R(old_state(v, c, tc)) - coef * div);
                   out[v * kNC + c] = Un[q][v];
                 }
               }

@@ -30,9 +30,9 @@ template <class S> struct PolyVariant;
 template <> struct PolyVariant<double> { static constexpr int nt = 512, minb = 1; static constexpr bool pair = false; };
 template <> struct PolyVariant<float> { static constexpr int nt = 448, minb = 2; static constexpr bool pair = true; };
 
-template <class P> struct PolyKernel {
+template <class P, bool G = false> struct PolyKernel {
   using Cfg = PolyVariant<typename P::S>;
-  static constexpr auto fn = patch_kernel<P, Cfg::nt, Cfg::minb, Cfg::pair, EosPoly>;
+  static constexpr auto fn = patch_kernel<P, Cfg::nt, Cfg::minb, Cfg::pair, EosPoly, G>;
 };
 
 // The VL kernel: one configuration per storage type (its shared memory,
@@ -46,15 +46,22 @@ template <class P, class E> struct VlKernel {
   static constexpr auto fn = vl_patch_kernel<P, Cfg::nt, Cfg::minb, E>;
 };
 
-template <class P, int V> struct PatchKernel {
+// G: the uniform-grid gather instantiation (srhd_advance_uniform)
+template <class P, int V, bool G = false> struct PatchKernel {
   using S = typename P::S;
   using Cfg = PatchVariant<S, V>;
-  static constexpr auto fn = patch_kernel<P, Cfg::nt, Cfg::minb, Cfg::pair>;
+  static constexpr auto fn = patch_kernel<P, Cfg::nt, Cfg::minb, Cfg::pair, EosTM, G>;
 };
 
 template <class P, int V> static cudaError_t setup_variant() {
-  return cudaFuncSetAttribute(PatchKernel<P, V>::fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              int(SmemLayout<typename P::S>::bytes));
+  cudaError_t e = cudaFuncSetAttribute(PatchKernel<P, V>::fn,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       int(SmemLayout<typename P::S>::bytes));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(PatchKernel<P, V, true>::fn,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             int(SmemLayout<typename P::S>::bytes));
+  return e;
 }
 
 template <class P> cudaError_t Launch<P>::setup() {
@@ -64,6 +71,9 @@ template <class P> cudaError_t Launch<P>::setup() {
   if (e == cudaSuccess) e = setup_variant<P, 3>();
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(PolyKernel<P>::fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             int(SmemLayout<typename P::S>::bytes));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(PolyKernel<P, true>::fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              int(SmemLayout<typename P::S>::bytes));
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(VlKernel<P, EosTM>::fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -123,25 +133,34 @@ template <class P> int Launch<P>::patch_blocks_per_sm(int variant) {
   }
 }
 
-template <class P, int V>
+template <class P, int V, bool G>
 static cudaError_t launch_variant(const PatchArgs& a, int grid, cudaStream_t s) {
-  PatchKernel<P, V>::fn<<<grid, PatchKernel<P, V>::Cfg::nt, SmemLayout<typename P::S>::bytes, s>>>(a);
+  using K = PatchKernel<P, V, G>;
+  K::fn<<<grid, K::Cfg::nt, SmemLayout<typename P::S>::bytes, s>>>(a);
   return cudaGetLastError();
+}
+
+template <class P, bool G>
+static cudaError_t launch_patches(const PatchArgs& a, int variant, int poly, int grid,
+                                  cudaStream_t s) {
+  if (poly) {
+    using K = PolyKernel<P, G>;
+    K::fn<<<grid, K::Cfg::nt, SmemLayout<typename P::S>::bytes, s>>>(a);
+    return cudaGetLastError();
+  }
+  switch (variant) {
+    case 0: return launch_variant<P, 0, G>(a, grid, s);
+    case 1: return launch_variant<P, 1, G>(a, grid, s);
+    case 2: return launch_variant<P, 2, G>(a, grid, s);
+    default: return launch_variant<P, 3, G>(a, grid, s);
+  }
 }
 
 template <class P>
 cudaError_t Launch<P>::patches(const PatchArgs& a, int variant, int poly, int grid,
                                cudaStream_t s) {
-  if (poly) {
-    PolyKernel<P>::fn<<<grid, PolyKernel<P>::Cfg::nt, SmemLayout<typename P::S>::bytes, s>>>(a);
-    return cudaGetLastError();
-  }
-  switch (variant) {
-    case 0: return launch_variant<P, 0>(a, grid, s);
-    case 1: return launch_variant<P, 1>(a, grid, s);
-    case 2: return launch_variant<P, 2>(a, grid, s);
-    default: return launch_variant<P, 3>(a, grid, s);
-  }
+  return a.gather ? launch_patches<P, true>(a, variant, poly, grid, s)
+                  : launch_patches<P, false>(a, variant, poly, grid, s);
 }
 
 template <class P>
