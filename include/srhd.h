@@ -294,6 +294,32 @@ srhd_status srhd_amr_fill_ghosts(srhd_ctx* ctx, srhd_prec prec, const void* cur,
                                  int32_t ntotal, int32_t p0, int32_t n, double w,
                                  const void* special, int32_t nspecial, void* stream);
 
+/* srhd_amr_fill_ghosts and srhd_advance_patches in one launch, without the
+ * ghosted copy: the patch kernel reads each listed patch's 12^3 tile through
+ * its map row while it loads the tile. Tile cell c of patch p takes
+ *   map[p][c] >= 0 without SRHD_AMR_COARSE: level_state[q];
+ *   with SRHD_AMR_COARSE: (1-w) coarse_old[q'] + w coarse_new[q'];
+ *   < 0: special state -1-map[p][c] (NaN if out of range or invalid),
+ * i.e. the tile srhd_amr_fill_ghosts writes with cur = level_state for the
+ * first kind and (prev, cur) = (coarse_old, coarse_new) for the second, and
+ * the step and its outputs are those of srhd_advance_patches on that tile
+ * (bit-identical results). A driver copies the level's state to prev first
+ * and passes level_state = coarse_old = prev, coarse_new = cur,
+ * cons_out = cur.
+ *   level_state, coarse_old, coarse_new [ntotal][5][8^3]; map [ntotal][12^3];
+ *   cons_out [ntotal][5][8^3]: rows of the processed patches written; they
+ *       must not be rows that the map rows of the processed patches read;
+ *   npatch, worklist (nullable: 0..npatch-1, indices < ntotal, not checked
+ *   on the device), dt_dh [ntotal][2], patch_face_flux (nullable)
+ *   [ntotal][6][5][64], dt_next, patch_status (nullable) [ntotal] as
+ *   srhd_advance_patches; w, special, nspecial as srhd_amr_fill_ghosts. */
+srhd_status srhd_advance_amr(srhd_ctx* ctx, srhd_prec prec, const void* level_state,
+                             const void* coarse_old, const void* coarse_new, const int32_t* map,
+                             int32_t ntotal, double w, const void* special, int32_t nspecial,
+                             void* cons_out, void* patch_face_flux, int32_t npatch,
+                             const double* dt_dh, const int32_t* worklist, double* dt_next,
+                             int32_t* patch_status, void* stream);
+
 /* Restriction: each listed parent patch takes, in every cell, the mean of
  * the 2x2x2 cells of its child covering that cell (volume average, so the
  * mass, momentum and energy of the coarse level equal those of the fine one

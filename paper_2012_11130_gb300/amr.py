@@ -257,24 +257,29 @@ class Hierarchy:
 
 class AmrRun:
     """Advance a Hierarchy on the GPU: one coarse step advances level l
-    2^l times (dt_l = cfl_dt_factor * dh_l), each substep = ghost fill, a copy
-    of the level's state (for the finer levels' time interpolation), one fused
-    srhd_advance_patches launch over the level's patches (writing the
-    patch-face fluxes), and after the two substeps of level l + 1 the
-    restriction of l + 1 onto l and the coarse-fine flux correction of l.
-    A coarse step has no host synchronisation or allocation and can be
-    captured into a CUDA graph (capture / replay)."""
+    2^l times (dt_l = cfl_dt_factor * dh_l), each substep = a copy of the
+    level's state (for the finer levels' time interpolation) and one fused
+    launch over the level's patches that reads each tile through the source
+    map (srhd_advance_amr; with fused=False a separate ghost fill into a
+    ghosted batch and srhd_advance_patches, which give the same bits), and
+    after the two substeps of level l + 1 the restriction of l + 1 onto l and
+    the coarse-fine flux correction of l. A coarse step has no host
+    synchronisation or allocation and can be captured into a CUDA graph
+    (capture / replay)."""
 
     def __init__(self, ctx: S.Context, hier: Hierarchy, cons0: torch.Tensor, dh0: float,
-                 cfl_dt_factor: float = 0.4, prec: str | None = None, special=None):
+                 cfl_dt_factor: float = 0.4, prec: str | None = None, special=None,
+                 fused: bool = True):
         self.ctx, self.h, self.prec = ctx, hier, prec
         dev = cons0.device
         dt = cons0.dtype
         n = hier.ntotal
         assert cons0.shape == (n, 5, 8, 8, 8)
+        self.fused = fused
         self.cur = cons0.clone()
         self.prev = cons0.clone()
-        self.ghosted = torch.zeros((n, 5, 12, 12, 12), dtype=dt, device=dev)
+        self.ghosted = (None if fused else
+                        torch.zeros((n, 5, 12, 12, 12), dtype=dt, device=dev))
         self.flux = [torch.zeros((n, 6, 5, 64), dtype=dt, device=dev) for _ in range(2)]
         self.status = torch.zeros(n, dtype=torch.int32, device=dev)
         self.map = torch.from_numpy(hier.map).to(dev)
@@ -304,16 +309,27 @@ class AmrRun:
     def _advance(self, l, w, parity, stream):
         h, ctx = self.h, self.ctx
         o, c = h.offsets[l], h.counts[l]
-        ctx.amr_fill_ghosts(self.cur, self.prev, self.ghosted, self.map, o, c, w, self.special,
-                            stream=stream, prec=self.prec)
+        if not self.fused:
+            ctx.amr_fill_ghosts(self.cur, self.prev, self.ghosted, self.map, o, c, w,
+                                self.special, stream=stream, prec=self.prec)
         self.prev[o:o + c].copy_(self.cur[o:o + c])
         ev = None
         if self.timer is not None:
             ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
             ev[0].record()
-        ctx.advance_patches(self.ghosted, self.dt_dh, cons_out=self.cur,
-                            patch_face_flux=self.flux[parity], worklist=self.worklists[l],
-                            npatch=c, patch_status=self.status, stream=stream, prec=self.prec)
+        if self.fused:
+            # same-level sources from prev (the level's state before this
+            # substep), coarse ones interpolated between the coarser level's
+            # states before (prev) and after (cur) its step
+            ctx.advance_amr(self.prev, self.prev, self.cur, self.map, self.dt_dh, self.cur, w=w,
+                            special=self.special, patch_face_flux=self.flux[parity],
+                            worklist=self.worklists[l], npatch=c, patch_status=self.status,
+                            stream=stream, prec=self.prec)
+        else:
+            ctx.advance_patches(self.ghosted, self.dt_dh, cons_out=self.cur,
+                                patch_face_flux=self.flux[parity], worklist=self.worklists[l],
+                                npatch=c, patch_status=self.status, stream=stream,
+                                prec=self.prec)
         if ev is not None:
             ev[1].record()
             self.timer.append(ev)

@@ -25,6 +25,55 @@ constexpr int kAmrTile = 12 * 12 * 12;   // ghosted tile cells
 constexpr int kAmrInt = 8 * 8 * 8;       // interior cells
 constexpr int32_t kAmrCoarseBit = 1 << 30;
 
+// Linear interpolation in time of a coarse cell, x at w = 0 and y at w = 1,
+// one rounding (the same in the fill kernels and in the gathering patch
+// kernel, so that both give the same bits).
+__device__ __forceinline__ float amr_lerp(float x, float y, float w) {
+  return __fmaf_rn(w, y - x, x);
+}
+__device__ __forceinline__ double amr_lerp(double x, double y, double w) {
+  return __fma_rn(w, y - x, x);
+}
+
+// One decoded entry of the source map: where the five variables of a tile
+// cell come from. get() loads unconditionally (the pointers and stride are
+// chosen per kind), so that the loads of a cell issue together.
+template <class S> struct AmrSrc {
+  const S* a;     // same-level cell, coarse old state, or special state
+  const S* b;     // coarse new state (= a for the other kinds)
+  int stride;     // between variables: kAmrInt, or 1 for a special state
+  bool coarse;    // interpolate in time between a and b
+  bool invalid;   // out-of-range entry: NaN
+  __device__ __forceinline__ S get(int v, S w) const {
+    const S x = a[v * stride], y = b[v * stride];
+    const S r = coarse ? amr_lerp(x, y, w) : x;
+    return invalid ? S(__longlong_as_double(0x7ff8000000000000ULL)) : r;
+  }
+};
+
+// Decodes map entry m: >= 0 without kAmrCoarseBit -> same[q]; with it ->
+// (old[q], new[q]); < 0 -> special[-1 - m]; out of range -> invalid (its
+// pointers then address same[0], which exists).
+template <class S>
+__device__ __forceinline__ AmrSrc<S> amr_decode(int32_t m, const S* same, const S* old_,
+                                                const S* new_, int64_t ncells,
+                                                const S* special, int nspecial) {
+  if (m < 0) {
+    const int k = -1 - m;
+    const bool ok = k < nspecial;
+    const S* s = ok ? special + k * 5 : same;
+    return AmrSrc<S>{s, s, 1, false, !ok};
+  }
+  const bool coarse = (m & kAmrCoarseBit) != 0;
+  const int64_t src = m & ~kAmrCoarseBit;
+  const bool ok = src < ncells;
+  const int64_t sp = src / kAmrInt, sc = src - sp * kAmrInt;
+  const int64_t off = ok ? sp * 5 * kAmrInt + sc : 0;
+  const S* x = (coarse ? old_ : same) + off;
+  const S* y = (coarse ? new_ : same) + off;
+  return AmrSrc<S>{x, y, kAmrInt, coarse, !ok};
+}
+
 // ghosted[p][v][c] for p in [p0, p0 + n), c in the 12^3 tile, from
 // map[p][c]: >= 0 without kAmrCoarseBit -> cur[q] (q = patch * 512 + cell);
 // with kAmrCoarseBit -> (1 - w) prev[q] + w cur[q]; < 0 -> special[-1 - m].
@@ -63,7 +112,7 @@ __global__ void amr_fill_kernel(const S* __restrict__ cur, const S* __restrict__
 #pragma unroll
       for (int v = 0; v < 5; ++v) {
         const S x = b[v * kAmrInt], y = a[v * kAmrInt];
-        g[v * kAmrTile] = x + w * (y - x);
+        g[v * kAmrTile] = amr_lerp(x, y, w);
       }
     } else {
 #pragma unroll
@@ -124,7 +173,7 @@ __global__ void amr_fill4_kernel(const S* __restrict__ cur, const S* __restrict_
 #pragma unroll
         for (int v = 0; v < 5; ++v) {
           const S x = b[v * kAmrInt], y = a[v * kAmrInt];
-          val[v][e] = x + w * (y - x);
+          val[v][e] = amr_lerp(x, y, w);
         }
       } else {
 #pragma unroll

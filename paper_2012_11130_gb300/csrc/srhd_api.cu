@@ -407,6 +407,11 @@ static void fill_common(const srhd_ctx* c, srhd_prec prec, srhd::PatchArgs& a) {
   a.gnx = a.gny = a.gnz = 1;
   a.gbcx = a.gbcy = a.gbcz = 0;
   a.gp0 = 0;
+  a.amr_map = nullptr;
+  a.amr_old = a.amr_new = a.amr_special = nullptr;
+  a.amr_ncells = 0;
+  a.amr_w = 0.0;
+  a.amr_nspecial = 0;
 }
 
 srhd_status srhd_flux_patches(srhd_ctx* c, srhd_prec prec, const void* cons_ghosted,
@@ -669,6 +674,45 @@ srhd_status srhd_amr_fill_ghosts(srhd_ctx* c, srhd_prec prec, const void* cur, c
   }
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? SRHD_OK : cuda_fail(e, "amr_fill launch");
+}
+
+srhd_status srhd_advance_amr(srhd_ctx* c, srhd_prec prec, const void* level_state,
+                             const void* coarse_old, const void* coarse_new, const int32_t* map,
+                             int32_t ntotal, double w, const void* special, int32_t nspecial,
+                             void* cons_out, void* patch_face_flux, int32_t npatch,
+                             const double* dt_dh, const int32_t* worklist, double* dt_next,
+                             int32_t* patch_status, void* stream) {
+  srhd_status st = check_ctx(c);
+  if (st != SRHD_OK) return st;
+  if (!valid_prec(prec)) return fail(SRHD_ERR_ARG, "invalid precision %d", int(prec));
+  if (ntotal < 1 || npatch < 0 || npatch > ntotal)
+    return fail(SRHD_ERR_ARG, "need ntotal >= 1 and 0 <= npatch <= ntotal");
+  if (!(w >= 0.0 && w <= 1.0)) return fail(SRHD_ERR_ARG, "time weight w must be in [0, 1]");
+  if (nspecial < 0 || (nspecial > 0 && !special))
+    return fail(SRHD_ERR_ARG, "special states: nspecial < 0 or NULL array");
+  if (npatch > 0 && (!level_state || !coarse_old || !coarse_new || !map || !cons_out || !dt_dh))
+    return fail(SRHD_ERR_ARG, "level_state/coarse_old/coarse_new/map/cons_out/dt_dh is NULL");
+  if (npatch == 0 && !dt_next) return SRHD_OK;
+  srhd::PatchArgs a;
+  fill_common(c, prec, a);
+  a.in = level_state;
+  a.gather = 2;
+  a.amr_map = map;
+  a.amr_old = coarse_old;
+  a.amr_new = coarse_new;
+  a.amr_special = special;
+  a.amr_nspecial = nspecial;
+  a.amr_ncells = (int64_t)ntotal * srhd::kAmrInt;
+  a.amr_w = w;
+  a.out = cons_out;
+  a.pflux = patch_face_flux;
+  a.face_flux = nullptr;
+  a.npatch = npatch;
+  a.dt_dh = dt_dh;
+  a.worklist = worklist;
+  a.status = patch_status;
+  a.flux_only = 0;
+  return launch_patches(c, prec, a, dt_next, static_cast<cudaStream_t>(stream));
 }
 
 srhd_status srhd_amr_restrict(srhd_ctx* c, srhd_prec prec, void* cur, const int32_t* children,

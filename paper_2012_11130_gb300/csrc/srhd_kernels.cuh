@@ -24,6 +24,7 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "srhd_amr.cuh"
 #include "srhd_physics.cuh"
 
 namespace srhd {
@@ -59,6 +60,17 @@ struct PatchArgs {
   // from that patch and its neighbours (gbc*: 0 periodic, 1 outflow).
   int gather, gnx, gny, gnz, gbcx, gbcy, gbcz;
   int64_t gp0;
+  // AMR gather (gather = 2): tile cell c of item p comes from amr_map[p][c]
+  // (as in srhd_amr_fill_ghosts): entries without the coarse bit from `in`
+  // (the same level's state before the step), coarse entries
+  // (1 - amr_w) amr_old + amr_w amr_new, negative ones amr_special.
+  const int32_t* amr_map;
+  const void* amr_old;
+  const void* amr_new;
+  const void* amr_special;
+  int64_t amr_ncells;
+  double amr_w;
+  int amr_nspecial;
 };
 
 // EoS object of a launch: the TM tag, or the polytropic EoS with the
@@ -306,9 +318,9 @@ __device__ __forceinline__ int face_flux(typename P::S* face, const typename P::
   return fail;
 }
 
-// GATHER: the uniform-grid gather mode of PatchArgs (a.gather must be 1);
-// otherwise a.in is a ghosted batch.
-template <class P, int NT, int MINB, bool PAIR, class E = EosTM, bool GATHER = false>
+// GATHER: 0 ghosted batch (a.in), 1 uniform-grid gather, 2 AMR gather
+// (a.gather must equal it).
+template <class P, int NT, int MINB, bool PAIR, class E = EosTM, int GATHER = 0>
 __global__ void __launch_bounds__(NT, MINB) patch_kernel(PatchArgs a) {
   static_assert(NT % 32 == 0 && NT >= 64 && NT <= 1024, "block size");
   using S = typename P::S;
@@ -319,6 +331,9 @@ __global__ void __launch_bounds__(NT, MINB) patch_kernel(PatchArgs a) {
   S* hts = face + SmemLayout<S>::face_elems;
   __shared__ double s_red[NT / 32];
   __shared__ int s_bad[NT / 32];
+  // AMR gather: 1 if some interior tile cell of the patch is not mapped to
+  // the patch's own cell of the same level
+  [[maybe_unused]] __shared__ int s_nonid;
   const int tid = threadIdx.x;
   const int maxit = a.maxit;
   const int ori = a.ori;
@@ -333,7 +348,9 @@ __global__ void __launch_bounds__(NT, MINB) patch_kernel(PatchArgs a) {
     // ghosted batch: this patch's tile; gathered grid: this patch's interior
     int gpx = 0, gpy = 0, gpz = 0;
     const S* in;
-    if constexpr (GATHER) {
+    if constexpr (GATHER == 2) {
+      in = base;
+    } else if constexpr (GATHER == 1) {
       const int64_t q = a.gp0 + p;
       gpx = int(q % a.gnx);
       gpy = int((q / a.gnx) % a.gny);
@@ -343,8 +360,29 @@ __global__ void __launch_bounds__(NT, MINB) patch_kernel(PatchArgs a) {
       in = base + (size_t)p * 5 * kGC;
     }
     // the five conserved variables of tile cell c (12^3 index)
-    auto load_tile = [&](int c, S (&U)[5]) {
-      if constexpr (GATHER) {
+    // AMR gather: the patch's map row; phase 4 reads the old state directly
+    // unless s_nonid, else through the map
+    [[maybe_unused]] const int32_t* amap = nullptr;
+    [[maybe_unused]] S aw = S(0);
+    if constexpr (GATHER == 2) {
+      amap = a.amr_map + (size_t)p * kGC;
+      aw = S(a.amr_w);
+    }
+    [[maybe_unused]] auto amr_cell = [&](int32_t m) {
+      return amr_decode<S>(m, base, static_cast<const S*>(a.amr_old),
+                           static_cast<const S*>(a.amr_new), a.amr_ncells,
+                           static_cast<const S*>(a.amr_special), a.amr_nspecial);
+    };
+    // r: the cell's rank in the list of needed tile cells (the first kNC
+    // are the interior cells in 8^3 order)
+    auto load_tile = [&](int c, [[maybe_unused]] int r, S (&U)[5]) {
+      if constexpr (GATHER == 2) {
+        const int32_t m = amap[c];
+        const AmrSrc<S> src = amr_cell(m);
+#pragma unroll
+        for (int v = 0; v < 5; ++v) U[v] = src.get(v, aw);
+        if (r < kNC && m != (int32_t)((int64_t)p * kNC + r)) s_nonid = 1;
+      } else if constexpr (GATHER == 1) {
         const int gz = c / (kG * kG), gy = (c / kG) % kG, gx = c % kG;
         int qx, lx, qy, ly, qz, lz;
         ghost_src(gx - 2, gpx, a.gnx, a.gbcx, qx, lx);
@@ -360,21 +398,25 @@ __global__ void __launch_bounds__(NT, MINB) patch_kernel(PatchArgs a) {
       }
     };
     // old state of interior cell c (8^3 index; tc its tile index), variable v
+    // (AMR gather: through the map, see amr_cell)
     auto old_state = [&](int v, int c, int tc) -> S {
-      if constexpr (GATHER) return in[v * kNC + c];
+      if constexpr (GATHER == 1) return in[v * kNC + c];
       else return in[v * kGC + tc];
     };
     const double dt = a.dt_dh[2 * p], dh = a.dt_dh[2 * p + 1];
     int code = 0;
 
+    if constexpr (GATHER == 2) {
+      if (tid == 0) s_nonid = 0;
+    }
     __syncthreads();  // the previous patch is done with shared memory
     // ---- phase 1: primitive tile ------------------------------------------
     if constexpr (PAIR) {
       for (int r = tid; r < kTileNeeded / 2; r += NT) {
         const int ca = needed_tile_cell(r), cb = needed_tile_cell(r + kTileNeeded / 2);
         S Ua[5], Ub[5];
-        load_tile(ca, Ua);
-        load_tile(cb, Ub);
+        load_tile(ca, r, Ua);
+        load_tile(cb, r + kTileNeeded / 2, Ub);
         PrimX<R> Wa, Wb;
         int sa, sb;
         con2pri_x2<P>(Ua, Ub, Wa, Wb, maxit, sa, sb, S(0), S(0), ori, eos);
@@ -397,7 +439,7 @@ __global__ void __launch_bounds__(NT, MINB) patch_kernel(PatchArgs a) {
       for (int r = tid; r < kTileNeeded; r += NT) {
         const int c = needed_tile_cell(r);
         S U[5];
-        load_tile(c, U);
+        load_tile(c, r, U);
         PrimX<R> W;
         int st = con2pri<P>(U[0], U[1], U[2], U[3], U[4], W, maxit, S(0), ori, eos);
         if (st == 1) code |= CODE_BAD_INPUT;
@@ -481,12 +523,18 @@ __global__ void __launch_bounds__(NT, MINB) patch_kernel(PatchArgs a) {
             if constexpr (PAIR && sizeof(R) == 4) {
               // both cells' divergences in packed arithmetic
               int tcq[2], cq[2], fq[2][6];
+              [[maybe_unused]] AmrSrc<S> osrc[2];
 #pragma unroll
               for (int q = 0; q < 2; ++q) {
                 const int c = c0 + q * kItems;
                 const int i = c & 7, j = (c >> 3) & 7, k = c >> 6;
                 cq[q] = c;
                 tcq[q] = tile_index(i, j, k);
+                if constexpr (GATHER == 2) {
+                  if (s_nonid) osrc[q] = amr_cell(amap[tcq[q]]);
+                  else osrc[q] = AmrSrc<S>{base + (size_t)p * 5 * kNC + c,
+                                           base + (size_t)p * 5 * kNC + c, kNC, false, false};
+                }
                 g0[q] = hts[tcq[q]];
                 fq[q][0] = face_index<0>(i, j, k, i);
                 fq[q][1] = face_index<0>(i, j, k, i + 1);
@@ -505,8 +553,12 @@ __global__ void __launch_bounds__(NT, MINB) patch_kernel(PatchArgs a) {
                 const float2 div = pk::add(pk::add(pk::sub(ld(0, 1), ld(0, 0)),
                                                    pk::sub(ld(1, 3), ld(1, 2))),
                                            pk::sub(ld(2, 5), ld(2, 4)));
-                const float2 un = pk::fma(mcoef, div, make_float2(old_state(v, cq[0], tcq[0]),
-                                                                  old_state(v, cq[1], tcq[1])));
+                float2 old;
+                if constexpr (GATHER == 2)
+                  old = make_float2(osrc[0].get(v, aw), osrc[1].get(v, aw));
+                else
+                  old = make_float2(old_state(v, cq[0], tcq[0]), old_state(v, cq[1], tcq[1]));
+                const float2 un = pk::fma(mcoef, div, old);
                 Un[0][v] = un.x;
                 Un[1][v] = un.y;
                 out[v * kNC + c0] = un.x;
@@ -519,6 +571,12 @@ __global__ void __launch_bounds__(NT, MINB) patch_kernel(PatchArgs a) {
                 const int i = c & 7, j = (c >> 3) & 7, k = c >> 6;
                 const int tc = tile_index(i, j, k);
                 g0[q] = hts[tc];
+                [[maybe_unused]] AmrSrc<S> os1;
+                if constexpr (GATHER == 2) {
+                  if (s_nonid) os1 = amr_cell(amap[tc]);
+                  else os1 = AmrSrc<S>{base + (size_t)p * 5 * kNC + c,
+                                       base + (size_t)p * 5 * kNC + c, kNC, false, false};
+                }
                 const int fx0 = face_index<0>(i, j, k, i), fx1 = face_index<0>(i, j, k, i + 1);
                 const int fy0 = face_index<1>(i, j, k, j), fy1 = face_index<1>(i, j, k, j + 1);
                 const int fz0 = face_index<2>(i, j, k, k), fz1 = face_index<2>(i, j, k, k + 1);
@@ -528,7 +586,10 @@ __global__ void __launch_bounds__(NT, MINB) patch_kernel(PatchArgs a) {
                   div = div + (R(face_slot(face, 0, 0, v)[fx1]) - R(face_slot(face, 0, 0, v)[fx0]));
                   div = div + (R(face_slot(face, 1, 0, v)[fy1]) - R(face_slot(face, 1, 0, v)[fy0]));
                   div = div + (R(face_slot(face, 2, 0, v)[fz1]) - R(face_slot(face, 2, 0, v)[fz0]));
-                  Un[q][v] = S(R(old_state(v, c, tc)) - coef * div);
+                  S old;
+                  if constexpr (GATHER == 2) old = os1.get(v, aw);
+                  else old = old_state(v, c, tc);
+                  Un[q][v] = S(R(old) - coef * div);
                   out[v * kNC + c] = Un[q][v];
                 }
               }

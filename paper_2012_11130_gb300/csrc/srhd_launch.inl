@@ -30,7 +30,7 @@ template <class S> struct PolyVariant;
 template <> struct PolyVariant<double> { static constexpr int nt = 512, minb = 1; static constexpr bool pair = false; };
 template <> struct PolyVariant<float> { static constexpr int nt = 448, minb = 2; static constexpr bool pair = true; };
 
-template <class P, bool G = false> struct PolyKernel {
+template <class P, int G = 0> struct PolyKernel {
   using Cfg = PolyVariant<typename P::S>;
   static constexpr auto fn = patch_kernel<P, Cfg::nt, Cfg::minb, Cfg::pair, EosPoly, G>;
 };
@@ -46,8 +46,9 @@ template <class P, class E> struct VlKernel {
   static constexpr auto fn = vl_patch_kernel<P, Cfg::nt, Cfg::minb, E>;
 };
 
-// G: the uniform-grid gather instantiation (srhd_advance_uniform)
-template <class P, int V, bool G = false> struct PatchKernel {
+// G: 0 ghosted batch, 1 uniform-grid gather (srhd_advance_uniform), 2 AMR
+// gather (srhd_advance_amr)
+template <class P, int V, int G = 0> struct PatchKernel {
   using S = typename P::S;
   using Cfg = PatchVariant<S, V>;
   static constexpr auto fn = patch_kernel<P, Cfg::nt, Cfg::minb, Cfg::pair, EosTM, G>;
@@ -58,7 +59,11 @@ template <class P, int V> static cudaError_t setup_variant() {
                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        int(SmemLayout<typename P::S>::bytes));
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(PatchKernel<P, V, true>::fn,
+    e = cudaFuncSetAttribute(PatchKernel<P, V, 1>::fn,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             int(SmemLayout<typename P::S>::bytes));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(PatchKernel<P, V, 2>::fn,
                              cudaFuncAttributeMaxDynamicSharedMemorySize,
                              int(SmemLayout<typename P::S>::bytes));
   return e;
@@ -73,7 +78,10 @@ template <class P> cudaError_t Launch<P>::setup() {
     e = cudaFuncSetAttribute(PolyKernel<P>::fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              int(SmemLayout<typename P::S>::bytes));
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(PolyKernel<P, true>::fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    e = cudaFuncSetAttribute(PolyKernel<P, 1>::fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             int(SmemLayout<typename P::S>::bytes));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(PolyKernel<P, 2>::fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              int(SmemLayout<typename P::S>::bytes));
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(VlKernel<P, EosTM>::fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -133,14 +141,14 @@ template <class P> int Launch<P>::patch_blocks_per_sm(int variant) {
   }
 }
 
-template <class P, int V, bool G>
+template <class P, int V, int G>
 static cudaError_t launch_variant(const PatchArgs& a, int grid, cudaStream_t s) {
   using K = PatchKernel<P, V, G>;
   K::fn<<<grid, K::Cfg::nt, SmemLayout<typename P::S>::bytes, s>>>(a);
   return cudaGetLastError();
 }
 
-template <class P, bool G>
+template <class P, int G>
 static cudaError_t launch_patches(const PatchArgs& a, int variant, int poly, int grid,
                                   cudaStream_t s) {
   if (poly) {
@@ -159,8 +167,9 @@ static cudaError_t launch_patches(const PatchArgs& a, int variant, int poly, int
 template <class P>
 cudaError_t Launch<P>::patches(const PatchArgs& a, int variant, int poly, int grid,
                                cudaStream_t s) {
-  return a.gather ? launch_patches<P, true>(a, variant, poly, grid, s)
-                  : launch_patches<P, false>(a, variant, poly, grid, s);
+  if (a.gather == 2) return launch_patches<P, 2>(a, variant, poly, grid, s);
+  if (a.gather == 1) return launch_patches<P, 1>(a, variant, poly, grid, s);
+  return launch_patches<P, 0>(a, variant, poly, grid, s);
 }
 
 template <class P>

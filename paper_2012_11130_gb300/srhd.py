@@ -398,6 +398,40 @@ class Context:
                 "srhd_amr_fill_ghosts")
         return ghosted
 
+    def advance_amr(self, level_state, coarse_old, coarse_new, amr_map, dt_dh, cons_out,
+                    w=0.0, special=None, patch_face_flux=None, worklist=None, npatch=None,
+                    dt_next=None, patch_status=None, stream=None, prec=None):
+        """Ghost fill from the source map and fused step in one launch
+        (srhd_advance_amr): map entries without the coarse bit read
+        level_state, coarse ones (1-w) coarse_old + w coarse_new; the
+        processed patches' rows of cons_out are written. All state arrays
+        [ntotal][5][8][8][8]."""
+        _need_cuda(level_state, "level_state")
+        dt = level_state.dtype
+        for name, t in (("coarse_old", coarse_old), ("coarse_new", coarse_new),
+                        ("cons_out", cons_out)):
+            _need_cuda(t, name, dt)
+        _need_cuda(amr_map, "map", torch.int32)
+        _need_cuda(dt_dh, "dt_dh", torch.float64)
+        ntotal = level_state.shape[0]
+        if npatch is None:
+            npatch = worklist.numel() if worklist is not None else ntotal
+        for name, t, tdt in (("patch_face_flux", patch_face_flux, dt),
+                             ("worklist", worklist, torch.int32),
+                             ("dt_next", dt_next, torch.float64),
+                             ("patch_status", patch_status, torch.int32)):
+            if t is not None:
+                _need_cuda(t, name, tdt)
+        nsp = 0 if special is None else special.shape[0]
+        if special is not None:
+            _need_cuda(special, "special", dt)
+        N.check(self._L.srhd_advance_amr(
+            self._h, _prec(level_state, prec), _ptr(level_state), _ptr(coarse_old),
+            _ptr(coarse_new), _ptr(amr_map), ntotal, float(w), _ptr(special), nsp, _ptr(cons_out),
+            _ptr(patch_face_flux), npatch, _ptr(dt_dh), _ptr(worklist), _ptr(dt_next),
+            _ptr(patch_status), _stream(stream)), "srhd_advance_amr")
+        return cons_out
+
     def amr_restrict(self, cur, children, stream=None, prec=None):
         """Fine -> coarse averaging; children [nparent][9] int32."""
         _need_cuda(cur, "cur")

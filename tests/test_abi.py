@@ -75,3 +75,15 @@ def test_host_side_validation(lib):
     assert lib.srhd_create(ctypes.byref(h), ctypes.byref(bad)) == N.SRHD_ERR_ARG
     assert b"ndim" in lib.srhd_last_error()
     assert not h.value
+
+
+def test_binding_arity_matches_header(lib):
+    # every declaration's parameter count equals the ctypes argtypes length
+    src = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    decls = re.findall(r"^(?:srhd_status|const char\*)\s+(srhd_\w+)\(([^;]*?)\);", src, re.M | re.S)
+    assert decls
+    for name, params in decls:
+        params = params.strip()
+        n = 0 if params in ("", "void") else params.count(",") + 1
+        argtypes = getattr(lib, name).argtypes
+        assert argtypes is not None and len(argtypes) == n, (name, n, argtypes)

@@ -1,6 +1,7 @@
 """GPU parity of the AMR exchange (srhd_amr_fill_ghosts, srhd_amr_restrict,
 srhd_amr_flux_correct) and of whole subcycled AMR steps (amr.AmrRun) against
-the CPU oracle (oracle/amr_oracle.py), through the C ABI."""
+the CPU oracle (oracle/amr_oracle.py), through the C ABI; the fused
+fill-and-step launch (srhd_advance_amr) against the separate fill and step."""
 import numpy as np
 import pytest
 
@@ -98,12 +99,14 @@ def test_bad_map_entries_give_nan_and_args_are_checked(oracle):
         ctx.amr_fill_ghosts(cur, cur, G, mp, 0, 2, 1.5, sp)
 
 
-def _gpu_run(torch, srhd, h, levs, data, prec, steps, graph=False):
+def _gpu_run(torch, srhd, h, levs, data, prec, steps, graph=False, fused=True, special=None,
+             dh0=DH0):
     from paper_2012_11130_gb300.amr import AmrRun
     dt = torch_dtype(torch, prec)
     C0 = to_dev(torch, _stack(h, levs, data), dt)
     ctx = srhd.Context(srhd.Params(cfl_mode="light"))
-    run = AmrRun(ctx, h, C0, DH0, prec=prec)
+    run = AmrRun(ctx, h, C0, dh0, prec=prec, fused=fused,
+                 special=None if special is None else to_dev(torch, special, dt))
     for l in range(h.nlev - 2, -1, -1):    # consistent t = 0 state
         ctx.amr_restrict(run.cur, run.children[l], prec=prec)
     run.prev.copy_(run.cur)
@@ -186,3 +189,69 @@ def test_jet_inflow_small_hierarchy(oracle):
             assert err.max() <= 1e-11, err.max()
             # the beam has entered: D in the bottom cells on the axis changed
             assert not np.allclose(got, _stack(h, levs, data))
+
+
+def _same_bits(torch, a, b):
+    it = {8: torch.int64, 4: torch.int32}[a.element_size()]
+    return torch.equal(a.contiguous().view(it), b.contiguous().view(it))
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed", "mixed_cf"])
+def test_fused_amr_step_equals_fill_and_step(oracle, prec):
+    # three nested periodic levels (same-level copies, coarse cells at w = 0
+    # and 1/2) and a jet inflow hierarchy (outflow copies, special states):
+    # the fused launch reads exactly the tile the fill writes
+    torch, srhd = require_gpu()
+    h, levs, data = _setup(oracle, 3, Wk.bump_prims)
+    runs = [_gpu_run(torch, srhd, h, levs, data, prec, 2, fused=f) for f in (True, False)]
+    assert _same_bits(torch, runs[0].cur, runs[1].cur)
+    assert _same_bits(torch, runs[0].prev, runs[1].prev)
+    for k in range(2):
+        assert _same_bits(torch, runs[0].flux[k], runs[1].flux[k])
+    assert torch.equal(runs[0].status, runs[1].status)
+    from paper_2012_11130_gb300.amr import Hierarchy
+    lev = Wk.jet_hierarchy(base=(4, 4, 8), radii=(0.1,), heights=(0.5,))
+    inflow = dict(axis=2, side=0, center=(16.0, 16.0), radius=2.0, index=0)
+    hj = Hierarchy((4, 4, 8), lev, bc=("outflow",) * 3, inflow=inflow)
+    amb, jet = Wk.jet_states(gamma_jet=10.0)
+    Camb, _ = oracle.prim2con(np.asarray(amb, float).reshape(5, 1))
+    Cjet, _ = oracle.prim2con(np.asarray(jet, float).reshape(5, 1))
+    levj = [[tuple(c) for c in l] for l in lev]
+    dataj = [{c: np.broadcast_to(Camb[:, 0, None, None, None], (5, 8, 8, 8)).copy()
+              for c in levj[l]} for l in range(len(lev))]
+    runs = [_gpu_run(torch, srhd, hj, levj, dataj, prec, 3, fused=f, special=Cjet.T,
+                     dh0=1.0 / 32) for f in (True, False)]
+    assert _same_bits(torch, runs[0].cur, runs[1].cur)
+    assert torch.equal(runs[0].status, runs[1].status)
+    assert not torch.equal(runs[0].cur, runs[0].prev)
+
+
+def test_fused_amr_bad_map_entry(oracle):
+    # an out-of-range source in a read tile cell makes the patch bad input
+    # (NaN output), as the fill's NaN does in the separate path
+    torch, srhd = require_gpu()
+    h, levs, data = _setup(oracle, 2, Wk.bump_prims)
+    C0 = to_dev(torch, _stack(h, levs, data), torch.float64)
+    n = C0.shape[0]
+    amap = torch.from_numpy(h.map).cuda()
+    amap[3, (5 * 12 + 5) * 12 + 1] = n * 512 + 7           # x ghost cell of patch 3
+    ctx = srhd.Context()
+    dd = torch.tensor([[1e-3, DH0]] * n, dtype=torch.float64, device="cuda")
+    outs = []
+    for fused in (True, False):
+        out = C0.clone()
+        st = torch.zeros(n, dtype=torch.int32, device="cuda")
+        wl = torch.arange(h.counts[0], dtype=torch.int32, device="cuda")
+        if fused:
+            ctx.advance_amr(C0, C0, C0, amap, dd, out, worklist=wl, patch_status=st)
+        else:
+            G = torch.zeros((n, 5, 12, 12, 12), dtype=torch.float64, device="cuda")
+            ctx.amr_fill_ghosts(C0, C0, G, amap, 0, h.counts[0])
+            ctx.advance_patches(G, dd, cons_out=out, worklist=wl, patch_status=st)
+        outs.append((out, st))
+        s_ = st.cpu().numpy()
+        assert s_[3] >> 8 == 2 and torch.isnan(out[3]).all()
+        assert (np.delete(s_[:h.counts[0]], 3) >> 8 == 0).all()
+    assert _same_bits(torch, outs[0][0], outs[1][0]) and torch.equal(outs[0][1], outs[1][1])
+    with pytest.raises(Exception, match="w"):
+        ctx.advance_amr(C0, C0, C0, amap, dd, C0.clone(), w=1.5)
