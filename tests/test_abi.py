@@ -65,6 +65,16 @@ def test_host_side_validation(lib):
     assert lib.srhd_advance_patches(None, 0, vp(1), vp(1), None, 1, vp(1), None, None, None,
                                     None) == N.SRHD_ERR_ARG
     assert lib.srhd_cfl_dt(None, 0, vp(1), 1, 0.1, vp(1), None) == N.SRHD_ERR_ARG
+    bc = (ctypes.c_int32 * 3)(0, 0, 0)
+    dn = ctypes.c_double()
+    assert lib.srhd_advance_uniform(None, 0, vp(1), 1, 1, 1, bc, 0, 1, vp(1), None, vp(1), None,
+                                    None, None) == N.SRHD_ERR_ARG
+    assert lib.srhd_advance_uniform_host(None, 0, vp(1), vp(1), 1, 1, 1, bc, 1e-3, 0.1,
+                                         ctypes.byref(dn), None, 8, None) == N.SRHD_ERR_ARG
+    assert lib.srhd_advance_amr(None, 0, vp(1), vp(1), vp(1), vp(1), 1, 0.0, None, 0, vp(1),
+                                None, 1, vp(1), None, None, None, None) == N.SRHD_ERR_ARG
+    assert lib.srhd_fill_ghosts_uniform_range(None, 0, vp(1), vp(1), 1, 1, 1, bc, 0, 1,
+                                              None) == N.SRHD_ERR_ARG
     assert b"ctx is NULL" in lib.srhd_last_error()
     assert lib.srhd_destroy(None) == N.SRHD_OK
     # invalid parameters are refused at creation

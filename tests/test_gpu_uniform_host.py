@@ -169,3 +169,34 @@ def test_unphysical_cell_and_bad_arguments(oracle):
                                      chunks=args["chunks"])
     with pytest.raises(ValueError):
         ctx.advance_uniform_host(U.cuda(), NPX, NPY, NPZ, 1e-3, 1.0 / 32)
+
+
+def test_uniform_edge_cases(oracle):
+    torch, srhd = require_gpu()
+    ctx = srhd.Context()
+    # a grid one slab deep (npz = 1): one chunk whatever is asked, z periodic
+    npx, npy, npz = 4, 3, 1
+    rng = np.random.default_rng(11)
+    W = np.stack([1 + 0.2 * rng.random((8, 24, 32)), 0.1 * rng.standard_normal((8, 24, 32)),
+                  0.1 * rng.standard_normal((8, 24, 32)), 0.1 * rng.standard_normal((8, 24, 32)),
+                  1 + 0.2 * rng.random((8, 24, 32))]).reshape(5, -1)
+    C, st = oracle.prim2con(W)
+    assert np.all(st == 0)
+    C = C.reshape(5, 8, 24, 32)
+    U = _host(workloads.patchify(C), torch.float64)
+    out, dn = ctx.advance_uniform_host(U, npx, npy, npz, 1e-3, 1 / 32, chunks=8)
+    ref = oracle.advance_block(_pad(C, ("periodic",) * 3), (32, 24, 8), (1, 1, 1), 1e-3, 1 / 32)
+    got = workloads.unpatchify(out.numpy(), npx, npy, npz)
+    assert cons_rel_err(got.reshape(5, -1), ref["out"].reshape(5, -1)).max() <= 1e-12
+    assert abs(dn / oracle.cfl_dt(ref["out"], 1 / 32) - 1) <= 1e-12
+    # an empty range still reports the CFL bound of nothing (+inf); ranges
+    # outside the grid and foreign tensors are refused
+    Ud = U.cuda()
+    dd = torch.tensor([[1e-3, 1 / 32]] * 12, dtype=torch.float64, device="cuda")
+    dnd = torch.zeros(1, dtype=torch.float64, device="cuda")
+    ctx.advance_uniform(Ud, npx, npy, npz, dd, p0=5, n=0, dt_next=dnd)
+    assert dnd.item() == float("inf")
+    with pytest.raises(Exception, match="range"):
+        ctx.advance_uniform(Ud, npx, npy, npz, dd, p0=10, n=3)
+    with pytest.raises(Exception):
+        ctx.advance_uniform(Ud, npx, npy, npz + 1, dd)
