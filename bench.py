@@ -61,10 +61,10 @@ PEAK_FP64_TFLOPS = 1.25
 # only for the kernel sources with the recorded hash.
 # Captured at 128^3 (4096 patches) and scaled by 8 to the 32768-patch launch
 # (profiles/patch_kernel_advection128.md).
-NCU_TRAFFIC = {"sources_sha": "a11dc006f1abc8d2",
-               "mixed_cf": 8 * (141.704192e6 + 23.876096e6),
-               "mixed": 8 * (141.704448e6 + 24.325888e6),
-               "fp64": 8 * (273.109504e6 + 67.365632e6)}
+NCU_TRAFFIC = {"sources_sha": "9d93bd6f95e52089",
+               "mixed_cf": 8 * (141.690624e6 + 23.909120e6),
+               "mixed": 8 * (141.704192e6 + 25.122560e6),
+               "fp64": 8 * (273.112576e6 + 67.150336e6)}
 
 
 def kernel_sources_sha() -> str:
