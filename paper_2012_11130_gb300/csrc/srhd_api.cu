@@ -100,16 +100,16 @@ struct UniformStage {
     cudaFree(dn);
     cudaFree(part_dt);
     cudaFree(part_bad);
-    cudaFreeHost(host_dn);
-    if (have_streams) {
-      for (auto& x : s) cudaStreamDestroy(x);
-      for (int k = 0; k < kMaxChunks; ++k) {
-        cudaEventDestroy(copied[k]);
-        cudaEventDestroy(stepped[k]);
-      }
-      cudaEventDestroy(start);
-      cudaEventDestroy(fin);
+    if (host_dn) cudaFreeHost(host_dn);
+    // handles a failed creation left null are skipped
+    for (auto& x : s)
+      if (x) cudaStreamDestroy(x);
+    for (int k = 0; k < kMaxChunks; ++k) {
+      if (copied[k]) cudaEventDestroy(copied[k]);
+      if (stepped[k]) cudaEventDestroy(stepped[k]);
     }
+    if (start) cudaEventDestroy(start);
+    if (fin) cudaEventDestroy(fin);
   }
 };
 
@@ -791,7 +791,6 @@ srhd_status uniform_stage(srhd_ctx* c, int64_t np, int64_t esz) {
     if (e == cudaSuccess) e = cudaMallocHost(&u.host_dn, sizeof(double));
     if (e != cudaSuccess) {
       // a partly made stage is destroyed whole and made again on the next call
-      u.have_streams = true;
       delete c->uniform;
       c->uniform = nullptr;
       return cuda_fail(e, "uniform stage streams/events");
