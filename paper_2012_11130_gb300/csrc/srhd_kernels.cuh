@@ -36,7 +36,9 @@ constexpr int kNC = kN * kN * kN;   // 512 interior cells
 constexpr int kNF = 9 * 8 * 8;      // 576 faces per direction
 constexpr int kRC = 512 + 6 * 64;   // 896 reconstructed cells
 
-enum { CODE_UNPHYSICAL = 1, CODE_BAD_INPUT = 2, CODE_NOCONV = 4 };
+// CODE_STAGE_TIMEOUT: a bulk copy of a tile did not complete within the
+// bounded wait of bulk::wait; the CTA stopped (see patch_kernel)
+enum { CODE_UNPHYSICAL = 1, CODE_BAD_INPUT = 2, CODE_NOCONV = 4, CODE_STAGE_TIMEOUT = 8 };
 
 struct PatchArgs {
   const void* in;         // [np][5][12^3], or the interior array of a gathered grid
@@ -72,6 +74,61 @@ struct PatchArgs {
   double amr_w;
   int amr_nspecial;
 };
+
+// ---- bulk asynchronous copies into shared memory -------------------------
+// The copy engine (cp.async.bulk) moves a contiguous global range into
+// shared memory and reports the bytes on an mbarrier; the threads that then
+// see the barrier's phase complete also see the data. Waits are bounded.
+namespace bulk {
+__device__ __forceinline__ uint32_t saddr(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void init(uint64_t* mbar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(mbar)) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+// Thread's earlier shared-memory accesses (made visible to it by a barrier)
+// are ordered before later copies into the same bytes.
+__device__ __forceinline__ void fence_before_copy() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void expect(uint64_t* mbar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(saddr(mbar)),
+               "r"(bytes)
+               : "memory");
+}
+// bytes: a multiple of 16; both addresses 16-byte aligned
+__device__ __forceinline__ void copy(void* dst, const void* src, uint32_t bytes, uint64_t* mbar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(saddr(dst)),
+      "l"(src), "r"(bytes), "r"(saddr(mbar))
+      : "memory");
+}
+// Wait for the completion of the barrier phase of this parity; false if it
+// has not completed after kWaitPolls polls (each non-blocking, then a sleep
+// of about kPollNs nanoseconds: about 1 s in all).
+constexpr int kWaitPolls = 1 << 23;
+constexpr unsigned kPollNs = 128;
+__device__ __forceinline__ bool test_wait(uint64_t* mbar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred q;\n\t"
+      "mbarrier.test_wait.parity.shared::cta.b64 q, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, q;\n\t}"
+      : "=r"(ok)
+      : "r"(saddr(mbar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ bool wait(uint64_t* mbar, uint32_t parity) {
+  for (int i = 0; i < kWaitPolls; ++i) {
+    if (test_wait(mbar, parity)) return true;
+    __nanosleep(kPollNs);
+  }
+  return false;
+}
+}  // namespace bulk
 
 // EoS object of a launch: the TM tag, or the polytropic EoS with the
 // launch's Gamma.
@@ -177,9 +234,16 @@ template <int d> __device__ __forceinline__ int face_index(int i, int j, int k, 
   return (fd * 8 + j) * 8 + i;
 }
 
+// Face slots are side-major: the 15 slots [d][v] of the left states (side
+// 0, overwritten by the fluxes in phase 3) first, then the 15 of the right
+// states (side 1). Nothing reads the right states after phase 3, so from
+// then until phase 2 of the next patch their 3 x 5 x 576 = 5 x 12^3
+// elements hold the next patch's ghosted tile.
 template <class S> __device__ __forceinline__ S* face_slot(S* face, int d, int side, int v) {
-  return face + ((d * 2 + side) * 5 + v) * kNF;
+  return face + ((side * 3 + d) * 5 + v) * kNF;
 }
+constexpr int kStageOffset = 3 * 5 * kNF;  // first right-state slot
+static_assert(5 * kGC == 3 * 5 * kNF, "a ghosted tile fills the right-state slots");
 
 template <int d, class R, class S, class E>
 __device__ __forceinline__ void recon_direction(const S* prim, int tc, const PrimX<R>& W, R theta,
@@ -342,6 +406,48 @@ __global__ void __launch_bounds__(NT, MINB) patch_kernel(PatchArgs a) {
   double dt_min = DBL_MAX;
   int cfl_bad = 0;
 
+  // Ghosted batch: while a patch is updated (phase 4) the copy engine brings
+  // the CTA's next tile into the right-state face slots (`stage`), where
+  // phase 1 of that patch reads it. Needs 16-byte aligned tiles. s_stg:
+  // bit 0 the parity of the s_mbar phase that the next copy completes, bit 1
+  // set while a copy is issued and not yet waited for. It is kept in shared
+  // memory (read by all threads, written by one between barriers) so that
+  // it holds no register through the phases.
+  [[maybe_unused]] S* stage = face + kStageOffset;
+  [[maybe_unused]] __shared__ __align__(8) uint64_t s_mbar;
+  [[maybe_unused]] __shared__ uint32_t s_stg;
+  [[maybe_unused]] __shared__ int s_stage_timeout;
+  auto stage_ok = [&]() {
+    return GATHER == 0 && !a.flux_only && (reinterpret_cast<uintptr_t>(a.in) & 15) == 0;
+  };
+  if constexpr (GATHER == 0) {
+    if (stage_ok() && tid == 0) {
+      bulk::init(&s_mbar);
+      s_stg = 0;
+      s_stage_timeout = 0;
+    }
+  }
+  // A copy that did not complete in time sets s_stage_timeout. The patch
+  // that waited for it is marked CODE_STAGE_TIMEOUT, the CTA's CFL minimum
+  // becomes NaN, and before its next patch (or at its end) the CTA waits
+  // once more, bounded, for the last copy it issued and stops; its remaining
+  // patches keep their previous contents and status.
+  // Parity of the s_mbar phase of the last copy issued, from a stage word
+  // (a phase that never began reads as complete).
+  [[maybe_unused]] auto last_copy_parity = [](uint32_t st) {
+    return (st & 2) ? (st & 1) : ((st & 1) ^ 1);
+  };
+  [[maybe_unused]] auto stage_abort = [&](int p, uint32_t st) {
+    if (tid == 0) {
+      if (a.status) a.status[p] = CODE_STAGE_TIMEOUT << 8;
+      if (a.partial_dt) {
+        a.partial_dt[blockIdx.x] = DBL_MAX;
+        a.partial_bad[blockIdx.x] = 1;
+      }
+    }
+    bulk::wait(&s_mbar, last_copy_parity(st));
+  };
+
   for (int w = blockIdx.x; w < a.npatch; w += gridDim.x) {
     const int p = a.worklist ? a.worklist[w] : w;
     const S* base = static_cast<const S*>(a.in);
@@ -373,6 +479,9 @@ __global__ void __launch_bounds__(NT, MINB) patch_kernel(PatchArgs a) {
                            static_cast<const S*>(a.amr_new), a.amr_ncells,
                            static_cast<const S*>(a.amr_special), a.amr_nspecial);
     };
+    // stage word as this patch starts; bit 1: its tile was copied during the
+    // last update and phase 1 reads it from `stage`
+    [[maybe_unused]] uint32_t st1 = 0;
     // r: the cell's rank in the list of needed tile cells (the first kNC
     // are the interior cells in 8^3 order)
     auto load_tile = [&](int c, [[maybe_unused]] int r, S (&U)[5]) {
@@ -393,8 +502,13 @@ __global__ void __launch_bounds__(NT, MINB) patch_kernel(PatchArgs a) {
 #pragma unroll
         for (int v = 0; v < 5; ++v) U[v] = src[v * kNC];
       } else {
+        if (st1 & 2) {
 #pragma unroll
-        for (int v = 0; v < 5; ++v) U[v] = in[v * kGC + c];
+          for (int v = 0; v < 5; ++v) U[v] = stage[v * kGC + c];
+        } else {
+#pragma unroll
+          for (int v = 0; v < 5; ++v) U[v] = in[v * kGC + c];
+        }
       }
     };
     // old state of interior cell c (8^3 index; tc its tile index), variable v
@@ -410,6 +524,10 @@ __global__ void __launch_bounds__(NT, MINB) patch_kernel(PatchArgs a) {
       if (tid == 0) s_nonid = 0;
     }
     __syncthreads();  // the previous patch is done with shared memory
+    if constexpr (GATHER == 0) {
+      if (stage_ok()) st1 = s_stg;
+      if ((st1 & 2) && !bulk::wait(&s_mbar, st1 & 1)) s_stage_timeout = 1;
+    }
     // ---- phase 1: primitive tile ------------------------------------------
     if constexpr (PAIR) {
       for (int r = tid; r < kTileNeeded / 2; r += NT) {
@@ -453,6 +571,15 @@ __global__ void __launch_bounds__(NT, MINB) patch_kernel(PatchArgs a) {
       }
     }
     const int bad_input = __syncthreads_or(code & CODE_BAD_INPUT);
+    if constexpr (GATHER == 0) {
+      if (stage_ok()) {
+        if (s_stage_timeout) {
+          stage_abort(p, st1);
+          return;
+        }
+        if ((st1 & 2) && tid == 0) s_stg = (st1 & 1) ^ 1;  // waited: next parity, none pending
+      }
+    }
 
     int retries = 0;
     int final_code = 0;
@@ -508,6 +635,25 @@ __global__ void __launch_bounds__(NT, MINB) patch_kernel(PatchArgs a) {
         att_smax = R(0);
         att_bad = 0;
         if (!fail || last) {
+          if constexpr (GATHER == 0) {
+            // the right states are consumed (phase 3 ended at a barrier):
+            // copy the CTA's next tile into their slots. The last thread
+            // issues the copy: it has no update work when NT > 256.
+            const int wn = w + gridDim.x;  // the CTA's next work item
+            if (stage_ok() && wn < a.npatch) {
+              if (tid == NT - 1) {
+                constexpr uint32_t kVarBytes = kGC * sizeof(S);
+                const int pn = a.worklist ? a.worklist[wn] : wn;
+                const S* src = base + (size_t)pn * 5 * kGC;
+                bulk::fence_before_copy();
+                bulk::expect(&s_mbar, 5 * kVarBytes);
+#pragma unroll
+                for (int v = 0; v < 5; ++v)
+                  bulk::copy(stage + v * kGC, src + v * kGC, kVarBytes, &s_mbar);
+                s_stg |= 2;  // read next after the phase-4 barrier
+              }
+            }
+          }
           S* out = static_cast<S*>(a.out) + (size_t)p * 5 * kNC;
           int fail4 = 0;
           // PAIR: the work item c0 in [0, 256) updates cells c0 and c0 + 256
@@ -628,6 +774,16 @@ __global__ void __launch_bounds__(NT, MINB) patch_kernel(PatchArgs a) {
         }
         if (!fail) break;
         if (last) { final_code |= CODE_UNPHYSICAL; break; }
+        if constexpr (GATHER == 0) {
+          // the retry's phase 2 rewrites the right-state slots: let the copy
+          // land first; the next patch then reads its tile from `in`
+          const uint32_t st = stage_ok() ? s_stg : 0u;
+          if (st & 2) {
+            if (!bulk::wait(&s_mbar, st & 1)) s_stage_timeout = 1;
+            __syncthreads();
+            if (tid == 0) s_stg = (st & 1) ^ 1;  // read next in the retry's phase 4
+          }
+        }
         ++retries;
         theta = theta * R(a.retry_factor);
         if (theta < R(a.theta_floor * a.theta0)) theta = R(0);
@@ -647,8 +803,7 @@ __global__ void __launch_bounds__(NT, MINB) patch_kernel(PatchArgs a) {
     if (a.flux_only && !bad_input) {
       S* ff = static_cast<S*>(a.face_flux) + (size_t)p * 3 * 5 * kNF;
       for (int q = tid; q < 3 * 5 * kNF; q += NT) {
-        int d = q / (5 * kNF), rem = q - d * 5 * kNF;
-        ff[q] = face[(d * 2) * 5 * kNF + rem];
+        ff[q] = face[q];  // the flux slots (side 0), [d][v][576]
       }
     }
     if (a.pflux && !a.flux_only && !bad_input) {
@@ -663,10 +818,20 @@ __global__ void __launch_bounds__(NT, MINB) patch_kernel(PatchArgs a) {
       }
     }
     code = __syncthreads_or(code & CODE_NOCONV);
+    if constexpr (GATHER == 0) {
+      if (tid == 0 && stage_ok() && s_stage_timeout) {  // a retry's wait ran out
+        final_code |= CODE_STAGE_TIMEOUT;
+        cfl_bad = 1;
+      }
+    }
     if (tid == 0 && a.status) {
       final_code |= code ? CODE_NOCONV : 0;
       a.status[p] = (final_code << 8) | (retries < 255 ? retries : 255);
     }
+  }
+  if constexpr (GATHER == 0) {
+    // a copy that ran out on the CTA's last patch: wait once more (bounded)
+    if (stage_ok() && s_stage_timeout) bulk::wait(&s_mbar, last_copy_parity(s_stg));
   }
 
   // ---- CFL partial minimum of this CTA -------------------------------------

@@ -130,3 +130,28 @@ def test_variant_indices_in_bounds(var):
                 chk("out", 4 * kNC + c, 5 * kNC)
         chk("red", tid >> 5, NT // 32)
     assert not bad, bad[:5]
+
+
+def face_slot(d, side, v):
+    """Offset of face slot (d, side, v): side-major, [side][d][v][576]."""
+    return ((side * 3 + d) * 5 + v) * kNF
+
+
+@pytest.mark.parametrize("elem", [4, 8])
+def test_stage_region_is_the_right_state_slots(elem):
+    # The next patch's ghosted tile (5 x 12^3 elements) is copied into the
+    # right-state slots (side 1) during phase 4; phase 4 and the outputs read
+    # only the flux slots (side 0), which must not overlap it.
+    stage0, stage_len = 3 * 5 * kNF, 5 * kGC
+    assert stage_len == 3 * 5 * kNF
+    offs = sorted(face_slot(d, s, v) for d in range(3) for s in range(2) for v in range(5))
+    assert offs == [q * kNF for q in range(30)]          # 30 disjoint slots fill the region
+    side1 = {face_slot(d, 1, v) + i for d in range(3) for v in range(5) for i in (0, kNF - 1)}
+    assert min(side1) == stage0 and max(side1) == stage0 + stage_len - 1
+    for d in range(3):
+        for v in range(5):
+            assert face_slot(d, 0, v) + kNF <= stage0      # flux slots end before the stage
+    # copy sizes and addresses: one copy per variable of kGC elements, tiles
+    # of 5 kGC elements; shared offset of the stage after the primitive tile
+    assert (kGC * elem) % 16 == 0 and (5 * kGC * elem) % 16 == 0
+    assert ((5 * kGC + stage0) * elem) % 16 == 0
