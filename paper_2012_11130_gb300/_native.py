@@ -20,7 +20,7 @@ SRHD_BC_PERIODIC, SRHD_BC_OUTFLOW = 0, 1
 SRHD_SCHEME_REDUCED, SRHD_SCHEME_TOTAL = 0, 1
 SRHD_EOS_TM, SRHD_EOS_POLYTROPIC = 0, 1
 CELL_OK, CELL_UNPHYSICAL, CELL_NOCONV = 0, 1, 2
-PATCH_UNPHYSICAL, PATCH_BAD_INPUT, PATCH_NOCONV = 1, 2, 4
+PATCH_UNPHYSICAL, PATCH_BAD_INPUT, PATCH_NOCONV, PATCH_STAGE_TIMEOUT = 1, 2, 4, 8
 
 # Every symbol declared in include/srhd.h.
 EXPORTS = ("srhd_default_params", "srhd_create", "srhd_destroy", "srhd_last_error",
