@@ -226,6 +226,61 @@ def time_device(torch, ctx, G, dt_dh, steps, warmup, barrier, prec, vl=False):
     return total_ms, per, dn.item(), status_max
 
 
+def time_uniform_loop(torch, ctx, G, dt_dh, steps, warmup, barrier, prec, cached):
+    """A time loop on the device-resident uniform grid: each step advances
+    the whole grid from the previous step's output (state ping-pong), with
+    the fused CFL bound and the patch status. cached: srhd_advance_uniform_prim
+    (the tiles' primitives gathered from the previous step's cache, which is
+    seeded once by srhd_con2pri_patches before the loop); otherwise
+    srhd_advance_uniform (every tile cell converted). The grid (0.34 GB
+    float state, 0.40 GB cache, twice) exceeds L2, so no flush."""
+    npatch = G.shape[0]
+    npx = round(npatch ** (1 / 3))
+    U = G[:, :, 2:10, 2:10, 2:10].contiguous()
+    V = torch.empty_like(U)
+    dn = torch.empty(1, dtype=torch.float64, device="cuda")
+    st = torch.empty(npatch, dtype=torch.int32, device="cuda")
+    stream = torch.cuda.current_stream()
+    if cached:
+        P = ctx.con2pri_patches(U, prec=prec)
+        Q = torch.empty_like(P)
+
+    def step():
+        nonlocal U, V, P, Q
+        if cached:
+            ctx.advance_uniform_prim(U, P, npx, npx, npx, dt_dh, cons_out=V, prim_out=Q,
+                                     dt_next=dn, patch_status=st, prec=prec)
+            P, Q = Q, P
+        else:
+            ctx.advance_uniform(U, npx, npx, npx, dt_dh, cons_out=V, dt_next=dn,
+                                patch_status=st, prec=prec)
+        U, V = V, U
+    if not cached:
+        P = Q = None
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(steps)]
+    barrier()
+    torch.cuda.synchronize()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for e0, e1 in evs:
+        e0.record(stream)
+        step()
+        e1.record(stream)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    total_ms = t0.elapsed_time(t1)
+    per = [e0.elapsed_time(e1) for e0, e1 in evs]
+    status_max = int(st.abs().max().item())
+    del U, V, P, Q
+    return total_ms, per, dn.item(), status_max
+
+
 def time_e2e(torch, ctx, G, dt_dh, steps, warmup, prec):
     """Headline end-to-end number: the uniform grid lives in pinned host
     memory and each step is one srhd_advance_uniform_host call, which copies
@@ -724,6 +779,19 @@ def run_ours(args):
                                                        args.warmup, barrier, prec)
         clocks = clk.summary()
         value, total_ms = job_throughput(total_ms, cells, args.steps, device="cuda")
+        loop = None
+        if not args.no_loop:
+            loop = {}
+            for cached in (True, False):
+                lt, lper, ldn, lsmax = time_uniform_loop(torch, ctx, G, dt_dh, args.steps,
+                                                         args.warmup, barrier, prec, cached)
+                lv, lt = job_throughput(lt, cells, args.steps, device="cuda")
+                loop["cached" if cached else "uncached"] = {
+                    "value": lv, "ms_per_step": lt / args.steps,
+                    "launch_ms_mean": statistics.mean(lper), "dt_next": ldn,
+                    "patch_status_max": lsmax,
+                    "api": ("srhd_advance_uniform_prim (primitive cache)" if cached
+                            else "srhd_advance_uniform")}
         e2e = None
         if not args.no_e2e:
             secs, h2d, d2h = time_e2e(torch, ctx, G, dt_dh, max(3, args.steps // 4), 1, prec)
@@ -758,6 +826,7 @@ def run_ours(args):
             "clocks": clocks, "e2e": e2e, "dt_next": dt_next, "patch_status_max": smax,
             "autotune": tuned,
             "launch_ms_mean": launch_ms, "launch_ms_min": min(per),
+            "uniform_loop": loop,
         }
         del G, dt_dh
         torch.cuda.empty_cache()
@@ -841,9 +910,10 @@ def run_ours(args):
         "clocks": m["clocks"], "e2e": m["e2e"], "cpu_baseline": cpu,
         "gpu_launches": 2 * args.steps,
         "autotune": m["autotune"],
+        "uniform_loop": m["uniform_loop"],
         "other_precisions": {q: {k: results[q][k] for k in ("value", "ms_per_step", "roofline",
                                                              "hbm_roofline", "clocks", "e2e",
-                                                             "autotune")}
+                                                             "autotune", "uniform_loop")}
                              for q in precs[1:]} or None,
         "l1_rho": l1 or None,
         "l1_shock_tube": st_l1,
@@ -868,6 +938,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-loop", action="store_true",
+                    help="skip the uniform-grid time loops (cached and uncached primitives)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-l1", action="store_true")
     ap.add_argument("--no-amr", action="store_true")

@@ -230,6 +230,42 @@ srhd_status srhd_advance_uniform(srhd_ctx* ctx, srhd_prec prec, const void* inte
                                  const double* dt_dh, double* dt_next, int32_t* patch_status,
                                  void* stream);
 
+/* Conserved-to-primitive conversion (Section 2.3, Eqs. transcendental
+ * equation and p = rho T; unphysical states per Eq. Unphysical result) of
+ * npatch interior patches into the primitive-cache layout of
+ * srhd_advance_uniform_prim:
+ *   cons [npatch][5][8^3] (D, M^x, M^y, M^z, Etilde);
+ *   prim_out [npatch][6][8^3] = (rho, U^x, U^y, U^z, p, tau), where tau is
+ *   the converged root-finding variable of the conversion (the conic
+ *   parameter h - T - 1 of the TM EoS, htilde for the polytropic EoS);
+ *   all six are NaN for an unphysical cell. Storage type as prec. */
+srhd_status srhd_con2pri_patches(srhd_ctx* ctx, srhd_prec prec, const void* cons, int64_t npatch,
+                                 void* prim_out, void* stream);
+
+/* srhd_advance_uniform with a primitive cache: each step's update phase
+ * already converts the new state (for the CFL bound of Section 3.2, and as
+ * the check of Eq. Unphysical result), so it also writes those primitives,
+ * and the next step gathers the primitives of its tiles from them instead
+ * of converting every tile cell again (about 2.7 conversions per updated
+ * cell, because neighbouring tiles overlap). The method and its results are
+ * those of srhd_advance_uniform, up to the rounding of the Newton root
+ * (the cached conversion starts from the cell's previous root).
+ *   interior [npx*npy*npz][5][8^3] and prim_in [npx*npy*npz][6][8^3]: the
+ *   state and its primitives (from srhd_con2pri_patches, or prim_out of the
+ *   previous step over the whole grid); a cell whose cached primitives are
+ *   NaN or non-positive (rho, p) makes every patch that reads it
+ *   SRHD_PATCH_BAD_INPUT;
+ *   cons_out [n][5][8^3] and prim_out [n][6][8^3] (row i: patch p0+i), the
+ *   new state and its primitives (NaN where unphysical); neither may
+ *   overlap interior or prim_in;
+ *   bc, p0, n, patch_face_flux, dt_dh, dt_next, patch_status as in
+ *   srhd_advance_uniform. */
+srhd_status srhd_advance_uniform_prim(srhd_ctx* ctx, srhd_prec prec, const void* interior,
+                                      const void* prim_in, int32_t npx, int32_t npy, int32_t npz,
+                                      const int32_t* bc, int32_t p0, int32_t n, void* cons_out,
+                                      void* prim_out, void* patch_face_flux, const double* dt_dh,
+                                      double* dt_next, int32_t* patch_status, void* stream);
+
 /* One VL step (the predictor-corrector integrator GAMER-SR offers beside
  * MUSCL-Hancock, Section 3.1) of a batch of independent patches with THREE
  * ghost cells per side: a first-order unsplit predictor to the half step

@@ -489,6 +489,8 @@ static void gather_args(const srhd_ctx* c, srhd_prec prec, srhd::PatchArgs& a,
   a.face_flux = nullptr;
   a.worklist = nullptr;
   a.flux_only = 0;
+  a.prim_in = nullptr;
+  a.prim_out = nullptr;
 }
 
 srhd_status srhd_advance_uniform(srhd_ctx* c, srhd_prec prec, const void* interior, int32_t npx,
@@ -510,6 +512,58 @@ srhd_status srhd_advance_uniform(srhd_ctx* c, srhd_prec prec, const void* interi
   if (n == 0 && !dt_next) return SRHD_OK;
   srhd::PatchArgs a;
   gather_args(c, prec, a, interior, npx, npy, npz, bc, p0);
+  a.out = cons_out;
+  a.pflux = patch_face_flux;
+  a.npatch = n;
+  a.dt_dh = dt_dh;
+  a.status = patch_status;
+  return launch_patches(c, prec, a, dt_next, static_cast<cudaStream_t>(stream));
+}
+
+srhd_status srhd_con2pri_patches(srhd_ctx* c, srhd_prec prec, const void* cons, int64_t npatch,
+                                 void* prim_out, void* stream) {
+  srhd_status st = check_ctx(c);
+  if (st != SRHD_OK) return st;
+  if (!valid_prec(prec)) return fail(SRHD_ERR_ARG, "invalid precision %d", int(prec));
+  if (npatch < 0) return fail(SRHD_ERR_ARG, "npatch < 0");
+  if (npatch == 0) return SRHD_OK;
+  if (npatch > INT64_MAX / (6 * srhd::kNC)) return fail(SRHD_ERR_ARG, "npatch too large");
+  if (!cons || !prim_out) return fail(SRHD_ERR_ARG, "cons/prim_out is NULL");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int grid = grid_for(c, npatch * srhd::kNC, 16);
+  const int maxit = newton_maxit(c, prec);
+  cudaError_t e = dispatch(prec, [&](auto L) {
+    return decltype(L)::prim_cache(cons, prim_out, npatch, maxit, c->params.scheme,
+                                   eos_arg(c->params), grid, s);
+  });
+  return e == cudaSuccess ? SRHD_OK : cuda_fail(e, "con2pri_patches launch");
+}
+
+srhd_status srhd_advance_uniform_prim(srhd_ctx* c, srhd_prec prec, const void* interior,
+                                      const void* prim_in, int32_t npx, int32_t npy, int32_t npz,
+                                      const int32_t* bc, int32_t p0, int32_t n, void* cons_out,
+                                      void* prim_out, void* patch_face_flux, const double* dt_dh,
+                                      double* dt_next, int32_t* patch_status, void* stream) {
+  srhd_status st = check_ctx(c);
+  if (st != SRHD_OK) return st;
+  if (!valid_prec(prec)) return fail(SRHD_ERR_ARG, "invalid precision %d", int(prec));
+  if (npx < 1 || npy < 1 || npz < 1) return fail(SRHD_ERR_ARG, "patch counts must be >= 1");
+  const int64_t np = (int64_t)npx * npy * npz;
+  if (np > INT32_MAX) return fail(SRHD_ERR_ARG, "more than 2^31-1 patches");
+  if (p0 < 0 || n < 0 || p0 + (int64_t)n > np)
+    return fail(SRHD_ERR_ARG, "patch range [%d, %d) outside the grid", p0, p0 + n);
+  if ((st = check_bc(bc)) != SRHD_OK) return st;
+  if (n > 0 && (!interior || !prim_in || !cons_out || !prim_out || !dt_dh))
+    return fail(SRHD_ERR_ARG, "interior/prim_in/cons_out/prim_out/dt_dh is NULL");
+  if (n > 0 && (prim_out == prim_in || prim_out == interior || cons_out == prim_in ||
+                cons_out == interior))
+    return fail(SRHD_ERR_ARG, "prim_out/cons_out must not alias the inputs");
+  if (n == 0 && !dt_next) return SRHD_OK;
+  srhd::PatchArgs a;
+  gather_args(c, prec, a, interior, npx, npy, npz, bc, p0);
+  a.gather = 3;
+  a.prim_in = prim_in;
+  a.prim_out = prim_out;
   a.out = cons_out;
   a.pflux = patch_face_flux;
   a.npatch = n;

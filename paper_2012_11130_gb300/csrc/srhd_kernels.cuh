@@ -62,6 +62,12 @@ struct PatchArgs {
   // from that patch and its neighbours (gbc*: 0 periodic, 1 outflow).
   int gather, gnx, gny, gnz, gbcx, gbcy, gbcz;
   int64_t gp0;
+  // Uniform-grid gather with primitive cache (gather = 3): as gather = 1,
+  // but the tile's primitives and solver variable come from prim_in
+  // [.][6][8^3] (rho, U^x, U^y, U^z, p, tau of every grid patch) instead of
+  // a conversion, and the new state's are written to prim_out [n][6][8^3].
+  const void* prim_in;
+  void* prim_out;
   // AMR gather (gather = 2): tile cell c of item p comes from amr_map[p][c]
   // (as in srhd_amr_fill_ghosts): entries without the coarse bit from `in`
   // (the same level's state before the step), coarse entries
@@ -165,8 +171,7 @@ constexpr int kTileNeeded = 512 + 768 + 96;  // 1376 cells read by the step
 // r-th cell of the tile that the step reads (tile_cell_needed), as a
 // 12^3 index: the 8^3 interior, then the six faces two layers deep, then the
 // twelve edges of the first layer.
-__device__ __forceinline__ int needed_tile_cell(int r) {
-  int g[3];
+__device__ __forceinline__ void needed_tile_coords(int r, int (&g)[3]) {
   if (r < 512) {
     g[0] = 2 + (r & 7); g[1] = 2 + ((r >> 3) & 7); g[2] = 2 + (r >> 6);
   } else if (r < 1280) {
@@ -185,6 +190,10 @@ __device__ __forceinline__ int needed_tile_cell(int r) {
     else if (pair == 1) { g[0] = ca; g[1] = w; g[2] = cb; }
     else { g[0] = w; g[1] = ca; g[2] = cb; }
   }
+}
+__device__ __forceinline__ int needed_tile_cell(int r) {
+  int g[3];
+  needed_tile_coords(r, g);
   return (g[2] * kG + g[1]) * kG + g[0];
 }
 
@@ -456,7 +465,7 @@ __global__ void __launch_bounds__(NT, MINB) patch_kernel(PatchArgs a) {
     const S* in;
     if constexpr (GATHER == 2) {
       in = base;
-    } else if constexpr (GATHER == 1) {
+    } else if constexpr (GATHER == 1 || GATHER == 3) {
       const int64_t q = a.gp0 + p;
       gpx = int(q % a.gnx);
       gpy = int((q / a.gnx) % a.gny);
@@ -514,7 +523,7 @@ __global__ void __launch_bounds__(NT, MINB) patch_kernel(PatchArgs a) {
     // old state of interior cell c (8^3 index; tc its tile index), variable v
     // (AMR gather: through the map, see amr_cell)
     auto old_state = [&](int v, int c, int tc) -> S {
-      if constexpr (GATHER == 1) return in[v * kNC + c];
+      if constexpr (GATHER == 1 || GATHER == 3) return in[v * kNC + c];
       else return in[v * kGC + tc];
     };
     const double dt = a.dt_dh[2 * p], dh = a.dt_dh[2 * p + 1];
@@ -529,7 +538,31 @@ __global__ void __launch_bounds__(NT, MINB) patch_kernel(PatchArgs a) {
       if ((st1 & 2) && !bulk::wait(&s_mbar, st1 & 1)) s_stage_timeout = 1;
     }
     // ---- phase 1: primitive tile ------------------------------------------
-    if constexpr (PAIR) {
+    if constexpr (GATHER == 3) {
+      // the primitives and solver variable that the previous step kept for
+      // the cells of the tile: a gather, no conversion. A state left
+      // unphysical by that step is stored as NaN.
+      const S* pbase = static_cast<const S*>(a.prim_in);
+      for (int r = tid; r < kTileNeeded; r += NT) {
+        int g[3];
+        needed_tile_coords(r, g);
+        const int c = (g[2] * kG + g[1]) * kG + g[0];
+        int qx, lx, qy, ly, qz, lz;
+        ghost_src(g[0] - 2, gpx, a.gnx, a.gbcx, qx, lx);
+        ghost_src(g[1] - 2, gpy, a.gny, a.gbcy, qy, ly);
+        ghost_src(g[2] - 2, gpz, a.gnz, a.gbcz, qz, lz);
+        const S* src = pbase + ((int64_t)(qz * a.gny + qy) * a.gnx + qx) * (6 * kNC) +
+                       ((lz * kN + ly) * kN + lx);
+        S w[6];
+#pragma unroll
+        for (int v = 0; v < 6; ++v) w[v] = __ldg(src + v * kNC);
+        if (!(w[0] > S(0) && w[4] > S(0) && isfinite(w[1] + w[2] + w[3] + w[5])))
+          code |= CODE_BAD_INPUT;
+#pragma unroll
+        for (int v = 0; v < 5; ++v) prim[v * kGC + c] = w[v];
+        hts[c] = w[5];
+      }
+    } else if constexpr (PAIR) {
       for (int r = tid; r < kTileNeeded / 2; r += NT) {
         const int ca = needed_tile_cell(r), cb = needed_tile_cell(r + kTileNeeded / 2);
         S Ua[5], Ub[5];
@@ -661,8 +694,9 @@ __global__ void __launch_bounds__(NT, MINB) patch_kernel(PatchArgs a) {
           constexpr int NPC = PAIR ? 2 : 1;
           constexpr int kItems = kNC / NPC;
           // the signal-speed CFL bound converts the new state; its status 1
-          // is the Eq. (Unphysical result) check, otherwise made directly
-          const bool signal = a.partial_dt && a.cfl_mode != 1;
+          // is the Eq. (Unphysical result) check, otherwise made directly.
+          // The primitive cache converts it in any case, for prim_out.
+          const bool signal = (a.partial_dt && a.cfl_mode != 1) || GATHER == 3;
           for (int c0 = tid; c0 < kItems; c0 += NT) {
             S Un[NPC][5];
             S g0[NPC];  // tau of the cell before the step: warm start of the CFL solve
@@ -754,11 +788,27 @@ __global__ void __launch_bounds__(NT, MINB) patch_kernel(PatchArgs a) {
               for (int q = 0; q < NPC; ++q) {
                 // the largest signal speed of the patch; dt = C dh / S_max once
                 if (st[q] != 1) {
-                  att_smax = fmax(att_smax, smax_of(W[q], a.ndim, eos));
+                  if (GATHER != 3 || a.cfl_mode != 1)
+                    att_smax = fmax(att_smax, smax_of(W[q], a.ndim, eos));
                 } else {
                   att_bad = 1;
                   fail4 = 1;
                 }
+              }
+              if constexpr (GATHER == 3) {
+                // keep the new state's primitives (NaN where unphysical)
+                S* po = static_cast<S*>(a.prim_out) + (size_t)p * 6 * kNC;
+#pragma unroll
+                for (int q = 0; q < NPC; ++q) {
+                  const int c = c0 + q * kItems;
+                  po[c] = S(W[q].rho);
+                  po[kNC + c] = S(W[q].u[0]);
+                  po[2 * kNC + c] = S(W[q].u[1]);
+                  po[3 * kNC + c] = S(W[q].u[2]);
+                  po[4 * kNC + c] = S(W[q].p);
+                  po[5 * kNC + c] = S(W[q].tau);
+                }
+                if (a.partial_dt && a.cfl_mode == 1) att_min = fmin(att_min, a.cfl * dh);
               }
             } else {
 #pragma unroll
@@ -784,6 +834,7 @@ __global__ void __launch_bounds__(NT, MINB) patch_kernel(PatchArgs a) {
             if (tid == 0) s_stg = (st & 1) ^ 1;  // read next in the retry's phase 4
           }
         }
+
         ++retries;
         theta = theta * R(a.retry_factor);
         if (theta < R(a.theta_floor * a.theta0)) theta = R(0);
@@ -797,6 +848,10 @@ __global__ void __launch_bounds__(NT, MINB) patch_kernel(PatchArgs a) {
       if (!a.flux_only) {
         S* out = static_cast<S*>(a.out) + (size_t)p * 5 * kNC;
         for (int c = tid; c < 5 * kNC; c += NT) out[c] = S(__longlong_as_double(0x7ff8000000000000ULL));
+        if constexpr (GATHER == 3) {
+          S* po = static_cast<S*>(a.prim_out) + (size_t)p * 6 * kNC;
+          for (int c = tid; c < 6 * kNC; c += NT) po[c] = S(__longlong_as_double(0x7ff8000000000000ULL));
+        }
       }
     }
     // ---- outputs ----------------------------------------------------------
@@ -892,6 +947,31 @@ __global__ void con2pri_kernel(const typename P::S* cons, typename P::S* prim, i
     prim[3 * stride + i] = W.u[2];
     prim[4 * stride + i] = W.p;
     if (status) status[i] = st;
+  }
+}
+
+// Primitive cache of interior patches: cons [np][5][8^3] -> prim
+// [np][6][8^3] = (rho, U^x, U^y, U^z, p, tau), tau the converged solver
+// variable (conic parameter for TM, htilde for the polytropic EoS); NaN for
+// unphysical cells.
+template <class P, class E = EosTM>
+__global__ void prim_cache_kernel(const typename P::S* cons, typename P::S* prim, int64_t ncell,
+                                  int maxit, int ori, E eos) {
+  using S = typename P::S;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < ncell;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t pt = i / kNC;
+    const int c = int(i - pt * kNC);
+    const S* u = cons + pt * 5 * kNC + c;
+    S* w = prim + pt * 6 * kNC + c;
+    PrimX<S> W;
+    con2pri<P>(u[0], u[kNC], u[2 * kNC], u[3 * kNC], u[4 * kNC], W, maxit, S(0), ori, eos);
+    w[0] = W.rho;
+    w[kNC] = W.u[0];
+    w[2 * kNC] = W.u[1];
+    w[3 * kNC] = W.u[2];
+    w[4 * kNC] = W.p;
+    w[5 * kNC] = W.tau;
   }
 }
 
@@ -1032,6 +1112,9 @@ template <class P> struct Launch {
   static cudaError_t con2pri(const void* cons, void* prim, int64_t n, int64_t stride,
                              int32_t* status, int maxit, int ori, EosArg eos, int grid,
                              cudaStream_t s);
+  // primitive cache of npatch interior patches (prim_cache_kernel)
+  static cudaError_t prim_cache(const void* cons, void* prim, int64_t npatch, int maxit, int ori,
+                                EosArg eos, int grid, cudaStream_t s);
   static cudaError_t cfl(const void* cons, int64_t ncell, double dh, double cfl, int ndim, int mode,
                          int maxit, int ori, EosArg eos, double* partial, int32_t* bad, int grid,
                          cudaStream_t s);

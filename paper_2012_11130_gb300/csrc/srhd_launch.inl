@@ -47,7 +47,8 @@ template <class P, class E> struct VlKernel {
 };
 
 // G: 0 ghosted batch, 1 uniform-grid gather (srhd_advance_uniform), 2 AMR
-// gather (srhd_advance_amr)
+// gather (srhd_advance_amr), 3 uniform-grid gather with primitive cache
+// (srhd_advance_uniform_prim)
 template <class P, int V, int G = 0> struct PatchKernel {
   using S = typename P::S;
   using Cfg = PatchVariant<S, V>;
@@ -66,6 +67,10 @@ template <class P, int V> static cudaError_t setup_variant() {
     e = cudaFuncSetAttribute(PatchKernel<P, V, 2>::fn,
                              cudaFuncAttributeMaxDynamicSharedMemorySize,
                              int(SmemLayout<typename P::S>::bytes));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(PatchKernel<P, V, 3>::fn,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             int(SmemLayout<typename P::S>::bytes));
   return e;
 }
 
@@ -82,6 +87,9 @@ template <class P> cudaError_t Launch<P>::setup() {
                              int(SmemLayout<typename P::S>::bytes));
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(PolyKernel<P, 2>::fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             int(SmemLayout<typename P::S>::bytes));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(PolyKernel<P, 3>::fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              int(SmemLayout<typename P::S>::bytes));
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(VlKernel<P, EosTM>::fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -167,6 +175,7 @@ static cudaError_t launch_patches(const PatchArgs& a, int variant, int poly, int
 template <class P>
 cudaError_t Launch<P>::patches(const PatchArgs& a, int variant, int poly, int grid,
                                cudaStream_t s) {
+  if (a.gather == 3) return launch_patches<P, 3>(a, variant, poly, grid, s);
   if (a.gather == 2) return launch_patches<P, 2>(a, variant, poly, grid, s);
   if (a.gather == 1) return launch_patches<P, 1>(a, variant, poly, grid, s);
   return launch_patches<P, 0>(a, variant, poly, grid, s);
@@ -198,6 +207,22 @@ cudaError_t Launch<P>::con2pri(const void* cons, void* prim, int64_t n, int64_t 
     con2pri_kernel<P, EosTM><<<grid, 256, 0, s>>>(static_cast<const S*>(cons),
                                                   static_cast<S*>(prim), n, stride, status, maxit,
                                                   ori, EosTM{});
+  return cudaGetLastError();
+}
+
+template <class P>
+cudaError_t Launch<P>::prim_cache(const void* cons, void* prim, int64_t npatch, int maxit, int ori,
+                                  EosArg eos, int grid, cudaStream_t s) {
+  using S = typename P::S;
+  const int64_t n = npatch * kNC;
+  if (eos.poly)
+    prim_cache_kernel<P, EosPoly><<<grid, 256, 0, s>>>(static_cast<const S*>(cons),
+                                                       static_cast<S*>(prim), n, maxit, ori,
+                                                       EosPoly{eos.gam});
+  else
+    prim_cache_kernel<P, EosTM><<<grid, 256, 0, s>>>(static_cast<const S*>(cons),
+                                                     static_cast<S*>(prim), n, maxit, ori,
+                                                     EosTM{});
   return cudaGetLastError();
 }
 

@@ -308,6 +308,54 @@ class Context:
             _ptr(patch_status), _stream(stream)), "srhd_advance_uniform")
         return cons_out
 
+    def con2pri_patches(self, cons, prim_out=None, stream=None, prec=None):
+        """Primitive cache of interior patches (srhd_con2pri_patches):
+        cons [np][5][8][8][8] -> [np][6][8][8][8] = (rho, U^x, U^y, U^z, p,
+        tau), NaN for unphysical cells."""
+        _need_cuda(cons, "cons")
+        n = cons.shape[0]
+        if prim_out is None:
+            prim_out = torch.empty((n, 6, 8, 8, 8), dtype=cons.dtype, device=cons.device)
+        _need_cuda(prim_out, "prim_out", cons.dtype)
+        N.check(self._L.srhd_con2pri_patches(self._h, _prec(cons, prec), _ptr(cons), n,
+                                             _ptr(prim_out), _stream(stream)),
+                "srhd_con2pri_patches")
+        return prim_out
+
+    def advance_uniform_prim(self, interior, prim_in, npx, npy, npz, dt_dh, bc=("periodic",) * 3,
+                             p0=0, n=None, cons_out=None, prim_out=None, patch_face_flux=None,
+                             dt_next=None, patch_status=None, stream=None, prec=None):
+        """advance_uniform with the primitive cache (srhd_advance_uniform_prim):
+        the tiles' primitives come from prim_in [np][6][8][8][8] (from
+        con2pri_patches or the previous step's prim_out) and the new state's
+        are written to prim_out. Returns (cons_out, prim_out)."""
+        _need_cuda(interior, "interior")
+        _need_cuda(prim_in, "prim_in", interior.dtype)
+        npatch = npx * npy * npz
+        if n is None:
+            n = npatch - p0
+        if interior.shape[0] != npatch or prim_in.shape[0] != npatch:
+            raise ValueError(f"interior/prim_in must hold the grid's {npatch} patches")
+        if cons_out is None:
+            cons_out = torch.empty((n, 5, 8, 8, 8), dtype=interior.dtype, device=interior.device)
+        if prim_out is None:
+            prim_out = torch.empty((n, 6, 8, 8, 8), dtype=interior.dtype, device=interior.device)
+        _need_cuda(cons_out, "cons_out", interior.dtype)
+        _need_cuda(prim_out, "prim_out", interior.dtype)
+        _need_cuda(dt_dh, "dt_dh", torch.float64)
+        for name, t, dt in (("patch_face_flux", patch_face_flux, interior.dtype),
+                            ("dt_next", dt_next, torch.float64),
+                            ("patch_status", patch_status, torch.int32)):
+            if t is not None:
+                _need_cuda(t, name, dt)
+        code = {"periodic": N.SRHD_BC_PERIODIC, "outflow": N.SRHD_BC_OUTFLOW}
+        bcs = (ctypes.c_int32 * 3)(*[code[b] for b in bc])
+        N.check(self._L.srhd_advance_uniform_prim(
+            self._h, _prec(interior, prec), _ptr(interior), _ptr(prim_in), npx, npy, npz, bcs, p0,
+            n, _ptr(cons_out), _ptr(prim_out), _ptr(patch_face_flux), _ptr(dt_dh), _ptr(dt_next),
+            _ptr(patch_status), _stream(stream)), "srhd_advance_uniform_prim")
+        return cons_out, prim_out
+
     def advance_uniform_host(self, interior, npx, npy, npz, dt, dh, bc=("periodic",) * 3,
                              cons_out=None, patch_status=None, chunks=32, stream=None, prec=None):
         """One step of a uniform grid held in host memory

@@ -101,24 +101,27 @@ def test_vector_stores_aligned(esz, gh):
     assert tile % align == 0 and (te * esz) % align == 0
 
 
-def tile_src(c, gp, dims, bc):
-    """The patch kernel's gather offset of 12^3 tile cell c of grid patch gp."""
+def tile_src(c, gp, dims, bc, nvar=5):
+    """The patch kernel's gather offset of 12^3 tile cell c of grid patch gp
+    in an array [np][nvar][8^3] (nvar 5: the conserved interiors; 6: the
+    primitive cache of srhd_advance_uniform_prim)."""
     npx, npy, npz = dims
     gpx, gpy, gpz = gp % npx, (gp // npx) % npy, gp // (npx * npy)
     gz, gy, gx = c // 144, (c // 12) % 12, c % 12
     qx, lx = ghost_src(gx - 2, gpx, npx, bc[0])
     qy, ly = ghost_src(gy - 2, gpy, npy, bc[1])
     qz, lz = ghost_src(gz - 2, gpz, npz, bc[2])
-    return ((qz * npy + qy) * npx + qx) * 2560 + (lz * 8 + ly) * 8 + lx
+    return ((qz * npy + qy) * npx + qx) * (nvar * 512) + (lz * 8 + ly) * 8 + lx
 
 
+@pytest.mark.parametrize("nvar", [5, 6])
 @pytest.mark.parametrize("dims,bc", [((3, 2, 4), (0, 0, 0)), ((3, 2, 4), (1, 0, 1)),
                                      ((1, 1, 1), (0, 1, 0))])
-def test_gather_offsets_match_padding(dims, bc):
+def test_gather_offsets_match_padding(dims, bc, nvar):
     npx, npy, npz = dims
     rng = np.random.default_rng(3)
-    field = rng.normal(size=(5, 8 * npz, 8 * npy, 8 * npx))
-    flat = field.reshape(5, npz, 8, npy, 8, npx, 8).transpose(1, 3, 5, 0, 2, 4, 6).reshape(-1)
+    field = rng.normal(size=(nvar, 8 * npz, 8 * npy, 8 * npx))
+    flat = field.reshape(nvar, npz, 8, npy, 8, npx, 8).transpose(1, 3, 5, 0, 2, 4, 6).reshape(-1)
     padded = field
     for ax, b in zip((3, 2, 1), bc):
         pads = [(0, 0)] * 4
@@ -127,11 +130,12 @@ def test_gather_offsets_match_padding(dims, bc):
     for gp in range(npx * npy * npz):
         px, py, pz = gp % npx, (gp // npx) % npy, gp // (npx * npy)
         want = padded[:, 8 * pz:8 * pz + 12, 8 * py:8 * py + 12, 8 * px:8 * px + 12]
-        off = np.array([tile_src(c, gp, dims, bc) for c in range(1728)])
-        assert off.min() >= 0 and off.max() + 4 * 512 < flat.size
-        for v in range(5):
+        off = np.array([tile_src(c, gp, dims, bc, nvar) for c in range(1728)])
+        assert off.min() >= 0 and off.max() + (nvar - 1) * 512 < flat.size
+        for v in range(nvar):
             assert np.array_equal(flat[off + v * 512], want[v].reshape(-1))
-        # the interior cells' own offsets (phase 4) are gp*2560 + c
+        # the interior cells' own offsets (phase 4) are gp*nvar*512 + c
         for c in (0, 7, 63, 511):
             i, j, k = c & 7, (c >> 3) & 7, c >> 6
-            assert tile_src(((k + 2) * 12 + j + 2) * 12 + i + 2, gp, dims, bc) == gp * 2560 + c
+            assert (tile_src(((k + 2) * 12 + j + 2) * 12 + i + 2, gp, dims, bc, nvar)
+                    == gp * nvar * 512 + c)
