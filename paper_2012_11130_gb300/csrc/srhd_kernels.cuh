@@ -412,7 +412,21 @@ __global__ void __launch_bounds__(NT, MINB) patch_kernel(PatchArgs a) {
   const int ori = a.ori;
   const E eos = make_eos<E>(a);
 
-  double dt_min = DBL_MAX;
+  // Limiter constants of the launch and the step factors of the current
+  // patch in the arithmetic type, converted by one thread: per-thread double
+  // arithmetic would queue every warp of the float kernels on the FP64 pipe
+  // (1/64 of the FP32 rate) and keep doubles in registers through the phases.
+  __shared__ R s_kc[3];     // theta0, retry_factor, theta_floor * theta0
+  __shared__ R s_pc[3];     // dt/dh, dt/(2 dh), C dh (of the current patch)
+  __shared__ double s_dtl;  // light-speed CFL mode: min of C dh over the CTA's patches
+  if (tid == 0) {
+    s_kc[0] = R(a.theta0);
+    s_kc[1] = R(a.retry_factor);
+    s_kc[2] = R(a.theta_floor * a.theta0);
+    s_dtl = DBL_MAX;
+  }
+  constexpr R kRMax = sizeof(R) == 4 ? R(FLT_MAX) : R(DBL_MAX);
+  R dtr = kRMax;  // signal-speed CFL mode: min of C dh / S_max (this thread's cells)
   int cfl_bad = 0;
 
   // Ghosted batch: while a patch is updated (phase 4) the copy engine brings
@@ -526,7 +540,6 @@ __global__ void __launch_bounds__(NT, MINB) patch_kernel(PatchArgs a) {
       if constexpr (GATHER == 1 || GATHER == 3) return in[v * kNC + c];
       else return in[v * kGC + tc];
     };
-    const double dt = a.dt_dh[2 * p], dh = a.dt_dh[2 * p + 1];
     int code = 0;
 
     if constexpr (GATHER == 2) {
@@ -603,6 +616,17 @@ __global__ void __launch_bounds__(NT, MINB) patch_kernel(PatchArgs a) {
         hts[c] = S(W.tau);
       }
     }
+    // the last thread, which has the least phase-1 work, converts the step
+    // factors of the patch (read after the barrier; the previous patch's
+    // readers are past its final barrier)
+    if (tid == NT - 1) {
+      const double dt = a.dt_dh[2 * p], dh = a.dt_dh[2 * p + 1];
+      const R coef = R(dt) / R(dh);
+      s_pc[0] = coef;
+      s_pc[1] = R(0.5) * coef;
+      s_pc[2] = R(a.cfl * dh);
+      if (a.partial_dt && a.cfl_mode == 1) s_dtl = fmin(s_dtl, a.cfl * dh);
+    }
     const int bad_input = __syncthreads_or(code & CODE_BAD_INPUT);
     if constexpr (GATHER == 0) {
       if (stage_ok()) {
@@ -616,15 +640,10 @@ __global__ void __launch_bounds__(NT, MINB) patch_kernel(PatchArgs a) {
 
     int retries = 0;
     int final_code = 0;
-    double att_min = DBL_MAX;   // light-speed mode: C dh
     R att_smax = R(0);          // signal mode: largest S_max of the attempt
     int att_bad = 0;
     if (!bad_input) {
-      R theta = R(a.theta0);
-      // dt/dh in the arithmetic type (a double division per thread and patch
-      // would occupy the FP64 pipe of the float kernels)
-      const R coef = R(dt) / R(dh);
-      const R half = R(0.5) * coef;
+      R theta = s_kc[0];
       for (;;) {
         // ---- phase 2: reconstruction + Hancock half step --------------------
         int fail = 0;
@@ -640,6 +659,7 @@ __global__ void __launch_bounds__(NT, MINB) patch_kernel(PatchArgs a) {
           W.u[2] = R(prim[3 * kGC + tc]);
           W.p = R(prim[4 * kGC + tc]);
           R dF[5] = {R(0), R(0), R(0), R(0), R(0)};
+          const R half = s_pc[1];
           recon_direction<0>(prim, tc, W, theta, i, j, k, interior, face, dF, fail, ori, eos);
           recon_direction<1>(prim, tc, W, theta, i, j, k, interior, face, dF, fail, ori, eos);
           recon_direction<2>(prim, tc, W, theta, i, j, k, interior, face, dF, fail, ori, eos);
@@ -664,7 +684,6 @@ __global__ void __launch_bounds__(NT, MINB) patch_kernel(PatchArgs a) {
         }
         const bool last = (theta == R(0));
         // ---- phase 4: conservative update ----------------------------------
-        att_min = DBL_MAX;
         att_smax = R(0);
         att_bad = 0;
         if (!fail || last) {
@@ -698,6 +717,7 @@ __global__ void __launch_bounds__(NT, MINB) patch_kernel(PatchArgs a) {
           // The primitive cache converts it in any case, for prim_out.
           const bool signal = (a.partial_dt && a.cfl_mode != 1) || GATHER == 3;
           for (int c0 = tid; c0 < kItems; c0 += NT) {
+            const R coef = s_pc[0];
             S Un[NPC][5];
             S g0[NPC];  // tau of the cell before the step: warm start of the CFL solve
             if constexpr (PAIR && sizeof(R) == 4) {
@@ -808,7 +828,6 @@ __global__ void __launch_bounds__(NT, MINB) patch_kernel(PatchArgs a) {
                   po[4 * kNC + c] = S(W[q].p);
                   po[5 * kNC + c] = S(W[q].tau);
                 }
-                if (a.partial_dt && a.cfl_mode == 1) att_min = fmin(att_min, a.cfl * dh);
               }
             } else {
 #pragma unroll
@@ -817,7 +836,6 @@ __global__ void __launch_bounds__(NT, MINB) patch_kernel(PatchArgs a) {
                 if (!A_and_m2<P>(Un[q][0], Un[q][1], Un[q][2], Un[q][3], Un[q][4], Ac, m2c, ori))
                   fail4 = 1;
               }
-              if (a.partial_dt) att_min = fmin(att_min, a.cfl * dh);
             }
           }
           fail = __syncthreads_or(fail4) | fail;
@@ -836,11 +854,10 @@ __global__ void __launch_bounds__(NT, MINB) patch_kernel(PatchArgs a) {
         }
 
         ++retries;
-        theta = theta * R(a.retry_factor);
-        if (theta < R(a.theta_floor * a.theta0)) theta = R(0);
+        theta = theta * s_kc[1];
+        if (theta < s_kc[2]) theta = R(0);
       }
-      if (att_smax > R(0)) att_min = fmin(att_min, double(R(a.cfl * dh) / att_smax));
-      dt_min = fmin(dt_min, att_min);
+      if (att_smax > R(0)) dtr = fmin(dtr, s_pc[2] / att_smax);
       cfl_bad |= att_bad;
     } else {
       final_code |= CODE_BAD_INPUT;
@@ -892,13 +909,16 @@ __global__ void __launch_bounds__(NT, MINB) patch_kernel(PatchArgs a) {
   // ---- CFL partial minimum of this CTA -------------------------------------
   if (a.partial_dt) {
     for (int o = 16; o > 0; o >>= 1) {
-      dt_min = fmin(dt_min, __shfl_xor_sync(0xffffffffu, dt_min, o));
+      dtr = fmin(dtr, __shfl_xor_sync(0xffffffffu, dtr, o));
       cfl_bad |= __shfl_xor_sync(0xffffffffu, cfl_bad, o);
     }
-    if ((tid & 31) == 0) { s_red[tid >> 5] = dt_min; s_bad[tid >> 5] = cfl_bad; }
+    if ((tid & 31) == 0) {
+      s_red[tid >> 5] = dtr < kRMax ? double(dtr) : DBL_MAX;
+      s_bad[tid >> 5] = cfl_bad;
+    }
     __syncthreads();
     if (tid == 0) {
-      double m = DBL_MAX;
+      double m = s_dtl;
       int b = 0;
       for (int q = 0; q < NT / 32; ++q) { m = fmin(m, s_red[q]); b |= s_bad[q]; }
       a.partial_dt[blockIdx.x] = m;
