@@ -221,13 +221,24 @@ __global__ void __launch_bounds__(NT, MINB) vl_patch_kernel(PatchArgs a) {
   const int maxit = a.maxit;
   const int ori = a.ori;
   const E eos = make_eos<E>(a);
-  double dt_min = DBL_MAX;
+  // limiter constants and per-patch step factors in the arithmetic type,
+  // converted by one thread (as in patch_kernel)
+  __shared__ R s_kc[3];     // theta0, retry_factor, theta_floor * theta0
+  __shared__ R s_pc[3];     // dt/dh, dt/(2 dh), C dh (of the current patch)
+  __shared__ double s_dtl;  // light-speed CFL mode: min of C dh over the CTA's patches
+  if (tid == 0) {
+    s_kc[0] = R(a.theta0);
+    s_kc[1] = R(a.retry_factor);
+    s_kc[2] = R(a.theta_floor * a.theta0);
+    s_dtl = DBL_MAX;
+  }
+  constexpr R kRMax = sizeof(R) == 4 ? R(FLT_MAX) : R(DBL_MAX);
+  R dtr = kRMax;  // signal-speed CFL mode: min of C dh / S_max (this thread's cells)
   int cfl_bad = 0;
 
   for (int w = blockIdx.x; w < a.npatch; w += gridDim.x) {
     const int p = a.worklist ? a.worklist[w] : w;
     const S* in = static_cast<const S*>(a.in) + (size_t)p * 5 * kVTC;
-    const double dt = a.dt_dh[2 * p], dh = a.dt_dh[2 * p + 1];
     int code = 0;
     __syncthreads();  // the previous patch is done with shared memory
     // ---- phase 1: W^n on N --------------------------------------------------
@@ -254,10 +265,17 @@ __global__ void __launch_bounds__(NT, MINB) vl_patch_kernel(PatchArgs a) {
       Wn[3 * kVTC + cb] = Wb.u[2]; Wn[4 * kVTC + cb] = Wb.p;
     }
     for (int q = tid; q < 5 * kVH; q += NT) Wh[q] = S(0);
+    if (tid == NT - 1) {
+      const double dt = a.dt_dh[2 * p], dh = a.dt_dh[2 * p + 1];
+      const R coef = R(dt) / R(dh);
+      s_pc[0] = coef;
+      s_pc[1] = R(0.5) * coef;
+      s_pc[2] = R(a.cfl * dh);
+      if (a.partial_dt && a.cfl_mode == 1) s_dtl = fmin(s_dtl, a.cfl * dh);
+    }
     const int bad_input = __syncthreads_or(code & CODE_BAD_INPUT);
     int retries = 0;
     int final_code = 0;
-    double att_min = DBL_MAX;
     R att_smax = R(0);
     int att_bad = 0;
     bool nan_out = bad_input != 0;
@@ -267,8 +285,7 @@ __global__ void __launch_bounds__(NT, MINB) vl_patch_kernel(PatchArgs a) {
       vl_predict_dir<1, P, E, NT>(in, Wn, Fs, Wh, a.riemann, ori, eos);
       vl_predict_dir<2, P, E, NT>(in, Wn, Fs, Wh, a.riemann, ori, eos);
       // ---- phase 3: half-step state and its primitives ---------------------
-      const R coef = R(dt) / R(dh);
-      const R half = R(0.5) * coef;
+      const R half = s_pc[1];
       int pbad = 0;
       for (int r = tid; r < kVH / 2; r += NT) {
         int i, j, k;
@@ -301,7 +318,7 @@ __global__ void __launch_bounds__(NT, MINB) vl_patch_kernel(PatchArgs a) {
         nan_out = true;
         att_bad = 1;
       } else {
-        R theta = R(a.theta0);
+        R theta = s_kc[0];
         for (;;) {
           // ---- phase 4: corrector fluxes ------------------------------------
           int fail = 0;
@@ -348,7 +365,6 @@ __global__ void __launch_bounds__(NT, MINB) vl_patch_kernel(PatchArgs a) {
           }
           const bool last = (theta == R(0));
           // ---- phase 5: conservative update ---------------------------------
-          att_min = DBL_MAX;
           att_smax = R(0);
           att_bad = 0;
           if (!fail || last) {
@@ -356,6 +372,7 @@ __global__ void __launch_bounds__(NT, MINB) vl_patch_kernel(PatchArgs a) {
             const bool signal = a.partial_dt && a.cfl_mode != 1;
             int fail5 = 0;
             for (int c = tid; c < kNC; c += NT) {
+              const R coef = s_pc[0];
               const int i = c & 7, j = (c >> 3) & 7, k = c >> 6;
               const int tc = vl_t14(i, j, k);
               const int fx0 = face_index<0>(i, j, k, i), fx1 = face_index<0>(i, j, k, i + 1);
@@ -384,7 +401,6 @@ __global__ void __launch_bounds__(NT, MINB) vl_patch_kernel(PatchArgs a) {
               } else {
                 typename P::AT Ac, m2c;
                 if (!A_and_m2<P>(Un[0], Un[1], Un[2], Un[3], Un[4], Ac, m2c, ori)) fail5 = 1;
-                if (a.partial_dt) att_min = fmin(att_min, a.cfl * dh);
               }
             }
             fail = __syncthreads_or(fail5) | fail;
@@ -392,12 +408,11 @@ __global__ void __launch_bounds__(NT, MINB) vl_patch_kernel(PatchArgs a) {
           if (!fail) break;
           if (last) { final_code |= CODE_UNPHYSICAL; break; }
           ++retries;
-          theta = theta * R(a.retry_factor);
-          if (theta < R(a.theta_floor * a.theta0)) theta = R(0);
+          theta = theta * s_kc[1];
+          if (theta < s_kc[2]) theta = R(0);
         }
       }
-      if (att_smax > R(0)) att_min = fmin(att_min, double(R(a.cfl * dh) / att_smax));
-      dt_min = fmin(dt_min, att_min);
+      if (att_smax > R(0)) dtr = fmin(dtr, s_pc[2] / att_smax);
       cfl_bad |= att_bad;
     } else {
       final_code |= CODE_BAD_INPUT;
@@ -436,13 +451,16 @@ __global__ void __launch_bounds__(NT, MINB) vl_patch_kernel(PatchArgs a) {
   // ---- CFL partial minimum of this CTA ---------------------------------------
   if (a.partial_dt) {
     for (int o = 16; o > 0; o >>= 1) {
-      dt_min = fmin(dt_min, __shfl_xor_sync(0xffffffffu, dt_min, o));
+      dtr = fmin(dtr, __shfl_xor_sync(0xffffffffu, dtr, o));
       cfl_bad |= __shfl_xor_sync(0xffffffffu, cfl_bad, o);
     }
-    if ((tid & 31) == 0) { s_red[tid >> 5] = dt_min; s_bad[tid >> 5] = cfl_bad; }
+    if ((tid & 31) == 0) {
+      s_red[tid >> 5] = dtr < kRMax ? double(dtr) : DBL_MAX;
+      s_bad[tid >> 5] = cfl_bad;
+    }
     __syncthreads();
     if (tid == 0) {
-      double m = DBL_MAX;
+      double m = s_dtl;
       int b = 0;
       for (int q = 0; q < NT / 32; ++q) { m = fmin(m, s_red[q]); b |= s_bad[q]; }
       a.partial_dt[blockIdx.x] = m;
