@@ -442,6 +442,17 @@ srhd_status srhd_advance_uniform_host(srhd_ctx* ctx, srhd_prec prec, const void*
                                       const int32_t* bc, double dt, double dh, double* dt_next,
                                       int32_t* patch_status, int32_t chunks, void* stream);
 
+/* The double-precision reciprocal that the FP64 arithmetic of the kernels
+ * uses for its quotients (the paper has no counterpart: it fixes the
+ * precision of the arithmetic, not how a division is evaluated): the
+ * hardware approximation refined by two Newton-Raphson steps, within about
+ * one ulp of the IEEE reciprocal; zero, subnormal, |x| >= 2^1021 and
+ * non-finite x give the IEEE result exactly. Exported so that its error can
+ * be checked on the device.
+ *   x, y: device arrays of n >= 0 doubles (y may be x); no context, no
+ *   allocation; asynchronous on stream. */
+srhd_status srhd_reciprocal_f64(const double* x, double* y, int64_t n, void* stream);
+
 /* CFL time step of a batch of interior patches, like srhd_cfl_dt, for
  * callers that cannot allocate device memory. (The paper has no counterpart:
  * this is a deployment variant of srhd_cfl_dt.) Some callers cannot call

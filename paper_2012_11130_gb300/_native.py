@@ -30,7 +30,7 @@ EXPORTS = ("srhd_default_params", "srhd_create", "srhd_destroy", "srhd_last_erro
            "srhd_advance_patches_vl", "srhd_fill_ghosts_uniform3",
            "srhd_fill_ghosts_uniform_range", "srhd_advance_uniform_host",
            "srhd_advance_uniform", "srhd_advance_amr", "srhd_con2pri_patches",
-           "srhd_advance_uniform_prim")
+           "srhd_advance_uniform_prim", "srhd_reciprocal_f64")
 SRHD_AMR_COARSE = 1 << 30
 
 
@@ -94,6 +94,8 @@ def load(path: str = LIB_PATH):
     L.srhd_advance_uniform_prim.restype = st
     L.srhd_advance_uniform_prim.argtypes = [vp, ctypes.c_int, vp, vp, i32, i32, i32, i32p, i32,
                                             i32, vp, vp, vp, vp, vp, vp, vp]
+    L.srhd_reciprocal_f64.restype = st
+    L.srhd_reciprocal_f64.argtypes = [vp, vp, i64, vp]
     L.srhd_advance_amr.restype = st
     L.srhd_advance_amr.argtypes = [vp, ctypes.c_int, vp, vp, vp, vp, i32, ctypes.c_double, vp,
                                    i32, vp, vp, i32, vp, vp, vp, vp, vp]

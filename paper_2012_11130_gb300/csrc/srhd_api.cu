@@ -597,6 +597,24 @@ srhd_status srhd_advance_patches_vl(srhd_ctx* c, srhd_prec prec, const void* con
   return launch_patches(c, prec, a, dt_next, static_cast<cudaStream_t>(stream), true);
 }
 
+namespace {
+__global__ void reciprocal_f64_kernel(const double* x, double* y, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = srhd::drcp(x[i]);
+}
+}  // namespace
+
+srhd_status srhd_reciprocal_f64(const double* x, double* y, int64_t n, void* stream) {
+  if (n < 0) return fail(SRHD_ERR_ARG, "n < 0");
+  if (n == 0) return SRHD_OK;
+  if (!x || !y) return fail(SRHD_ERR_ARG, "x/y is NULL");
+  const int64_t blocks = std::min<int64_t>((n + 255) / 256, 4096);
+  reciprocal_f64_kernel<<<int(blocks), 256, 0, static_cast<cudaStream_t>(stream)>>>(x, y, n);
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? SRHD_OK : cuda_fail(e, "reciprocal launch");
+}
+
 srhd_status srhd_cfl_dt(srhd_ctx* c, srhd_prec prec, const void* cons, int32_t npatch, double dh,
                         double* dt_out, void* stream) {
   srhd_status st = check_ctx(c);

@@ -46,15 +46,39 @@ template <> struct NewtonCfg<float> {
 __device__ __forceinline__ float rsqrt_r(float x) { return rsqrtf(x); }
 __device__ __forceinline__ double rsqrt_r(double x) { return rsqrt(x); }
 
+// Reciprocal in double by Newton-Raphson refinement of the hardware
+// approximation (rcp.approx.ftz.f64): each step r <- r + r (1 - x r) squares
+// the relative error, and the approximation is good to about 2^-20 or better, so two
+// steps leave only the rounding of the last fused multiply-add (the result
+// is within about one ulp of 1/x; tests/test_gpu_fast_rcp.py bounds it
+// against the IEEE division). The IEEE division is several times longer on
+// the FP64 pipe, which bounds the FP64 kernels. Zero, subnormal, huge
+// (|x| >= 2^1021, whose reciprocal is subnormal) and non-finite x take the
+// IEEE division, so those keep its results exactly.
+__device__ __forceinline__ double drcp(double x) {
+  const int ex = (__double2hiint(x) >> 20) & 0x7ff;
+  if (ex == 0 || ex >= 0x7fd) return 1.0 / x;
+  double r;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
+  double e = fma(-x, r, 1.0);
+  r = fma(r, e, r);
+  e = fma(-x, r, 1.0);
+  return fma(r, e, r);
+}
+
 // Quotient and reciprocal in the arithmetic type. In float they are the
 // hardware approximate division (at most 2 ulp, like the '/' operator under
 // -prec-div=false, but without its range scaling: valid for divisors of
 // magnitude below 2^126, which every denominator they are used on stays far
-// below); in double they are the IEEE operations.
+// below); in double the product with drcp (within about two ulp).
 __device__ __forceinline__ float qdiv(float a, float b) { return __fdividef(a, b); }
-__device__ __forceinline__ double qdiv(double a, double b) { return a / b; }
+__device__ __forceinline__ double qdiv(double a, double b) { return a * drcp(b); }
 __device__ __forceinline__ float qrcp(float b) { return __fdividef(1.0f, b); }
-__device__ __forceinline__ double qrcp(double b) { return 1.0 / b; }
+__device__ __forceinline__ double qrcp(double b) { return drcp(b); }
+// The '/' operator in float (the full-range approximate division under
+// -prec-div=false), qdiv in double.
+__device__ __forceinline__ float fdiv(float a, float b) { return a / b; }
+__device__ __forceinline__ double fdiv(double a, double b) { return qdiv(a, b); }
 
 // Primitive state with the derived quantities reused downstream.
 template <class R> struct PrimX {
@@ -95,10 +119,10 @@ __device__ __forceinline__ void eos_ht(const EosPoly& e, R T, R& ht, R& hmT) {
 // Sound speed squared. TM: Eq. (sound_speed), c_s^2 = T (5h - 8T) / (3h (h - T)).
 // Polytropic: Gamma T / h.
 template <class R> __device__ __forceinline__ R cs2_of(const EosTM&, R T, R h) {
-  return T * (R(5) * h - R(8) * T) / (R(3) * h * (h - T));
+  return fdiv(T * (R(5) * h - R(8) * T), R(3) * h * (h - T));
 }
 template <class R> __device__ __forceinline__ R cs2_of(const EosPoly& e, R T, R h) {
-  return R(e.gam) * T / h;
+  return fdiv(R(e.gam) * T, h);
 }
 
 // Packed FP32: the sm_100 family executes an add, a multiply or a fused
@@ -244,7 +268,7 @@ struct PrecMixedCF {  // SRHD_MIXED_CF: float, A by a compensated float sum
 template <class S>
 __device__ __forceinline__ double A_of_cons(S D, S Mx, S My, S Mz, S Et, double& m2,
                                             int ori = 0) {
-  double rD = 1.0 / double(D);
+  double rD = drcp(double(D));
   double eD = double(Et) * rD;
   double M2 = double(Mx) * double(Mx) + double(My) * double(My) + double(Mz) * double(Mz);
   m2 = M2 * rD * rD;
@@ -393,7 +417,7 @@ __device__ __forceinline__ void prims_from_tau(S D, S Mx, S My, S Mz, R tau, Pri
   const R r3t = qrcp(R(3) * (R(1) + tau));
   const R ht = tau * (R(5) + R(4) * tau) * r3t;
   const R h = R(1) + ht;
-  const R rDh = R(1) / (R(D) * h);
+  const R rDh = fdiv(R(1), R(D) * h);
   W.u[0] = R(Mx) * rDh;
   W.u[1] = R(My) * rDh;
   W.u[2] = R(Mz) * rDh;
@@ -440,7 +464,7 @@ template <class R, class S>
 __device__ __forceinline__ void prims_from_ht_poly(S D, S Mx, S My, S Mz, R ht, R k,
                                                    PrimX<R>& W) {
   const R h = R(1) + ht;
-  const R rDh = R(1) / (R(D) * h);
+  const R rDh = fdiv(R(1), R(D) * h);
   W.u[0] = R(Mx) * rDh;
   W.u[1] = R(My) * rDh;
   W.u[2] = R(Mz) * rDh;
