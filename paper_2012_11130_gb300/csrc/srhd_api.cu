@@ -8,6 +8,8 @@
 #include <cstring>
 #include <new>
 
+#include <cudaTypedefs.h>
+
 #include "srhd.h"
 #include "srhd_amr.cuh"
 #include "srhd_kernels.cuh"
@@ -412,6 +414,47 @@ static void fill_common(const srhd_ctx* c, srhd_prec prec, srhd::PatchArgs& a) {
   a.amr_ncells = 0;
   a.amr_w = 0.0;
   a.amr_nspecial = 0;
+  a.tma = 0;
+}
+
+// cuTensorMapEncodeTiled of the driver, looked up once through the runtime
+// (the library does not link libcuda); NULL if the driver lacks it.
+static PFN_cuTensorMapEncodeTiled_v12000 encode_tiled() {
+  static const PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault,
+                                         &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      f = nullptr;
+    return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+  }();
+  return fn;
+}
+
+// Tensor maps of a uniform grid's interior array [np][5][8][8][8], viewed as
+// a 5-D tensor (x, y, z, var, patch), with the boxes of the staged gather
+// (PatchArgs::tmap: interior, x, y and z face slabs). False when they cannot
+// be made (no driver entry point, an address not 16-byte aligned, a refused
+// encoding); the kernel then gathers every tile with plain loads.
+static bool uniform_tmaps(srhd_prec prec, const void* interior, int64_t np, CUtensorMap (&m)[4]) {
+  const auto fn = encode_tiled();
+  if (!fn || (reinterpret_cast<uintptr_t>(interior) & 15) != 0 || np < 1 || np > 0xffffffffLL)
+    return false;
+  const cuuint64_t es = prec == SRHD_FP64 ? 8 : 4;
+  const CUtensorMapDataType dt =
+      prec == SRHD_FP64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+  const cuuint64_t dims[5] = {8, 8, 8, 5, cuuint64_t(np)};
+  const cuuint64_t strides[4] = {8 * es, 64 * es, 512 * es, 2560 * es};  // bytes, dims 1..4
+  const cuuint32_t boxes[4][5] = {{8, 8, 8, 5, 1}, {4, 8, 8, 5, 1}, {8, 2, 8, 5, 1},
+                                  {8, 8, 2, 5, 1}};
+  const cuuint32_t unit[5] = {1, 1, 1, 1, 1};
+  for (int k = 0; k < 4; ++k)
+    if (fn(&m[k], dt, 5, const_cast<void*>(interior), dims, strides, boxes[k], unit,
+           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+           CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return false;
+  return true;
 }
 
 srhd_status srhd_flux_patches(srhd_ctx* c, srhd_prec prec, const void* cons_ghosted,
@@ -473,10 +516,16 @@ static srhd_status check_bc(const int32_t* bc) {
 
 // The fused step of srhd_advance_patches on patches p0 .. p0+n-1 of a uniform
 // grid, reading each 12^3 tile from the grid (gather mode of patch_kernel).
+// maps (nullable): tensor maps of `interior` from uniform_tmaps, for the
+// staged gather.
 static void gather_args(const srhd_ctx* c, srhd_prec prec, srhd::PatchArgs& a,
                         const void* interior, int32_t npx, int32_t npy, int32_t npz,
-                        const int32_t* bc, int64_t p0) {
+                        const int32_t* bc, int64_t p0, const CUtensorMap* maps = nullptr) {
   fill_common(c, prec, a);
+  if (maps) {
+    for (int k = 0; k < 4; ++k) a.tmap[k] = maps[k];
+    a.tma = 1;
+  }
   a.in = interior;
   a.gather = 1;
   a.gnx = npx;
@@ -511,7 +560,9 @@ srhd_status srhd_advance_uniform(srhd_ctx* c, srhd_prec prec, const void* interi
     return fail(SRHD_ERR_ARG, "interior/cons_out/dt_dh is NULL");
   if (n == 0 && !dt_next) return SRHD_OK;
   srhd::PatchArgs a;
-  gather_args(c, prec, a, interior, npx, npy, npz, bc, p0);
+  CUtensorMap maps[4];
+  const bool tma = n > 0 && uniform_tmaps(prec, interior, np, maps);
+  gather_args(c, prec, a, interior, npx, npy, npz, bc, p0, tma ? maps : nullptr);
   a.out = cons_out;
   a.pflux = patch_face_flux;
   a.npatch = n;
@@ -966,6 +1017,8 @@ srhd_status srhd_advance_uniform_host(srhd_ctx* c, srhd_prec prec, const void* h
   // Chunk k steps on compute stream k % 2 with CFL scratch k % 2 (its tiles
   // gathered from the grid copy), so that a launch's last partly filled wave
   // overlaps the next chunk's launch.
+  CUtensorMap maps[4];
+  const bool tma = uniform_tmaps(prec, u.in, np, maps);
   for (int k = 0; k < K && e == cudaSuccess; ++k) {
     const int par = k & 1;
     cudaStream_t comp = u.s[1 + par];
@@ -977,7 +1030,7 @@ srhd_status srhd_advance_uniform_host(srhd_ctx* c, srhd_prec prec, const void* h
     if (e != cudaSuccess) break;
     const int64_t a = z0[k] * slab, n = (z0[k + 1] - z0[k]) * slab;
     srhd::PatchArgs pa;
-    gather_args(c, prec, pa, u.in, npx, npy, npz, bc, a);
+    gather_args(c, prec, pa, u.in, npx, npy, npz, bc, a, tma ? maps : nullptr);
     pa.out = static_cast<char*>(u.out) + a * pbytes;
     pa.pflux = nullptr;
     pa.npatch = int32_t(n);

@@ -22,6 +22,7 @@
 
 #include <cfloat>
 #include <cstdint>
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include "srhd_amr.cuh"
@@ -62,6 +63,12 @@ struct PatchArgs {
   // from that patch and its neighbours (gbc*: 0 periodic, 1 outflow).
   int gather, gnx, gny, gnz, gbcx, gbcy, gbcz;
   int64_t gp0;
+  // gather = 1 with tma = 1: tmap holds 5-D tensor maps of `in` viewed as
+  // [patch][var][z][y][x], with boxes (x, y, z, var, patch) of a patch
+  // interior (8, 8, 8, 5, 1) and of its x (4, 8, 8, 5, 1), y (8, 2, 8, 5, 1)
+  // and z (8, 8, 2, 5, 1) face slabs (kTmapCenter .. kTmapZ).
+  int tma;
+  CUtensorMap tmap[4];
   // Uniform-grid gather with primitive cache (gather = 3): as gather = 1,
   // but the tile's primitives and solver variable come from prim_in
   // [.][6][8^3] (rho, U^x, U^y, U^z, p, tau of every grid patch) instead of
@@ -109,6 +116,18 @@ __device__ __forceinline__ void copy(void* dst, const void* src, uint32_t bytes,
       "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
           "r"(saddr(dst)),
       "l"(src), "r"(bytes), "r"(saddr(mbar))
+      : "memory");
+}
+// Tensor copy of the box at coordinates (x, y, z, v, p) of the 5-D map into
+// shared memory (128-byte aligned), completing on mbar. x * element size
+// must be a multiple of 16 bytes.
+__device__ __forceinline__ void copy_box(void* dst, const CUtensorMap* map, int x, int y, int z,
+                                         int v, int p, uint64_t* mbar) {
+  asm volatile(
+      "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4, %5, %6}], [%7];" ::"r"(saddr(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(v), "r"(p),
+      "r"(saddr(mbar))
       : "memory");
 }
 // Wait for the completion of the barrier phase of this parity; false if it
@@ -254,6 +273,56 @@ template <class S> __device__ __forceinline__ S* face_slot(S* face, int d, int s
 constexpr int kStageOffset = 3 * 5 * kNF;  // first right-state slot
 static_assert(5 * kGC == 3 * 5 * kNF, "a ghosted tile fills the right-state slots");
 
+// Uniform-grid tiles staged by tensor copies (gather mode 1): the patch
+// interior and its six face slabs, five variables each, as dense boxes in
+// the stage (x fastest): centre [5][8][8][8], then -x and +x [5][8][8][4]
+// (neighbour x 4..7 and 0..3: rows of 16 bytes), -y and +y [5][8][2][8]
+// (neighbour y 6..7 and 0..1), -z and +z [5][2][8][8]. Every box starts on
+// a 128-byte boundary. The 96 first-layer edge cells of the tile are not
+// staged.
+enum { kTmapCenter = 0, kTmapX = 1, kTmapY = 2, kTmapZ = 3 };
+constexpr int kBoxC = 8 * 8 * 8 * 5;
+constexpr int kBoxX = 4 * 8 * 8 * 5;
+constexpr int kBoxY = 8 * 2 * 8 * 5;
+constexpr int kBoxZ = 8 * 8 * 2 * 5;
+constexpr int kBoxXm = kBoxC, kBoxXp = kBoxXm + kBoxX, kBoxYm = kBoxXp + kBoxX,
+              kBoxYp = kBoxYm + kBoxY, kBoxZm = kBoxYp + kBoxY, kBoxZp = kBoxZm + kBoxZ;
+constexpr int kBoxTotal = kBoxZp + kBoxZ;  // 7680
+static_assert(kBoxTotal <= 5 * kGC, "the staged boxes fit the stage");
+static_assert(kBoxC % 32 == 0 && kBoxX % 32 == 0 && kBoxY % 32 == 0 && kBoxZ % 32 == 0,
+              "boxes of 4-byte elements start on 128-byte boundaries");
+
+// Stage offset of variable 0 of tile cell (gx, gy, gz) and the distance
+// between its variables, for a cell in the interior or in one face slab;
+// false for the first-layer edge cells (two coordinates in the ghost zone).
+__device__ __forceinline__ bool box_offset(int gx, int gy, int gz, int& off, int& vstride) {
+  const int ax = gx < 2 ? 0 : (gx < 10 ? 1 : 2);
+  const int ay = gy < 2 ? 0 : (gy < 10 ? 1 : 2);
+  const int az = gz < 2 ? 0 : (gz < 10 ? 1 : 2);
+  const int x = gx - 2, y = gy - 2, z = gz - 2;  // patch-interior coordinates
+  if (ay == 1 && az == 1) {
+    if (ax == 1) {
+      off = (z * 8 + y) * 8 + x;
+      vstride = 512;
+    } else {  // -x slab: gx 0, 1 -> neighbour x 6, 7 -> box x 2, 3; +x: gx 10, 11 -> 0, 1
+      off = (ax == 0 ? kBoxXm + gx + 2 : kBoxXp + gx - 10) + (z * 8 + y) * 4;
+      vstride = 256;
+    }
+    return true;
+  }
+  if (ax == 1 && az == 1) {  // -y slab: gy 0, 1 -> neighbour y 6, 7 -> box y 0, 1
+    off = (ay == 0 ? kBoxYm + gy * 8 : kBoxYp + (gy - 10) * 8) + z * 16 + x;
+    vstride = 128;
+    return true;
+  }
+  if (ax == 1 && ay == 1) {  // -z slab: gz 0, 1 -> box z 0, 1
+    off = (az == 0 ? kBoxZm + gz * 64 : kBoxZp + (gz - 10) * 64) + y * 8 + x;
+    vstride = 128;
+    return true;
+  }
+  return false;
+}
+
 template <int d, class R, class S, class E>
 __device__ __forceinline__ void recon_direction(const S* prim, int tc, const PrimX<R>& W, R theta,
                                                 int i, int j, int k, bool interior, S* face,
@@ -394,11 +463,11 @@ __device__ __forceinline__ int face_flux(typename P::S* face, const typename P::
 // GATHER: 0 ghosted batch (a.in), 1 uniform-grid gather, 2 AMR gather
 // (a.gather must equal it).
 template <class P, int NT, int MINB, bool PAIR, class E = EosTM, int GATHER = 0>
-__global__ void __launch_bounds__(NT, MINB) patch_kernel(PatchArgs a) {
+__global__ void __launch_bounds__(NT, MINB) patch_kernel(const __grid_constant__ PatchArgs a) {
   static_assert(NT % 32 == 0 && NT >= 64 && NT <= 1024, "block size");
   using S = typename P::S;
   using R = S;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   S* prim = reinterpret_cast<S*>(smem_raw);
   S* face = prim + SmemLayout<S>::prim_elems;
   S* hts = face + SmemLayout<S>::face_elems;
@@ -431,7 +500,11 @@ __global__ void __launch_bounds__(NT, MINB) patch_kernel(PatchArgs a) {
 
   // Ghosted batch: while a patch is updated (phase 4) the copy engine brings
   // the CTA's next tile into the right-state face slots (`stage`), where
-  // phase 1 of that patch reads it. Needs 16-byte aligned tiles. s_stg:
+  // phase 1 of that patch reads it. Needs 16-byte aligned tiles. Uniform
+  // grid (gather mode 1 with tensor maps): the same with the seven boxes of
+  // the next patch's tile (box_offset), for patches whose six face
+  // neighbours exist (periodic or interior; other patches, and the first
+  // patch of each CTA, gather with plain loads). s_stg:
   // bit 0 the parity of the s_mbar phase that the next copy completes, bit 1
   // set while a copy is issued and not yet waited for. It is kept in shared
   // memory (read by all threads, written by one between barriers) so that
@@ -440,10 +513,14 @@ __global__ void __launch_bounds__(NT, MINB) patch_kernel(PatchArgs a) {
   [[maybe_unused]] __shared__ __align__(8) uint64_t s_mbar;
   [[maybe_unused]] __shared__ uint32_t s_stg;
   [[maybe_unused]] __shared__ int s_stage_timeout;
+  constexpr bool kStaged = GATHER == 0 || GATHER == 1;
   auto stage_ok = [&]() {
+    // tensor copies need 128-byte aligned destinations (the boxes are laid
+    // out on 128-byte boundaries from `stage`)
+    if constexpr (GATHER == 1) return a.tma != 0 && (bulk::saddr(stage) & 127) == 0;
     return GATHER == 0 && !a.flux_only && (reinterpret_cast<uintptr_t>(a.in) & 15) == 0;
   };
-  if constexpr (GATHER == 0) {
+  if constexpr (kStaged) {
     if (stage_ok() && tid == 0) {
       bulk::init(&s_mbar);
       s_stg = 0;
@@ -516,6 +593,12 @@ __global__ void __launch_bounds__(NT, MINB) patch_kernel(PatchArgs a) {
         if (r < kNC && m != (int32_t)((int64_t)p * kNC + r)) s_nonid = 1;
       } else if constexpr (GATHER == 1) {
         const int gz = c / (kG * kG), gy = (c / kG) % kG, gx = c % kG;
+        int off, vs;
+        if ((st1 & 2) && box_offset(gx, gy, gz, off, vs)) {
+#pragma unroll
+          for (int v = 0; v < 5; ++v) U[v] = stage[off + v * vs];
+          return;
+        }
         int qx, lx, qy, ly, qz, lz;
         ghost_src(gx - 2, gpx, a.gnx, a.gbcx, qx, lx);
         ghost_src(gy - 2, gpy, a.gny, a.gbcy, qy, ly);
@@ -546,7 +629,7 @@ __global__ void __launch_bounds__(NT, MINB) patch_kernel(PatchArgs a) {
       if (tid == 0) s_nonid = 0;
     }
     __syncthreads();  // the previous patch is done with shared memory
-    if constexpr (GATHER == 0) {
+    if constexpr (kStaged) {
       if (stage_ok()) st1 = s_stg;
       if ((st1 & 2) && !bulk::wait(&s_mbar, st1 & 1)) s_stage_timeout = 1;
     }
@@ -628,7 +711,7 @@ __global__ void __launch_bounds__(NT, MINB) patch_kernel(PatchArgs a) {
       if (a.partial_dt && a.cfl_mode == 1) s_dtl = fmin(s_dtl, a.cfl * dh);
     }
     const int bad_input = __syncthreads_or(code & CODE_BAD_INPUT);
-    if constexpr (GATHER == 0) {
+    if constexpr (kStaged) {
       if (stage_ok()) {
         if (s_stage_timeout) {
           stage_abort(p, st1);
@@ -702,6 +785,43 @@ __global__ void __launch_bounds__(NT, MINB) patch_kernel(PatchArgs a) {
 #pragma unroll
                 for (int v = 0; v < 5; ++v)
                   bulk::copy(stage + v * kGC, src + v * kGC, kVarBytes, &s_mbar);
+                s_stg |= 2;  // read next after the phase-4 barrier
+              }
+            }
+          } else if constexpr (GATHER == 1) {
+            // uniform grid: the seven boxes of the CTA's next patch, when its
+            // six face neighbours exist
+            const int wn = w + gridDim.x;
+            if (stage_ok() && wn < a.npatch && tid == NT - 1) {
+              const int64_t qn = a.gp0 + wn;
+              const int cx = int(qn % a.gnx), cy = int((qn / a.gnx) % a.gny);
+              const int cz = int(qn / ((int64_t)a.gnx * a.gny));
+              // neighbour coordinate along an axis of n patches, -1 if none
+              auto nb = [](int c, int n, int bc) {
+                if (c >= 0 && c < n) return c;
+                if (bc != 0) return -1;
+                return c < 0 ? c + n : c - n;
+              };
+              const int xm = nb(cx - 1, a.gnx, a.gbcx), xp = nb(cx + 1, a.gnx, a.gbcx);
+              const int ym = nb(cy - 1, a.gny, a.gbcy), yp = nb(cy + 1, a.gny, a.gbcy);
+              const int zm = nb(cz - 1, a.gnz, a.gbcz), zp = nb(cz + 1, a.gnz, a.gbcz);
+              if ((xm | xp | ym | yp | zm | zp) >= 0) {
+                auto pid = [&](int ix, int iy, int iz) { return (iz * a.gny + iy) * a.gnx + ix; };
+                bulk::fence_before_copy();
+                bulk::expect(&s_mbar, kBoxTotal * sizeof(S));
+                bulk::copy_box(stage, &a.tmap[kTmapCenter], 0, 0, 0, 0, int(qn), &s_mbar);
+                bulk::copy_box(stage + kBoxXm, &a.tmap[kTmapX], 4, 0, 0, 0, pid(xm, cy, cz),
+                               &s_mbar);
+                bulk::copy_box(stage + kBoxXp, &a.tmap[kTmapX], 0, 0, 0, 0, pid(xp, cy, cz),
+                               &s_mbar);
+                bulk::copy_box(stage + kBoxYm, &a.tmap[kTmapY], 0, 6, 0, 0, pid(cx, ym, cz),
+                               &s_mbar);
+                bulk::copy_box(stage + kBoxYp, &a.tmap[kTmapY], 0, 0, 0, 0, pid(cx, yp, cz),
+                               &s_mbar);
+                bulk::copy_box(stage + kBoxZm, &a.tmap[kTmapZ], 0, 0, 6, 0, pid(cx, cy, zm),
+                               &s_mbar);
+                bulk::copy_box(stage + kBoxZp, &a.tmap[kTmapZ], 0, 0, 0, 0, pid(cx, cy, zp),
+                               &s_mbar);
                 s_stg |= 2;  // read next after the phase-4 barrier
               }
             }
@@ -842,7 +962,7 @@ __global__ void __launch_bounds__(NT, MINB) patch_kernel(PatchArgs a) {
         }
         if (!fail) break;
         if (last) { final_code |= CODE_UNPHYSICAL; break; }
-        if constexpr (GATHER == 0) {
+        if constexpr (kStaged) {
           // the retry's phase 2 rewrites the right-state slots: let the copy
           // land first; the next patch then reads its tile from `in`
           const uint32_t st = stage_ok() ? s_stg : 0u;
@@ -890,7 +1010,7 @@ __global__ void __launch_bounds__(NT, MINB) patch_kernel(PatchArgs a) {
       }
     }
     code = __syncthreads_or(code & CODE_NOCONV);
-    if constexpr (GATHER == 0) {
+    if constexpr (kStaged) {
       if (tid == 0 && stage_ok() && s_stage_timeout) {  // a retry's wait ran out
         final_code |= CODE_STAGE_TIMEOUT;
         cfl_bad = 1;
@@ -901,7 +1021,7 @@ __global__ void __launch_bounds__(NT, MINB) patch_kernel(PatchArgs a) {
       a.status[p] = (final_code << 8) | (retries < 255 ? retries : 255);
     }
   }
-  if constexpr (GATHER == 0) {
+  if constexpr (kStaged) {
     // a copy that ran out on the CTA's last patch: wait once more (bounded)
     if (stage_ok() && s_stage_timeout) bulk::wait(&s_mbar, last_copy_parity(s_stg));
   }

@@ -210,7 +210,7 @@ template <class P, int NT, int MINB, class E = EosTM>
 __global__ void __launch_bounds__(NT, MINB) vl_patch_kernel(PatchArgs a) {
   using S = typename P::S;
   using R = S;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   S* Wn = reinterpret_cast<S*>(smem_raw);
   S* Fs = Wn + VlSmem<S>::wn;
   S* Wh = Fs + VlSmem<S>::fs;       // [5][kVH] W* (dU before phase 3), then [kVH] solver variable

@@ -139,3 +139,68 @@ def test_gather_offsets_match_padding(dims, bc, nvar):
             i, j, k = c & 7, (c >> 3) & 7, c >> 6
             assert (tile_src(((k + 2) * 12 + j + 2) * 12 + i + 2, gp, dims, bc, nvar)
                     == gp * nvar * 512 + c)
+
+
+# Staged uniform gather (tensor maps): box layout of the stage and the
+# offsets box_offset gives, restated from srhd_kernels.cuh.
+KBOX_C, KBOX_X, KBOX_Y, KBOX_Z = 2560, 1280, 640, 640
+KXM = KBOX_C
+KXP, KYM = KXM + KBOX_X, KXM + 2 * KBOX_X
+KYP, KZM = KYM + KBOX_Y, KYM + 2 * KBOX_Y
+KZP = KZM + KBOX_Z
+
+
+def box_offset(gx, gy, gz):
+    ax = 0 if gx < 2 else (1 if gx < 10 else 2)
+    ay = 0 if gy < 2 else (1 if gy < 10 else 2)
+    az = 0 if gz < 2 else (1 if gz < 10 else 2)
+    x, y, z = gx - 2, gy - 2, gz - 2
+    if ay == 1 and az == 1:
+        if ax == 1:
+            return (z * 8 + y) * 8 + x, 512
+        return (KXM + gx + 2 if ax == 0 else KXP + gx - 10) + (z * 8 + y) * 4, 256
+    if ax == 1 and az == 1:
+        return (KYM + gy * 8 if ay == 0 else KYP + (gy - 10) * 8) + z * 16 + x, 128
+    if ax == 1 and ay == 1:
+        return (KZM + gz * 64 if az == 0 else KZP + (gz - 10) * 64) + y * 8 + x, 128
+    return None
+
+
+def test_staged_boxes_give_the_tile():
+    # boxes as the tensor copies deliver them (dense, x fastest) for a patch
+    # of a periodic grid, against numpy.pad of the whole field
+    from test_kernel_indexing import NEED, needed_tile_cell
+    npx, npy, npz = 3, 4, 5
+    rng = np.random.default_rng(8)
+    field = rng.normal(size=(5, 8 * npz, 8 * npy, 8 * npx))
+    P = field.reshape(5, npz, 8, npy, 8, npx, 8).transpose(1, 3, 5, 0, 2, 4, 6)  # [z][y][x][v][8][8][8]
+    padded = np.pad(field, [(0, 0), (2, 2), (2, 2), (2, 2)], mode="wrap")
+    needed = [needed_tile_cell(r) for r in range(NEED)]
+    for (cz, cy, cx) in ((0, 0, 0), (2, 1, 1), (4, 3, 2)):
+        nb = lambda dz, dy, dx: P[(cz + dz) % npz, (cy + dy) % npy, (cx + dx) % npx]  # noqa: E731
+        stage = np.full(KZP + KBOX_Z, np.nan)
+        stage[0:KBOX_C] = nb(0, 0, 0).reshape(-1)                       # [v][z][y][x]
+        stage[KXM:KXM + KBOX_X] = nb(0, 0, -1)[:, :, :, 4:8].reshape(-1)
+        stage[KXP:KXP + KBOX_X] = nb(0, 0, 1)[:, :, :, 0:4].reshape(-1)
+        stage[KYM:KYM + KBOX_Y] = nb(0, -1, 0)[:, :, 6:8, :].reshape(-1)
+        stage[KYP:KYP + KBOX_Y] = nb(0, 1, 0)[:, :, 0:2, :].reshape(-1)
+        stage[KZM:KZM + KBOX_Z] = nb(-1, 0, 0)[:, 6:8, :, :].reshape(-1)
+        stage[KZP:KZP + KBOX_Z] = nb(1, 0, 0)[:, 0:2, :, :].reshape(-1)
+        want = padded[:, 8 * cz:8 * cz + 12, 8 * cy:8 * cy + 12, 8 * cx:8 * cx + 12]
+        nstaged = 0
+        for c in needed:
+            gz, gy, gx = c // 144, (c // 12) % 12, c % 12
+            got = box_offset(gx, gy, gz)
+            nout = sum(1 for g in (gx, gy, gz) if g < 2 or g > 9)
+            if got is None:
+                assert nout == 2            # only the first-layer edges are not staged
+                continue
+            off, vs = got
+            assert 0 <= off and off + 4 * vs < KZP + KBOX_Z
+            for v in range(5):
+                assert stage[off + v * vs] == want[v, gz, gy, gx]
+            nstaged += 1
+        assert nstaged == NEED - 96
+    # every box starts on a 128-byte boundary for 4- and 8-byte elements
+    for off in (0, KXM, KXP, KYM, KYP, KZM, KZP):
+        assert (off * 4) % 128 == 0
