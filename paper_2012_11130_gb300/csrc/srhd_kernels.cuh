@@ -17,7 +17,11 @@
 //   retry    if any predicted state or updated cell is unphysical, phases 2-4
 //            are redone with the limiter coefficient times retry_factor
 //            (block-wide vote), down to theta = 0 (piecewise constant)
-// Shared memory: 25920 elements of S (207 KB double, 101 KB float).
+// While phase 4 runs, the copy engine stages the CTA's next tile in the
+// right-state face slots: one bulk copy per variable for a ghosted batch,
+// seven tensor-map boxes for a uniform grid (see patch_kernel).
+// Shared memory: 27648 elements of S (primitive tile, face slots, conic
+// parameter of the tile cells: 216 KB double, 108 KB float).
 #pragma once
 
 #include <cfloat>

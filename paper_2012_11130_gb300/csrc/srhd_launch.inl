@@ -12,8 +12,8 @@ namespace srhd {
 // Launch variants of the patch kernel (threads per CTA, CTAs per SM,
 // two Newton solves per thread in lockstep or one). Variant 0 is the
 // default; the rest are the search space of the autotuner
-// (paper_2012_11130_gb300/autotune.py). Shared memory per CTA is 207 KB for
-// double storage (one CTA per SM) and 101 KB for float storage (at most
+// (paper_2012_11130_gb300/autotune.py). Shared memory per CTA is 216 KB for
+// double storage (one CTA per SM) and 108 KB for float storage (at most
 // two).
 template <class S, int V> struct PatchVariant;
 template <> struct PatchVariant<double, 0> { static constexpr int nt = 512, minb = 1; static constexpr bool pair = false; };
