@@ -14,9 +14,10 @@
  *   x fastest: a ghosted patch holds 12^3 cells (an 8^3 interior plus two
  *   ghost cells on every side, Section 3.1), an interior patch 8^3 cells.
  *   Precision: SRHD_FP64 = double storage and double arithmetic;
- *   SRHD_MIXED = float storage, float arithmetic, except the left-hand side
- *   A of Eq. (transcendental equation) / Eq. (Unphysical result), which is
- *   formed in double in every conserved-to-primitive conversion;
+ *   SRHD_MIXED = float storage, float arithmetic, except the cancelling sum
+ *   A D^2 = Etilde (Etilde + 2D) - |M|^2 behind the left-hand side A of
+ *   Eq. (transcendental equation) / Eq. (Unphysical result), which is formed
+ *   in double in every conserved-to-primitive conversion;
  *   SRHD_MIXED_CF = as SRHD_MIXED but with A formed by compensated float
  *   arithmetic (see srhd_prec).
  *
@@ -57,8 +58,8 @@ typedef enum srhd_status {
 
 typedef enum srhd_prec {
   SRHD_FP64 = 0,     /* double storage, double arithmetic */
-  SRHD_MIXED = 1,    /* float storage and arithmetic; A of Eq. (transcendental
-                        equation) in double */
+  SRHD_MIXED = 1,    /* float storage and arithmetic; the cancelling sum A D^2
+                        of Eq. (transcendental equation) in double */
   SRHD_MIXED_CF = 2, /* float storage and arithmetic; A of Eq. (transcendental
                         equation) from error-free float products and a
                         compensated float sum (about 2^-44 of the cancelling

@@ -250,9 +250,9 @@ struct PrecFP64 {     // SRHD_FP64: double everywhere
   using AT = double;
   static constexpr bool comp_a = false;
 };
-struct PrecMixed {    // SRHD_MIXED: float, A in double
+struct PrecMixed {    // SRHD_MIXED: float, the cancelling part of A in double (A_mixed)
   using S = float;
-  using AT = double;
+  using AT = float;
   static constexpr bool comp_a = false;
 };
 struct PrecMixedCF {  // SRHD_MIXED_CF: float, A by a compensated float sum
@@ -274,6 +274,35 @@ __device__ __forceinline__ double A_of_cons(S D, S Mx, S My, S Mz, S Et, double&
   m2 = M2 * rD * rD;
   if (ori) return (eD * eD - m2) - 1.0;
   return eD * (eD + 2.0) - m2;
+}
+
+// A and m^2 of a float-stored state with the cancellation in double
+// (SRHD_MIXED): A D^2 = Et (Et + 2D) - |M|^2 (original scheme:
+// E^2 - D^2 - |M|^2) is formed in double without a division; its rounding to
+// float is scaled by 1/D^2 in float, and m^2 = (|M|/D)^2 is formed in float
+// (neither step cancels, so A keeps a few float ulps of relative accuracy, the
+// precision of the float iteration that uses it). For D >= 1e18, where 1/D^2
+// leaves the float range, A and m^2 are formed in double (A_of_cons).
+__device__ __forceinline__ bool A_mixed(float D, float Mx, float My, float Mz, float Et, float& A,
+                                        float& m2, int ori) {
+  if (!(D > 0.0f)) return false;
+  if (!(D < 1e18f)) {
+    double m2d;
+    const double Ad = A_of_cons(D, Mx, My, Mz, Et, m2d, ori);
+    A = float(Ad);
+    m2 = float(m2d);
+    return Ad > kEpsUnphysical;
+  }
+  const double d = D, e = Et, mx = Mx, my = My, mz = Mz;
+  double ad2 = ori ? fma(e, e, -(d * d)) : e * fma(2.0, d, e);
+  ad2 = fma(-mx, mx, ad2);
+  ad2 = fma(-my, my, ad2);
+  ad2 = fma(-mz, mz, ad2);
+  const float rD = qrcp(D);
+  A = float(ad2) * (rD * rD);
+  const float ux = Mx * rD, uy = My * rD, uz = Mz * rD;
+  m2 = ux * ux + uy * uy + uz * uz;
+  return A > float(kEpsUnphysical);
 }
 
 // Correctly rounded float operations on one lane (float) or two lanes
@@ -399,6 +428,8 @@ __device__ __forceinline__ bool A_and_m2(typename P::S D, typename P::S Mx, type
   if constexpr (P::comp_a) {
     if (!A_comp_float(D, Mx, My, Mz, Et, A, m2, ori)) return false;
     return A > float(kEpsUnphysical);
+  } else if constexpr (sizeof(typename P::S) == 4) {
+    return A_mixed(D, Mx, My, Mz, Et, A, m2, ori);
   } else {
     if (!(double(D) > 0.0)) return false;
     double m2d;
