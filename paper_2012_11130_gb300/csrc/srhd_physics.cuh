@@ -214,6 +214,29 @@ __device__ __forceinline__ V tau_step(V tau, V ml, V ml9, V nA, V lam) {
   const V dG = fma(t2, r, mul(P, dr));                        // d(P r)/dtau, P' = 2t
   return mul(fma(P, r, nA), rcp(dG));
 }
+// In double the same step over the common denominator Dn^2, with one
+// reciprocal instead of two (the products stay far inside the double range;
+// in float they could overflow): delta = (P N - A Dn) Dn /
+// (2t N Dn + P (dN Dn - N dD)). The residual P N - A Dn cancels exactly as
+// P N/Dn - A does.
+template <>
+__device__ __forceinline__ double tau_step<double>(double tau, double ml, double ml9, double nA,
+                                                   double lam) {
+  const double t = tau + 1.0;
+  const double t2 = t + t;
+  const double s = t * t;
+  const double P = tau * (tau + 2.0);
+  const double Q = fma(tau, 2.0, 1.0) * fma(tau, 2.0, 3.0);
+  const double Ql = Q * lam;
+  const double QQl = Q * Ql;
+  const double N = fma(ml, fma(s, 8.0, 1.0), QQl);
+  const double Dn = fma(ml9, s, QQl);
+  const double dN = (t2 * 8.0) * (Ql + ml);
+  const double dD = t2 * fma(Ql, 8.0, ml9);
+  const double num = fma(P, N, nA * Dn) * Dn;
+  const double den = fma(t2 * N, Dn, P * fma(dN, Dn, -(N * dD)));
+  return num * qrcp(den);
+}
 
 // ---- conserved -> primitive for the polytropic EoS --------------------------
 // With T = k htilde (k = (Gamma-1)/Gamma) and (h - T) = 1 + (1-k) htilde, the
@@ -241,6 +264,19 @@ __device__ __forceinline__ V poly_step(V x, V m2, V omk, V k2, V nA) {
   const V dG = mul(c<V>(2.0), fma(neg(mul(km, x)), mul(fma(neg(x), h, q), rq),
                                   mul(omk, add(ox, c<V>(1.0)))));
   return mul(G, rcp(dG));
+}
+// In double the same step times q^2 above and below, with one reciprocal:
+// delta = (f - A) q^2 / (f' q^2).
+template <>
+__device__ __forceinline__ double poly_step<double>(double x, double m2, double omk, double k2,
+                                                    double nA) {
+  const double h = x + 1.0;
+  const double q = fma(h, h, m2);
+  const double ox = omk * x;
+  const double kmx = (k2 * m2) * x;
+  const double Gq = fma(fma(ox, ox + 2.0, nA), q, -(kmx * x));       // (f - A) q
+  const double den = 2.0 * fma(omk * (ox + 1.0), q * q, -(kmx * fma(-x, h, q)));  // f' q^2
+  return Gq * q * qrcp(den);
 }
 
 // Precision tags. S is the storage and arithmetic type; AT is the type in
