@@ -61,10 +61,10 @@ PEAK_FP64_TFLOPS = 1.25
 # only for the kernel sources with the recorded hash.
 # Captured at 128^3 (4096 patches) and scaled by 8 to the 32768-patch launch
 # (profiles/patch_kernel_advection128.md).
-NCU_TRAFFIC = {"sources_sha": "f84c5292a2ce621d",
-               "mixed_cf": 8 * (141.748736e6 + 23.682048e6),
-               "mixed": 8 * (142.111232e6 + 24.098560e6),
-               "fp64": 8 * (283.365632e6 + 67.833856e6)}
+NCU_TRAFFIC = {"sources_sha": "cde3e66be9476b3f",
+               "mixed_cf": 8 * (141.721600e6 + 23.894784e6),
+               "mixed": 8 * (141.720832e6 + 23.980544e6),
+               "fp64": 8 * (284.001792e6 + 67.888384e6)}
 
 
 # The sources that make the patch kernel's device code (its translation units
