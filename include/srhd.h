@@ -97,8 +97,9 @@ enum {
   SRHD_PATCH_UNPHYSICAL = 1, /* still unphysical with piecewise-constant data */
   SRHD_PATCH_BAD_INPUT = 2,  /* a cell of the ghosted input is unphysical */
   SRHD_PATCH_NOCONV = 4,     /* some Newton solve hit its iteration cap */
-  SRHD_PATCH_STAGE_TIMEOUT = 8, /* ghosted batches: the asynchronous copy of a
-                               tile into shared memory did not complete within
+  SRHD_PATCH_STAGE_TIMEOUT = 8, /* ghosted batches and uniform grids: the
+                               asynchronous copy of the next tile into shared
+                               memory did not complete within
                                about a second (a device fault); the CTA that
                                waited stopped, so this patch and the later
                                patches of that CTA were not updated, and
