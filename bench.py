@@ -335,10 +335,12 @@ def time_e2e_ghosted(torch, ctx, G, dt_dh, steps, warmup, prec):
     return secs, h2d, d2h
 
 
-def l1_one_period(torch, srhd, prec, n=64, params=None, vl=False):
+def l1_one_period(torch, srhd, prec, n=64, params=None, vl=False, with_drift=False):
     """L1 error of rho (Eq. relative L1 error) after one period of the
     diagonal wave at n^3, evolved on the GPU with the fused CFL (uniform p
-    and velocity: the wave is translated exactly, whatever the EoS)."""
+    and velocity: the wave is translated exactly, whatever the EoS).
+    with_drift: also the largest relative change over the period of the
+    domain sums of D, M and Etilde (periodic: conserved to round-off)."""
     import numpy as np
     from paper_2012_11130_gb300 import workloads
     ctx = srhd.Context(params or srhd.Params())
@@ -354,6 +356,7 @@ def l1_one_period(torch, srhd, prec, n=64, params=None, vl=False):
     dd = torch.empty((U.shape[0], 2), dtype=torch.float64, device="cuda")
     dn = torch.empty(1, dtype=torch.float64, device="cuda")
     out = torch.empty_like(U)
+    sums0 = U.double().sum(dim=(0, 2, 3, 4))
     dt = ctx.cfl_dt(U, dh, prec=prec).item()
     t = 0.0
     steps = 0
@@ -375,7 +378,12 @@ def l1_one_period(torch, srhd, prec, n=64, params=None, vl=False):
     rho = Pd[0].double().reshape(npx, npx, npx, 8, 8, 8).permute(0, 3, 1, 4, 2, 5).reshape(
         n, n, n).cpu().numpy()
     exact = workloads.advection_prims(n, t=t_end)[0]
-    return float(np.mean(np.abs(1.0 - rho / exact))), steps
+    l1 = float(np.mean(np.abs(1.0 - rho / exact)))
+    if with_drift:
+        sums1 = U.double().sum(dim=(0, 2, 3, 4))
+        drift = float(((sums1 - sums0).abs() / sums0.abs()).max())
+        return l1, steps, drift
+    return l1, steps
 
 
 def bench_amr(torch, srhd, steps: int, warmup: int, prec: str = "mixed_cf"):
@@ -855,10 +863,20 @@ def run_ours(args):
                             precs=tuple(q for q in ("mixed_cf", "fp64") if q in precs))
 
     l1 = {}
+    l1_conv = {}
     stress = {}
     if not args.no_l1 and rank == 0:
         for prec in precs:
-            l1[prec], l1_steps = l1_one_period(torch, srhd, prec)
+            # configuration 3: one period at 64^3, 128^3 and 256^3 (about 35 s
+            # of the FP64 path at 256^3)
+            runs = {}
+            for n in (64, 128, 256):
+                e, nsteps, drift = l1_one_period(torch, srhd, prec, n=n, with_drift=True)
+                runs[str(n)] = {"l1_rho": e, "steps": nsteps, "conservation_drift": drift}
+            ns = sorted(runs, key=int)
+            l1_conv[prec] = {"runs": runs, "order": [
+                math.log2(runs[a]["l1_rho"] / runs[b]["l1_rho"]) for a, b in zip(ns, ns[1:])]}
+            l1[prec] = runs["64"]["l1_rho"]
         l1["grid"] = "64^3, one period, fused CFL 0.5"
         for prec in precs:
             stress[prec] = bench_con2pri_stress(torch, srhd, prec)
@@ -916,6 +934,7 @@ def run_ours(args):
                                                              "autotune", "uniform_loop")}
                              for q in precs[1:]} or None,
         "l1_rho": l1 or None,
+        "l1_convergence": l1_conv or None,
         "l1_shock_tube": st_l1,
         "con2pri_stress": stress or None,
         "amr_blast": amr_res,
