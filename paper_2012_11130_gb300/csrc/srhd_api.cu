@@ -432,20 +432,22 @@ static PFN_cuTensorMapEncodeTiled_v12000 encode_tiled() {
   return fn;
 }
 
-// Tensor maps of a uniform grid's interior array [np][5][8][8][8], viewed as
-// a 5-D tensor (x, y, z, var, patch), with the boxes of the staged gather
-// (PatchArgs::tmap: interior, x, y and z face slabs). False when they cannot
+// Tensor maps of a uniform grid's array [np][nvar][8][8][8] (the interiors,
+// nvar 5, or the primitive cache, nvar 6), viewed as a 5-D tensor (x, y, z,
+// var, patch), with the boxes of the staged gather (PatchArgs::tmap:
+// interior, x, y and z face slabs, variables 0..4). False when they cannot
 // be made (no driver entry point, an address not 16-byte aligned, a refused
 // encoding); the kernel then gathers every tile with plain loads.
-static bool uniform_tmaps(srhd_prec prec, const void* interior, int64_t np, CUtensorMap (&m)[4]) {
+static bool uniform_tmaps(srhd_prec prec, const void* interior, int64_t np, CUtensorMap (&m)[4],
+                          int nvar = 5) {
   const auto fn = encode_tiled();
   if (!fn || (reinterpret_cast<uintptr_t>(interior) & 15) != 0 || np < 1 || np > 0xffffffffLL)
     return false;
   const cuuint64_t es = prec == SRHD_FP64 ? 8 : 4;
   const CUtensorMapDataType dt =
       prec == SRHD_FP64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
-  const cuuint64_t dims[5] = {8, 8, 8, 5, cuuint64_t(np)};
-  const cuuint64_t strides[4] = {8 * es, 64 * es, 512 * es, 2560 * es};  // bytes, dims 1..4
+  const cuuint64_t dims[5] = {8, 8, 8, cuuint64_t(nvar), cuuint64_t(np)};
+  const cuuint64_t strides[4] = {8 * es, 64 * es, 512 * es, cuuint64_t(nvar) * 512 * es};
   const cuuint32_t boxes[4][5] = {{8, 8, 8, 5, 1}, {4, 8, 8, 5, 1}, {8, 2, 8, 5, 1},
                                   {8, 8, 2, 5, 1}};
   const cuuint32_t unit[5] = {1, 1, 1, 1, 1};
@@ -611,7 +613,9 @@ srhd_status srhd_advance_uniform_prim(srhd_ctx* c, srhd_prec prec, const void* i
     return fail(SRHD_ERR_ARG, "prim_out/cons_out must not alias the inputs");
   if (n == 0 && !dt_next) return SRHD_OK;
   srhd::PatchArgs a;
-  gather_args(c, prec, a, interior, npx, npy, npz, bc, p0);
+  CUtensorMap maps[4];
+  const bool tma = n > 0 && uniform_tmaps(prec, prim_in, np, maps, 6);
+  gather_args(c, prec, a, interior, npx, npy, npz, bc, p0, tma ? maps : nullptr);
   a.gather = 3;
   a.prim_in = prim_in;
   a.prim_out = prim_out;

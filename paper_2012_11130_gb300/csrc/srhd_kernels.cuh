@@ -517,11 +517,12 @@ __global__ void __launch_bounds__(NT, MINB) patch_kernel(const __grid_constant__
   [[maybe_unused]] __shared__ __align__(8) uint64_t s_mbar;
   [[maybe_unused]] __shared__ uint32_t s_stg;
   [[maybe_unused]] __shared__ int s_stage_timeout;
-  constexpr bool kStaged = GATHER == 0 || GATHER == 1;
+  constexpr bool kStaged = GATHER == 0 || GATHER == 1 || GATHER == 3;
   auto stage_ok = [&]() {
     // tensor copies need 128-byte aligned destinations (the boxes are laid
     // out on 128-byte boundaries from `stage`)
-    if constexpr (GATHER == 1) return a.tma != 0 && (bulk::saddr(stage) & 127) == 0;
+    if constexpr (GATHER == 1 || GATHER == 3)
+      return a.tma != 0 && (bulk::saddr(stage) & 127) == 0;
     return GATHER == 0 && !a.flux_only && (reinterpret_cast<uintptr_t>(a.in) & 15) == 0;
   };
   if constexpr (kStaged) {
@@ -654,8 +655,16 @@ __global__ void __launch_bounds__(NT, MINB) patch_kernel(const __grid_constant__
         const S* src = pbase + ((int64_t)(qz * a.gny + qy) * a.gnx + qx) * (6 * kNC) +
                        ((lz * kN + ly) * kN + lx);
         S w[6];
+        int off, vs;
+        if ((st1 & 2) && box_offset(g[0], g[1], g[2], off, vs)) {
+          // variables 0..4 staged by the tensor copies, tau from the cache
 #pragma unroll
-        for (int v = 0; v < 6; ++v) w[v] = __ldg(src + v * kNC);
+          for (int v = 0; v < 5; ++v) w[v] = stage[off + v * vs];
+          w[5] = __ldg(src + 5 * kNC);
+        } else {
+#pragma unroll
+          for (int v = 0; v < 6; ++v) w[v] = __ldg(src + v * kNC);
+        }
         if (!(w[0] > S(0) && w[4] > S(0) && isfinite(w[1] + w[2] + w[3] + w[5])))
           code |= CODE_BAD_INPUT;
 #pragma unroll
@@ -792,9 +801,9 @@ __global__ void __launch_bounds__(NT, MINB) patch_kernel(const __grid_constant__
                 s_stg |= 2;  // read next after the phase-4 barrier
               }
             }
-          } else if constexpr (GATHER == 1) {
+          } else if constexpr (GATHER == 1 || GATHER == 3) {
             // uniform grid: the seven boxes of the CTA's next patch, when its
-            // six face neighbours exist
+            // six face neighbours exist (mode 3: variables 0..4 of the cache)
             const int wn = w + gridDim.x;
             if (stage_ok() && wn < a.npatch && tid == NT - 1) {
               const int64_t qn = a.gp0 + wn;

@@ -6,7 +6,9 @@ equal the ghost fill followed by srhd_advance_patches bitwise: whole grids
 and patch ranges, periodic boundaries (every later patch staged) and outflow
 ones (boundary patches keep plain loads), a field that makes patches retry
 (a retry waits for the copies before it rewrites the stage), and the
-host-resident step, whose slabs are launched one by one."""
+host-resident step, whose slabs are launched one by one. The cached step
+(primitive cache, mode 3) stages variables 0..4 of the cache the same way
+and must equal the same step taken in ranges too small to stage."""
 import numpy as np
 import pytest
 
@@ -90,3 +92,31 @@ def test_host_step_with_staged_slabs(oracle):
     want = ctx.advance_patches(G, dd, dt_next=dnd)
     torch.cuda.synchronize()
     assert _same(out, want.cpu()) and dn == dnd.item()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed", "mixed_cf"])
+@pytest.mark.parametrize("bc", [("periodic",) * 3, ("outflow", "periodic", "outflow")])
+def test_staged_cached_step_equals_unstaged(oracle, prec, bc):
+    # mode 3 (primitive cache): variables 0..4 of the cached tile come from
+    # the tensor copies on the second and later patches of each CTA. The
+    # whole-grid step must equal the same step taken in ranges of 128
+    # patches, fewer than the CTAs of a launch, so that nothing is staged.
+    torch, srhd = require_gpu()
+    dtype = torch.float64 if prec == "fp64" else torch.float32
+    U = torch.from_numpy(_grid(oracle)).to(dtype).cuda()
+    dd = torch.tensor([[0.004, 1 / 32]] * NP, dtype=torch.float64, device="cuda")
+    ctx = srhd.Context(srhd.Params(patch_variant=1 if prec != "fp64" else 0))
+    P = ctx.con2pri_patches(U, prec=prec)
+    st = torch.full((NP,), -1, dtype=torch.int32, device="cuda")
+    whole_u, whole_p = ctx.advance_uniform_prim(U, P, NPX, NPY, NPZ, dd, bc=bc, patch_status=st,
+                                                prec=prec)
+    part_u, part_p = torch.empty_like(whole_u), torch.empty_like(whole_p)
+    st2 = torch.full((NP,), -1, dtype=torch.int32, device="cuda")
+    for p0 in range(0, NP, 128):
+        ctx.advance_uniform_prim(U, P, NPX, NPY, NPZ, dd[p0:p0 + 128].contiguous(), bc=bc,
+                                 p0=p0, n=128, cons_out=part_u[p0:p0 + 128],
+                                 prim_out=part_p[p0:p0 + 128], patch_status=st2[p0:p0 + 128],
+                                 prec=prec)
+    torch.cuda.synchronize()
+    assert torch.equal(st, st2) and int((st & 255).max()) > 0
+    assert _same(whole_u, part_u) and _same(whole_p, part_p)
