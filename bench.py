@@ -61,10 +61,10 @@ PEAK_FP64_TFLOPS = 1.25
 # only for the kernel sources with the recorded hash.
 # Captured at 128^3 (4096 patches) and scaled by 8 to the 32768-patch launch
 # (profiles/patch_kernel_advection128.md).
-NCU_TRAFFIC = {"sources_sha": "cde3e66be9476b3f",
-               "mixed_cf": 8 * (141.721600e6 + 23.894784e6),
-               "mixed": 8 * (141.720832e6 + 23.980544e6),
-               "fp64": 8 * (284.001792e6 + 67.888384e6)}
+NCU_TRAFFIC = {"sources_sha": "bd9eecbac0fe8a32",
+               "mixed_cf": 8 * (141.702144e6 + 23.499776e6),
+               "mixed": 8 * (141.723392e6 + 24.378368e6),
+               "fp64": 8 * (284.111360e6 + 67.482624e6)}
 
 
 # The sources that make the patch kernel's device code (its translation units
