@@ -505,10 +505,11 @@ __global__ void __launch_bounds__(NT, MINB) patch_kernel(const __grid_constant__
   // Ghosted batch: while a patch is updated (phase 4) the copy engine brings
   // the CTA's next tile into the right-state face slots (`stage`), where
   // phase 1 of that patch reads it. Needs 16-byte aligned tiles. Uniform
-  // grid (gather mode 1 with tensor maps): the same with the seven boxes of
-  // the next patch's tile (box_offset), for patches whose six face
-  // neighbours exist (periodic or interior; other patches, and the first
-  // patch of each CTA, gather with plain loads). s_stg:
+  // grid (gather modes 1 and 3 with tensor maps): the same with the seven
+  // boxes of the next patch's tile (box_offset; in mode 3 variables 0..4 of
+  // the primitive cache), for patches whose six face neighbours exist
+  // (periodic or interior; other patches, and the first patch of each CTA,
+  // gather with plain loads). s_stg:
   // bit 0 the parity of the s_mbar phase that the next copy completes, bit 1
   // set while a copy is issued and not yet waited for. It is kept in shared
   // memory (read by all threads, written by one between barriers) so that
