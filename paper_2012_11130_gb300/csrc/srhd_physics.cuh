@@ -312,35 +312,6 @@ __device__ __forceinline__ double A_of_cons(S D, S Mx, S My, S Mz, S Et, double&
   return eD * (eD + 2.0) - m2;
 }
 
-// A and m^2 of a float-stored state with the cancellation in double
-// (SRHD_MIXED): A D^2 = Et (Et + 2D) - |M|^2 (original scheme:
-// E^2 - D^2 - |M|^2) is formed in double without a division; its rounding to
-// float is scaled by 1/D^2 in float, and m^2 = (|M|/D)^2 is formed in float
-// (neither step cancels, so A keeps a few float ulps of relative accuracy, the
-// precision of the float iteration that uses it). For D >= 1e18, where 1/D^2
-// leaves the float range, A and m^2 are formed in double (A_of_cons).
-__device__ __forceinline__ bool A_mixed(float D, float Mx, float My, float Mz, float Et, float& A,
-                                        float& m2, int ori) {
-  if (!(D > 0.0f)) return false;
-  if (!(D < 1e18f)) {
-    double m2d;
-    const double Ad = A_of_cons(D, Mx, My, Mz, Et, m2d, ori);
-    A = float(Ad);
-    m2 = float(m2d);
-    return Ad > kEpsUnphysical;
-  }
-  const double d = D, e = Et, mx = Mx, my = My, mz = Mz;
-  double ad2 = ori ? fma(e, e, -(d * d)) : e * fma(2.0, d, e);
-  ad2 = fma(-mx, mx, ad2);
-  ad2 = fma(-my, my, ad2);
-  ad2 = fma(-mz, mz, ad2);
-  const float rD = qrcp(D);
-  A = float(ad2) * (rD * rD);
-  const float ux = Mx * rD, uy = My * rD, uz = Mz * rD;
-  m2 = ux * ux + uy * uy + uz * uz;
-  return A > float(kEpsUnphysical);
-}
-
 // Correctly rounded float operations on one lane (float) or two lanes
 // (float2, packed instructions); the _rn forms keep the compiler from
 // contracting them into other FMAs.
@@ -378,6 +349,32 @@ __device__ __forceinline__ bool comp_scale(float D, float& sc) {
   const int ex = (__float_as_int(D) >> 23) & 0xff;
   sc = __int_as_float((254 - (ex > 253 ? 253 : ex)) << 23);
   return D > 0.0f && ex <= 253;
+}
+
+// A and m^2 of a float-stored state with the cancellation in double
+// (SRHD_MIXED). The state is first scaled by the power of two that brings D
+// into [1, 2) (comp_scale; exact in float, and A and m^2 do not change);
+// then A d^2 = e (e + 2d) - |m|^2 (original scheme: e^2 - d^2 - |m|^2) of
+// the scaled values is formed in double without a division, rounded to
+// float and scaled by 1/d^2 in float, and m^2 = (|m|/d)^2 is formed in
+// float: neither step cancels, so A keeps a few float ulps of relative
+// accuracy, the precision of the float iteration that uses it, with no
+// range limit on D.
+__device__ __forceinline__ bool A_mixed(float D, float Mx, float My, float Mz, float Et, float& A,
+                                        float& m2, int ori) {
+  float sc;
+  if (!comp_scale(D, sc)) return false;
+  const float d = D * sc, ef = Et * sc, mxf = Mx * sc, myf = My * sc, mzf = Mz * sc;
+  const double dd = d, e = ef, mx = mxf, my = myf, mz = mzf;
+  double ad2 = ori ? fma(e, e, -(dd * dd)) : e * fma(2.0, dd, e);
+  ad2 = fma(-mx, mx, ad2);
+  ad2 = fma(-my, my, ad2);
+  ad2 = fma(-mz, mz, ad2);
+  const float rd = qrcp(d);
+  A = float(ad2) * (rd * rd);
+  const float ux = mxf * rd, uy = myf * rd, uz = mzf * rd;
+  m2 = ux * ux + uy * uy + uz * uz;
+  return A > float(kEpsUnphysical);
 }
 
 // A and m^2 from float conserved values without double arithmetic.

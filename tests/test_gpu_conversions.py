@@ -104,3 +104,35 @@ def test_round_trip_tracks_conditioning(oracle):
     ht2 = oracle.htilde_of_T(P[4] / P[0])
     err = np.abs(1 - ht0 / ht2)
     assert np.all(err <= 64 * (1 + mach ** 2) * EPS64)
+
+
+def test_mixed_conversion_at_large_density(oracle):
+    # SRHD_MIXED forms A D^2 in double from the state scaled by the power of
+    # two that brings D into [1, 2), then scales it back in float: densities
+    # whose A D^2 (up to ~1e45 here) or 1/D^2 leave the float range must
+    # convert like the oracle.
+    torch, srhd = require_gpu()
+    rng = np.random.default_rng(19)
+    n = 4096
+    rho = 10.0 ** rng.uniform(16.0, 20.0, n)          # D = rho gamma from 1e16 to ~1e21
+    T = 10.0 ** rng.uniform(-3.0, 2.0, n)
+    gam = 10.0 ** rng.uniform(0.0, 1.0, n)
+    d = rng.normal(size=(3, n))
+    d /= np.linalg.norm(d, axis=0)
+    U = np.sqrt(gam * gam - 1.0) * d
+    W = np.vstack([rho, U, rho * T])
+    C, st = oracle.prim2con(W)
+    assert np.all(st == 0)
+    C = C.astype(np.float32).astype(np.float64)
+    assert (C[0] >= 1e19).mean() > 0.2
+    ref = oracle.con2pri(C)
+    st = torch.full((n,), -7, dtype=torch.int32, device="cuda")
+    P = srhd.con2pri(to_dev(torch, C, torch.float32), cell_status=st, prec="mixed")
+    torch.cuda.synchronize()
+    Pg, stg = to_np(P), st.cpu().numpy()
+    ok = ref["status"] == 0
+    assert np.array_equal(stg, ref["status"])
+    kappa = kappa_of_prims(oracle, ref["prim"][:, ok])
+    tol = np.maximum(BASE["mixed"], 10 * kappa * EPS_A["mixed"])
+    err = prim_rel_err(Pg[:, ok], ref["prim"][:, ok])
+    assert np.all(err <= tol), err.max()
