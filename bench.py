@@ -62,10 +62,10 @@ PEAK_FP64_TFLOPS = 1.25
 # only for the kernel sources with the recorded hash.
 # Captured at 128^3 (4096 patches) and scaled by 8 to the 32768-patch launch
 # (profiles/patch_kernel_advection128.md).
-NCU_TRAFFIC = {"sources_sha": "e9f095cb21ee08a4",
-               "mixed_cf": 8 * (141.702144e6 + 23.499776e6),
-               "mixed": 8 * (141.723392e6 + 24.378368e6),
-               "fp64": 8 * (284.111360e6 + 67.482624e6)}
+NCU_TRAFFIC = {"sources_sha": "0062a97e98619585",
+               "mixed_cf": 8 * (141.771520e6 + 24.168192e6),
+               "mixed": 8 * (141.717760e6 + 24.079616e6),
+               "fp64": 8 * (283.968512e6 + 68.002560e6)}
 
 
 # The sources that make the patch kernel's device code (its translation units
