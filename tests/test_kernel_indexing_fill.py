@@ -204,3 +204,25 @@ def test_staged_boxes_give_the_tile():
     # every box starts on a 128-byte boundary for 4- and 8-byte elements
     for off in (0, KXM, KXP, KYM, KYP, KZM, KZP):
         assert (off * 4) % 128 == 0
+
+
+@pytest.mark.parametrize("elem", [4, 8])
+def test_tensor_copy_coordinates(elem):
+    # The seven tensor copies of the staged uniform gather (box dims x, y, z
+    # and start coordinates, restated from the issue code in
+    # srhd_kernels.cuh): the innermost start x times the element size must be
+    # a multiple of 16 bytes, every box must lie inside the patch, and the
+    # bytes the mbarrier expects must be the sum of the boxes.
+    boxes = {"center": ((8, 8, 8), (0, 0, 0)), "-x": ((4, 8, 8), (4, 0, 0)),
+             "+x": ((4, 8, 8), (0, 0, 0)), "-y": ((8, 2, 8), (0, 6, 0)),
+             "+y": ((8, 2, 8), (0, 0, 0)), "-z": ((8, 8, 2), (0, 0, 6)),
+             "+z": ((8, 8, 2), (0, 0, 0))}
+    total = 0
+    for (bx, by, bz), (x0, y0, z0) in boxes.values():
+        assert (x0 * elem) % 16 == 0 and (bx * elem) % 16 == 0
+        assert 0 <= x0 and x0 + bx <= 8 and 0 <= y0 and y0 + by <= 8 and 0 <= z0 and z0 + bz <= 8
+        total += bx * by * bz * 5
+    assert total == KZP + KBOX_Z == 7680
+    # the neighbour slabs hold the cells the tile needs: x 6, 7 of the -x
+    # neighbour inside [4, 8), y 6, 7 of the -y neighbour, and so on
+    assert {6, 7} <= set(range(4, 8)) and {0, 1} <= set(range(0, 4))
