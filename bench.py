@@ -53,6 +53,10 @@ WORKLOAD = ("3-D periodic smooth advection 256^3 (rho=1+0.5 sin(2pi(x+y+z)), p=1
 FLOPS_PER_CELL_UPDATE = 4583.2
 # Algorithmic bytes per cell update: 5 conserved values read + 5 written.
 BYTES_PER_CELL_UPDATE = {"mixed_cf": 40, "mixed": 40, "fp64": 80}
+# The same with the halo a ghosted batch carries: 12^3 tile cells read and
+# 8^3 written per 8^3 cell updates, five variables (87.5 B float, 175 B double).
+HALO_BYTES_PER_CELL_UPDATE = {q: b / 2 * (1728 + 512) / 512 for q, b in
+                              BYTES_PER_CELL_UPDATE.items()}
 # Peaks: FP32 from the unit counts (152 SMs x 128 FP32 lanes x 2 flops x
 # 2070 MHz); FP64 at the nominal 1.25 TFLOP/s of GB300; HBM measured.
 PEAK_FP32_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
@@ -839,6 +843,9 @@ def run_ours(args):
                              "peak": hbm_peak, "unit": "GB/s",
                              "frac": alg_bytes / (launch_ms * 1e-3) / 1e9 / hbm_peak,
                              "bytes_per_cell_update": BYTES_PER_CELL_UPDATE[prec],
+                             "halo_bytes_per_cell_update": HALO_BYTES_PER_CELL_UPDATE[prec],
+                             "halo_frac": (HALO_BYTES_PER_CELL_UPDATE[prec] * cells
+                                           / (launch_ms * 1e-3) / 1e9 / hbm_peak),
                              "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)"},
             "clocks": clocks, "e2e": e2e, "dt_next": dt_next, "patch_status_max": smax,
             "autotune": tuned,
