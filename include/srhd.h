@@ -165,10 +165,16 @@ const char* srhd_last_error(void);
 srhd_status srhd_prim2con(srhd_ctx* ctx, srhd_prec prec, const void* prim, void* cons,
                           int64_t n, int64_t var_stride, void* stream);
 
-/* Conserved -> primitive, n independent cells (Section 2.3: Newton-Raphson
- * on Eq. transcendental equation in htilde with the initial guesses and
- * derivative of Appendix A, then Eq. four-velocity, Eq. new expression of
- * Lorentz factor, Eq. density, Eq. T of h, Eq. p=rhoT).
+/* Conserved -> primitive, n independent cells (Section 2.3: the root of
+ * Eq. transcendental equation, f(htilde) = A, then Eq. four-velocity, Eq. new
+ * expression of Lorentz factor, Eq. density, Eq. T of h, Eq. p=rhoT). The
+ * kernels solve the same equation for the same root by Newton-Raphson in the
+ * conic parameter tau = h - T - 1 of the TM hyperbola (h - 4T)(h - T) = 1,
+ * in which f is a ratio of polynomials, starting from
+ * tau0 = A / (1 + sqrt(1 + A)) (the root for |M| = 0) instead of the
+ * htilde guesses of Appendix A; htilde and T follow from tau in closed form.
+ * A is formed in double (SRHD_FP64, SRHD_MIXED) or by compensated float
+ * arithmetic (SRHD_MIXED_CF) and checked against Eq. (Unphysical result).
  *   cons, prim as in srhd_prim2con.
  *   cell_status [n] int32 (nullable): SRHD_CELL_* per cell. */
 srhd_status srhd_con2pri(srhd_ctx* ctx, srhd_prec prec, const void* cons, void* prim,
@@ -315,7 +321,7 @@ srhd_status srhd_fill_ghosts_uniform(srhd_ctx* ctx, srhd_prec prec, const void* 
 /* Ghost-zone fill of the patches p0 .. p0+n-1 (all cells of their 12^3
  * tiles, interior included), from a source map. The paper fills the ghost
  * zones of a fine patch from its own level where that level covers them and
- * otherwise from the coarser level; here the coarse value is the
+ * otherwise from the coarser level (Section 3.3 (3)); here the coarse value is the
  * coarse cell containing the ghost cell (piecewise-constant prolongation,
  * conservative and physical whenever the coarse state is), interpolated
  * linearly in time between the coarse level's states before and after its
@@ -375,7 +381,7 @@ srhd_status srhd_amr_restrict(srhd_ctx* ctx, srhd_prec prec, void* cur,
                               const int32_t* children, int32_t nparent, int32_t ntotal,
                               void* stream);
 
-/* Coarse-fine flux correction (the correction that keeps the
+/* Coarse-fine flux correction (Section 3.3 (4), the correction that keeps the
  * composite grid conservative): the coarse cells on a patch face bordering
  * the finer level are corrected by U += s (dt/dh) (F_coarse - <F_fine>),
  * s = +1 on a high face and -1 on a low one, with F_coarse the patch-face
@@ -464,7 +470,9 @@ srhd_status srhd_reciprocal_f64(const double* x, double* y, int64_t n, void* str
  * entry point takes no context and allocates nothing.
  *   cons [npatch][5][8^3]; 0 <= npatch <= 131072 (larger batches are refused
  *   with SRHD_ERR_ARG); dh > 0; params (nullable: defaults) supplies cfl,
- *   cfl_mode, ndim and newton_max_iter; dt_out: one device double receiving
+ *   cfl_mode, ndim, newton_max_iter, scheme (SRHD_SCHEME_TOTAL converts the
+ *   total-energy form), eos and gamma (the polytropic EoS), all validated as
+ *   in srhd_create; its other fields are ignored; dt_out: one device double receiving
  *   min over cells of C_CFL dh / S_max, NaN if a cell is unphysical, +inf if
  *   npatch == 0.
  * Its scratch is a fixed 1.5 MB static device array that every GPU loading

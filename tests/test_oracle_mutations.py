@@ -79,6 +79,28 @@ MUTANTS = [
      "test_oracle_scheme.py::test_original_scheme_round_trip_tracks_its_error_estimate"),
     ("original_scheme_flux_index", "F[4] = ori ? U[1 + d] :", "F[4] = ori ? U[1] :",
      "test_oracle_scheme.py::test_original_scheme_agrees_for_hot_gas_and_conserves"),
+    ("retry_factor_compounded_twice",
+     "    theta = theta * P.retry_factor;\n    if (theta < P.theta_floor * theta0) theta = 0.0;\n"
+     "  }\n  if (retries_out) *retries_out = attempt;\n  if (flux_out) {",
+     "    theta = theta * P.retry_factor * P.retry_factor;\n"
+     "    if (theta < P.theta_floor * theta0) theta = 0.0;\n"
+     "  }\n  if (retries_out) *retries_out = attempt;\n  if (flux_out) {",
+     "test_oracle_retry.py::test_retry_count_matches_single_attempt_at_theta_k"),
+    ("retry_floor_absolute",
+     "    if (theta < P.theta_floor * theta0) theta = 0.0;\n"
+     "  }\n  if (retries_out) *retries_out = attempt;\n  if (flux_out) {",
+     "    if (theta < P.theta_floor) theta = 0.0;\n"
+     "  }\n  if (retries_out) *retries_out = attempt;\n  if (flux_out) {",
+     "test_oracle_retry.py::test_floor_gives_piecewise_constant_attempt"),
+    ("retry_skips_an_attempt",
+     "    ++attempt;\n    theta = theta * P.retry_factor;\n"
+     "    if (theta < P.theta_floor * theta0) theta = 0.0;\n"
+     "  }\n  if (retries_out) *retries_out = attempt;\n  if (flux_out) {",
+     "    ++attempt;\n    theta = theta * P.retry_factor;\n"
+     "    if (attempt == 3) theta = theta * P.retry_factor;\n"
+     "    if (theta < P.theta_floor * theta0) theta = 0.0;\n"
+     "  }\n  if (retries_out) *retries_out = attempt;\n  if (flux_out) {",
+     "test_oracle_retry.py::test_retry_count_matches_single_attempt_at_theta_k"),
     ("cold_guess_coefficient", "R a = (R(43.0) * m2 + R(63.0)) / (R(125.0) * P);",
      "R a = (R(43.0) * m2 + R(60.0)) / (R(125.0) * P);",
      "test_oracle_eos.py::test_guess_threshold_is_crossing"),
