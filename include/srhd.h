@@ -387,7 +387,11 @@ srhd_status srhd_amr_restrict(srhd_ctx* ctx, srhd_prec prec, void* cur,
  * s = +1 on a high face and -1 on a low one, with F_coarse the patch-face
  * flux of the coarse step and <F_fine> the mean of the fine patch-face fluxes
  * over the 2x2 fine faces covering the coarse face and over the two fine
- * substeps.
+ * substeps; a cell on several such faces takes their corrections in the
+ * face order below. A cell whose corrected state fails Eq. (Unphysical
+ * result) (D > 0 and A > 2e-16, A in double from the stored values, in the
+ * context's scheme) keeps its uncorrected state, as the paper prescribes;
+ * this breaks exact conservation on that cell only.
  *   cur [ntotal][5][8^3] in/out;
  *   flux_coarse, flux_fine0, flux_fine1 [ntotal][6][5][64]: patch-face
  *       fluxes (srhd_advance_patches' patch_face_flux) of the coarse step and
@@ -396,11 +400,14 @@ srhd_status srhd_amr_restrict(srhd_ctx* ctx, srhd_prec prec, void* cur,
  *       the four fine patches across it, ordered qa + 2 qb by quadrant (qa
  *       along the lower transverse axis), or -1 for a face that does not
  *       border the finer level; a coarse patch appears in one row only;
- *   dt_dh [ntotal][2] device doubles (the coarse patch's dt, dh). */
+ *   dt_dh [ntotal][2] device doubles (the coarse patch's dt, dh);
+ *   skipped (nullable): one device int32 to which the number of cells whose
+ *       correction was skipped is added (atomically; the caller zeroes it). */
 srhd_status srhd_amr_flux_correct(srhd_ctx* ctx, srhd_prec prec, void* cur,
                                   const void* flux_coarse, const void* flux_fine0,
                                   const void* flux_fine1, const int32_t* faces, int32_t nrows,
-                                  const double* dt_dh, int32_t ntotal, void* stream);
+                                  const double* dt_dh, int32_t ntotal, int32_t* skipped,
+                                  void* stream);
 
 /* srhd_fill_ghosts_uniform restricted to the patches p0 .. p0+n-1, so that a
  * caller can fill and advance part of a grid while the rest is in transit:

@@ -19,7 +19,8 @@ between the coarse states before and after the coarse step, which is
 piecewise-constant prolongation); restriction is the mean of the eight child
 cells; the flux correction replaces, for a coarse cell on a coarse-fine face,
 the coarse face flux by the mean of the fine face fluxes over the 2x2 fine
-faces and the two substeps. The per-patch step is oracle.advance_patches.
+faces and the two substeps, and is ignored on a cell that it would leave
+unphysical. The per-patch step is oracle.advance_patches.
 """
 from __future__ import annotations
 
@@ -48,6 +49,7 @@ class OracleAmr:
         self.inflow = inflow
         self.flux_correction = flux_correction
         self.face_flux = [dict() for _ in self.levels]   # [l][coord] -> list per substep
+        self.skipped = 0     # cells whose flux correction was ignored (Section 3.3 (4))
 
     def ncell(self, l):
         return [8 * (b << l) for b in self.base]
@@ -131,13 +133,30 @@ class OracleAmr:
                 out[:, b, a] = F[:, q]
         return out
 
+    @staticmethod
+    def physical(u):
+        """Eq. (Unphysical result) of conserved states u [5][...]: D > 0 and
+        A = eD (eD + 2) - m2 > 2e-16, eD = Etilde/D, m2 = |M|^2/D^2."""
+        D = u[0]
+        with np.errstate(divide="ignore", invalid="ignore"):
+            m2 = (u[1] * u[1] + u[2] * u[2] + u[3] * u[3]) / (D * D)
+            eD = u[4] / D
+            A = eD * (eD + 2.0) - m2
+        return (D > 0) & (A > 2e-16)
+
     def flux_correct(self, l, coarse_flux):
+        """Correct the unrefined coarse patches of level l next to level
+        l + 1; a cell whose corrected state fails Eq. (Unphysical result)
+        keeps its uncorrected state (Section 3.3 (4)) and is counted in
+        self.skipped."""
         P = [b << l for b in self.base]
         dt, dh = self.cfl * self.dh0 / 2 ** l, self.dh0 / 2 ** l
         for c in self.levels[l]:
             if self.children(l, c) is not None:
                 continue
-            u = self.data[l][c]
+            u0 = self.data[l][c]
+            u = u0.copy()
+            touched = np.zeros((8, 8, 8), bool)
             for d in range(3):
                 for high in (0, 1):
                     q = list(c)
@@ -172,6 +191,13 @@ class OracleAmr:
                         view += du
                     else:
                         view -= du
+                    touched[tuple(sl)] = True
+            # Section 3.3 (4): the correction is ignored on cells it leaves
+            # unphysical
+            bad = touched & ~self.physical(u)
+            u[:, bad] = u0[:, bad]
+            self.skipped += int(bad.sum())
+            u0[...] = u
 
     # -- time stepping --------------------------------------------------------
     def _advance(self, l, w):

@@ -113,7 +113,8 @@ def load(path: str = LIB_PATH):
     L.srhd_amr_restrict.restype = st
     L.srhd_amr_restrict.argtypes = [vp, ctypes.c_int, vp, vp, i32, i32, vp]
     L.srhd_amr_flux_correct.restype = st
-    L.srhd_amr_flux_correct.argtypes = [vp, ctypes.c_int, vp, vp, vp, vp, vp, i32, vp, i32, vp]
+    L.srhd_amr_flux_correct.argtypes = [vp, ctypes.c_int, vp, vp, vp, vp, vp, i32, vp, i32, vp,
+                                         vp]
     _lib = L
     return L
 

@@ -282,6 +282,9 @@ class AmrRun:
                         torch.zeros((n, 5, 12, 12, 12), dtype=dt, device=dev))
         self.flux = [torch.zeros((n, 6, 5, 64), dtype=dt, device=dev) for _ in range(2)]
         self.status = torch.zeros(n, dtype=torch.int32, device=dev)
+        # cells whose flux correction was skipped because it left them
+        # unphysical (Section 3.3 (4)), summed over all steps so far
+        self.skipped = torch.zeros(1, dtype=torch.int32, device=dev)
         self.map = torch.from_numpy(hier.map).to(dev)
         self.children = [torch.from_numpy(c).to(dev) for c in hier.children]
         self.faces = [torch.from_numpy(f).to(dev) for f in hier.faces]
@@ -338,7 +341,8 @@ class AmrRun:
             self._advance(l + 1, 0.5, 1, stream)
             ctx.amr_restrict(self.cur, self.children[l], stream=stream, prec=self.prec)
             ctx.amr_flux_correct(self.cur, self.flux[parity], self.flux[0], self.flux[1],
-                                 self.faces[l], self.dt_dh, stream=stream, prec=self.prec)
+                                 self.faces[l], self.dt_dh, stream=stream, prec=self.prec,
+                                 skipped=self.skipped)
 
     def step(self, stream=None):
         """One coarse step (every level advanced by dt_0), on `stream` (or the

@@ -9,7 +9,8 @@
 //   amr_restrict_kernel        fine -> coarse averaging (2x2x2 children);
 //   amr_flux_correct_kernel    coarse-fine flux correction with the patch-face
 //                              fluxes of the coarse step and of the two fine
-//                              substeps.
+//                              substeps, skipped on cells it would leave
+//                              unphysical.
 // All three move data: they are bound by HBM bandwidth. Every index that
 // comes from a map is range checked on the device; an invalid entry gives
 // NaN (fill) or is skipped (restriction, correction), never an access out of
@@ -215,57 +216,90 @@ __global__ void amr_restrict_kernel(S* __restrict__ cur, const int32_t* __restri
   }
 }
 
-// Flux correction of unrefined coarse patches. faces[r] = {coarse patch,
-// then for each patch face f = 0..5 (-x, +x, -y, +y, -z, +z) the four fine
-// patches across it, ordered qa + 2 qb by the quadrant of the face
-// (qa along the lower transverse axis), or -1 where the face does not border
-// the finer level}. flux_* are patch-face fluxes [patch][6][5][64]
-// (face cell t = a + 8 b, a along the lower transverse axis). For a coarse
-// cell on face f: U += s (dt/dh) (F_coarse - <F_fine>), s = +1 on a high face,
-// -1 on a low one, <F_fine> the mean over the 2x2 fine faces and the two fine
-// substeps. One block per listed coarse patch; the faces of a patch are done
-// one after another (a corner cell borders several).
+// Eq. (Unphysical result) of a corrected state, evaluated in double with
+// IEEE operations in a fixed order (no contraction), for both storage types:
+// D > 0 and A = eD (eD + 2) - m2 > 2e-16 with eD = Etilde/D and
+// m2 = |M|^2/D^2 (the original scheme, ori = 1: (E/D)^2 - m2 - 1).
+template <class S> __device__ __forceinline__ bool amr_physical(const S (&u)[5], int ori) {
+  const double D = double(u[0]);
+  if (!(D > 0.0)) return false;
+  const double M2 = __dadd_rn(__dadd_rn(__dmul_rn(double(u[1]), double(u[1])),
+                                        __dmul_rn(double(u[2]), double(u[2]))),
+                              __dmul_rn(double(u[3]), double(u[3])));
+  const double m2 = __ddiv_rn(M2, __dmul_rn(D, D));
+  const double eD = __ddiv_rn(double(u[4]), D);
+  const double A = ori ? __dsub_rn(__dsub_rn(__dmul_rn(eD, eD), m2), 1.0)
+                       : __dsub_rn(__dmul_rn(eD, __dadd_rn(eD, 2.0)), m2);
+  return A > 2e-16;
+}
+
+// Flux correction of unrefined coarse patches (Section 3.3 (4)).
+// faces[r] = {coarse patch, then for each patch face f = 0..5 (-x, +x, -y,
+// +y, -z, +z) the four fine patches across it, ordered qa + 2 qb by the
+// quadrant of the face (qa along the lower transverse axis), or -1 where the
+// face does not border the finer level}. flux_* are patch-face fluxes
+// [patch][6][5][64] (face cell t = a + 8 b, a along the lower transverse
+// axis). A coarse cell on face f gets U += s (dt/dh) (F_coarse - <F_fine>),
+// s = +1 on a high face, -1 on a low one, <F_fine> the mean over the 2x2
+// fine faces and the two fine substeps; a cell on several such faces (an
+// edge or corner) takes their corrections in face order. If the corrected
+// state fails Eq. (Unphysical result), the cell keeps its uncorrected state
+// (the paper ignores the correction on failed cells) and, when `skipped` is
+// given, adds one to *skipped. One block per listed coarse patch, one thread
+// per cell with all five variables.
 template <class S>
 __global__ void amr_flux_correct_kernel(S* __restrict__ cur, const S* __restrict__ flux_c,
                                         const S* __restrict__ flux_f0,
                                         const S* __restrict__ flux_f1,
                                         const int32_t* __restrict__ faces, int64_t nface_rows,
                                         const double* __restrict__ dt_dh,
-                                        int64_t npatch_total) {
+                                        int64_t npatch_total, int ori,
+                                        int32_t* __restrict__ skipped) {
   constexpr int kF = 6 * 5 * 64;
   for (int64_t r = blockIdx.x; r < nface_rows; r += gridDim.x) {
     const int32_t cp = faces[r * 25];
     if (cp < 0 || cp >= npatch_total) continue;  // uniform per block
     const S coef = S(dt_dh[2 * cp] / dt_dh[2 * cp + 1]);
-    for (int f = 0; f < 6; ++f) {
-      const int32_t* fp = faces + r * 25 + 1 + 4 * f;
-      const bool active = fp[0] >= 0;
-      if (active) {
+    const int32_t* row = faces + r * 25 + 1;
+    for (int c = threadIdx.x; c < kAmrInt; c += blockDim.x) {
+      const int ijk[3] = {c & 7, (c >> 3) & 7, c >> 6};
+      S* u = cur + (int64_t)cp * 5 * kAmrInt + c;
+      S un[5];
+      bool touched = false;
+      for (int f = 0; f < 6; ++f) {
         const int d = f >> 1, high = f & 1;
-        for (int q = threadIdx.x; q < 5 * 64; q += blockDim.x) {
-          const int v = q >> 6, t = q & 63, a = t & 7, b = t >> 3;
-          const int32_t fine = fp[(a >> 2) + 2 * (b >> 2)];
-          if (fine < 0 || fine >= npatch_total) continue;
-          // fine face cells covering coarse face cell (a, b)
-          const int fa = 2 * (a & 3), fb = 2 * (b & 3);
-          const int fside = 2 * d + (1 - high);
+        if (ijk[d] != (high ? 7 : 0) || row[4 * f] < 0) continue;
+        // face cell (a, b): a along the lower transverse axis
+        const int a = d == 0 ? ijk[1] : ijk[0];
+        const int b = d == 2 ? ijk[1] : ijk[2];
+        const int32_t fine = row[4 * f + (a >> 2) + 2 * (b >> 2)];
+        if (fine < 0 || fine >= npatch_total) continue;
+        if (!touched) {
+#pragma unroll
+          for (int v = 0; v < 5; ++v) un[v] = u[v * kAmrInt];
+          touched = true;
+        }
+        // fine face cells covering coarse face cell (a, b)
+        const int t0 = (2 * (b & 3)) * 8 + 2 * (a & 3);
+        const int fside = 2 * d + (1 - high);
+#pragma unroll
+        for (int v = 0; v < 5; ++v) {
           const S* F0 = flux_f0 + (int64_t)fine * kF + (fside * 5 + v) * 64;
           const S* F1 = flux_f1 + (int64_t)fine * kF + (fside * 5 + v) * 64;
-          const int t0 = fb * 8 + fa;
           const S fsum = ((F0[t0] + F0[t0 + 1]) + (F0[t0 + 8] + F0[t0 + 9])) +
                          ((F1[t0] + F1[t0 + 1]) + (F1[t0 + 8] + F1[t0 + 9]));
-          const S fc = flux_c[(int64_t)cp * kF + (f * 5 + v) * 64 + t];
+          const S fc = flux_c[(int64_t)cp * kF + (f * 5 + v) * 64 + b * 8 + a];
           const S du = coef * (fc - S(0.125) * fsum);
-          const int e = high ? 7 : 0;
-          int i, j, k;
-          if (d == 0) { i = e; j = a; k = b; }
-          else if (d == 1) { i = a; j = e; k = b; }
-          else { i = a; j = b; k = e; }
-          S* u = cur + (int64_t)cp * 5 * kAmrInt + v * kAmrInt + (k * 8 + j) * 8 + i;
-          *u = high ? *u + du : *u - du;
+          un[v] = high ? un[v] + du : un[v] - du;
         }
       }
-      __syncthreads();
+      if (!touched) continue;
+      if (amr_physical(un, ori)) {
+#pragma unroll
+        for (int v = 0; v < 5; ++v) u[v * kAmrInt] = un[v];
+      } else if (skipped) {
+        atomicAdd(skipped, 1);
+      }
     }
   }
 }

@@ -865,7 +865,7 @@ srhd_status srhd_amr_restrict(srhd_ctx* c, srhd_prec prec, void* cur, const int3
 srhd_status srhd_amr_flux_correct(srhd_ctx* c, srhd_prec prec, void* cur, const void* flux_coarse,
                                   const void* flux_fine0, const void* flux_fine1,
                                   const int32_t* faces, int32_t nrows, const double* dt_dh,
-                                  int32_t ntotal, void* stream) {
+                                  int32_t ntotal, int32_t* skipped, void* stream) {
   srhd_status st = check_ctx(c);
   if (st != SRHD_OK) return st;
   if (!valid_prec(prec)) return fail(SRHD_ERR_ARG, "invalid precision %d", int(prec));
@@ -875,16 +875,17 @@ srhd_status srhd_amr_flux_correct(srhd_ctx* c, srhd_prec prec, void* cur, const 
     return fail(SRHD_ERR_ARG, "a pointer argument is NULL");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const int grid = nrows < c->num_sms * 8 ? nrows : c->num_sms * 8;
+  const int ori = c->params.scheme == SRHD_SCHEME_TOTAL ? 1 : 0;
   if (is_double(prec))
-    srhd::amr_flux_correct_kernel<double><<<grid, 320, 0, s>>>(
+    srhd::amr_flux_correct_kernel<double><<<grid, 256, 0, s>>>(
         static_cast<double*>(cur), static_cast<const double*>(flux_coarse),
         static_cast<const double*>(flux_fine0), static_cast<const double*>(flux_fine1), faces,
-        nrows, dt_dh, ntotal);
+        nrows, dt_dh, ntotal, ori, skipped);
   else
-    srhd::amr_flux_correct_kernel<float><<<grid, 320, 0, s>>>(
+    srhd::amr_flux_correct_kernel<float><<<grid, 256, 0, s>>>(
         static_cast<float*>(cur), static_cast<const float*>(flux_coarse),
         static_cast<const float*>(flux_fine0), static_cast<const float*>(flux_fine1), faces,
-        nrows, dt_dh, ntotal);
+        nrows, dt_dh, ntotal, ori, skipped);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? SRHD_OK : cuda_fail(e, "amr_flux_correct launch");
 }

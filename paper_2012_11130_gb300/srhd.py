@@ -490,10 +490,14 @@ class Context:
         return cur
 
     def amr_flux_correct(self, cur, flux_coarse, flux_fine0, flux_fine1, faces, dt_dh,
-                         stream=None, prec=None):
+                         stream=None, prec=None, skipped=None):
         """Coarse-fine flux correction; faces [nrows][25] int32; patch-face
-        fluxes [ntotal][6][5][64]; dt_dh [ntotal][2] float64."""
+        fluxes [ntotal][6][5][64]; dt_dh [ntotal][2] float64; skipped
+        (optional) one device int32 to which the number of cells whose
+        correction was skipped (left unphysical by it) is added."""
         _need_cuda(cur, "cur")
+        if skipped is not None:
+            _need_cuda(skipped, "skipped", torch.int32)
         for t, nm in ((flux_coarse, "flux_coarse"), (flux_fine0, "flux_fine0"),
                       (flux_fine1, "flux_fine1")):
             _need_cuda(t, nm, cur.dtype)
@@ -502,7 +506,8 @@ class Context:
         N.check(self._L.srhd_amr_flux_correct(self._h, _prec(cur, prec), _ptr(cur),
                                               _ptr(flux_coarse), _ptr(flux_fine0),
                                               _ptr(flux_fine1), _ptr(faces), faces.shape[0],
-                                              _ptr(dt_dh), cur.shape[0], _stream(stream)),
+                                              _ptr(dt_dh), cur.shape[0], _ptr(skipped),
+                                              _stream(stream)),
                 "srhd_amr_flux_correct")
         return cur
 
@@ -569,9 +574,9 @@ def amr_restrict(cur, children, stream=None, prec=None):
 
 
 def amr_flux_correct(cur, flux_coarse, flux_fine0, flux_fine1, faces, dt_dh, stream=None,
-                     prec=None):
+                     prec=None, skipped=None):
     return default_context().amr_flux_correct(cur, flux_coarse, flux_fine0, flux_fine1, faces,
-                                              dt_dh, stream, prec)
+                                              dt_dh, stream, prec, skipped)
 
 
 def advance_patches_vl(cons_ghosted, dt_dh, **kw):

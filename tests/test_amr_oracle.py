@@ -167,3 +167,44 @@ def test_host_tables_match_hierarchy():
         Hierarchy((4, 4, 4), [lev[0], lev[1], np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0],
                                                        [1, 1, 0], [0, 0, 1], [1, 0, 1],
                                                        [0, 1, 1], [1, 1, 1]])])
+
+
+def test_flux_correction_skips_cells_left_unphysical(oracle):
+    # Section 3.3 (4): the correction is ignored on a cell whose corrected
+    # state fails Eq. (Unphysical result). Coarse patch (0, 1, 1) is
+    # unrefined and its +x face borders the refined block. With zero fine
+    # fluxes every cell on that face gets U += (dt/dh) F_coarse; one face
+    # cell gets a flux that turns its Etilde negative and must keep its
+    # state, the other 63 take the correction exactly.
+    levs, lev = _two_level()
+    data = _level_data(oracle, lev, Wk.bump_prims, DH0)
+    amr = amr_oracle.OracleAmr((4, 4, 4), levs, data, DH0)
+    zero = np.zeros((3, 5, 576))
+    for c in levs[1]:
+        amr.face_flux[1][c] = [zero, zero]
+    coarse_flux = {c: np.zeros((3, 5, 576)) for c in levs[0]}
+    c0 = (0, 1, 1)
+    before = {c: v.copy() for c, v in amr.data[0].items()}
+    coef = 0.4   # dt/dh of level 0
+    rng = np.random.default_rng(1)
+    u = before[c0]
+    F = coarse_flux[c0]
+    for k in range(8):
+        for j in range(8):
+            # a physical correction: a few per cent of each variable
+            F[0, :, (k * 8 + j) * 9 + 8] = 0.03 * rng.uniform(-1, 1, 5) * \
+                np.abs(u[:, k, j, 7]).max() / coef
+    F[0, 4, (5 * 8 + 3) * 9 + 8] = -2.0 * u[4, 5, 3, 7] / coef    # Etilde -> -Etilde
+    amr.flux_correct(0, coarse_flux)
+    assert amr.skipped == 1
+    for c, v in amr.data[0].items():
+        if c != c0:
+            assert np.array_equal(v, before[c])
+    got = amr.data[0][c0]
+    want = before[c0].copy()
+    for k in range(8):
+        for j in range(8):
+            if (j, k) != (3, 5):
+                want[:, k, j, 7] = want[:, k, j, 7] + coef * F[0, :, (k * 8 + j) * 9 + 8]
+    assert np.array_equal(got, want)
+    assert amr_oracle.OracleAmr.physical(got.reshape(5, -1)).all()

@@ -141,6 +141,9 @@ def test_amr_composite_conservation_and_graph_replay(oracle):
     a = _gpu_run(torch, srhd, h, levs, data, "fp64", 3)
     b = _gpu_run(torch, srhd, h, levs, data, "fp64", 3, graph=True)
     assert torch.equal(a.cur, b.cur)
+    # no flux correction was skipped (Section 3.3 (4)), so the composite
+    # update is conservative
+    assert a.skipped.item() == 0
     o, n = h.offsets[0], h.counts[0]
     C0 = _stack(h, levs, data)[o:o + n]
     # the t = 0 level-0 totals are those of the consistent (restricted) state
@@ -255,3 +258,58 @@ def test_fused_amr_bad_map_entry(oracle):
     assert _same_bits(torch, outs[0][0], outs[1][0]) and torch.equal(outs[0][1], outs[1][1])
     with pytest.raises(Exception, match="w"):
         ctx.advance_amr(C0, C0, C0, amap, dd, C0.clone(), w=1.5)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed_cf"])
+def test_flux_correction_skips_cells_left_unphysical(oracle, prec):
+    # Section 3.3 (4): the construction of the oracle pin
+    # (test_amr_oracle.py): with zero fine fluxes the cells on the +x face of
+    # coarse patch (0, 1, 1) get U += (dt/dh) F_coarse; one face cell's flux
+    # turns its Etilde negative, so that cell keeps its state and the
+    # library counts one skipped cell.
+    torch, srhd = require_gpu()
+    h, levs, data = _setup(oracle, 2, Wk.bump_prims)
+    if prec != "fp64":
+        data = [{c: v.astype(np.float32).astype(np.float64) for c, v in d.items()} for d in data]
+    c0 = (0, 1, 1)
+    p0 = h.offsets[0] + levs[0].index(c0)
+    u = data[0][c0]
+    rng = np.random.default_rng(1)
+    F = np.zeros((3, 5, 576))
+    for k in range(8):
+        for j in range(8):
+            F[0, :, (k * 8 + j) * 9 + 8] = 0.03 * rng.uniform(-1, 1, 5) * \
+                np.abs(u[:, k, j, 7]).max() / 0.4
+    F[0, 4, (5 * 8 + 3) * 9 + 8] = -2.0 * u[4, 5, 3, 7] / 0.4
+    if prec != "fp64":
+        F = F.astype(np.float32).astype(np.float64)
+    amr = amr_oracle.OracleAmr((4, 4, 4), levs, data, DH0)
+    zero = np.zeros((3, 5, 576))
+    for c in levs[1]:
+        amr.face_flux[1][c] = [zero, zero]
+    amr.flux_correct(0, {c: (F if c == c0 else zero) for c in levs[0]})
+    assert amr.skipped == 1
+    dt = torch_dtype(torch, prec)
+    n = h.ntotal
+    cur = to_dev(torch, _stack(h, levs, data), dt)
+    fc = np.zeros((n, 6, 5, 64))
+    for k in range(8):
+        for j in range(8):
+            fc[p0, 1, :, k * 8 + j] = F[0, :, (k * 8 + j) * 9 + 8]
+    fz = torch.zeros((n, 6, 5, 64), dtype=dt, device="cuda")
+    dd = np.tile([0.4 * DH0, DH0], (n, 1))
+    skipped = torch.zeros(1, dtype=torch.int32, device="cuda")
+    ctx = srhd.Context()
+    ctx.amr_flux_correct(cur, to_dev(torch, fc, dt), fz, fz,
+                         torch.from_numpy(h.faces[0]).cuda(),
+                         to_dev(torch, dd, torch.float64), prec=prec, skipped=skipped)
+    torch.cuda.synchronize()
+    assert skipped.item() == 1
+    got = to_np(cur)
+    ref = _stack(h, levs, amr.data)
+    tol = 1e-15 if prec == "fp64" else 2e-7
+    err = cons_rel_err(got.transpose(1, 0, 2, 3, 4), ref.transpose(1, 0, 2, 3, 4))
+    assert err.max() <= tol, err.max()
+    # the skipped cell kept its state exactly; its neighbours were corrected
+    assert np.array_equal(got[p0, :, 5, 3, 7], u[:, 5, 3, 7])
+    assert not np.array_equal(got[p0, :, 5, 4, 7], u[:, 5, 4, 7])
