@@ -294,13 +294,74 @@ def time_uniform_loop(torch, ctx, G, dt_dh, steps, warmup, barrier, prec, cached
     return total_ms, per, dn.item(), status_max
 
 
+def measure_link(torch, nbytes: int, reps: int = 5):
+    """Host link bandwidth of this run (GB/s): a pinned host buffer of
+    `nbytes` copied to the device, back, and both at once on two streams
+    (best of `reps`, CUDA events). Recorded beside the end-to-end figure,
+    whose copies move the same number of bytes per step."""
+    n = nbytes // 4
+    h_in = torch.empty(n, dtype=torch.float32, pin_memory=True)
+    h_out = torch.empty(n, dtype=torch.float32, pin_memory=True)
+    h_in.fill_(1.0)
+    d_a = torch.empty(n, dtype=torch.float32, device="cuda")
+    d_b = torch.empty(n, dtype=torch.float32, device="cuda")
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    best = {"h2d": 0.0, "d2h": 0.0, "both": 0.0}
+    for _ in range(reps):
+        for kind in ("h2d", "d2h", "both"):
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(s1)
+            s2.wait_event(e0)
+            if kind in ("h2d", "both"):
+                with torch.cuda.stream(s1):
+                    d_a.copy_(h_in, non_blocking=True)
+            if kind in ("d2h", "both"):
+                with torch.cuda.stream(s2):
+                    h_out.copy_(d_b, non_blocking=True)
+            s1.wait_stream(s2)
+            e1.record(s1)
+            torch.cuda.synchronize()
+            moved = nbytes * (2 if kind == "both" else 1)
+            best[kind] = max(best[kind], moved / (e0.elapsed_time(e1) * 1e-3) / 1e9)
+    del h_in, h_out, d_a, d_b
+    return {"h2d_gbs": best["h2d"], "d2h_gbs": best["d2h"], "both_directions_gbs": best["both"],
+            "bytes": nbytes, "how": "pinned host <-> device copy of the interior grid's size, "
+                                     "best of %d, CUDA events" % reps}
+
+
+def host_numa():
+    """NUMA placement of GPU 0 and of this process (Linux sysfs), for the
+    record of the end-to-end figure."""
+    out = {}
+    try:
+        import torch
+        p = torch.cuda.get_device_properties(0)
+        bus = f"{p.pci_domain_id:04x}:{p.pci_bus_id:02x}:{p.pci_device_id:02x}.0"
+        out["gpu_pci"] = bus
+        path = f"/sys/bus/pci/devices/{bus}/numa_node"
+        if os.path.exists(path):
+            out["gpu_numa_node"] = int(open(path).read().strip())
+    except Exception as e:  # noqa: BLE001
+        out["gpu_numa_error"] = str(e)[:120]
+    try:
+        out["cpus_allowed"] = len(os.sched_getaffinity(0))
+        out["host_numa_nodes"] = len([d for d in os.listdir("/sys/devices/system/node")
+                                      if re.fullmatch(r"node\d+", d)])
+    except Exception:  # noqa: BLE001
+        pass
+    return out
+
+
 def time_e2e(torch, ctx, G, dt_dh, steps, warmup, prec):
     """Headline end-to-end number: the uniform grid lives in pinned host
     memory and each step is one srhd_advance_uniform_host call, which copies
-    the interiors in, fills the ghost zones, steps and copies the updated
+    the interiors in, gathers the ghost zones, steps and copies the updated
     interiors, the patch status and the next time step out (chunked over
     four streams). Successive steps ping-pong between two host arrays, so
-    each step's input is the previous step's output."""
+    each step's input is the previous step's output. The call is
+    synchronous, so each step's wall time is taken on the host around it.
+    Returns (total seconds, per-step seconds, H2D bytes, D2H bytes)."""
     npatch = G.shape[0]
     npx = round(npatch ** (1 / 3))
     dh = float(dt_dh[0, 1])
@@ -311,18 +372,22 @@ def time_e2e(torch, ctx, G, dt_dh, steps, warmup, prec):
     st = torch.empty(npatch, dtype=torch.int32, pin_memory=True)
     for _ in range(warmup):
         ctx.advance_uniform_host(A, npx, npx, npx, dt, dh, cons_out=B, patch_status=st, prec=prec)
+        A, B = B, A
     torch.cuda.synchronize()
+    per = []
     t = time.perf_counter()
     for _ in range(steps):
+        t1 = time.perf_counter()
         _, dn = ctx.advance_uniform_host(A, npx, npx, npx, dt, dh, cons_out=B, patch_status=st,
                                          prec=prec)
+        per.append(time.perf_counter() - t1)
         A, B = B, A
     torch.cuda.synchronize()
     secs = time.perf_counter() - t
     h2d = A.numel() * A.element_size()
     d2h = B.numel() * B.element_size() + st.numel() * 4 + 8
     del A, B
-    return secs, h2d, d2h
+    return secs, per, h2d, d2h
 
 
 def time_e2e_ghosted(torch, ctx, G, dt_dh, steps, warmup, prec):
@@ -504,10 +569,13 @@ def bench_jet(torch, srhd, steps: int, gammas=(10.0, 20.0, 50.0, 100.0),
     with Lorentz factor gamma, density contrast 1e-3, T_jet = 10 into a cold
     static ambient (T = 1e-6); outflow elsewhere; dt_l = 0.4 dh_l. Every
     coarse step: per level substep ghost fill + update, then restriction and
-    coarse-fine flux correction (amr.AmrRun), as one CUDA graph. Reports
-    cell updates/s of the update launches alone (CUDA events around them,
-    eager steps) and of the whole step (graph replay), and the L1 difference
-    of rho between each float run and the FP64 run after `steps` steps."""
+    coarse-fine flux correction (amr.AmrRun), as one CUDA graph. Reports,
+    over the same `steps` coarse steps from the same initial state, cell
+    updates/s of the update launches alone (CUDA events around them, eager
+    steps), of the whole eager step and of the whole step replayed from the
+    graph, the cells whose flux correction was skipped (Section 3.3 (4)), and
+    the L1 difference of rho between each float run and the FP64 run after
+    `steps` steps."""
     from paper_2012_11130_gb300 import amr, workloads
     base, dh0 = (8, 8, 16), 1.0 / 64
     lev = workloads.jet_hierarchy(base=base)
@@ -534,38 +602,55 @@ def bench_jet(torch, srhd, steps: int, gammas=(10.0, 20.0, 50.0, 100.0),
             ctx = srhd.Context(srhd.Params(patch_variant=v))
             run = amr.AmrRun(ctx, h, C0, dh0, prec=prec, special=Cj.t().to(dt))
             out["cell_updates_per_coarse_step"] = run.cell_updates_per_step
-            run.step()                      # warm-up (one coarse step)
+            start = (run.cur.clone(), run.prev.clone())
+
+            def restore():
+                run.cur.copy_(start[0])
+                run.prev.copy_(start[1])
+                run.status.zero_()
+                run.skipped.zero_()
+            run.step()                      # warm-up (one coarse step), then the initial state
             torch.cuda.synchronize()
-            ne = min(4, max(1, steps - 1))
+            restore()
+            # eager: `steps` coarse steps, CUDA events around every update launch
             run.timer = []
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record()
-            for _ in range(ne):
+            for _ in range(steps):
                 run.step()
             e1.record()
             torch.cuda.synchronize()
-            upd_ms = sum(a.elapsed_time(b) for a, b in run.timer) / ne
-            eager_ms = e0.elapsed_time(e1) / ne
+            upd_ms = sum(a.elapsed_time(b) for a, b in run.timer) / steps
+            eager_ms = e0.elapsed_time(e1) / steps
             run.timer = None
-            nr = steps - 1 - ne
-            graph_ms = None
-            if nr > 0:
+            st = run.status.cpu()
+            skipped = int(run.skipped.item())
+            eager_final = run.cur.clone()
+            # graph replay of the same `steps` coarse steps from the same
+            # initial state (float paths; the FP64 step is long enough that
+            # launch overhead does not matter)
+            graph_ms = graph_equal = None
+            if prec != "fp64":
+                restore()
                 run.capture(warmup=0)
                 e0.record()
-                for _ in range(nr):
+                for _ in range(steps):
                     run.replay()
                 e1.record()
                 torch.cuda.synchronize()
-                graph_ms = e0.elapsed_time(e1) / nr
-            st = run.status.cpu()
+                graph_ms = e0.elapsed_time(e1) / steps
+                graph_equal = bool(torch.equal(run.cur, eager_final))
+            del eager_final
             upd = run.cell_updates_per_step
             out["runs"][f"{prec}_gamma{g:g}"] = {
                 "cell_updates_per_s_update_only": upd / (upd_ms * 1e-3),
-                "cell_updates_per_s_whole_step": upd / (graph_ms * 1e-3) if graph_ms else None,
+                "cell_updates_per_s_whole_step": upd / ((graph_ms or eager_ms) * 1e-3),
                 "ms_update_per_coarse_step": upd_ms, "ms_whole_step_graph": graph_ms,
-                "ms_whole_step_eager": eager_ms,
+                "ms_whole_step_eager": eager_ms, "graph_equals_eager": graph_equal,
+                "timed_steps": f"the same {steps} coarse steps for all three figures",
                 "patches_unphysical": int(((st >> 8) & 1).sum()),
                 "patches_retried_last_step": int(((st & 255) > 0).sum()),
+                "flux_corrections_skipped": skipped,
             }
             o, n = h.offsets[0], h.counts[0]
             lo, ln = h.offsets[-1], h.counts[-1]
@@ -627,8 +712,16 @@ def bench_con2pri_stress(torch, srhd, prec: str, log2n: int = 26, reps: int = 5)
         sel = ok & (lm >= lo) & (lm < lo + 2)
         if int(sel.sum()) > 0:
             bins[f"1e{lo}..1e{lo + 2}"] = float(err[sel].max())
+    accepted = int((st == 0).sum())
     out = {"cells": n, "cells_per_s": n / (ms * 1e-3), "ms": ms,
            "unphysical_fraction": float((st == 1).double().mean()),
+           "accepted_cells": accepted,
+           "cells_per_s_accepted": accepted / (ms * 1e-3),
+           "accepted_note": ("cells the conversion returns as physical (status 0); the others "
+                             "fail Eq. (Unphysical result) on their stored state: rounding the "
+                             "conserved state to the storage type perturbs A by about "
+                             "(1 + Mach^2) eps of that type, which in float storage reaches A "
+                             "itself for cold gas moving relativistically"),
            "max_roundtrip_error_by_mach": bins}
     del W, C, P, st, Pd, err, T0, h0, cs2, mach2, lm, ok
     torch.cuda.empty_cache()
@@ -815,9 +908,14 @@ def run_ours(args):
                             else "srhd_advance_uniform")}
         e2e = None
         if not args.no_e2e:
-            secs, h2d, d2h = time_e2e(torch, ctx, G, dt_dh, max(3, args.steps // 4), 1, prec)
-            e2e = {"value": world * cells * max(3, args.steps // 4) / secs, "unit": UNIT,
+            ne = max(3, args.steps)
+            secs, eper, h2d, d2h = time_e2e(torch, ctx, G, dt_dh, ne, max(3, args.warmup), prec)
+            e2e = {"value": world * cells * ne / secs, "unit": UNIT,
                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                   "steps": ne, "ms_per_step_median": 1e3 * statistics.median(eper),
+                   "ms_per_step_min": 1e3 * min(eper), "ms_per_step_max": 1e3 * max(eper),
+                   "value_at_median_step": world * cells / statistics.median(eper),
+                   "link": measure_link(torch, h2d), "numa": host_numa(),
                    "api": "srhd_advance_uniform_host (interiors in pinned host memory)"}
             if prec == precs[0]:
                 secs, h2d, d2h = time_e2e_ghosted(torch, ctx, G, dt_dh, 3, 1, prec)
