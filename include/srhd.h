@@ -409,6 +409,34 @@ srhd_status srhd_amr_flux_correct(srhd_ctx* ctx, srhd_prec prec, void* cur,
                                   const double* dt_dh, int32_t ntotal, int32_t* skipped,
                                   void* stream);
 
+/* Limited linear prolongation of the ghost cells that a fine level takes
+ * from the coarser level (Section 3.3 (3), ghost-zone interpolation): the
+ * conserved variables are interpolated, and where that gives a state failing
+ * Eq. (Unphysical result) the primitive variables (rho, U^x, U^y, U^z, p) are
+ * interpolated instead and converted back (always physical). Per axis the
+ * slope is the minmod of the two one-sided differences of the coarse cell
+ * with its neighbours; the fine cell centre lies a quarter of a coarse cell
+ * below or above the coarse centre along each axis. Coarse states are taken
+ * at the fine substep's time, (1 - w) prev + w cur, as in
+ * srhd_amr_fill_ghosts. The results go to rows of a special-state array that
+ * the maps of srhd_amr_fill_ghosts and srhd_advance_amr then reference
+ * (paper_2012_11130_gb300/amr.py builds such maps and tables).
+ *   cur, prev [ntotal][5][8^3]: coarse states after and before the coarse
+ *       level's step;
+ *   table [nrows][8] int32 per fine ghost cell: the coarse cell containing
+ *       it, its neighbours along -x, +x, -y, +y, -z, +z (flat indices
+ *       patch * 512 + cell; -1 where the coarse level does not cover the
+ *       neighbour, which gives a zero one-sided difference), then parity
+ *       bits (bit d set: the fine cell is in the upper half along axis d);
+ *   out [nrows][5] output (rows of the special-state array); a row whose
+ *       coarse cell index is out of range gives NaN;
+ *   fallbacks (nullable): one device int32 to which the number of rows
+ *       interpolated in primitive variables is added (the caller zeroes it);
+ *   0 <= w <= 1. */
+srhd_status srhd_amr_prolong(srhd_ctx* ctx, srhd_prec prec, const void* cur, const void* prev,
+                             const int32_t* table, int32_t nrows, int32_t ntotal, double w,
+                             void* out, int32_t* fallbacks, void* stream);
+
 /* srhd_fill_ghosts_uniform restricted to the patches p0 .. p0+n-1, so that a
  * caller can fill and advance part of a grid while the rest is in transit:
  * ghosted [n][5][12^3] receives patch p0+i in row i; interior [np][5][8^3]

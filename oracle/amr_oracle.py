@@ -15,8 +15,10 @@ update conservative.
 
 Written as the plain definitions: each ghost cell is looked up cell by cell
 (same-level patch, else the coarse cell containing it, taken linearly in time
-between the coarse states before and after the coarse step, which is
-piecewise-constant prolongation); restriction is the mean of the eight child
+between the coarse states before and after the coarse step: piecewise-constant
+prolongation, or, with prolong="linear", the limited linear interpolation of
+the conserved variables with the primitive-variable fallback of the
+ghost-zone passage of Section 3.3); restriction is the mean of the eight child
 cells; the flux correction replaces, for a coarse cell on a coarse-fine face,
 the coarse face flux by the mean of the fine face fluxes over the 2x2 fine
 faces and the two substeps, and is ignored on a cell that it would leave
@@ -37,7 +39,7 @@ class OracleAmr:
     data[l][(X, Y, Z)] = conserved [5][8][8][8] (z, y, x order)."""
 
     def __init__(self, base, levels, data, dh0, cfl_dt_factor=0.4, bc=("periodic",) * 3,
-                 inflow=None, flux_correction=True):
+                 inflow=None, flux_correction=True, prolong="constant"):
         self.base = tuple(base)
         self.levels = [[tuple(int(v) for v in c) for c in lev] for lev in levels]
         self.data = [{c: np.array(data[l][c], dtype=np.float64) for c in self.levels[l]}
@@ -50,6 +52,13 @@ class OracleAmr:
         self.flux_correction = flux_correction
         self.face_flux = [dict() for _ in self.levels]   # [l][coord] -> list per substep
         self.skipped = 0     # cells whose flux correction was ignored (Section 3.3 (4))
+        # ghost cells taken from the coarser level: "constant" (the coarse cell
+        # containing the ghost cell) or "linear" (limited linear interpolation
+        # of the conserved variables, primitive variables where that is
+        # unphysical: Section 3.3 (3))
+        assert prolong in ("constant", "linear")
+        self.prolong = prolong
+        self.prim_fallbacks = 0   # linear ghost cells interpolated in primitive variables
 
     def ncell(self, l):
         return [8 * (b << l) for b in self.base]
@@ -78,11 +87,80 @@ class OracleAmr:
             return self.data[l][key][:, z % 8, y % 8, x % 8]
         assert l > 0, "level 0 must cover the domain"
         xc, yc, zc = x // 2, y // 2, z // 2
-        kc = (xc // 8, yc // 8, zc // 8)
-        assert kc in self.data[l - 1], "proper nesting violated"
-        new = self.data[l - 1][kc][:, zc % 8, yc % 8, xc % 8]
-        old = self.old[l - 1][kc][:, zc % 8, yc % 8, xc % 8]
+        U = self._coarse(l - 1, xc, yc, zc, w)
+        assert U is not None, "proper nesting violated"
+        if self.prolong == "constant":
+            return U
+        return self._prolong_linear(l - 1, (xc, yc, zc), (x % 2, y % 2, z % 2), w)
+
+    def _coarse(self, l, x, y, z, w):
+        """State of level-l cell (x, y, z) between its level's states before
+        (w = 0) and after (w = 1) its step, after the boundary rule (periodic
+        wrap, outflow clamp); None where level l does not cover the cell."""
+        N = self.ncell(l)
+        co = [x, y, z]
+        for a in range(3):
+            if co[a] < 0 or co[a] >= N[a]:
+                co[a] = co[a] % N[a] if self.bc[a] == "periodic" else min(max(co[a], 0), N[a] - 1)
+        x, y, z = co
+        kc = (x // 8, y // 8, z // 8)
+        if kc not in self.data[l]:
+            return None
+        new = self.data[l][kc][:, z % 8, y % 8, x % 8]
+        old = self.old[l][kc][:, z % 8, y % 8, x % 8]
         return (1.0 - w) * old + w * new
+
+    @staticmethod
+    def _minmod(a, b):
+        """minmod of the one-sided differences (elementwise): the one of
+        smaller magnitude if they have the same sign, else 0."""
+        return np.where(a * b > 0, np.where(np.abs(a) < np.abs(b), a, b), 0.0)
+
+    def _prolong_linear(self, lc, c, parity, w):
+        """Section 3.3 (3): the state of a fine ghost cell in coarse cell c
+        (level lc) by limited linear interpolation, the fine cell centre lying
+        at a quarter of a coarse cell from the coarse centre along each axis
+        (parity 0: below, 1: above). Per axis the slope is the minmod of the
+        two one-sided differences of the coarse cell with its neighbours (0
+        where a neighbour is not on level lc). The conserved variables are
+        interpolated; if the result fails Eq. (Unphysical result), the
+        primitive variables (rho, U^x, U^y, U^z, p) of the same coarse cells
+        are interpolated instead and converted to conserved variables."""
+        x, y, z = c
+        Uc = self._coarse(lc, x, y, z, w)
+        nb = []
+        for d in range(3):
+            pair = []
+            for s in (-1, 1):
+                q = [x, y, z]
+                q[d] += s
+                pair.append(self._coarse(lc, *q, w))
+            nb.append(pair)
+
+        def interp(center, nbs):
+            out = center.copy()
+            for d in range(3):
+                m, p = nbs[d]
+                lo = center - m if m is not None else np.zeros(5)
+                hi = p - center if p is not None else np.zeros(5)
+                out = out + (0.25 if parity[d] else -0.25) * self._minmod(lo, hi)
+            return out
+
+        U = interp(Uc, nb)
+        if self.physical(U.reshape(5, 1))[0]:
+            return U
+        self.prim_fallbacks += 1
+
+        def prim(u):
+            if u is None:
+                return None
+            r = O.con2pri(u.reshape(5, 1))
+            assert r["status"][0] != O.UNPHYSICAL, "unphysical coarse state"
+            return r["prim"][:, 0]
+        Wf = interp(prim(Uc), [[prim(m), prim(p)] for m, p in nb])
+        C, st = O.prim2con(Wf.reshape(5, 1))
+        assert st[0] == 0
+        return C[:, 0]
 
     def ghosted(self, l, c, w):
         X, Y, Z = c

@@ -30,7 +30,7 @@ EXPORTS = ("srhd_default_params", "srhd_create", "srhd_destroy", "srhd_last_erro
            "srhd_advance_patches_vl", "srhd_fill_ghosts_uniform3",
            "srhd_fill_ghosts_uniform_range", "srhd_advance_uniform_host",
            "srhd_advance_uniform", "srhd_advance_amr", "srhd_con2pri_patches",
-           "srhd_advance_uniform_prim", "srhd_reciprocal_f64")
+           "srhd_advance_uniform_prim", "srhd_reciprocal_f64", "srhd_amr_prolong")
 SRHD_AMR_COARSE = 1 << 30
 
 
@@ -115,6 +115,8 @@ def load(path: str = LIB_PATH):
     L.srhd_amr_flux_correct.restype = st
     L.srhd_amr_flux_correct.argtypes = [vp, ctypes.c_int, vp, vp, vp, vp, vp, i32, vp, i32, vp,
                                          vp]
+    L.srhd_amr_prolong.restype = st
+    L.srhd_amr_prolong.argtypes = [vp, ctypes.c_int, vp, vp, vp, i32, i32, d, vp, vp, vp]
     _lib = L
     return L
 

@@ -128,9 +128,28 @@ class Hierarchy:
     `center` (the two transverse coordinates, level-0 cell units); those cells
     take special state `index` instead of the outflow copy.
     Patches are numbered level by level in the given order.
+    prolong: how a level takes the ghost cells that lie on the coarser level:
+    "constant" (map entries with SRHD_AMR_COARSE: the coarse cell containing
+    the ghost cell) or "linear" (Section 3.3 (3): limited linear
+    interpolation with the primitive-variable fallback, srhd_amr_prolong).
+    With "linear", every distinct such ghost cell of level l is a row of
+    prolong_tables[l] ([rows][8] int32, the format of srhd_amr_prolong) and
+    the map entries that read it are special states nspecial +
+    prolong_offsets[l] + row: the caller's special array holds its nspecial
+    fixed states (inflow) followed by the prolongation rows of all levels,
+    which srhd_amr_prolong rewrites before each substep of the level.
     """
 
-    def __init__(self, base, levels, bc=("periodic",) * 3, inflow=None):
+    def __init__(self, base, levels, bc=("periodic",) * 3, inflow=None, prolong="constant",
+                 nspecial=None):
+        if prolong not in ("constant", "linear"):
+            raise ValueError("prolong must be 'constant' or 'linear'")
+        self.prolong = prolong
+        self.nspecial = (int(nspecial) if nspecial is not None else
+                         (int(inflow["index"]) + 1 if inflow is not None else 0))
+        self.prolong_tables = []
+        self.prolong_offsets = []
+        self._prolong_rows = 0
         self.base = tuple(int(b) for b in base)
         self.coords = [np.asarray(c, dtype=np.int64).reshape(-1, 3) for c in levels]
         self.nlev = len(self.coords)
@@ -160,6 +179,9 @@ class Hierarchy:
         c = self.coords[l]
         n = len(c)
         if n == 0:
+            if self.prolong == "linear":
+                self.prolong_offsets.append(self._prolong_rows)
+                self.prolong_tables.append(np.zeros((0, 8), np.int32))
             return np.zeros((0, 1728), np.int64)
         N = self.cells(l)
         g = np.arange(12) - 2
@@ -196,9 +218,52 @@ class Hierarchy:
                 raise ValueError(f"level {l}: ghost zones not covered by level {l - 1} "
                                  "(proper nesting violated)")
             cc = ((zc % 8) * 8 + (yc % 8)) * 8 + (xc % 8)
-            src[need] = (ic * 512 + cc) | (1 << 30)
+            if self.prolong == "constant":
+                src[need] = (ic * 512 + cc) | (1 << 30)
+            else:
+                rows, which = self._prolong_table(l, x[need], y[need], z[need])
+                src[need] = -1 - (self.nspecial + self._prolong_rows + which)
+                self.prolong_offsets.append(self._prolong_rows)
+                self.prolong_tables.append(rows)
+                self._prolong_rows += len(rows)
+        if self.prolong == "linear" and len(self.prolong_tables) <= l:
+            self.prolong_offsets.append(self._prolong_rows)
+            self.prolong_tables.append(np.zeros((0, 8), np.int32))
         out = np.where(special >= 0, -1 - special, src)
         return out.reshape(n, 1728)
+
+    def _coarse_flat(self, l, x, y, z):
+        """Flat index patch * 512 + cell of level-l cells (x, y, z) after the
+        boundary rule (periodic wrap, outflow clamp), -1 where level l does
+        not cover the cell."""
+        N = self.cells(l)
+        co = [np.array(v, dtype=np.int64) for v in (x, y, z)]
+        for a in range(3):
+            if self.bc[a] == "periodic":
+                co[a] %= N[a]
+            else:
+                np.clip(co[a], 0, N[a] - 1, out=co[a])
+        x, y, z = co
+        idx = self.grids[l][z // 8, y // 8, x // 8]
+        cell = ((z % 8) * 8 + (y % 8)) * 8 + (x % 8)
+        return np.where(idx >= 0, idx * 512 + cell, -1)
+
+    def _prolong_table(self, l, x, y, z):
+        """Rows of srhd_amr_prolong for the level-l ghost cells (x, y, z)
+        (boundary rule already applied) taken from level l - 1, one row per
+        distinct cell; returns (rows [m][8] int32, row of each input cell)."""
+        key = np.stack([x, y, z], axis=1)
+        uniq, which = np.unique(key, axis=0, return_inverse=True)
+        xf, yf, zf = uniq[:, 0], uniq[:, 1], uniq[:, 2]
+        xc, yc, zc = xf // 2, yf // 2, zf // 2
+        rows = np.empty((len(uniq), 8), np.int64)
+        rows[:, 0] = self._coarse_flat(l - 1, xc, yc, zc)
+        for k, (dx, dy, dz) in enumerate(((-1, 0, 0), (1, 0, 0), (0, -1, 0), (0, 1, 0),
+                                          (0, 0, -1), (0, 0, 1))):
+            rows[:, 1 + k] = self._coarse_flat(l - 1, xc + dx, yc + dy, zc + dz)
+        rows[:, 7] = (xf % 2) | ((yf % 2) << 1) | ((zf % 2) << 2)
+        assert np.all(rows[:, 0] >= 0)
+        return rows.astype(np.int32), which.reshape(-1)
 
     def _child_index(self, l, X, Y, Z):
         g = self.grids[l + 1]
@@ -263,7 +328,10 @@ class AmrRun:
     map (srhd_advance_amr; with fused=False a separate ghost fill into a
     ghosted batch and srhd_advance_patches, which give the same bits), and
     after the two substeps of level l + 1 the restriction of l + 1 onto l and
-    the coarse-fine flux correction of l. A coarse step has no host
+    the coarse-fine flux correction of l. With a hierarchy built with
+    prolong="linear", each substep of a level l >= 1 first computes the
+    level's coarse-sourced ghost cells by srhd_amr_prolong (counting the
+    primitive-variable fallbacks in prolong_fallbacks). A coarse step has no host
     synchronisation or allocation and can be captured into a CUDA graph
     (capture / replay)."""
 
@@ -289,6 +357,22 @@ class AmrRun:
         self.children = [torch.from_numpy(c).to(dev) for c in hier.children]
         self.faces = [torch.from_numpy(f).to(dev) for f in hier.faces]
         self.special = None if special is None else special.to(device=dev, dtype=dt).contiguous()
+        # limited linear prolongation (Section 3.3 (3)): the special-state
+        # array holds the fixed states, then one row per coarse-sourced ghost
+        # cell of every level, rewritten by srhd_amr_prolong before each
+        # substep of the level
+        self.prolong_tables = None
+        self.prolong_fallbacks = torch.zeros(1, dtype=torch.int32, device=dev)
+        if hier.prolong == "linear":
+            nfix = hier.nspecial
+            if nfix and (self.special is None or self.special.shape[0] < nfix):
+                raise ValueError(f"the hierarchy's maps use {nfix} fixed special states")
+            rows = sum(len(t) for t in hier.prolong_tables)
+            sp = torch.zeros((nfix + rows, 5), dtype=dt, device=dev)
+            if nfix:
+                sp[:nfix] = self.special[:nfix]
+            self.special = sp
+            self.prolong_tables = [torch.from_numpy(t).to(dev) for t in hier.prolong_tables]
         dd = torch.empty((n, 2), dtype=torch.float64)
         for l in range(hier.nlev):
             o, c = hier.offsets[l], hier.counts[l]
@@ -312,6 +396,12 @@ class AmrRun:
     def _advance(self, l, w, parity, stream):
         h, ctx = self.h, self.ctx
         o, c = h.offsets[l], h.counts[l]
+        if self.prolong_tables is not None and len(self.prolong_tables[l]):
+            r0 = h.nspecial + h.prolong_offsets[l]
+            nr = len(self.prolong_tables[l])
+            ctx.amr_prolong(self.cur, self.prev, self.prolong_tables[l],
+                            self.special[r0:r0 + nr], w=w, fallbacks=self.prolong_fallbacks,
+                            stream=stream, prec=self.prec)
         if not self.fused:
             ctx.amr_fill_ghosts(self.cur, self.prev, self.ghosted, self.map, o, c, w,
                                 self.special, stream=stream, prec=self.prec)

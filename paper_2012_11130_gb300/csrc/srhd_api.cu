@@ -890,6 +890,27 @@ srhd_status srhd_amr_flux_correct(srhd_ctx* c, srhd_prec prec, void* cur, const 
   return e == cudaSuccess ? SRHD_OK : cuda_fail(e, "amr_flux_correct launch");
 }
 
+srhd_status srhd_amr_prolong(srhd_ctx* c, srhd_prec prec, const void* cur, const void* prev,
+                             const int32_t* table, int32_t nrows, int32_t ntotal, double w,
+                             void* out, int32_t* fallbacks, void* stream) {
+  srhd_status st = check_ctx(c);
+  if (st != SRHD_OK) return st;
+  if (!valid_prec(prec)) return fail(SRHD_ERR_ARG, "invalid precision %d", int(prec));
+  if (nrows < 0 || ntotal < 1) return fail(SRHD_ERR_ARG, "nrows < 0 or ntotal < 1");
+  if (!(w >= 0.0 && w <= 1.0)) return fail(SRHD_ERR_ARG, "time weight w must be in [0, 1]");
+  if (nrows == 0) return SRHD_OK;
+  if (!cur || !prev || !table || !out) return fail(SRHD_ERR_ARG, "cur/prev/table/out is NULL");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int grid = grid_for(c, nrows, 8);
+  const int maxit = newton_maxit(c, prec);
+  cudaError_t e = dispatch(prec, [&](auto L) {
+    return decltype(L)::prolong(cur, prev, table, nrows, w, out,
+                                (int64_t)ntotal * srhd::kAmrInt, maxit, c->params.scheme,
+                                eos_arg(c->params), fallbacks, grid, s);
+  });
+  return e == cudaSuccess ? SRHD_OK : cuda_fail(e, "amr_prolong launch");
+}
+
 }  // extern "C"
 
 // ---- uniform grid resident in host memory ----------------------------------

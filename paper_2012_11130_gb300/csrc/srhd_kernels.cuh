@@ -1279,6 +1279,10 @@ template <class P> struct Launch {
   static cudaError_t fill_ghosts(const void* interior, void* ghosted, int npx, int npy, int npz,
                                  const int32_t* bc, int gh, int64_t p0, int64_t n, int grid,
                                  cudaStream_t s);
+  // limited linear prolongation of AMR ghost cells (srhd_prolong.cuh)
+  static cudaError_t prolong(const void* cur, const void* prev, const int32_t* table,
+                             int64_t nrows, double w, void* out, int64_t ncells, int maxit,
+                             int ori, EosArg eos, int32_t* fallbacks, int grid, cudaStream_t s);
 };
 
 constexpr int kCflThreads = 256;

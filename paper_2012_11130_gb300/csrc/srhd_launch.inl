@@ -5,6 +5,7 @@
 #pragma once
 
 #include "srhd_kernels.cuh"
+#include "srhd_prolong.cuh"
 #include "srhd_vl.cuh"
 
 namespace srhd {
@@ -259,6 +260,22 @@ cudaError_t Launch<P>::fill_ghosts(const void* interior, void* ghosted, int npx,
                                                   static_cast<S*>(ghosted), npx, npy, npz, bc[0],
                                                   bc[1], bc[2], p0, n, wide);
   }
+  return cudaGetLastError();
+}
+
+template <class P>
+cudaError_t Launch<P>::prolong(const void* cur, const void* prev, const int32_t* table,
+                               int64_t nrows, double w, void* out, int64_t ncells, int maxit,
+                               int ori, EosArg eos, int32_t* fallbacks, int grid, cudaStream_t s) {
+  using S = typename P::S;
+  if (eos.poly)
+    amr_prolong_kernel<P, EosPoly><<<grid, 128, 0, s>>>(
+        static_cast<const S*>(cur), static_cast<const S*>(prev), table, nrows, S(w),
+        static_cast<S*>(out), ncells, maxit, ori, EosPoly{eos.gam}, fallbacks);
+  else
+    amr_prolong_kernel<P, EosTM><<<grid, 128, 0, s>>>(
+        static_cast<const S*>(cur), static_cast<const S*>(prev), table, nrows, S(w),
+        static_cast<S*>(out), ncells, maxit, ori, EosTM{}, fallbacks);
   return cudaGetLastError();
 }
 

@@ -27,7 +27,7 @@ from . import _native as N
 __all__ = ["Params", "Context", "prim2con", "con2pri", "flux_patches", "advance_patches",
            "cfl_dt", "cfl_dt_noalloc", "fill_ghosts_uniform", "fill_ghosts_uniform3",
            "advance_patches_vl", "amr_fill_ghosts", "amr_restrict",
-           "amr_flux_correct", "default_context"]
+           "amr_flux_correct", "amr_prolong", "default_context"]
 
 
 @dataclass
@@ -511,6 +511,25 @@ class Context:
                 "srhd_amr_flux_correct")
         return cur
 
+    def amr_prolong(self, cur, prev, table, out, w=0.0, fallbacks=None, stream=None, prec=None):
+        """Limited linear prolongation of coarse-sourced ghost cells (rows of
+        `table` [nrows][8] int32) into `out` [nrows][5]; fallbacks (optional)
+        one device int32 counting the rows interpolated in primitive
+        variables."""
+        _need_cuda(cur, "cur")
+        _need_cuda(prev, "prev", cur.dtype)
+        _need_cuda(out, "out", cur.dtype)
+        _need_cuda(table, "table", torch.int32)
+        if fallbacks is not None:
+            _need_cuda(fallbacks, "fallbacks", torch.int32)
+        if out.shape[0] < table.shape[0] or not out.is_contiguous():
+            raise ValueError("out must be a contiguous [>= nrows][5] tensor")
+        N.check(self._L.srhd_amr_prolong(self._h, _prec(cur, prec), _ptr(cur), _ptr(prev),
+                                         _ptr(table), table.shape[0], cur.shape[0], float(w),
+                                         _ptr(out), _ptr(fallbacks), _stream(stream)),
+                "srhd_amr_prolong")
+        return out
+
 
 _default = {}
 
@@ -577,6 +596,10 @@ def amr_flux_correct(cur, flux_coarse, flux_fine0, flux_fine1, faces, dt_dh, str
                      prec=None, skipped=None):
     return default_context().amr_flux_correct(cur, flux_coarse, flux_fine0, flux_fine1, faces,
                                               dt_dh, stream, prec, skipped)
+
+
+def amr_prolong(cur, prev, table, out, w=0.0, fallbacks=None, stream=None, prec=None):
+    return default_context().amr_prolong(cur, prev, table, out, w, fallbacks, stream, prec)
 
 
 def advance_patches_vl(cons_ghosted, dt_dh, **kw):

@@ -208,3 +208,182 @@ def test_flux_correction_skips_cells_left_unphysical(oracle):
                 want[:, k, j, 7] = want[:, k, j, 7] + coef * F[0, :, (k * 8 + j) * 9 + 8]
     assert np.array_equal(got, want)
     assert amr_oracle.OracleAmr.physical(got.reshape(5, -1)).all()
+
+
+def _one_patch_amr(oracle, prims_fn):
+    """A one-patch level 0 (outflow) whose 8^3 conserved cells come from
+    prims_fn(i, j, k) -> (rho, Ux, Uy, Uz, p); for direct prolongation calls."""
+    W = np.array([[[prims_fn(i, j, k) for i in range(8)] for j in range(8)] for k in range(8)])
+    W = W.transpose(3, 0, 1, 2).reshape(5, -1)
+    C, st = oracle.prim2con(W)
+    assert np.all(st == 0)
+    data = [{(0, 0, 0): C.reshape(5, 8, 8, 8)}, {}]
+    return amr_oracle.OracleAmr((1, 1, 1), [[(0, 0, 0)], []], data, DH0,
+                                bc=("outflow",) * 3, prolong="linear")
+
+
+def test_linear_prolongation_is_exact_for_linear_data(oracle):
+    # Section 3.3 (3), limited linear interpolation: for conserved variables
+    # that are linear in the cell coordinates, both one-sided differences
+    # are equal, the limiter keeps them, and the fine ghost value is the
+    # linear function at the fine cell centre, a quarter of a coarse cell
+    # from the coarse centre along each axis.
+    amr = _one_patch_amr(oracle, lambda i, j, k: (1.0, 0.0, 0.0, 0.0, 1.0))
+    u = amr.data[0][(0, 0, 0)]
+    k, j, i = np.meshgrid(np.arange(8), np.arange(8), np.arange(8), indexing="ij")
+    lin = np.array([2.0 + 0.01 * i - 0.02 * j + 0.03 * k, 0.1 + 0.005 * i, -0.05 + 0.004 * k,
+                    0.02 * j, 3.0 + 0.01 * i + 0.01 * j - 0.02 * k])
+    u[...] = lin
+    amr.old[0][(0, 0, 0)] = u.copy()
+    for c in ((3, 4, 2), (1, 6, 5), (6, 1, 1)):
+        for par in ((0, 0, 0), (1, 0, 1), (1, 1, 1), (0, 1, 0)):
+            got = amr._prolong_linear(0, c, par, 0.0)
+            x = [c[a] + (0.25 if par[a] else -0.25) for a in range(3)]
+            want = np.array([2.0 + 0.01 * x[0] - 0.02 * x[1] + 0.03 * x[2], 0.1 + 0.005 * x[0],
+                             -0.05 + 0.004 * x[2], 0.02 * x[1],
+                             3.0 + 0.01 * x[0] + 0.01 * x[1] - 0.02 * x[2]])
+            assert np.allclose(got, want, rtol=1e-14, atol=1e-16), (c, par, got - want)
+    assert amr.prim_fallbacks == 0
+
+
+def test_linear_prolongation_conserves_and_limits(oracle):
+    # The eight fine cells of a coarse cell average to the coarse state
+    # (offsets +-1/4 cancel), and at a local extremum the slope is zero
+    # (minmod of one-sided differences of opposite sign).
+    rng = np.random.default_rng(4)
+    R = rng.uniform(0.5, 2.0, (8, 8, 8))
+    amr = _one_patch_amr(oracle, lambda i, j, k: (R[k, j, i], 0.1 * R[j, i, k], 0.0, 0.0,
+                                                  1.0 + 0.5 * R[i, k, j]))
+    for c in ((3, 4, 2), (1, 1, 6)):
+        kids = [amr._prolong_linear(0, c, ((o & 1), (o >> 1) & 1, o >> 2), 0.0)
+                for o in range(8)]
+        Uc = amr.data[0][(0, 0, 0)][:, c[2], c[1], c[0]]
+        assert np.allclose(np.mean(kids, axis=0), Uc, rtol=1e-15, atol=1e-16)
+    u = amr.data[0][(0, 0, 0)]
+    u[:, 3, 3, 3] = 2.0 * u.reshape(5, -1).max(axis=1)   # a local maximum of every variable
+    amr.old[0][(0, 0, 0)] = u.copy()
+    peak = [amr._prolong_linear(0, (3, 3, 3), (o & 1, (o >> 1) & 1, o >> 2), 0.0)
+            for o in range(8)]
+    for p in peak:
+        assert np.array_equal(p, u[:, 3, 3, 3])
+    assert amr.prim_fallbacks == 0
+
+
+def test_linear_prolongation_falls_back_to_primitives(oracle):
+    # Cold gas (T = 1e-6) moving at U^x = 9, 10, 12 in three neighbouring
+    # cells: cold states lie on the boundary of the physical cone
+    # E^2 >= D^2 + |M|^2, so extrapolating the conserved variables from the
+    # middle cell towards the right (1.25 C - 0.25 L, the minmod picks the
+    # smaller left difference) leaves the cone: Eq. (Unphysical result)
+    # fails and the primitive variables are interpolated instead
+    # (U^x = 10 + 0.25 * 1), which Eq. (Unphysical result) always accepts.
+    ux = {2: 9.0, 3: 10.0, 4: 12.0}
+    amr = _one_patch_amr(oracle, lambda i, j, k: (1.0, ux.get(i, 10.0), 0.0, 0.0, 1e-6))
+    c = (3, 4, 4)
+    Cc = amr.data[0][(0, 0, 0)][:, 4, 4, 3]
+    Cl = amr.data[0][(0, 0, 0)][:, 4, 4, 2]
+    cons_interp = Cc + 0.25 * (Cc - Cl)
+    assert not amr_oracle.OracleAmr.physical(cons_interp.reshape(5, 1))[0]
+    got = amr._prolong_linear(0, c, (1, 0, 0), 0.0)
+    assert amr.prim_fallbacks == 1
+    want, _ = oracle.prim2con(np.array([[1.0], [10.25], [0.0], [0.0], [1e-6]]))
+    assert np.allclose(got, want[:, 0], rtol=1e-7, atol=0)
+    assert amr_oracle.OracleAmr.physical(got.reshape(5, 1))[0]
+    # towards the left the conserved interpolation (1.25 C - 0.25 L again,
+    # the same minmod side) fails too; at parity 0 along an axis with equal
+    # neighbours nothing changes
+    same = amr._prolong_linear(0, c, (0, 0, 0), 0.0)
+    assert amr_oracle.OracleAmr.physical(same.reshape(5, 1))[0]
+
+
+def test_linear_prolongation_reduces_interface_error(oracle):
+    # A two-level run of a smooth field against the uniform grid at the fine
+    # resolution: taking the fine level's ghost zones by limited linear
+    # interpolation instead of the containing coarse cell makes the fine
+    # level's error after one coarse step markedly smaller (the ghost values
+    # are second- instead of first-order accurate).
+    base = (4, 4, 4)
+    lev = Wk.nested_hierarchy(base=base, nlev=2)
+    levs = [[tuple(c) for c in l] for l in lev]
+    data = _level_data(oracle, lev, Wk.bump_prims, DH0)
+    # uniform fine-grid reference from the same smooth field
+    W = Wk.level_prims([(x, y, z) for z in range(8) for y in range(8) for x in range(8)], 1,
+                       Wk.bump_prims, DH0)
+    C, _ = oracle.prim2con(W.transpose(1, 0, 2, 3, 4).reshape(5, -1))
+    C = C.reshape(5, 8, 8, 8, 8, 8, 8)   # [v][Z][Y][X][k][j][i] for patches (X, Y, Z) in z,y,x order
+    fine = np.zeros((5, 64, 64, 64))
+    n = 0
+    for z in range(8):
+        for y in range(8):
+            for x in range(8):
+                fine[:, 8 * z:8 * z + 8, 8 * y:8 * y + 8, 8 * x:8 * x + 8] = \
+                    C.reshape(5, 512, 8, 8, 8)[:, n]
+                n += 1
+    dh1 = DH0 / 2
+    ref = fine
+    for _ in range(2):
+        ref = oracle.advance_block(oracle.fill_ghosts(ref, (1, 1, 1), "periodic"), (64, 64, 64),
+                                   (1, 1, 1), 0.4 * dh1, dh1)["out"]
+    errs = {}
+    for mode in ("constant", "linear"):
+        amr = amr_oracle.OracleAmr(base, levs, data, DH0, prolong=mode)
+        _consistent(amr)
+        amr.step()
+        e = []
+        for (X, Y, Z), u in amr.data[1].items():
+            r = ref[:, 8 * Z:8 * Z + 8, 8 * Y:8 * Y + 8, 8 * X:8 * X + 8]
+            e.append(np.abs(u[0] - r[0]) / r[0])
+        errs[mode] = float(np.max(e))
+    assert errs["linear"] < 0.6 * errs["constant"], errs
+
+
+def prolong_rows_coords(h, l):
+    """One fine-level cell (x, y, z) of level l (boundary rule applied) per
+    row of h.prolong_tables[l], found through the map."""
+    t = h.prolong_tables[l]
+    coords = np.full((len(t), 3), -1, np.int64)
+    base = h.nspecial + h.prolong_offsets[l]
+    N = h.cells(l)
+    for n, (X, Y, Z) in enumerate(h.coords[l]):
+        m = h.map[h.offsets[l] + n].astype(np.int64)
+        r = -1 - m - base
+        sel = (m < 0) & (r >= 0) & (r < len(t))
+        for c in np.nonzero(sel)[0]:
+            k, j, i = c // 144, (c // 12) % 12, c % 12
+            co = [8 * X + i - 2, 8 * Y + j - 2, 8 * Z + k - 2]
+            for a in range(3):
+                co[a] = co[a] % N[a] if h.bc[a] == "periodic" else min(max(co[a], 0), N[a] - 1)
+            coords[r[c]] = co
+    assert np.all(coords >= 0), "a table row that no map entry reads"
+    return coords
+
+
+@pytest.mark.parametrize("bc", [("periodic",) * 3, ("outflow", "periodic", "outflow")])
+def test_host_prolong_tables_match_oracle_neighbours(oracle, bc):
+    # The host tables of limited linear prolongation name, for every
+    # coarse-sourced ghost cell, the coarse cell the oracle's geometric
+    # lookup finds, its six neighbours (or -1 where the coarse level does
+    # not cover one) and the fine cell's parity along each axis.
+    lev = Wk.nested_hierarchy(base=(4, 4, 4), nlev=3)
+    h = Hierarchy((4, 4, 4), lev, bc=bc, prolong="linear")
+    rng = np.random.default_rng(5)
+    cur = rng.uniform(1, 2, (h.ntotal, 5, 8, 8, 8))
+    levs = [[tuple(c) for c in l] for l in lev]
+    data = [{c: cur[h.offsets[l] + n] for n, c in enumerate(levs[l])} for l in range(3)]
+    amr = amr_oracle.OracleAmr((4, 4, 4), levs, data, DH0, bc=bc, prolong="linear")
+    flat = cur.transpose(1, 0, 2, 3, 4).reshape(5, -1)
+    for l in (1, 2):
+        t = h.prolong_tables[l]
+        xyz = prolong_rows_coords(h, l)
+        for r in range(0, len(t), 17):
+            x, y, z = xyz[r]
+            xc, yc, zc = x // 2, y // 2, z // 2
+            assert np.array_equal(flat[:, t[r, 0]], amr._coarse(l - 1, xc, yc, zc, 1.0))
+            for k, (dx, dy, dz) in enumerate(((-1, 0, 0), (1, 0, 0), (0, -1, 0), (0, 1, 0),
+                                              (0, 0, -1), (0, 0, 1))):
+                want = amr._coarse(l - 1, xc + dx, yc + dy, zc + dz, 1.0)
+                if t[r, 1 + k] < 0:
+                    assert want is None
+                else:
+                    assert np.array_equal(flat[:, t[r, 1 + k]], want)
+            assert t[r, 7] == (x % 2) | ((y % 2) << 1) | ((z % 2) << 2)
