@@ -580,13 +580,15 @@ def bench_jet(torch, srhd, steps: int, gammas=(10.0, 20.0, 50.0, 100.0),
     base, dh0 = (8, 8, 16), 1.0 / 64
     lev = workloads.jet_hierarchy(base=base)
     inflow = dict(axis=2, side=0, center=(32.0, 32.0), radius=2.0, index=0)
-    h = amr.Hierarchy(base, lev, bc=("outflow",) * 3, inflow=inflow)
+    h = amr.Hierarchy(base, lev, bc=("outflow",) * 3, inflow=inflow, prolong="linear")
     c64 = srhd.Context(srhd.Params())
     out = {"workload": ("relativistic jet, [0,1]x[0,1]x[0,2], base 64x64x128, 4 levels of 8^3 "
                         "patches (finest-equivalent 512x512x1024) refined around beam and "
                         "cocoon; beam radius 16 finest cells through z = 0, density contrast "
-                        "1e-3, T_jet = 10, ambient T = 1e-6; ghost fill, restriction and "
-                        "flux correction on the GPU; one CUDA graph per coarse step"),
+                        "1e-3, T_jet = 10, ambient T = 1e-6; ghost fill (limited linear "
+                        "prolongation with the primitive-variable fallback), restriction and "
+                        "flux correction (skipped on cells it leaves unphysical) on the GPU; "
+                        "one CUDA graph per coarse step"),
            "patches_per_level": h.counts, "patches": h.ntotal,
            "cell_updates_per_coarse_step": None, "coarse_steps": steps, "runs": {}}
     dev = torch.device("cuda")
@@ -609,6 +611,7 @@ def bench_jet(torch, srhd, steps: int, gammas=(10.0, 20.0, 50.0, 100.0),
                 run.prev.copy_(start[1])
                 run.status.zero_()
                 run.skipped.zero_()
+                run.prolong_fallbacks.zero_()
             run.step()                      # warm-up (one coarse step), then the initial state
             torch.cuda.synchronize()
             restore()
@@ -625,6 +628,7 @@ def bench_jet(torch, srhd, steps: int, gammas=(10.0, 20.0, 50.0, 100.0),
             run.timer = None
             st = run.status.cpu()
             skipped = int(run.skipped.item())
+            fallbacks = int(run.prolong_fallbacks.item())
             eager_final = run.cur.clone()
             # graph replay of the same `steps` coarse steps from the same
             # initial state (float paths; the FP64 step is long enough that
@@ -651,6 +655,7 @@ def bench_jet(torch, srhd, steps: int, gammas=(10.0, 20.0, 50.0, 100.0),
                 "patches_unphysical": int(((st >> 8) & 1).sum()),
                 "patches_retried_last_step": int(((st & 255) > 0).sum()),
                 "flux_corrections_skipped": skipped,
+                "prolongation_primitive_fallbacks": fallbacks,
             }
             o, n = h.offsets[0], h.counts[0]
             lo, ln = h.offsets[-1], h.counts[-1]

@@ -29,17 +29,16 @@ constexpr double kEpsUnphysical = 2e-16;
 // after applying it is at most C tol^2: 3e-17 for tol = 2^-27 in double and
 // 8e-9 for tol = 2^-13 in float, below the rounding of either precision, so
 // the iteration stops there instead of taking one more step. (htilde and T
-// inherit the relative error of tau up to a factor below 2.) A step that
-// stops contracting at the rounding floor also ends it.
+// inherit the relative error of tau up to a factor below 2.) An iteration
+// that stalls at the rounding floor (steps of a few ulps of tau) meets the
+// rule too, since tol lies far above the rounding of either precision.
 template <class R> struct NewtonCfg;
 template <> struct NewtonCfg<double> {
   static constexpr double tol = 7.450580596923828e-09;  // 2^-27
-  static constexpr double floor = 1e-12;
   static constexpr int maxit = 50;
 };
 template <> struct NewtonCfg<float> {
   static constexpr float tol = 1.220703125e-04f;  // 2^-13
-  static constexpr float floor = 1e-4f;
   static constexpr int maxit = 30;
 };
 
@@ -508,7 +507,7 @@ __device__ __forceinline__ void prims_from_tau_x2(const float (&Ua)[5], const fl
   const float2 D = make_float2(Ua[0], Ub[0]);
   const float2 h = add(ht, s2(1.f));
   const float2 Dh = mul(D, h);
-  const float2 rDh = make_float2(1.0f / Dh.x, 1.0f / Dh.y);
+  const float2 rDh = rcp(Dh);
   const float2 ux = mul(make_float2(Ua[1], Ub[1]), rDh);
   const float2 uy = mul(make_float2(Ua[2], Ub[2]), rDh);
   const float2 uz = mul(make_float2(Ua[3], Ub[3]), rDh);
@@ -594,11 +593,9 @@ template <class R> __device__ __forceinline__ void set_nan(PrimX<R>& W) {
 }
 
 // Stopping rule of the Newton iterations (per state): the step just applied
-// was at most tol of tau, or it stopped contracting at the rounding floor.
-template <class R>
-__device__ __forceinline__ bool newton_done(R adh, R tau, R prev, int k) {
-  return adh <= NewtonCfg<R>::tol * tau ||
-         (k >= 3 && adh >= prev && adh <= NewtonCfg<R>::floor * tau);
+// was at most tol of tau.
+template <class R> __device__ __forceinline__ bool newton_done(R adh, R tau) {
+  return adh <= NewtonCfg<R>::tol * tau;
 }
 
 // Conserved -> primitive (Section 2.3). Returns 0 ok, 1 unphysical, 2 no
@@ -625,15 +622,12 @@ __device__ __forceinline__ int con2pri(typename P::S D, typename P::S Mx, typena
   const R t0 = sv.init(eos, A, m2);
   R tau = guess > R(0) ? guess : t0;
   int status = 2;
-  R prev = R(3.0e38);
   for (int k = 1; k <= maxit; ++k) {
     const R dh = sv.step(tau);
     R tn = tau - dh;
     if (!(tn > R(0))) tn = R(0.5) * tau;
-    const R adh = fabs(dh);
     tau = tn;
-    if (newton_done(adh, tau, prev, k)) { status = 0; break; }
-    prev = adh;
+    if (newton_done(fabs(dh), tau)) { status = 0; break; }
   }
   prims_from_x(eos, D, Mx, My, Mz, tau, W);
   return status;
@@ -665,9 +659,6 @@ __device__ __forceinline__ void con2pri_x2(const typename P::S (&Ua)[5],
   const R Aa = pa ? R(Aa_) : R(1), m2a = pa ? R(ma_) : R(0);
   const R Ab = pb ? R(Ab_) : R(1), m2b = pb ? R(mb_) : R(0);
   bool da = false, db = false;
-  sta = 2;
-  stb = 2;
-  R preva = R(3.0e38), prevb = R(3.0e38);
   if constexpr (sizeof(R) == 4) {
     using namespace pk;
     Solver<E, float2> sv;
@@ -675,22 +666,15 @@ __device__ __forceinline__ void con2pri_x2(const typename P::S (&Ua)[5],
     float2 tau = make_float2(ga > 0.0f ? ga : t0.x, gb > 0.0f ? gb : t0.y);
     for (int k = 1; k <= maxit && !(da && db); ++k) {
       const float2 dh = sv.step(tau);
-      if (!da) {
-        float tn = tau.x - dh.x;
-        if (!(tn > 0.0f)) tn = 0.5f * tau.x;
-        const float adh = fabsf(dh.x);
-        tau.x = tn;
-        if (newton_done(adh, tn, preva, k)) { da = true; sta = 0; }
-        preva = adh;
-      }
-      if (!db) {
-        float tn = tau.y - dh.y;
-        if (!(tn > 0.0f)) tn = 0.5f * tau.y;
-        const float adh = fabsf(dh.y);
-        tau.y = tn;
-        if (newton_done(adh, tn, prevb, k)) { db = true; stb = 0; }
-        prevb = adh;
-      }
+      const float2 tn = sub(tau, dh);
+      // a state that has stopped keeps its tau
+      const float tx = tn.x > 0.0f ? tn.x : 0.5f * tau.x;
+      const float ty = tn.y > 0.0f ? tn.y : 0.5f * tau.y;
+      const bool cx = newton_done(fabsf(dh.x), tx), cy = newton_done(fabsf(dh.y), ty);
+      tau.x = da ? tau.x : tx;
+      tau.y = db ? tau.y : ty;
+      da = da || cx;
+      db = db || cy;
     }
     if constexpr (std::is_same<E, EosTM>::value) {
       prims_from_tau_x2(Ua, Ub, tau, Wa, Wb);
@@ -705,26 +689,20 @@ __device__ __forceinline__ void con2pri_x2(const typename P::S (&Ua)[5],
     for (int k = 1; k <= maxit && !(da && db); ++k) {
       const R dha = sva.step(ta);
       const R dhb = svb.step(tb);
-      if (!da) {
-        R tn = ta - dha;
-        if (!(tn > R(0))) tn = R(0.5) * ta;
-        const R adh = fabs(dha);
-        ta = tn;
-        if (newton_done(adh, tn, preva, k)) { da = true; sta = 0; }
-        preva = adh;
-      }
-      if (!db) {
-        R tn = tb - dhb;
-        if (!(tn > R(0))) tn = R(0.5) * tb;
-        const R adh = fabs(dhb);
-        tb = tn;
-        if (newton_done(adh, tn, prevb, k)) { db = true; stb = 0; }
-        prevb = adh;
-      }
+      R tna = ta - dha, tnb = tb - dhb;
+      if (!(tna > R(0))) tna = R(0.5) * ta;
+      if (!(tnb > R(0))) tnb = R(0.5) * tb;
+      const bool ca = newton_done(fabs(dha), tna), cb = newton_done(fabs(dhb), tnb);
+      ta = da ? ta : tna;
+      tb = db ? tb : tnb;
+      da = da || ca;
+      db = db || cb;
     }
     prims_from_x(eos, Ua[0], Ua[1], Ua[2], Ua[3], ta, Wa);
     prims_from_x(eos, Ub[0], Ub[1], Ub[2], Ub[3], tb, Wb);
   }
+  sta = da ? 0 : 2;
+  stb = db ? 0 : 2;
   if (!pa) {
     set_nan(Wa);
     sta = 1;
@@ -894,7 +872,7 @@ __device__ __forceinline__ void outer_parts_x2(const PrimX<float>& WL, const flo
   if constexpr (std::is_same<E, EosTM>::value) {
     const float2 cnum = mul(T, fma(s2(-8.f), T, mul(s2(5.f), h)));
     const float2 cden = mul(mul(s2(3.f), h), sub(h, T));
-    cs2 = make_float2(cnum.x / cden.x, cnum.y / cden.y);
+    cs2 = make_float2(qdiv(cnum.x, cden.x), qdiv(cnum.y, cden.y));  // cden = 3h(h-T) in [3, 3h^2]
   } else {
     cs2 = mul(mul(s2(float(eos.gam)), T), rcp(h));
   }
