@@ -327,10 +327,14 @@ __device__ __forceinline__ bool box_offset(int gx, int gy, int gz, int& off, int
   return false;
 }
 
-template <int d, class R, class S, class E>
+// LAST: the last direction of the cell; its flux difference completes dF,
+// so its two face states take the Hancock half step (- half dF) before they
+// are stored (the other directions' are updated by halfstep_direction).
+template <int d, bool LAST = false, class R, class S, class E>
 __device__ __forceinline__ void recon_direction(const S* prim, int tc, const PrimX<R>& W, R theta,
                                                 int i, int j, int k, bool interior, S* face,
-                                                R dF[5], int& bad, int ori, const E& eos) {
+                                                R dF[5], int& bad, int ori, const E& eos,
+                                                R half = R(0)) {
   constexpr int off = (d == 0) ? 1 : ((d == 1) ? kG : kG * kG);
   R wc[5] = {W.rho, W.u[0], W.u[1], W.u[2], W.p};
   const int cd = (d == 0) ? i : ((d == 1) ? j : k);
@@ -340,18 +344,32 @@ __device__ __forceinline__ void recon_direction(const S* prim, int tc, const Pri
   if constexpr (sizeof(R) == 4) {
     // float: the minus (lane x) and plus (lane y) face states in packed form
     float2 Wq[5], Uq[5], Fq[5];
+    // limited slopes of the variable pairs (rho, U^x), (U^y, U^z) in packed
+    // form, p alone
 #pragma unroll
-    for (int v = 0; v < 5; ++v) {
-      R lo = R(prim[v * kGC + tc - off]);
-      R hi = R(prim[v * kGC + tc + off]);
-      R dW = limited_slope(wc[v] - lo, hi - wc[v], theta);
-      Wq[v] = pk::fma(pk::s2(dW), make_float2(-0.5f, 0.5f), pk::s2(wc[v]));
+    for (int v = 0; v < 4; v += 2) {
+      const float2 c = make_float2(wc[v], wc[v + 1]);
+      const float2 lo = make_float2(prim[v * kGC + tc - off], prim[(v + 1) * kGC + tc - off]);
+      const float2 hi = make_float2(prim[v * kGC + tc + off], prim[(v + 1) * kGC + tc + off]);
+      const float2 dW = limited_slope_x2(pk::sub(c, lo), pk::sub(hi, c), theta);
+      Wq[v] = pk::fma(pk::s2(dW.x), make_float2(-0.5f, 0.5f), pk::s2(wc[v]));
+      Wq[v + 1] = pk::fma(pk::s2(dW.y), make_float2(-0.5f, 0.5f), pk::s2(wc[v + 1]));
+    }
+    {
+      R lo = R(prim[4 * kGC + tc - off]);
+      R hi = R(prim[4 * kGC + tc + off]);
+      R dW = limited_slope(wc[4] - lo, hi - wc[4], theta);
+      Wq[4] = pk::fma(pk::s2(dW), make_float2(-0.5f, 0.5f), pk::s2(wc[4]));
     }
     bool okm, okp;
     prim2con_flux_x2<d>(Wq, Uq, Fq, okm, okp, ori, eos);
     if (!okm || !okp) bad = 1;
 #pragma unroll
     for (int v = 0; v < 5; ++v) dF[v] = dF[v] + (Fq[v].y - Fq[v].x);
+    if constexpr (LAST) {
+#pragma unroll
+      for (int v = 0; v < 5; ++v) Uq[v] = pk::fma(pk::s2(-half), pk::s2(dF[v]), Uq[v]);
+    }
     if (trans && cd >= 0) {
       int fi = face_index<d>(i, j, k, cd);
 #pragma unroll
@@ -382,6 +400,13 @@ __device__ __forceinline__ void recon_direction(const S* prim, int tc, const Pri
     phys_flux<d>(Wp, Up, Fp, ori);
 #pragma unroll
     for (int v = 0; v < 5; ++v) dF[v] = dF[v] + (Fp[v] - Fm[v]);
+    if constexpr (LAST) {
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        Um[v] = Um[v] - half * dF[v];
+        Up[v] = Up[v] - half * dF[v];
+      }
+    }
     if (trans && cd >= 0) {
       int fi = face_index<d>(i, j, k, cd);
 #pragma unroll
@@ -421,10 +446,16 @@ __device__ __forceinline__ void halfstep_direction(int i, int j, int k, bool int
 // Tile index of the cell on the left (side 0) or right (side 1) of face fi
 // along d: the cell whose half-step face state sits in that slot.
 template <int d> __device__ __forceinline__ int face_owner(int fi, int side) {
-  int i, j, k, fd;
-  if (d == 0) { fd = fi % 9; j = (fi / 9) & 7; k = fi / 72; i = fd - 1 + side; }
-  else if (d == 1) { i = fi & 7; fd = (fi >> 3) % 9; k = (fi >> 3) / 9; j = fd - 1 + side; }
-  else { i = fi & 7; j = (fi >> 3) & 7; fd = fi >> 6; k = fd - 1 + side; }
+  int i, j, k;
+  if (d == 0) {
+    const int q = fi / 9;                 // (k, j); fd = fi - 9 q
+    i = fi - 9 * q - 1 + side; j = q & 7; k = q >> 3;
+  } else if (d == 1) {
+    const int r = fi >> 3, q = r / 9;     // r = k * 9 + fd
+    i = fi & 7; j = r - 9 * q - 1 + side; k = q;
+  } else {
+    i = fi & 7; j = (fi >> 3) & 7; k = (fi >> 6) - 1 + side;
+  }
   return tile_index(i, j, k);
 }
 
@@ -759,10 +790,10 @@ __global__ void __launch_bounds__(NT, MINB) patch_kernel(const __grid_constant__
           const R half = s_pc[1];
           recon_direction<0>(prim, tc, W, theta, i, j, k, interior, face, dF, fail, ori, eos);
           recon_direction<1>(prim, tc, W, theta, i, j, k, interior, face, dF, fail, ori, eos);
-          recon_direction<2>(prim, tc, W, theta, i, j, k, interior, face, dF, fail, ori, eos);
+          recon_direction<2, true>(prim, tc, W, theta, i, j, k, interior, face, dF, fail, ori,
+                                   eos, half);
           halfstep_direction<0>(i, j, k, interior, face, dF, half);
           halfstep_direction<1>(i, j, k, interior, face, dF, half);
-          halfstep_direction<2>(i, j, k, interior, face, dF, half);
         }
         __syncthreads();
         // ---- phase 3: Riemann fluxes ----------------------------------------

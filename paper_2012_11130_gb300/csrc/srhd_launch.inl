@@ -21,10 +21,10 @@ template <> struct PatchVariant<double, 0> { static constexpr int nt = 512, minb
 template <> struct PatchVariant<double, 1> { static constexpr int nt = 256, minb = 1; static constexpr bool pair = false; };
 template <> struct PatchVariant<double, 2> { static constexpr int nt = 512, minb = 1; static constexpr bool pair = true; };
 template <> struct PatchVariant<double, 3> { static constexpr int nt = 384, minb = 1; static constexpr bool pair = false; };
-template <> struct PatchVariant<float, 0> { static constexpr int nt = 256, minb = 2; static constexpr bool pair = true; };
+template <> struct PatchVariant<float, 0> { static constexpr int nt = 384, minb = 2; static constexpr bool pair = true; };
 template <> struct PatchVariant<float, 1> { static constexpr int nt = 448, minb = 2; static constexpr bool pair = true; };
 template <> struct PatchVariant<float, 2> { static constexpr int nt = 320, minb = 2; static constexpr bool pair = true; };
-template <> struct PatchVariant<float, 3> { static constexpr int nt = 384, minb = 2; static constexpr bool pair = true; };
+template <> struct PatchVariant<float, 3> { static constexpr int nt = 256, minb = 2; static constexpr bool pair = true; };
 
 // The polytropic-EoS kernel runs one configuration per storage type.
 template <class S> struct PolyVariant;

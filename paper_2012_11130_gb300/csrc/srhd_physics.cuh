@@ -974,6 +974,19 @@ template <class R> __device__ __forceinline__ R limited_slope(R dl, R dr, R thet
   return copysign(mag, dl);
 }
 
+// limited_slope of two independent (dl, dr) pairs, the arithmetic in packed
+// form (lane by lane the same operations).
+__device__ __forceinline__ float2 limited_slope_x2(float2 dl, float2 dr, float theta) {
+  using namespace pk;
+  const float2 pr = mul(dl, dr);
+  const float2 vl = mul(mul(s2(2.0f), pr), rcp(add(dl, dr)));
+  const float2 mn = make_float2(fminf(fabsf(dl.x), fabsf(dr.x)), fminf(fabsf(dl.y), fabsf(dr.y)));
+  const float2 tm = mul(s2(theta), mn);
+  const float mx = fminf(fabsf(vl.x), tm.x), my = fminf(fabsf(vl.y), tm.y);
+  return make_float2(pr.x > 0.0f ? copysignf(mx, dl.x) : 0.0f,
+                     pr.y > 0.0f ? copysignf(my, dl.y) : 0.0f);
+}
+
 // Signal speed bound S_max of one cell (Section 3.2, Eqs. time_step_U_max
 // and SMax; |U_x|+|U_y|+|U_z| and ndim gamma U_s).
 template <class R, class E = EosTM>
