@@ -479,10 +479,10 @@ __device__ __forceinline__ int face_flux(typename P::S* face, const typename P::
   PrimX<R> WL, WR;
   int sl, sr;
   if constexpr (PAIR) {
-    con2pri_x2<P>(UL, UR, WL, WR, maxit, sl, sr, gL, gR, ori, eos);
+    con2pri_x2<P, E, true>(UL, UR, WL, WR, maxit, sl, sr, gL, gR, ori, eos);
   } else {
-    sl = con2pri<P>(UL[0], UL[1], UL[2], UL[3], UL[4], WL, maxit, gL, ori, eos);
-    sr = con2pri<P>(UR[0], UR[1], UR[2], UR[3], UR[4], WR, maxit, gR, ori, eos);
+    sl = con2pri<P, E, true>(UL[0], UL[1], UL[2], UL[3], UL[4], WL, maxit, gL, ori, eos);
+    sr = con2pri<P, E, true>(UR[0], UR[1], UR[2], UR[3], UR[4], WR, maxit, gR, ori, eos);
   }
   if (sl == 2 || sr == 2) code |= CODE_NOCONV;
   int fail = (sl == 1 || sr == 1);
@@ -963,11 +963,11 @@ __global__ void __launch_bounds__(NT, MINB) patch_kernel(const __grid_constant__
               PrimX<R> W[NPC];
               int st[NPC];
               if constexpr (PAIR) {
-                con2pri_x2<P>(Un[0], Un[1], W[0], W[1], maxit, st[0], st[1], g0[0], g0[NPC - 1],
-                              ori, eos);
+                con2pri_x2<P, E, true>(Un[0], Un[1], W[0], W[1], maxit, st[0], st[1], g0[0],
+                                       g0[NPC - 1], ori, eos);
               } else {
-                st[0] = con2pri<P>(Un[0][0], Un[0][1], Un[0][2], Un[0][3], Un[0][4], W[0], maxit,
-                                   g0[0], ori, eos);
+                st[0] = con2pri<P, E, true>(Un[0][0], Un[0][1], Un[0][2], Un[0][3], Un[0][4], W[0],
+                                            maxit, g0[0], ori, eos);
               }
 #pragma unroll
               for (int q = 0; q < NPC; ++q) {

@@ -550,27 +550,34 @@ __device__ __forceinline__ void prims_from_ht_poly(S D, S Mx, S My, S Mz, R ht, 
 template <class E, class V> struct Solver;
 template <class V> struct Solver<EosTM, V> {
   V ml, ml9, nA, lam;
-  __device__ __forceinline__ V init(const EosTM&, V A, V m2) {
+  // constants of a solve that starts at x0 (the scale lam = 1/(1 + x0)^2)
+  __device__ __forceinline__ void prepare(const EosTM&, V A, V m2, V x0) {
     using namespace ar;
-    const V t0 = tau_start(A);
-    const V t1 = add(t0, c<V>(1.0));
+    const V t1 = add(x0, c<V>(1.0));
     lam = rcp(mul(t1, t1));
     ml = mul(m2, lam);
     ml9 = mul(ml, c<V>(9.0));
     nA = neg(A);
+  }
+  __device__ __forceinline__ V init(const EosTM& e, V A, V m2) {
+    const V t0 = tau_start(A);
+    prepare(e, A, m2, t0);
     return t0;
   }
   __device__ __forceinline__ V step(V x) const { return tau_step(x, ml, ml9, nA, lam); }
 };
 template <class V> struct Solver<EosPoly, V> {
   V m2, omk, k2, nA;
-  __device__ __forceinline__ V init(const EosPoly& e, V A, V m2_) {
+  __device__ __forceinline__ void prepare(const EosPoly& e, V A, V m2_, V) {
     using namespace ar;
     const double k = (e.gam - 1.0) / e.gam;
     m2 = m2_;
     omk = c<V>(1.0 - k);
     k2 = c<V>(k * k);
     nA = neg(A);
+  }
+  __device__ __forceinline__ V init(const EosPoly& e, V A, V m2_) {
+    prepare(e, A, m2_, A);
     return poly_start(A, omk);
   }
   __device__ __forceinline__ V step(V x) const { return poly_step(x, m2, omk, k2, nA); }
@@ -605,7 +612,7 @@ template <class R> __device__ __forceinline__ bool newton_done(R adh, R tau) {
 // Stops by newton_done or after maxit steps (status 2). guess > 0 is a tau
 // to start from (a warm start from a nearby state); otherwise tau_start(A).
 // The root does not depend on the start.
-template <class P, class E = EosTM>
+template <class P, class E = EosTM, bool WARM = false>
 __device__ __forceinline__ int con2pri(typename P::S D, typename P::S Mx, typename P::S My,
                                        typename P::S Mz, typename P::S Et,
                                        PrimX<typename P::S>& W, int maxit,
@@ -619,8 +626,14 @@ __device__ __forceinline__ int con2pri(typename P::S D, typename P::S Mx, typena
   }
   const R A = R(Aa), m2 = R(m2a);
   Solver<E, R> sv;
-  const R t0 = sv.init(eos, A, m2);
-  R tau = guess > R(0) ? guess : t0;
+  R tau;
+  if constexpr (WARM) {
+    tau = guess > R(0) ? guess : R(1);
+    sv.prepare(eos, A, m2, tau);
+  } else {
+    const R t0 = sv.init(eos, A, m2);
+    tau = guess > R(0) ? guess : t0;
+  }
   int status = 2;
   for (int k = 1; k <= maxit; ++k) {
     const R dh = sv.step(tau);
@@ -638,7 +651,7 @@ __device__ __forceinline__ int con2pri(typename P::S D, typename P::S Mx, typena
 // so that their dependency chains interleave (in float, both lanes of each
 // step are one packed instruction). The loop runs until both have stopped;
 // a state that has stopped is not updated.
-template <class P, class E = EosTM>
+template <class P, class E = EosTM, bool WARM = false>
 __device__ __forceinline__ void con2pri_x2(const typename P::S (&Ua)[5],
                                            const typename P::S (&Ub)[5],
                                            PrimX<typename P::S>& Wa, PrimX<typename P::S>& Wb,
@@ -662,8 +675,14 @@ __device__ __forceinline__ void con2pri_x2(const typename P::S (&Ua)[5],
   if constexpr (sizeof(R) == 4) {
     using namespace pk;
     Solver<E, float2> sv;
-    const float2 t0 = sv.init(eos, make_float2(Aa, Ab), make_float2(m2a, m2b));
-    float2 tau = make_float2(ga > 0.0f ? ga : t0.x, gb > 0.0f ? gb : t0.y);
+    float2 tau;
+    if constexpr (WARM) {
+      tau = make_float2(ga > 0.0f ? ga : 1.0f, gb > 0.0f ? gb : 1.0f);
+      sv.prepare(eos, make_float2(Aa, Ab), make_float2(m2a, m2b), tau);
+    } else {
+      const float2 t0 = sv.init(eos, make_float2(Aa, Ab), make_float2(m2a, m2b));
+      tau = make_float2(ga > 0.0f ? ga : t0.x, gb > 0.0f ? gb : t0.y);
+    }
     for (int k = 1; k <= maxit && !(da && db); ++k) {
       const float2 dh = sv.step(tau);
       const float2 tn = sub(tau, dh);
@@ -684,8 +703,17 @@ __device__ __forceinline__ void con2pri_x2(const typename P::S (&Ua)[5],
     }
   } else {
     Solver<E, R> sva, svb;
-    const R t0a = sva.init(eos, Aa, m2a), t0b = svb.init(eos, Ab, m2b);
-    R ta = ga > R(0) ? ga : t0a, tb = gb > R(0) ? gb : t0b;
+    R ta, tb;
+    if constexpr (WARM) {
+      ta = ga > R(0) ? ga : R(1);
+      tb = gb > R(0) ? gb : R(1);
+      sva.prepare(eos, Aa, m2a, ta);
+      svb.prepare(eos, Ab, m2b, tb);
+    } else {
+      const R t0a = sva.init(eos, Aa, m2a), t0b = svb.init(eos, Ab, m2b);
+      ta = ga > R(0) ? ga : t0a;
+      tb = gb > R(0) ? gb : t0b;
+    }
     for (int k = 1; k <= maxit && !(da && db); ++k) {
       const R dha = sva.step(ta);
       const R dhb = svb.step(tb);

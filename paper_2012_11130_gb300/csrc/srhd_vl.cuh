@@ -303,7 +303,7 @@ __global__ void __launch_bounds__(NT, MINB) vl_patch_kernel(PatchArgs a) {
         const S gb = vl_guess(eos, R(qdiv(Wn[4 * kVTC + cb], Wn[cb])));
         PrimX<R> Wa, Wb;
         int sa, sb;
-        con2pri_x2<P>(Ua, Ub, Wa, Wb, maxit, sa, sb, ga, gb, ori, eos);
+        con2pri_x2<P, E, true>(Ua, Ub, Wa, Wb, maxit, sa, sb, ga, gb, ori, eos);
         if (sa == 1 || sb == 1) pbad = 1;
         if (sa == 2 || sb == 2) code |= CODE_NOCONV;
         const int rb = r + kVH / 2;
