@@ -66,17 +66,18 @@ PEAK_FP64_TFLOPS = 1.25
 # only for the kernel sources with the recorded hash.
 # Captured at 128^3 (4096 patches) and scaled by 8 to the 32768-patch launch
 # (profiles/patch_kernel_advection128.md).
-NCU_TRAFFIC = {"sources_sha": "0062a97e98619585",
-               "mixed_cf": 8 * (141.771520e6 + 24.168192e6),
-               "mixed": 8 * (141.717760e6 + 24.079616e6),
-               "fp64": 8 * (283.968512e6 + 68.002560e6)}
+NCU_TRAFFIC = {"sources_sha": "b28d9d7de639f1e8",
+               "mixed_cf": 8 * (141.725184e6 + 23.502080e6),
+               "mixed": 8 * (142.055424e6 + 24.515840e6),
+               "fp64": 8 * (283.967488e6 + 68.282880e6)}
 
 
 # The sources that make the patch kernel's device code (its translation units
 # and everything they include); host-side files (srhd_api.cu,
 # srhd_noalloc.cu) do not change it.
 KERNEL_SOURCES = ("srhd_amr.cuh", "srhd_fp64.cu", "srhd_kernels.cuh", "srhd_launch.inl",
-                  "srhd_mixed.cu", "srhd_mixed_cf.cu", "srhd_physics.cuh", "srhd_vl.cuh")
+                  "srhd_mixed.cu", "srhd_mixed_cf.cu", "srhd_physics.cuh", "srhd_prolong.cuh",
+                  "srhd_vl.cuh")
 
 
 def _code_only(text: str) -> str:

@@ -827,12 +827,11 @@ __device__ __forceinline__ void prim2con_flux_x2(const float2 (&W)[5], float2 (&
   F[3] = mul(U[3], v);
   F[1 + d] = add(F[1 + d], W[4]);
   F[4] = ori ? U[1 + d] : mul(add(U[4], W[4]), v);
+  // a state from a non-positive density or pressure: D = NaN marks it
+  // unphysical for every later conversion (its attempt is redone anyway)
   const float nan = __int_as_float(0x7fc00000);
-#pragma unroll
-  for (int q = 0; q < 5; ++q) {
-    if (!okx) U[q].x = nan;
-    if (!oky) U[q].y = nan;
-  }
+  if (!okx) U[0].x = nan;
+  if (!oky) U[0].y = nan;
 }
 
 // Physical flux along d (Eqs. D evolution, M evolution, ETilde evolution).
