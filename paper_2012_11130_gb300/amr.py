@@ -252,9 +252,11 @@ class Hierarchy:
         """Rows of srhd_amr_prolong for the level-l ghost cells (x, y, z)
         (boundary rule already applied) taken from level l - 1, one row per
         distinct cell; returns (rows [m][8] int32, row of each input cell)."""
-        key = np.stack([x, y, z], axis=1)
+        # rows ordered by (z, y, x), so that neighbouring rows read
+        # neighbouring coarse cells
+        key = np.stack([z, y, x], axis=1)
         uniq, which = np.unique(key, axis=0, return_inverse=True)
-        xf, yf, zf = uniq[:, 0], uniq[:, 1], uniq[:, 2]
+        zf, yf, xf = uniq[:, 0], uniq[:, 1], uniq[:, 2]
         xc, yc, zc = xf // 2, yf // 2, zf // 2
         rows = np.empty((len(uniq), 8), np.int64)
         rows[:, 0] = self._coarse_flat(l - 1, xc, yc, zc)

@@ -10,9 +10,10 @@
 // upper half of C along axis d, i.e. its centre is a quarter of a coarse
 // cell above C's centre, otherwise a quarter below). The coarse states are
 // first taken at the fine substep's time, (1 - w) prev + w cur (amr_lerp,
-// as in the piecewise-constant fill). Per axis the slope is the minmod of
-// the two one-sided differences (0 where a neighbour is missing or the
-// differences have opposite signs), and the fine value is
+// as in the piecewise-constant fill; prev itself at w = 0). Per axis the
+// slope is the minmod of the two one-sided differences (0 where a
+// neighbour is missing or the differences have opposite signs), and the
+// fine value is
 //   U_f = U_C + sum_d (+-1/4) slope_d      (axes in the order x, y, z).
 // The conserved variables are interpolated; where the result fails
 // Eq. (Unphysical result) (amr_physical), the primitive variables
@@ -60,13 +61,19 @@ __global__ void __launch_bounds__(128)
       continue;
     }
     const int par = row[7];
-    // the coarse state of flat cell q at the substep's time
+    // the coarse state of flat cell q at the substep's time (at w = 0 the
+    // state before the coarse step itself)
     auto coarse = [&](int32_t q, S (&u)[5]) {
       const int64_t p = q / kAmrInt, c = q - p * kAmrInt;
       const S* a = prev + p * 5 * kAmrInt + c;
       const S* b = cur + p * 5 * kAmrInt + c;
+      if (w == S(0)) {
 #pragma unroll
-      for (int v = 0; v < 5; ++v) u[v] = amr_lerp(a[v * kAmrInt], b[v * kAmrInt], w);
+        for (int v = 0; v < 5; ++v) u[v] = a[v * kAmrInt];
+      } else {
+#pragma unroll
+        for (int v = 0; v < 5; ++v) u[v] = amr_lerp(a[v * kAmrInt], b[v * kAmrInt], w);
+      }
     };
     S uc[5], un[6][5];
     coarse(qc, uc);
