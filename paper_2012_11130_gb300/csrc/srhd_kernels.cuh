@@ -330,6 +330,42 @@ __device__ __forceinline__ bool box_offset(int gx, int gy, int gz, int& off, int
 // LAST: the last direction of the cell; its flux difference completes dF,
 // so its two face states take the Hancock half step (- half dF) before they
 // are stored (the other directions' are updated by halfstep_direction).
+// The same for the r-th needed tile cell (needed_tile_coords) directly from
+// r, for r < 1280 (the interior and the six face slabs; the first-layer
+// edges are not staged): c its 12^3 tile index, off and vs as box_offset,
+// nb the patch the cell lies in (0 the patch itself, 1 + f for the face f =
+// -x, +x, -y, +y, -z, +z neighbour) and local its 8^3 index there.
+__device__ __forceinline__ void staged_cell(int r, int& c, int& off, int& vs, int& nb,
+                                            int& local) {
+  if (r < kNC) {
+    c = tile_index(r & 7, (r >> 3) & 7, r >> 6);
+    off = r;
+    vs = kNC;
+    nb = 0;
+    local = r;
+    return;
+  }
+  const int q = r - kNC, f = q >> 7, rem = q & 127;
+  const int depth = 1 + (rem >> 6), t = rem & 63;  // ghost layer 1 or 2, face cell
+  const int a = t & 7, b = t >> 3;                   // transverse, lower axis first
+  const int lo = 8 - depth, hi = depth - 1;          // neighbour cell along the normal
+  nb = 1 + f;
+  switch (f) {
+    case 0: c = tile_index(-depth, a, b); off = kBoxXm + 4 - depth + 4 * t; vs = 256;
+            local = t * 8 + lo; break;
+    case 1: c = tile_index(7 + depth, a, b); off = kBoxXp + hi + 4 * t; vs = 256;
+            local = t * 8 + hi; break;
+    case 2: c = tile_index(a, -depth, b); off = kBoxYm + (2 - depth) * 8 + b * 16 + a; vs = 128;
+            local = (b * 8 + lo) * 8 + a; break;
+    case 3: c = tile_index(a, 7 + depth, b); off = kBoxYp + hi * 8 + b * 16 + a; vs = 128;
+            local = (b * 8 + hi) * 8 + a; break;
+    case 4: c = tile_index(a, b, -depth); off = kBoxZm + (2 - depth) * 64 + t; vs = 128;
+            local = lo * 64 + t; break;
+    default: c = tile_index(a, b, 7 + depth); off = kBoxZp + hi * 64 + t; vs = 128;
+             local = hi * 64 + t; break;
+  }
+}
+
 template <int d, bool LAST = false, class R, class S, class E>
 __device__ __forceinline__ void recon_direction(const S* prim, int tc, const PrimX<R>& W, R theta,
                                                 int i, int j, int k, bool interior, S* face,
@@ -629,13 +665,14 @@ __global__ void __launch_bounds__(NT, MINB) patch_kernel(const __grid_constant__
         for (int v = 0; v < 5; ++v) U[v] = src.get(v, aw);
         if (r < kNC && m != (int32_t)((int64_t)p * kNC + r)) s_nonid = 1;
       } else if constexpr (GATHER == 1) {
-        const int gz = c / (kG * kG), gy = (c / kG) % kG, gx = c % kG;
-        int off, vs;
-        if ((st1 & 2) && box_offset(gx, gy, gz, off, vs)) {
+        if ((st1 & 2) && r < kNC + 768) {  // staged interior or face-slab cell
+          int cs, off, vs, nb, local;
+          staged_cell(r, cs, off, vs, nb, local);
 #pragma unroll
           for (int v = 0; v < 5; ++v) U[v] = stage[off + v * vs];
           return;
         }
+        const int gz = c / (kG * kG), gy = (c / kG) % kG, gx = c % kG;
         int qx, lx, qy, ly, qz, lz;
         ghost_src(gx - 2, gpx, a.gnx, a.gbcx, qx, lx);
         ghost_src(gy - 2, gpy, a.gny, a.gbcy, qy, ly);
@@ -676,7 +713,40 @@ __global__ void __launch_bounds__(NT, MINB) patch_kernel(const __grid_constant__
       // the cells of the tile: a gather, no conversion. A state left
       // unphysical by that step is stored as NaN.
       const S* pbase = static_cast<const S*>(a.prim_in);
-      for (int r = tid; r < kTileNeeded; r += NT) {
+      int r0 = tid;
+      if (st1 & 2) {
+        // staged tile (all six face neighbours exist, wrapping where
+        // periodic): the interior and face-slab cells by the closed-form
+        // mapping, tau from the cache of the patch holding the cell
+        const int64_t q0 = a.gp0 + p;
+        auto wrap = [](int c, int n) { return c < 0 ? c + n : (c >= n ? c - n : c); };
+        auto pid = [&](int ix, int iy, int iz) {
+          return ((int64_t)iz * a.gny + iy) * a.gnx + ix;
+        };
+        const int64_t qxm = pid(wrap(gpx - 1, a.gnx), gpy, gpz);
+        const int64_t qxp = pid(wrap(gpx + 1, a.gnx), gpy, gpz);
+        const int64_t qym = pid(gpx, wrap(gpy - 1, a.gny), gpz);
+        const int64_t qyp = pid(gpx, wrap(gpy + 1, a.gny), gpz);
+        const int64_t qzm = pid(gpx, gpy, wrap(gpz - 1, a.gnz));
+        const int64_t qzp = pid(gpx, gpy, wrap(gpz + 1, a.gnz));
+        for (int r = tid; r < kNC + 768; r += NT) {
+          int c, off, vs, nb, local;
+          staged_cell(r, c, off, vs, nb, local);
+          const int64_t qn = nb == 0 ? q0 : nb == 1 ? qxm : nb == 2 ? qxp : nb == 3 ? qym
+                           : nb == 4 ? qyp : nb == 5 ? qzm : qzp;
+          S w[6];
+#pragma unroll
+          for (int v = 0; v < 5; ++v) w[v] = stage[off + v * vs];
+          w[5] = __ldg(pbase + qn * (6 * kNC) + 5 * kNC + local);
+          if (!(w[0] > S(0) && w[4] > S(0) && isfinite(w[1] + w[2] + w[3] + w[5])))
+            code |= CODE_BAD_INPUT;
+#pragma unroll
+          for (int v = 0; v < 5; ++v) prim[v * kGC + c] = w[v];
+          hts[c] = w[5];
+        }
+        r0 = kNC + 768 + tid;  // the first-layer edge cells below
+      }
+      for (int r = r0; r < kTileNeeded; r += NT) {
         int g[3];
         needed_tile_coords(r, g);
         const int c = (g[2] * kG + g[1]) * kG + g[0];
@@ -852,9 +922,30 @@ __global__ void __launch_bounds__(NT, MINB) patch_kernel(const __grid_constant__
               const int zm = nb(cz - 1, a.gnz, a.gbcz), zp = nb(cz + 1, a.gnz, a.gbcz);
               if ((xm | xp | ym | yp | zm | zp) >= 0) {
                 auto pid = [&](int ix, int iy, int iz) { return (iz * a.gny + iy) * a.gnx + ix; };
+                // the patch interior (variables 0..4 contiguous) and the two
+                // z slabs (two contiguous planes per variable) are plain
+                // bulk copies; the x and y slabs, strided, are tensor boxes
                 bulk::fence_before_copy();
                 bulk::expect(&s_mbar, kBoxTotal * sizeof(S));
-                bulk::copy_box(stage, &a.tmap[kTmapCenter], 0, 0, 0, 0, int(qn), &s_mbar);
+                if constexpr (GATHER == 1) {
+                  // the interior array's patch interior (variables
+                  // contiguous) and z slabs (two contiguous planes per
+                  // variable) as plain bulk copies
+                  const S* zms = base + (int64_t)pid(cx, cy, zm) * (5 * kNC) + 6 * 64;
+                  const S* zps = base + (int64_t)pid(cx, cy, zp) * (5 * kNC);
+                  bulk::copy(stage, base + qn * (5 * kNC), kBoxC * sizeof(S), &s_mbar);
+#pragma unroll
+                  for (int v = 0; v < 5; ++v) {
+                    bulk::copy(stage + kBoxZm + v * 128, zms + v * kNC, 128 * sizeof(S), &s_mbar);
+                    bulk::copy(stage + kBoxZp + v * 128, zps + v * kNC, 128 * sizeof(S), &s_mbar);
+                  }
+                } else {
+                  bulk::copy_box(stage, &a.tmap[kTmapCenter], 0, 0, 0, 0, int(qn), &s_mbar);
+                  bulk::copy_box(stage + kBoxZm, &a.tmap[kTmapZ], 0, 0, 6, 0, pid(cx, cy, zm),
+                                 &s_mbar);
+                  bulk::copy_box(stage + kBoxZp, &a.tmap[kTmapZ], 0, 0, 0, 0, pid(cx, cy, zp),
+                                 &s_mbar);
+                }
                 bulk::copy_box(stage + kBoxXm, &a.tmap[kTmapX], 4, 0, 0, 0, pid(xm, cy, cz),
                                &s_mbar);
                 bulk::copy_box(stage + kBoxXp, &a.tmap[kTmapX], 0, 0, 0, 0, pid(xp, cy, cz),
@@ -862,10 +953,6 @@ __global__ void __launch_bounds__(NT, MINB) patch_kernel(const __grid_constant__
                 bulk::copy_box(stage + kBoxYm, &a.tmap[kTmapY], 0, 6, 0, 0, pid(cx, ym, cz),
                                &s_mbar);
                 bulk::copy_box(stage + kBoxYp, &a.tmap[kTmapY], 0, 0, 0, 0, pid(cx, yp, cz),
-                               &s_mbar);
-                bulk::copy_box(stage + kBoxZm, &a.tmap[kTmapZ], 0, 0, 6, 0, pid(cx, cy, zm),
-                               &s_mbar);
-                bulk::copy_box(stage + kBoxZp, &a.tmap[kTmapZ], 0, 0, 0, 0, pid(cx, cy, zp),
                                &s_mbar);
                 s_stg |= 2;  // read next after the phase-4 barrier
               }
@@ -969,17 +1056,6 @@ __global__ void __launch_bounds__(NT, MINB) patch_kernel(const __grid_constant__
                 st[0] = con2pri<P, E, true>(Un[0][0], Un[0][1], Un[0][2], Un[0][3], Un[0][4], W[0],
                                             maxit, g0[0], ori, eos);
               }
-#pragma unroll
-              for (int q = 0; q < NPC; ++q) {
-                // the largest signal speed of the patch; dt = C dh / S_max once
-                if (st[q] != 1) {
-                  if (GATHER != 3 || a.cfl_mode != 1)
-                    att_smax = fmax(att_smax, smax_of(W[q], a.ndim, eos));
-                } else {
-                  att_bad = 1;
-                  fail4 = 1;
-                }
-              }
               if constexpr (GATHER == 3) {
                 // keep the new state's primitives (NaN where unphysical)
                 S* po = static_cast<S*>(a.prim_out) + (size_t)p * 6 * kNC;
@@ -992,6 +1068,17 @@ __global__ void __launch_bounds__(NT, MINB) patch_kernel(const __grid_constant__
                   po[3 * kNC + c] = S(W[q].u[2]);
                   po[4 * kNC + c] = S(W[q].p);
                   po[5 * kNC + c] = S(W[q].tau);
+                }
+              }
+#pragma unroll
+              for (int q = 0; q < NPC; ++q) {
+                // the largest signal speed of the patch; dt = C dh / S_max once
+                if (st[q] != 1) {
+                  if (GATHER != 3 || a.cfl_mode != 1)
+                    att_smax = fmax(att_smax, smax_of(W[q], a.ndim, eos));
+                } else {
+                  att_bad = 1;
+                  fail4 = 1;
                 }
               }
             } else {

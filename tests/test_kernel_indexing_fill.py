@@ -226,3 +226,73 @@ def test_tensor_copy_coordinates(elem):
     # the neighbour slabs hold the cells the tile needs: x 6, 7 of the -x
     # neighbour inside [4, 8), y 6, 7 of the -y neighbour, and so on
     assert {6, 7} <= set(range(4, 8)) and {0, 1} <= set(range(0, 4))
+
+
+def staged_cell(r):
+    """Restatement of staged_cell (srhd_kernels.cuh): tile index, stage
+    offset, variable stride, holding patch (0 itself, 1 + face) and the
+    cell's 8^3 index there, for the needed cells r < 1280."""
+    def tile_index(i, j, k):
+        return ((k + 2) * 12 + j + 2) * 12 + i + 2
+    if r < 512:
+        return tile_index(r & 7, (r >> 3) & 7, r >> 6), r, 512, 0, r
+    q = r - 512
+    f, rem = q >> 7, q & 127
+    depth, t = 1 + (rem >> 6), rem & 63
+    a, b = t & 7, t >> 3
+    lo, hi = 8 - depth, depth - 1
+    if f == 0:
+        return tile_index(-depth, a, b), KXM + 4 - depth + 4 * t, 256, 1, t * 8 + lo
+    if f == 1:
+        return tile_index(7 + depth, a, b), KXP + hi + 4 * t, 256, 2, t * 8 + hi
+    if f == 2:
+        return tile_index(a, -depth, b), KYM + (2 - depth) * 8 + b * 16 + a, 128, 3, (b * 8 + lo) * 8 + a
+    if f == 3:
+        return tile_index(a, 7 + depth, b), KYP + hi * 8 + b * 16 + a, 128, 4, (b * 8 + hi) * 8 + a
+    if f == 4:
+        return tile_index(a, b, -depth), KZM + (2 - depth) * 64 + t, 128, 5, lo * 64 + t
+    return tile_index(a, b, 7 + depth), KZP + hi * 64 + t, 128, 6, hi * 64 + t
+
+
+def test_closed_form_staged_cells_match_box_offset_and_sources():
+    # The closed-form mapping of the staged gather (modes 1 and 3) gives, for
+    # every interior and face-slab cell of the needed list, the tile cell of
+    # needed_tile_cell, the stage offset and stride of box_offset, and the
+    # patch and cell that ghost_src finds (periodic grid, interior patch).
+    from test_kernel_indexing import needed_tile_cell
+    faces = {0: (0, 0, 0), 1: (-1, 0, 0), 2: (1, 0, 0), 3: (0, -1, 0), 4: (0, 1, 0),
+             5: (0, 0, -1), 6: (0, 0, 1)}
+    for r in range(512 + 768):
+        c, off, vs, nb, local = staged_cell(r)
+        assert c == needed_tile_cell(r)
+        gz, gy, gx = c // 144, (c // 12) % 12, c % 12
+        assert box_offset(gx, gy, gz) == (off, vs)
+        # the source by plain geometry: patch offset and cell of (g - 2)
+        src = []
+        for g in (gx, gy, gz):
+            o = -1 if g - 2 < 0 else (1 if g - 2 >= 8 else 0)
+            src.append((o, g - 2 - 8 * o))
+        assert tuple(s[0] for s in src) == faces[nb]
+        assert (src[2][1] * 8 + src[1][1]) * 8 + src[0][1] == local
+
+
+def test_bulk_copies_of_the_uniform_stage():
+    # Mode 1 stages the patch interior and the two z slabs with plain bulk
+    # copies (the x and y slabs stay tensor boxes): the interior is one run of
+    # 5 x 512 values; each z slab is, per variable, the 128 values of two
+    # planes (z 6, 7 of the -z neighbour at offset 384; z 0, 1 of the +z
+    # one at 0), landing at stage offsets KZM/KZP + 128 v: the layout of the
+    # [5][2][8][8] boxes. Every copy starts and ends on 16 bytes.
+    field = np.arange(5 * 512, dtype=np.float64).reshape(5, 8, 8, 8)  # [v][z][y][x]
+    zm = field[:, 6:8].reshape(5, 128)
+    zp = field[:, 0:2].reshape(5, 128)
+    flat = field.reshape(-1)
+    for v in range(5):
+        assert np.array_equal(flat[v * 512 + 384:v * 512 + 512], zm[v])
+        assert np.array_equal(flat[v * 512:v * 512 + 128], zp[v])
+    for elem in (4, 8):
+        for off, n in [(0, 2560)] + [(v * 512 + 384, 128) for v in range(5)]:
+            assert (off * elem) % 16 == 0 and (n * elem) % 16 == 0
+        for st in (0, KZM, KZP):
+            assert (st * elem) % 16 == 0
+    assert KZP + KBOX_Z - KZM == 2 * 5 * 128
