@@ -50,6 +50,10 @@ WORKLOAD = ("3-D periodic smooth advection 256^3 (rho=1+0.5 sin(2pi(x+y+z)), p=1
 # instantiation (oracle/count_flops.py): adds+subs, muls, divs, sqrts of one
 # MUSCL-Hancock step of the benchmark state in the large-block limit, plus
 # the CFL bound of the updated cell.
+# Patch tile of one CTA: one 8^3 patch (tiles of 2, 4 and 8 face-adjacent
+# patches as thread-block clusters cost more in lockstep than they save in
+# halo work on GB300, so the tuner's tile dimension has this one value).
+TILE_SHAPE = "1x1x1 patches of 8^3 per CTA"
 FLOPS_PER_CELL_UPDATE = 4583.2
 # Algorithmic bytes per cell update: 5 conserved values read + 5 written.
 BYTES_PER_CELL_UPDATE = {"mixed_cf": 40, "mixed": 40, "fp64": 80}
@@ -886,12 +890,14 @@ def run_ours(args):
         tuned = None
         if args.variant is not None:
             ctx = srhd.Context(srhd.Params(patch_variant=args.variant))
-            tuned = {"chosen_variant": args.variant, "ms_per_variant": None}
+            tuned = {"chosen_variant": args.variant, "ms_per_variant": None,
+                     "tile": TILE_SHAPE}
         elif not args.no_tune:
             best, times = autotune.tune(G, dt_dh, prec=prec, steps=2 if prec == "fp64" else 3)
             ctx = srhd.Context(best)
             tuned = {"chosen_variant": best.patch_variant,
-                     "ms_per_variant": {str(k): v for k, v in times.items()}}
+                     "ms_per_variant": {str(k): v for k, v in times.items()},
+                     "tile": TILE_SHAPE}
         else:
             ctx = srhd.Context(srhd.Params())
         with ClockSampler(local) as clk:
