@@ -46,14 +46,15 @@ WORKLOAD = ("3-D periodic smooth advection 256^3 (rho=1+0.5 sin(2pi(x+y+z)), p=1
             "along (1,1,1)); 32768 patches of 8^3 + 2 ghost cells; one fused MUSCL-Hancock/HLLC "
             "step with limiter retry and CFL min-reduction per step")
 
-# Algorithmic work per cell update, counted by the oracle's op-counting
-# instantiation (oracle/count_flops.py): adds+subs, muls, divs, sqrts of one
-# MUSCL-Hancock step of the benchmark state in the large-block limit, plus
-# the CFL bound of the updated cell.
 # Patch tile of one CTA: one 8^3 patch (tiles of 2, 4 and 8 face-adjacent
 # patches as thread-block clusters cost more in lockstep than they save in
 # halo work on GB300, so the tuner's tile dimension has this one value).
 TILE_SHAPE = "1x1x1 patches of 8^3 per CTA"
+
+# Algorithmic work per cell update, counted by the oracle's op-counting
+# instantiation (oracle/count_flops.py): adds+subs, muls, divs, sqrts of one
+# MUSCL-Hancock step of the benchmark state in the large-block limit, plus
+# the CFL bound of the updated cell.
 FLOPS_PER_CELL_UPDATE = 4583.2
 # Algorithmic bytes per cell update: 5 conserved values read + 5 written.
 BYTES_PER_CELL_UPDATE = {"mixed_cf": 40, "mixed": 40, "fp64": 80}
