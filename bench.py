@@ -71,10 +71,10 @@ PEAK_FP64_TFLOPS = 1.25
 # only for the kernel sources with the recorded hash.
 # Captured at 128^3 (4096 patches) and scaled by 8 to the 32768-patch launch
 # (profiles/patch_kernel_advection128.md).
-NCU_TRAFFIC = {"sources_sha": "b28d9d7de639f1e8",
-               "mixed_cf": 8 * (141.725184e6 + 23.502080e6),
-               "mixed": 8 * (142.055424e6 + 24.515840e6),
-               "fp64": 8 * (283.967488e6 + 68.282880e6)}
+NCU_TRAFFIC = {"sources_sha": "3aeded1035099bb3",
+               "mixed_cf": 8 * (141.715712e6 + 23.541504e6),
+               "mixed": 8 * (141.820928e6 + 24.083456e6),
+               "fp64": 8 * (284.587008e6 + 68.166912e6)}
 
 
 # The sources that make the patch kernel's device code (its translation units
