@@ -18,8 +18,10 @@
 //            are redone with the limiter coefficient times retry_factor
 //            (block-wide vote), down to theta = 0 (piecewise constant)
 // While phase 4 runs, the copy engine stages the CTA's next tile in the
-// right-state face slots: one bulk copy per variable for a ghosted batch,
-// seven tensor-map boxes for a uniform grid (see patch_kernel).
+// right-state face slots: one bulk copy per variable for a ghosted batch;
+// for a uniform grid the patch interior and its six face slabs as seven
+// dense boxes (bulk copies where the source is contiguous, tensor-map
+// copies where it is strided; see patch_kernel).
 // Shared memory: 27648 elements of S (primitive tile, face slots, conic
 // parameter of the tile cells: 216 KB double, 108 KB float).
 #pragma once
@@ -277,8 +279,8 @@ template <class S> __device__ __forceinline__ S* face_slot(S* face, int d, int s
 constexpr int kStageOffset = 3 * 5 * kNF;  // first right-state slot
 static_assert(5 * kGC == 3 * 5 * kNF, "a ghosted tile fills the right-state slots");
 
-// Uniform-grid tiles staged by tensor copies (gather mode 1): the patch
-// interior and its six face slabs, five variables each, as dense boxes in
+// Uniform-grid tiles staged by the copy engine (gather modes 1 and 3): the
+// patch interior and its six face slabs, five variables each, as dense boxes in
 // the stage (x fastest): centre [5][8][8][8], then -x and +x [5][8][8][4]
 // (neighbour x 4..7 and 0..3: rows of 16 bytes), -y and +y [5][8][2][8]
 // (neighbour y 6..7 and 0..1), -z and +z [5][2][8][8]. Every box starts on
@@ -574,7 +576,8 @@ __global__ void __launch_bounds__(NT, MINB) patch_kernel(const __grid_constant__
   // phase 1 of that patch reads it. Needs 16-byte aligned tiles. Uniform
   // grid (gather modes 1 and 3 with tensor maps): the same with the seven
   // boxes of the next patch's tile (box_offset; in mode 3 variables 0..4 of
-  // the primitive cache), for patches whose six face neighbours exist
+  // the primitive cache; mode 1 fills the centre and z boxes with plain bulk
+  // copies, the rest with tensor copies), for patches whose six face neighbours exist
   // (periodic or interior; other patches, and the first patch of each CTA,
   // gather with plain loads). s_stg:
   // bit 0 the parity of the s_mbar phase that the next copy completes, bit 1

@@ -208,11 +208,13 @@ def test_staged_boxes_give_the_tile():
 
 @pytest.mark.parametrize("elem", [4, 8])
 def test_tensor_copy_coordinates(elem):
-    # The seven tensor copies of the staged uniform gather (box dims x, y, z
-    # and start coordinates, restated from the issue code in
-    # srhd_kernels.cuh): the innermost start x times the element size must be
-    # a multiple of 16 bytes, every box must lie inside the patch, and the
-    # bytes the mbarrier expects must be the sum of the boxes.
+    # The seven boxes of the staged uniform gather (box dims x, y, z and
+    # start coordinates, restated from the issue code in srhd_kernels.cuh;
+    # all seven are tensor copies in mode 3, the x and y slabs in mode 1,
+    # whose centre and z slabs test_bulk_copies_of_the_uniform_stage covers):
+    # the innermost start x times the element size must be a multiple of 16
+    # bytes, every box must lie inside the patch, and the bytes the mbarrier
+    # expects must be the sum of the boxes.
     boxes = {"center": ((8, 8, 8), (0, 0, 0)), "-x": ((4, 8, 8), (4, 0, 0)),
              "+x": ((4, 8, 8), (0, 0, 0)), "-y": ((8, 2, 8), (0, 6, 0)),
              "+y": ((8, 2, 8), (0, 0, 0)), "-z": ((8, 8, 2), (0, 0, 6)),
