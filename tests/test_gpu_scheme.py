@@ -96,3 +96,117 @@ def test_cold_sound_wave_reduced_vs_total_energy(oracle):
     red32 = _sound_wave_gpu(torch, srhd, oracle, 64, "reduced", "mixed_cf")
     assert red32 is not None and red32 < 1e-6 and red32 < tot[1] / 3, (red32, tot)
     assert _sound_wave_gpu(torch, srhd, oracle, 64, "total", "mixed_cf") is None
+
+
+def _mixed_limits_gpu(torch, srhd, C, n, scheme, prec, t_end):
+    """The mixed-limits Riemann problem on the GPU as a row of n/8 patches
+    (periodic y, z; outflow x), the fused 1-D CFL bound setting each step."""
+    ctx = srhd.Context(srhd.Params(ndim=1, scheme=scheme))
+    npx = n // 8
+    F = np.broadcast_to(C.reshape(5, 1, 1, n), (5, 8, 8, n)).copy()
+    U = to_dev(torch, workloads.patchify(F), torch_dtype(torch, prec))
+    V = torch.empty_like(U)
+    dd = torch.empty((npx, 2), dtype=torch.float64, device="cuda")
+    dn = torch.empty(1, dtype=torch.float64, device="cuda")
+    st = torch.empty(npx, dtype=torch.int32, device="cuda")
+    dh = 1.0 / n
+    dt = ctx.cfl_dt(U, dh, prec=prec).item()
+    t, steps, worst = 0.0, 0, 0
+    while t < t_end:
+        dt = min(dt, t_end - t)
+        dd[:, 0] = dt
+        dd[:, 1] = dh
+        ctx.advance_uniform(U, npx, 1, 1, dd, bc=("outflow", "periodic", "periodic"), cons_out=V,
+                            dt_next=dn, patch_status=st, prec=prec)
+        worst = max(worst, int((st >> 8).max()))
+        U, V = V, U
+        t += dt
+        steps += 1
+        dt = dn.item()
+    G = workloads.unpatchify(to_np(U), npx, 1, 1)
+    assert np.array_equal(G, np.broadcast_to(G[:, :1, :1, :], G.shape))
+    return G[:, 0, 0, :].astype(np.float64), steps, worst
+
+
+def _mixed_limits_oracle(oracle, C, n, t_end):
+    """The oracle's run of the same problem with the GPU's retry granularity:
+    one 8-cell block per patch (a patch of the GPU's row is uniform in y and
+    z, so its y and z flux differences vanish and it fails or passes with
+    its 8-cell row), each block retried on its own (oracle.evolve retries
+    the whole domain at once)."""
+    dh = 1.0 / n
+    cons, t, steps = C.copy(), 0.0, 0
+    while t < t_end:
+        dt = min(oracle.cfl_dt(cons, dh, cfl=0.5, ndim=1), t_end - t)
+        G = oracle.fill_ghosts(cons.reshape(5, 1, 1, n), (1, 0, 0), "outflow")
+        out = np.empty_like(cons)
+        for b in range(n // 8):
+            r = oracle.advance_block(G[:, :, :, 8 * b:8 * b + 12], (8, 1, 1), (1, 0, 0), dt, dh)
+            assert r["status"] in (oracle.BLK_OK, oracle.BLK_NOCONV)
+            out[:, 8 * b:8 * b + 8] = r["out"].reshape(5, 8)
+        cons, t, steps = out, t + dt, steps + 1
+    return cons, steps
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed_cf"])
+def test_mixed_limits_riemann_problem(oracle, prec):
+    # The initial states of Section 4.2.2 (Table "tb:IC_RiemannProblems",
+    # second row: a cold left state, T = 1e-6, against an ultra-relativistic
+    # right-moving stream), shortened to [0, 1] with 1024 cells (the
+    # paper's cell size) and t = 0.4 so that the oracle runs it too. With the
+    # reduced energy the GPU's errors against the exact solution match the
+    # oracle's and the cold state keeps its pressure; with the
+    # total energy in float storage the cold state's pressure is off by about
+    # a per cent from the first step (E = D h gamma - p stores the thermal
+    # energy, 1.5e-6 of E, at float resolution: the error of the paper's
+    # Eq. (error in the NR limit) that makes its original-scheme run of this
+    # problem 23 % wrong near the rarefaction). The density jumps by 4e10
+    # across the contact, so a domain-wide relative L1 would measure only
+    # the few smeared contact cells; the comparison is made on the shocked
+    # right plateau (rho, p against the exact solution), the shock position
+    # and the cold state.
+    torch, srhd = require_gpu()
+    n, x0, t_end = 1024, 0.05, 0.4
+    x = (np.arange(n) + 0.5) / n
+    left = x < x0
+    W = np.zeros((5, n))
+    W[0] = np.where(left, 1e2, 1e-12)
+    W[1] = np.where(left, 1e-3, -1e2)
+    W[4] = np.where(left, 1e-4, 1e-10)
+    rho_ex, _, p_ex, info = oracle.exact_riemann((1e2, 1e-3, 1e-4), (1e-12, -1e2, 1e-10), x0,
+                                                 t_end, x)
+    us = info["Ushock_R"]
+    x_shock = x0 + t_end * us / np.sqrt(1 + us * us)
+    cold = x < 0.04  # the undisturbed left state at t = 0.4
+    plateau = (x > 0.07) & (x < x_shock - 0.02)
+
+    def plateau_err(P):
+        return (np.mean(np.abs(P[0][plateau] / rho_ex[plateau] - 1)),
+                np.mean(np.abs(P[4][plateau] / p_ex[plateau] - 1)))
+
+    def shock_cell(P):  # first cell past half the jump to the right state
+        return int(np.argmax((x > 0.1) & (P[0] < 0.5 * (info["rho_CR"] + 1e-12))))
+    C, _ = oracle.prim2con(W, oracle.NEW)
+    if prec != "fp64":
+        C = C.astype(np.float32).astype(np.float64)
+    G, steps, worst = _mixed_limits_gpu(torch, srhd, C, n, "reduced", prec, t_end)
+    assert worst == 0
+    Pg = oracle.con2pri(G, oracle.NEW)["prim"]
+    ref, ref_steps = _mixed_limits_oracle(oracle, C, n, t_end)
+    Pr = oracle.con2pri(ref, oracle.NEW)["prim"]
+    assert abs(steps - ref_steps) <= 1
+    # the plateau errors (about 2e-3, set by the shock's start-up) match the
+    # oracle's to 10 %, the shock lies in the same cell (+-1)
+    eg, er = plateau_err(Pg), plateau_err(Pr)
+    assert all(abs(a - b) < 0.1 * b for a, b in zip(eg, er)), (eg, er)
+    assert abs(shock_cell(Pg) - shock_cell(Pr)) <= 1
+    assert np.max(np.abs(Pg[4][cold] / 1e-4 - 1)) < (1e-12 if prec == "fp64" else 1e-5)
+    if prec == "fp64":
+        smooth = cold | plateau
+        assert np.max(np.abs(Pg[0][smooth] / Pr[0][smooth] - 1)) < 1e-6
+        return
+    Ct, _ = oracle.prim2con(W, oracle.ORIGINAL)
+    Ct = Ct.astype(np.float32).astype(np.float64)
+    Gt, _, worst_t = _mixed_limits_gpu(torch, srhd, Ct, n, "total", prec, t_end)
+    Pt = oracle.con2pri(Gt, oracle.ORIGINAL)["prim"]
+    assert np.max(np.abs(Pt[4][cold] / 1e-4 - 1)) > 5e-3, worst_t

@@ -88,3 +88,36 @@ def test_rapidity_integral_additive(oracle):
     c = oracle.rapidity_integral(1e-6, 1e3)
     assert abs((a + b) / c - 1) < 1e-14
     assert oracle.rapidity_integral(1e3, 1e-6) == -c
+
+
+def _fixture_keys(path):
+    keys = {}
+    for line in open(path):
+        if line.startswith("# key "):
+            k, v = line[6:].split("=")
+            keys[k.strip()] = float(v)
+    return keys
+
+
+def test_mixed_limits_cell_fixture(oracle):
+    # tests/golden/mixed_limits_cells_t80.txt (the mixed-limits solution at
+    # the cell centres of the paper's 102 400-cell grid, for the GPU run of
+    # Section 4.2.2 in bench.py) is this solver's output, and its constants
+    # are the paper's table: the right plateau's density and pressure, the
+    # contact four-velocity (to the table's 1e-9), and the shock inside the
+    # table's bracket; the rows run from the cold left state through the fan
+    # to the right plateau, ending at x < 0.3.
+    path = os.path.join(os.path.dirname(__file__), "golden", "mixed_limits_cells_t80.txt")
+    cells = np.loadtxt(path)
+    keys = _fixture_keys(path)
+    tab = np.loadtxt(GOLDEN)
+    x = cells[:, 0]
+    dx = 100.0 / 102400
+    assert np.allclose(x, (np.arange(x.size) + 0.5) * dx, rtol=0, atol=1e-15) and x[-1] < 0.3 <= x[-1] + dx
+    rho, U, p, _ = oracle.exact_riemann(MIXED_L, MIXED_R, 0.05, 80.0, x)
+    assert np.all(np.abs(cells[:, 1] / rho - 1) < 1e-14) and np.all(np.abs(cells[:, 3] / p - 1) < 1e-14)
+    assert abs(keys["rho_right_plateau"] / tab[17, 1] - 1) < 2e-12
+    assert abs(keys["p_star"] / tab[17, 3] - 1) < 2e-12
+    assert abs(keys["U_right_plateau"] / tab[17, 2] - 1) < 1e-9
+    assert tab[17, 0] < keys["x_shock"] < tab[18, 0]
+    assert cells[0, 1] == MIXED_L[0] and abs(cells[-1, 1] / keys["rho_right_plateau"] - 1) < 1e-12
