@@ -56,6 +56,11 @@ TILE_SHAPE = "1x1x1 patches of 8^3 per CTA"
 # MUSCL-Hancock step of the benchmark state in the large-block limit, plus
 # the CFL bound of the updated cell.
 FLOPS_PER_CELL_UPDATE = 4583.2
+# The same count for the VL integrator and for MUSCL-Hancock under the
+# polytropic EoS with Gamma = 4/3 on the same state (oracle/count_flops.py,
+# keys "vl" and "polytropic_gamma_4_3").
+FLOPS_PER_CELL_UPDATE_VL = 3105.9
+FLOPS_PER_CELL_UPDATE_POLY = 2778.0
 # Algorithmic bytes per cell update: 5 conserved values read + 5 written.
 BYTES_PER_CELL_UPDATE = {"mixed_cf": 40, "mixed": 40, "fp64": 80}
 # The same with the halo a ghosted batch carries: 12^3 tile cells read and
@@ -519,6 +524,16 @@ def bench_amr(torch, srhd, steps: int, warmup: int, prec: str = "mixed_cf"):
     return out
 
 
+def alu_roofline(flops_per_cell: float, cells: int, launch_ms: float, prec: str):
+    """ALU roofline of a fused step (as the headline's): algorithmic flops per
+    launch over the mean launch time, against the FP32 peak derived from
+    unit counts and clocks (float paths) or the nominal FP64 peak."""
+    achieved = flops_per_cell * cells / (launch_ms * 1e-3) / 1e12
+    peak = PEAK_FP64_TFLOPS if prec == "fp64" else PEAK_FP32_TFLOPS
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "flops_per_cell_update": flops_per_cell}
+
+
 def bench_polytropic(torch, srhd, steps: int, warmup: int, precs=("mixed_cf", "fp64"),
                      gamma=4.0 / 3.0, variants=None):
     """The 256^3 advection batch with the polytropic EoS (Gamma = 4/3, the
@@ -536,6 +551,9 @@ def bench_polytropic(torch, srhd, steps: int, warmup: int, precs=("mixed_cf", "f
             cells = G.shape[0] * CELLS_PER_PATCH
             r = {"value": cells * steps / (total_ms * 1e-3), "unit": UNIT,
                  "ms_per_step": total_ms / steps, "patch_status_max": smax}
+            if abs(gamma - 4.0 / 3.0) < 1e-12:
+                r["roofline"] = alu_roofline(FLOPS_PER_CELL_UPDATE_POLY, cells,
+                                             statistics.mean(per), prec)
             if riemann == "hllc":
                 r["l1_rho_64"], _ = l1_one_period(torch, srhd, prec, params=srhd.Params(
                     eos="polytropic", gamma=gamma))
@@ -558,7 +576,8 @@ def bench_vl(torch, srhd, steps: int, warmup: int, precs=("mixed_cf", "fp64")):
                                                    lambda: None, prec, vl=True)
         cells = G.shape[0] * CELLS_PER_PATCH
         r = {"value": cells * steps / (total_ms * 1e-3), "unit": UNIT,
-             "ms_per_step": total_ms / steps, "patch_status_max": smax}
+             "ms_per_step": total_ms / steps, "patch_status_max": smax,
+             "roofline": alu_roofline(FLOPS_PER_CELL_UPDATE_VL, cells, statistics.mean(per), prec)}
         r["l1_rho_64"], _ = l1_one_period(torch, srhd, prec, vl=True)
         out["runs"][prec] = r
         del G, dt_dh

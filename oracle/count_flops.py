@@ -7,7 +7,10 @@ n^3 periodic block is counted for n = 16, 32, 64; the count per interior
 cell is c(n) = a + b/n + c/n^2 (halo work scales with the surface), and
 a, the limit n -> infinity, is the algorithmic count of one cell update
 (ghost recomputation excluded). The CFL bound of the updated cell (one
-con2pri and S_max) is counted separately and added.
+con2pri and S_max) is counted separately and added. The same count is made
+for the VL integrator (key "vl") and for the MUSCL-Hancock step under the
+polytropic EoS with Gamma = 4/3 (key "polytropic_gamma_4_3"), the two other
+workloads the benchmark times on this state.
 
 Usage: python oracle/count_flops.py   (prints JSON)
 """
@@ -22,18 +25,22 @@ from oracle import oracle as O  # noqa: E402
 from paper_2012_11130_gb300 import workloads  # noqa: E402
 
 
-def per_cell(n, N=256):
+def per_cell(n, N=256, vl=False):
     W = workloads.advection_prims(N)
     C, _ = O.prim2con(W.reshape(5, -1))
-    C = C.reshape(5, N, N, N)[:, :n + 4, :n + 4, :n + 4].copy()  # n^3 block with ghosts
+    g = 6 if vl else 4  # ghost cells of both sides
+    C = C.reshape(5, N, N, N)[:, :n + g, :n + g, :n + g].copy()  # n^3 block with ghosts
     dh = 1.0 / N
-    c = O.count_advance_block(C, (n, n, n), (1, 1, 1), 0.4 * dh, dh)
+    count = O.count_advance_block_vl if vl else O.count_advance_block
+    c = count(C, (n, n, n), (1, 1, 1), 0.4 * dh, dh)
     return {k: v / n ** 3 for k, v in c.items()}
 
 
-def main():
+def count(vl=False):
+    """Per cell update: the step's count in the large-block limit plus the
+    CFL bound of the updated cell, under the EoS currently selected."""
     sizes = (16, 32, 64)
-    rows = [per_cell(n) for n in sizes]
+    rows = [per_cell(n, vl=vl) for n in sizes]
     kinds = ("add", "mul", "div", "sqrt")
     A = np.array([[1.0, 1.0 / n, 1.0 / n ** 2] for n in sizes])
     limit = {k: float(np.linalg.solve(A, np.array([r[k] for r in rows]))[0]) for k in kinds}
@@ -41,14 +48,21 @@ def main():
     C, _ = O.prim2con(W.reshape(5, -1))
     cfl = {k: v / C.shape[1] for k, v in O.count_cfl(C).items()}
     step = {k: limit[k] + cfl[k] for k in kinds}
-    out = {
-        "workload": "smooth advection, gamma 10 along (1,1,1), T ~ 1",
+    return {
         "per_cell_update_step": limit,
         "per_cell_cfl": cfl,
         "per_cell_update_with_cfl": step,
         "flops_per_cell_update": sum(step.values()),
         "measured_per_cell_at_n": {str(n): r for n, r in zip(sizes, rows)},
     }
+
+
+def main():
+    out = {"workload": "smooth advection, gamma 10 along (1,1,1), T ~ 1"}
+    out.update(count())  # MUSCL-Hancock, Taub-Mathews EoS
+    out["vl"] = count(vl=True)
+    with O.eos(O.EOS_POLYTROPIC, 4.0 / 3.0):
+        out["polytropic_gamma_4_3"] = count()
     print(json.dumps(out, indent=1))
 
 

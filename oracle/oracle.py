@@ -95,6 +95,8 @@ def lib():
             L.or_count_advance_block.restype = None
             L.or_count_advance_block.argtypes = [_dp, i32, i32, i32, i32, i32, i32, d, d, d, i32,
                                                  _up]
+            L.or_count_advance_block_vl.restype = None
+            L.or_count_advance_block_vl.argtypes = L.or_count_advance_block.argtypes
             L.or_count_cfl.restype = None
             L.or_count_cfl.argtypes = [_dp, i64, i32, _up]
             L.or_exact_riemann.restype = None
@@ -332,6 +334,15 @@ def count_advance_block(cons, n, act, dt, dh, theta=DEFAULT_THETA, riemann=0):
     c = np.zeros(4, np.uint64)
     lib().or_count_advance_block(_p(cons), n[0], n[1], n[2], int(act[0]), int(act[1]),
                                  int(act[2]), dt, dh, theta, riemann, _p(c, _up))
+    return dict(add=int(c[0]), mul=int(c[1]), div=int(c[2]), sqrt=int(c[3]))
+
+
+def count_advance_block_vl(cons, n, act, dt, dh, theta=DEFAULT_THETA, riemann=0):
+    """Operation tally of one VL block advance (3 ghost cells on active dims)."""
+    cons = _f64(cons)
+    c = np.zeros(4, np.uint64)
+    lib().or_count_advance_block_vl(_p(cons), n[0], n[1], n[2], int(act[0]), int(act[1]),
+                                    int(act[2]), dt, dh, theta, riemann, _p(c, _up))
     return dict(add=int(c[0]), mul=int(c[1]), div=int(c[2]), sqrt=int(c[3]))
 
 

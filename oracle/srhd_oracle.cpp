@@ -1285,6 +1285,27 @@ void or_count_advance_block(const double* in, int nx, int ny, int nz, int actx, 
   counts[3] = g_tally.sqrt;
 }
 
+// The same count for one VL block advance (3 ghost cells on active sides).
+void or_count_advance_block_vl(const double* in, int nx, int ny, int nz, int actx, int acty,
+                               int actz, double dt, double dh, double theta, int riemann,
+                               uint64_t* counts) {
+  int n[3] = {nx, ny, nz};
+  int act[3] = {actx, acty, actz};
+  Params P{theta, 0.75, 1e-2, riemann, actx + acty + actz, 0.5, 0, 0};
+  int nin = 1;
+  for (int d = 0; d < 3; ++d) nin *= n[d] + (act[d] ? 6 : 0);
+  std::vector<OpCount> cin((size_t)5 * nin), cout((size_t)5 * nx * ny * nz);
+  for (size_t q = 0; q < cin.size(); ++q) cin[q] = OpCount(in[q]);
+  g_tally = OpTally();
+  int r = 0;
+  advance_block_vl(cin.data(), cout.data(), (OpCount*)nullptr, n, act, OpCount(dt), OpCount(dh), P,
+                   &r);
+  counts[0] = g_tally.add;
+  counts[1] = g_tally.mul;
+  counts[2] = g_tally.div;
+  counts[3] = g_tally.sqrt;
+}
+
 // Operation count of the signal-speed CFL bound of n cells (con2pri + S_max).
 void or_count_cfl(const double* cons, int64_t n, int ndim, uint64_t* counts) {
   g_tally = OpTally();
