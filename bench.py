@@ -535,17 +535,17 @@ def alu_roofline(flops_per_cell: float, cells: int, launch_ms: float, prec: str)
 
 
 def bench_polytropic(torch, srhd, steps: int, warmup: int, precs=("mixed_cf", "fp64"),
-                     gamma=4.0 / 3.0, variants=None):
+                     gamma=4.0 / 3.0, variants=None, n=N_GRID):
     """The 256^3 advection batch with the polytropic EoS (Gamma = 4/3, the
     ultra-relativistic gas the paper keeps it for), HLLC and the HLLE-only
     path: cell updates/s of the fused step and the one-period L1 of rho at
     64^3 (the same exact translation as for TM)."""
-    out = {"workload": "256^3 periodic advection (as the headline) with the polytropic EoS, "
+    out = {"workload": f"{n}^3 periodic advection (as the headline) with the polytropic EoS, "
                        f"Gamma = {gamma:g}", "gamma": gamma, "runs": {}}
     for prec in precs:
         for riemann in ("hllc", "hlle"):
             ctx = srhd.Context(srhd.Params(eos="polytropic", gamma=gamma, riemann=riemann))
-            G, dt_dh = build_workload(torch, srhd, ctx, prec)
+            G, dt_dh = build_workload(torch, srhd, ctx, prec, n)
             total_ms, per, dt_next, smax = time_device(torch, ctx, G, dt_dh, steps, warmup,
                                                        lambda: None, prec)
             cells = G.shape[0] * CELLS_PER_PATCH
@@ -563,15 +563,15 @@ def bench_polytropic(torch, srhd, steps: int, warmup: int, precs=("mixed_cf", "f
     return out
 
 
-def bench_vl(torch, srhd, steps: int, warmup: int, precs=("mixed_cf", "fp64")):
+def bench_vl(torch, srhd, steps: int, warmup: int, precs=("mixed_cf", "fp64"), n=N_GRID):
     """The 256^3 advection batch advanced with the VL integrator (14^3 tiles,
     three ghost cells): cell updates/s of srhd_advance_patches_vl and the
     one-period L1 of rho at 64^3."""
-    out = {"workload": "256^3 periodic advection (as the headline), VL integrator, "
-                       "32768 patches of 8^3 + 3 ghost cells", "runs": {}}
+    out = {"workload": f"{n}^3 periodic advection (as the headline), VL integrator, "
+                       f"{(n // 8) ** 3} patches of 8^3 + 3 ghost cells", "runs": {}}
     for prec in precs:
         ctx = srhd.Context(srhd.Params())
-        G, dt_dh = build_workload(torch, srhd, ctx, prec, ghost=3)
+        G, dt_dh = build_workload(torch, srhd, ctx, prec, n, ghost=3)
         total_ms, per, dt_next, smax = time_device(torch, ctx, G, dt_dh, steps, warmup,
                                                    lambda: None, prec, vl=True)
         cells = G.shape[0] * CELLS_PER_PATCH
@@ -1116,18 +1116,19 @@ def run_ours(args):
                             else "mixed_cf")
 
     poly_res = None
-    if not args.no_poly and args.grid == N_GRID and rank == 0:
+    if not args.no_poly and rank == 0:
         poly_res = bench_polytropic(torch, srhd, max(3, args.steps // 2), 3,
-                                    precs=tuple(q for q in ("mixed_cf", "fp64") if q in precs))
+                                    precs=tuple(q for q in ("mixed_cf", "fp64") if q in precs),
+                                    n=args.grid)
 
     ml_res = None
     if args.mixed_limits and rank == 0:
         ml_res = bench_mixed_limits(torch, srhd)
 
     vl_res = None
-    if not args.no_vl and args.grid == N_GRID and rank == 0:
+    if not args.no_vl and rank == 0:
         vl_res = bench_vl(torch, srhd, max(3, args.steps // 2), 3,
-                          precs=tuple(q for q in ("mixed_cf", "fp64") if q in precs))
+                          precs=tuple(q for q in ("mixed_cf", "fp64") if q in precs), n=args.grid)
 
     jet_res = None
     if not args.no_jet and args.grid == N_GRID and rank == 0:
