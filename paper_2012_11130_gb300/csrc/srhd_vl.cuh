@@ -141,6 +141,36 @@ __device__ __forceinline__ void vl_derive(PrimX<R>& W, const E& eos) {
   W.gamma = g2 * W.rg;
 }
 
+// vl_derive of two float states with the lane-wise arithmetic packed.
+template <class E>
+__device__ __forceinline__ void vl_derive_x2(PrimX<float>& A, PrimX<float>& B, const E& eos) {
+  using namespace pk;
+  const float2 T = make_float2(qdiv(A.p, A.rho), qdiv(B.p, B.rho));
+  float2 ht;
+  if constexpr (std::is_same<E, EosTM>::value) {
+    const float2 q = mul(mul(s2(2.25f), T), T);
+    const float2 t2 = make_float2(qdiv(q.x, 1.0f + sqrtf(q.x + 1.0f)),
+                                  qdiv(q.y, 1.0f + sqrtf(q.y + 1.0f)));
+    ht = fma(s2(2.5f), T, t2);
+  } else {
+    float hA, mA, hB, mB;
+    eos_ht(eos, T.x, hA, mA);
+    eos_ht(eos, T.y, hB, mB);
+    ht = make_float2(hA, hB);
+  }
+  const float2 u0 = make_float2(A.u[0], B.u[0]), u1 = make_float2(A.u[1], B.u[1]);
+  const float2 u2 = make_float2(A.u[2], B.u[2]);
+  const float2 g2 = add(s2(1.0f), fma(u2, u2, fma(u1, u1, mul(u0, u0))));
+  const float2 rg = rsq(g2);
+  const float2 gm = mul(g2, rg);
+  const float2 h = add(s2(1.0f), ht);
+  A.T = T.x; B.T = T.y;
+  A.ht = ht.x; B.ht = ht.y;
+  A.h = h.x; B.h = h.y;
+  A.rg = rg.x; B.rg = rg.y;
+  A.gamma = gm.x; B.gamma = gm.y;
+}
+
 // Start of the conversion solver from a nearby state of temperature T: the
 // solver variable itself (tau = htilde - T for TM, htilde for polytropic).
 template <class R> __device__ __forceinline__ R vl_guess(const EosTM& e, R T) {
@@ -181,8 +211,12 @@ __device__ __forceinline__ void vl_predict_dir(const typename P::S* in, const ty
     PrimX<S> WL, WR;
     vl_load_prim(Wn, cl, WL);
     vl_load_prim(Wn, cr, WR);
-    vl_derive(WL, eos);
-    vl_derive(WR, eos);
+    if constexpr (sizeof(S) == 4) {
+      vl_derive_x2(WL, WR, eos);
+    } else {
+      vl_derive(WL, eos);
+      vl_derive(WR, eos);
+    }
     S UL[5], UR[5], F[5];
 #pragma unroll
     for (int v = 0; v < 5; ++v) {
@@ -371,6 +405,65 @@ __global__ void __launch_bounds__(NT, MINB) vl_patch_kernel(PatchArgs a) {
             S* out = static_cast<S*>(a.out) + (size_t)p * 5 * kNC;
             const bool signal = a.partial_dt && a.cfl_mode != 1;
             int fail5 = 0;
+            if constexpr (sizeof(R) == 4) {
+              // float: the work item c0 < 256 updates cells c0 and c0 + 256
+              // in packed arithmetic and converts both in lockstep for the
+              // CFL bound (warm starts from their half-step states)
+              constexpr int kItems = kNC / 2;
+              for (int c0 = tid; c0 < kItems; c0 += NT) {
+                const float2 mcoef = pk::s2(-float(s_pc[0]));
+                int tcq[2], fq[2][6];
+#pragma unroll
+                for (int q = 0; q < 2; ++q) {
+                  const int c = c0 + q * kItems;
+                  const int i = c & 7, j = (c >> 3) & 7, k = c >> 6;
+                  tcq[q] = vl_t14(i, j, k);
+                  fq[q][0] = face_index<0>(i, j, k, i);
+                  fq[q][1] = face_index<0>(i, j, k, i + 1);
+                  fq[q][2] = face_index<1>(i, j, k, j);
+                  fq[q][3] = face_index<1>(i, j, k, j + 1);
+                  fq[q][4] = face_index<2>(i, j, k, k);
+                  fq[q][5] = face_index<2>(i, j, k, k + 1);
+                }
+                S Un[2][5];
+#pragma unroll
+                for (int v = 0; v < 5; ++v) {
+                  auto ld = [&](int dd, int e) {
+                    const S* f = Fc + (dd * 5 + v) * kNF;
+                    return make_float2(f[fq[0][e]], f[fq[1][e]]);
+                  };
+                  const float2 div = pk::add(pk::add(pk::sub(ld(0, 1), ld(0, 0)),
+                                                     pk::sub(ld(1, 3), ld(1, 2))),
+                                             pk::sub(ld(2, 5), ld(2, 4)));
+                  const float2 old = make_float2(in[v * kVTC + tcq[0]], in[v * kVTC + tcq[1]]);
+                  const float2 un = pk::fma(mcoef, div, old);
+                  Un[0][v] = un.x;
+                  Un[1][v] = un.y;
+                  out[v * kNC + c0] = un.x;
+                  out[v * kNC + c0 + kItems] = un.y;
+                }
+                if (signal) {
+                  PrimX<R> W0, W1;
+                  int s0, s1;
+                  con2pri_x2<P, E, true>(Un[0], Un[1], W0, W1, maxit, s0, s1,
+                                         Wh[5 * kVH + c0], Wh[5 * kVH + c0 + kItems], ori, eos);
+                  if (s0 != 1) att_smax = fmax(att_smax, smax_of(W0, a.ndim, eos));
+                  if (s1 != 1) att_smax = fmax(att_smax, smax_of(W1, a.ndim, eos));
+                  if (s0 == 1 || s1 == 1) {
+                    att_bad = 1;
+                    fail5 = 1;
+                  }
+                } else {
+#pragma unroll
+                  for (int q = 0; q < 2; ++q) {
+                    typename P::AT Ac, m2c;
+                    if (!A_and_m2<P>(Un[q][0], Un[q][1], Un[q][2], Un[q][3], Un[q][4], Ac, m2c,
+                                     ori))
+                      fail5 = 1;
+                  }
+                }
+              }
+            } else {
             for (int c = tid; c < kNC; c += NT) {
               const R coef = s_pc[0];
               const int i = c & 7, j = (c >> 3) & 7, k = c >> 6;
@@ -402,6 +495,7 @@ __global__ void __launch_bounds__(NT, MINB) vl_patch_kernel(PatchArgs a) {
                 typename P::AT Ac, m2c;
                 if (!A_and_m2<P>(Un[0], Un[1], Un[2], Un[3], Un[4], Ac, m2c, ori)) fail5 = 1;
               }
+            }
             }
             fail = __syncthreads_or(fail5) | fail;
           }
