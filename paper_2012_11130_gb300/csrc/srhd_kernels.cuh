@@ -712,35 +712,23 @@ __global__ void __launch_bounds__(NT, MINB) patch_kernel(const __grid_constant__
     }
     // ---- phase 1: primitive tile ------------------------------------------
     if constexpr (GATHER == 3) {
-      // the primitives and solver variable that the previous step kept for
-      // the cells of the tile: a gather, no conversion. A state left
-      // unphysical by that step is stored as NaN.
+      // the primitives that the previous step kept for the cells of the
+      // tile: a gather, no conversion; the solver variable, the warm start of
+      // the later solves, from T = p / rho in closed form (solver_var_of_T).
+      // A state left unphysical by that step is stored as NaN.
       const S* pbase = static_cast<const S*>(a.prim_in);
       int r0 = tid;
       if (st1 & 2) {
         // staged tile (all six face neighbours exist, wrapping where
         // periodic): the interior and face-slab cells by the closed-form
-        // mapping, tau from the cache of the patch holding the cell
-        const int64_t q0 = a.gp0 + p;
-        auto wrap = [](int c, int n) { return c < 0 ? c + n : (c >= n ? c - n : c); };
-        auto pid = [&](int ix, int iy, int iz) {
-          return ((int64_t)iz * a.gny + iy) * a.gnx + ix;
-        };
-        const int64_t qxm = pid(wrap(gpx - 1, a.gnx), gpy, gpz);
-        const int64_t qxp = pid(wrap(gpx + 1, a.gnx), gpy, gpz);
-        const int64_t qym = pid(gpx, wrap(gpy - 1, a.gny), gpz);
-        const int64_t qyp = pid(gpx, wrap(gpy + 1, a.gny), gpz);
-        const int64_t qzm = pid(gpx, gpy, wrap(gpz - 1, a.gnz));
-        const int64_t qzp = pid(gpx, gpy, wrap(gpz + 1, a.gnz));
+        // mapping, entirely from the stage
         for (int r = tid; r < kNC + 768; r += NT) {
           int c, off, vs, nb, local;
           staged_cell(r, c, off, vs, nb, local);
-          const int64_t qn = nb == 0 ? q0 : nb == 1 ? qxm : nb == 2 ? qxp : nb == 3 ? qym
-                           : nb == 4 ? qyp : nb == 5 ? qzm : qzp;
           S w[6];
 #pragma unroll
           for (int v = 0; v < 5; ++v) w[v] = stage[off + v * vs];
-          w[5] = __ldg(pbase + qn * (6 * kNC) + 5 * kNC + local);
+          w[5] = solver_var_of_T(eos, qdiv(w[4], w[0]));
           if (!(w[0] > S(0) && w[4] > S(0) && isfinite(w[1] + w[2] + w[3] + w[5])))
             code |= CODE_BAD_INPUT;
 #pragma unroll
@@ -762,14 +750,14 @@ __global__ void __launch_bounds__(NT, MINB) patch_kernel(const __grid_constant__
         S w[6];
         int off, vs;
         if ((st1 & 2) && box_offset(g[0], g[1], g[2], off, vs)) {
-          // variables 0..4 staged by the tensor copies, tau from the cache
+          // variables 0..4 staged by the tensor copies
 #pragma unroll
           for (int v = 0; v < 5; ++v) w[v] = stage[off + v * vs];
-          w[5] = __ldg(src + 5 * kNC);
         } else {
 #pragma unroll
-          for (int v = 0; v < 6; ++v) w[v] = __ldg(src + v * kNC);
+          for (int v = 0; v < 5; ++v) w[v] = __ldg(src + v * kNC);
         }
+        w[5] = solver_var_of_T(eos, qdiv(w[4], w[0]));
         if (!(w[0] > S(0) && w[4] > S(0) && isfinite(w[1] + w[2] + w[3] + w[5])))
           code |= CODE_BAD_INPUT;
 #pragma unroll

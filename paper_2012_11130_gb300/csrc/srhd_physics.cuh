@@ -115,6 +115,22 @@ __device__ __forceinline__ void eos_ht(const EosPoly& e, R T, R& ht, R& hmT) {
   ht = T + hmT;
 }
 
+// The conversions' solver variable of a state of temperature T in closed
+// form: the conic parameter tau = h - T - 1 = htilde - T (TM) or htilde
+// (polytropic). The root a conversion converges to satisfies it to the
+// rounding of that root, so it is a warm start for the solve of a nearby
+// state.
+template <class R> __device__ __forceinline__ R solver_var_of_T(const EosTM& e, R T) {
+  R ht, hmT;
+  eos_ht(e, T, ht, hmT);
+  return hmT;
+}
+template <class R> __device__ __forceinline__ R solver_var_of_T(const EosPoly& e, R T) {
+  R ht, hmT;
+  eos_ht(e, T, ht, hmT);
+  return ht;
+}
+
 // Sound speed squared. TM: Eq. (sound_speed), c_s^2 = T (5h - 8T) / (3h (h - T)).
 // Polytropic: Gamma T / h.
 template <class R> __device__ __forceinline__ R cs2_of(const EosTM&, R T, R h) {
