@@ -25,6 +25,7 @@ bounded sample of the same workload per step).
 from __future__ import annotations
 
 import argparse
+import gc
 import hashlib
 import json
 import math
@@ -76,10 +77,10 @@ PEAK_FP64_TFLOPS = 1.25
 # only for the kernel sources with the recorded hash.
 # Captured at 128^3 (4096 patches) and scaled by 8 to the 32768-patch launch
 # (profiles/patch_kernel_advection128.md).
-NCU_TRAFFIC = {"sources_sha": "0c93312561434d76",
-               "mixed_cf": 8 * (141.715712e6 + 23.541504e6),
-               "mixed": 8 * (141.820928e6 + 24.083456e6),
-               "fp64": 8 * (284.587008e6 + 68.166912e6)}
+NCU_TRAFFIC = {"sources_sha": "2ad4069fd9a6a840",
+               "mixed_cf": 8 * (141.696512e6 + 23.350528e6),
+               "mixed": 8 * (141.796864e6 + 23.947520e6),
+               "fp64": 8 * (283.335168e6 + 67.212032e6)}
 
 
 # The sources that make the patch kernel's device code (its translation units
@@ -387,15 +388,23 @@ def time_e2e(torch, ctx, G, dt_dh, steps, warmup, prec):
         A, B = B, A
     torch.cuda.synchronize()
     per = []
-    t = time.perf_counter()
-    for _ in range(steps):
-        t1 = time.perf_counter()
-        _, dn = ctx.advance_uniform_host(A, npx, npx, npx, dt, dh, cons_out=B, patch_status=st,
-                                         prec=prec)
-        per.append(time.perf_counter() - t1)
-        A, B = B, A
-    torch.cuda.synchronize()
-    secs = time.perf_counter() - t
+    # the interpreter's cyclic garbage collector paused single steps for
+    # 15-20 ms (a full collection of the harness's heap): it runs before the
+    # timed steps, not inside them
+    gc.collect()
+    gc.disable()
+    try:
+        t = time.perf_counter()
+        for _ in range(steps):
+            t1 = time.perf_counter()
+            _, dn = ctx.advance_uniform_host(A, npx, npx, npx, dt, dh, cons_out=B,
+                                             patch_status=st, prec=prec)
+            per.append(time.perf_counter() - t1)
+            A, B = B, A
+        torch.cuda.synchronize()
+        secs = time.perf_counter() - t
+    finally:
+        gc.enable()
     h2d = A.numel() * A.element_size()
     d2h = B.numel() * B.element_size() + st.numel() * 4 + 8
     del A, B
@@ -1061,9 +1070,8 @@ def run_ours(args):
         e2e = None
         if not args.no_e2e:
             # five times the device steps in the float paths (about 0.26 s): a
-            # rare slow host step (about one in a few hundred, 10-15 ms, seen
-            # with the garbage collector on and off) then moves the mean by a
-            # few per cent instead of a quarter
+            # rare slow host step (10-20 ms) then moves the mean by a few per
+            # cent instead of a quarter
             ne = max(3, args.steps if prec == "fp64" else 5 * args.steps)
             secs, eper, h2d, d2h = time_e2e(torch, ctx, G, dt_dh, ne, max(3, args.warmup), prec)
             med = statistics.median(eper)
