@@ -388,9 +388,9 @@ def time_e2e(torch, ctx, G, dt_dh, steps, warmup, prec):
         A, B = B, A
     torch.cuda.synchronize()
     per = []
-    # the interpreter's cyclic garbage collector paused single steps for
-    # 15-20 ms (a full collection of the harness's heap): it runs before the
-    # timed steps, not inside them
+    # the interpreter's cyclic garbage collector runs before the timed
+    # steps, not inside them (a full collection of the harness's heap can
+    # stall the calling thread for milliseconds)
     gc.collect()
     gc.disable()
     try:
