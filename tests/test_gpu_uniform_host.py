@@ -6,7 +6,8 @@ fused step, copies out on four streams) equals the oracle's MUSCL-Hancock
 step of the whole periodic or mixed-boundary grid, is bit-identical for
 every chunk count, in place, with pageable memory and to the device-resident
 path (fill + srhd_advance_patches), and reports unphysical cells and bad
-arguments."""
+arguments; at the full 256^3 size of the benchmark it is bit-identical to the
+device-resident gathering step."""
 import numpy as np
 import pytest
 import torch as _torch
@@ -200,3 +201,38 @@ def test_uniform_edge_cases(oracle):
         ctx.advance_uniform(Ud, npx, npy, npz, dd, p0=10, n=3)
     with pytest.raises(Exception):
         ctx.advance_uniform(Ud, npx, npy, npz + 1, dd)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed_cf"])
+def test_full_size_host_step_equals_device_step(oracle, prec):
+    # The end-to-end configuration bench.py times: the 256^3 advection grid
+    # (32768 patches) in pinned host memory, 32 z-slab chunks on four
+    # streams. Its output, dt_next and statuses are bitwise those of the
+    # device-resident gathering step (srhd_advance_uniform) of the same
+    # state, which the full-size sampled test of test_gpu_runs.py compares
+    # with the oracle.
+    torch, srhd = require_gpu()
+    N = 256
+    npx = N // 8
+    Wf = workloads.advection_prims(N)
+    C, _ = oracle.prim2con(Wf.reshape(5, -1))
+    C = C.reshape(5, N, N, N)
+    dtype = torch.float64 if prec == "fp64" else torch.float32
+    U = workloads.patchify(C.astype(np.float64 if prec == "fp64" else np.float32))
+    dh = 1.0 / N
+    dt = 0.4 * dh
+    ctx = srhd.Context()
+    H = _host(U, dtype)
+    out_h = torch.empty_like(H).pin_memory()
+    st_h = torch.empty(npx ** 3, dtype=torch.int32).pin_memory()
+    _, dn_h = ctx.advance_uniform_host(H, npx, npx, npx, dt, dh, cons_out=out_h,
+                                       patch_status=st_h, prec=prec)
+    D = H.to("cuda")
+    dd = torch.tensor([[dt, dh]], dtype=torch.float64, device="cuda").repeat(npx ** 3, 1)
+    dn = torch.empty(1, dtype=torch.float64, device="cuda")
+    st = torch.empty(npx ** 3, dtype=torch.int32, device="cuda")
+    out_d = ctx.advance_uniform(D, npx, npx, npx, dd, dt_next=dn, patch_status=st, prec=prec)
+    torch.cuda.synchronize()
+    assert _same_bits(out_h, out_d.cpu())
+    assert np.array_equal(st_h.numpy(), st.cpu().numpy()) and int(st_h.abs().max()) == 0
+    assert dn_h == dn.item()
