@@ -1,7 +1,8 @@
 """Batched AMR on the GPU: a small off-centre blast hierarchy (3 levels of
 uneven size) through one fused launch per level substep. The CUDA-graph
 replay of a coarse step equals the eager launches bitwise, and sampled
-patches of every level equal the oracle's step from the same inputs."""
+patches of every level equal the oracle's step from the same inputs; the
+same sampled check on the full-size blast the benchmark times."""
 import numpy as np
 import pytest
 
@@ -76,3 +77,36 @@ def test_amr_graph_equals_eager_and_oracle(oracle, prec):
         cells = ref["out"][off[l]:off[l + 1]].transpose(1, 0, 2, 3, 4).reshape(5, -1)
         want = oracle.cfl_dt(cells, 1.0 / 32 / 2 ** l)
         assert abs(dt_eager[l] / want - 1) <= (1e-12 if prec == "fp64" else 1e-5)
+
+
+@pytest.mark.parametrize("prec", ["mixed_cf", "fp64"])
+def test_full_size_blast_step_sampled(oracle, prec):
+    # The batched AMR blast the benchmark times (5 levels, base 64^3, about
+    # 38 000 patches, 31 fused launches per coarse step): one coarse step,
+    # then sampled patches of every level recomputed by the oracle from the
+    # same ghosted inputs (each level's last substep wrote the output).
+    torch, srhd = require_gpu()
+    from paper_2012_11130_gb300 import amr
+    ctx = srhd.Context(srhd.Params())
+    batch, lev = amr.blast_batch(ctx, prec=prec)
+    assert batch.launches_per_step == 31 and sum(batch.counts) > 30000
+    batch.step()
+    torch.cuda.synchronize()
+    st = batch.status.cpu().numpy()
+    assert np.all((st >> 8) == 0)
+    rng = np.random.default_rng(4)
+    off = np.cumsum([0] + batch.counts)
+    pick = np.concatenate([off[l] + rng.choice(batch.counts[l], min(6, batch.counts[l]),
+                                               replace=False) for l in range(batch.nlev)])
+    idx = torch.as_tensor(pick, device="cuda")
+    G = to_np(batch.G[idx]).astype(np.float64)
+    dd = batch.dt_dh[idx].cpu().numpy()
+    ref = oracle.advance_patches(G, dd)
+    same = (st[pick] & 255) == ref["retries"]
+    if prec == "fp64":
+        assert same.all()
+    got = to_np(batch.out[idx])
+    err = cons_rel_err(got[same].transpose(1, 0, 2, 3, 4), ref["out"][same].transpose(1, 0, 2, 3, 4))
+    retried = ref["retries"][same] > 0
+    tol = np.where(retried, 1e-10, 1e-12) if prec == "fp64" else 1e-5
+    assert np.all(err.reshape(-1, 512).max(axis=1) <= tol), err.max()
