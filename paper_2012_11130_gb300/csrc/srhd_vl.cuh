@@ -171,6 +171,61 @@ __device__ __forceinline__ void vl_derive_x2(PrimX<float>& A, PrimX<float>& B, c
   A.gamma = gm.x; B.gamma = gm.y;
 }
 
+// prim2con of two float states (as the scalar prim2con, lane by lane, with
+// the arithmetic packed): conserved variables and the derived T, h, gamma,
+// 1/gamma of both; a state with rho <= 0 or p <= 0 gets NaN conserved
+// variables and its flag false.
+template <class E>
+__device__ __forceinline__ void vl_prim2con_x2(PrimX<float>& A, PrimX<float>& B, float (&UA)[5],
+                                               float (&UB)[5], bool& okA, bool& okB, int ori,
+                                               const E& eos) {
+  using namespace pk;
+  okA = A.rho > 0.0f && A.p > 0.0f;
+  okB = B.rho > 0.0f && B.p > 0.0f;
+  const float2 rho = make_float2(A.rho, B.rho), p = make_float2(A.p, B.p);
+  const float2 T = make_float2(qdiv(A.p, A.rho), qdiv(B.p, B.rho));
+  float2 ht, hmT;
+  if constexpr (std::is_same<E, EosTM>::value) {
+    const float2 q = mul(mul(s2(2.25f), T), T);
+    const float2 t2 = make_float2(qdiv(q.x, 1.0f + sqrtf(q.x + 1.0f)),
+                                  qdiv(q.y, 1.0f + sqrtf(q.y + 1.0f)));
+    ht = fma(s2(2.5f), T, t2);
+    hmT = fma(s2(1.5f), T, t2);
+  } else {
+    float a0, a1, b0, b1;
+    eos_ht(eos, T.x, a0, a1);
+    eos_ht(eos, T.y, b0, b1);
+    ht = make_float2(a0, b0);
+    hmT = make_float2(a1, b1);
+  }
+  const float2 u0 = make_float2(A.u[0], B.u[0]), u1 = make_float2(A.u[1], B.u[1]);
+  const float2 u2v = make_float2(A.u[2], B.u[2]);
+  const float2 u2 = fma(u2v, u2v, fma(u1, u1, mul(u0, u0)));
+  const float2 g2 = add(s2(1.0f), u2);
+  const float2 rg = rsq(g2);
+  const float2 gm = mul(g2, rg);
+  const float2 D = mul(rho, gm);
+  const float2 h = add(s2(1.0f), ht);
+  const float2 Dh = mul(D, h);
+  float2 U4;
+  if (ori) {
+    U4 = fma(Dh, gm, neg(p));
+  } else {
+    const float2 k1 = make_float2(qdiv(u2.x, gm.x + 1.0f), qdiv(u2.y, gm.y + 1.0f));
+    U4 = mul(D, fma(fma(ht, u2, hmT), rg, k1));
+  }
+  const float2 U1 = mul(Dh, u0), U2 = mul(Dh, u1), U3 = mul(Dh, u2v);
+  UA[0] = D.x; UA[1] = U1.x; UA[2] = U2.x; UA[3] = U3.x; UA[4] = U4.x;
+  UB[0] = D.y; UB[1] = U1.y; UB[2] = U2.y; UB[3] = U3.y; UB[4] = U4.y;
+  const float nan = __int_as_float(0x7fc00000);
+  if (!okA) for (int v = 0; v < 5; ++v) UA[v] = nan;
+  if (!okB) for (int v = 0; v < 5; ++v) UB[v] = nan;
+  A.T = T.x; B.T = T.y;
+  A.h = h.x; B.h = h.y;
+  A.gamma = gm.x; B.gamma = gm.y;
+  A.rg = rg.x; B.rg = rg.y;
+}
+
 // Start of the conversion solver from a nearby state of temperature T: the
 // solver variable itself (tau = htilde - T for TM, htilde for polytropic).
 template <class R> __device__ __forceinline__ R vl_guess(const EosTM& e, R T) {
@@ -374,18 +429,38 @@ __global__ void __launch_bounds__(NT, MINB) vl_patch_kernel(PatchArgs a) {
             }
             PrimX<R> WL, WR;
             R wl[5], wr[5];
-#pragma unroll
-            for (int v = 0; v < 5; ++v) {
-              const R w0 = R(Wh[v * kVH + hq[0]]), w1 = R(Wh[v * kVH + hq[1]]);
-              const R w2 = R(Wh[v * kVH + hq[2]]), w3 = R(Wh[v * kVH + hq[3]]);
-              wl[v] = w1 + R(0.5) * limited_slope(w1 - w0, w2 - w1, theta);
-              wr[v] = w2 - R(0.5) * limited_slope(w2 - w1, w3 - w2, theta);
-            }
-            WL.rho = wl[0]; WL.u[0] = wl[1]; WL.u[1] = wl[2]; WL.u[2] = wl[3]; WL.p = wl[4];
-            WR.rho = wr[0]; WR.u[0] = wr[1]; WR.u[1] = wr[2]; WR.u[2] = wr[3]; WR.p = wr[4];
             R UL[5], UR[5], F[5];
-            if (!prim2con(WL, UL, ori, eos)) fail = 1;
-            if (!prim2con(WR, UR, ori, eos)) fail = 1;
+            if constexpr (sizeof(R) == 4) {
+              // float: the left (lane x) and right (lane y) face states in
+              // packed form
+#pragma unroll
+              for (int v = 0; v < 5; ++v) {
+                const float w0 = Wh[v * kVH + hq[0]], w1 = Wh[v * kVH + hq[1]];
+                const float w2 = Wh[v * kVH + hq[2]], w3 = Wh[v * kVH + hq[3]];
+                const float2 sl = limited_slope_x2(make_float2(w1 - w0, w2 - w1),
+                                                   make_float2(w2 - w1, w3 - w2), theta);
+                const float2 lr = pk::fma(sl, make_float2(0.5f, -0.5f), make_float2(w1, w2));
+                wl[v] = lr.x;
+                wr[v] = lr.y;
+              }
+              WL.rho = wl[0]; WL.u[0] = wl[1]; WL.u[1] = wl[2]; WL.u[2] = wl[3]; WL.p = wl[4];
+              WR.rho = wr[0]; WR.u[0] = wr[1]; WR.u[1] = wr[2]; WR.u[2] = wr[3]; WR.p = wr[4];
+              bool okL, okR;
+              vl_prim2con_x2(WL, WR, UL, UR, okL, okR, ori, eos);
+              if (!okL || !okR) fail = 1;
+            } else {
+#pragma unroll
+              for (int v = 0; v < 5; ++v) {
+                const R w0 = R(Wh[v * kVH + hq[0]]), w1 = R(Wh[v * kVH + hq[1]]);
+                const R w2 = R(Wh[v * kVH + hq[2]]), w3 = R(Wh[v * kVH + hq[3]]);
+                wl[v] = w1 + R(0.5) * limited_slope(w1 - w0, w2 - w1, theta);
+                wr[v] = w2 - R(0.5) * limited_slope(w2 - w1, w3 - w2, theta);
+              }
+              WL.rho = wl[0]; WL.u[0] = wl[1]; WL.u[1] = wl[2]; WL.u[2] = wl[3]; WL.p = wl[4];
+              WR.rho = wr[0]; WR.u[0] = wr[1]; WR.u[1] = wr[2]; WR.u[2] = wr[3]; WR.p = wr[4];
+              if (!prim2con(WL, UL, ori, eos)) fail = 1;
+              if (!prim2con(WR, UR, ori, eos)) fail = 1;
+            }
             if (d == 0) riemann<0>(a.riemann, WL, UL, WR, UR, F, ori, eos);
             else if (d == 1) riemann<1>(a.riemann, WL, UL, WR, UR, F, ori, eos);
             else riemann<2>(a.riemann, WL, UL, WR, UR, F, ori, eos);
