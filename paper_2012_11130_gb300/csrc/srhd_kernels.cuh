@@ -22,8 +22,8 @@
 // for a uniform grid the patch interior and its six face slabs as seven
 // dense boxes (bulk copies where the source is contiguous, tensor-map
 // copies where it is strided; see patch_kernel).
-// Shared memory: 27648 elements of S (primitive tile, face slots, conic
-// parameter of the tile cells: 216 KB double, 108 KB float).
+// Shared memory: 27648 elements of S (primitive tile, face slots, warm-start
+// values of the tile cells: 216 KB double, 108 KB float).
 #pragma once
 
 #include <cfloat>
@@ -172,7 +172,7 @@ template <> __device__ __forceinline__ EosPoly make_eos<EosPoly>(const PatchArgs
 template <class S> struct SmemLayout {  // S: storage type
   static constexpr size_t prim_elems = 5 * kGC;        // primitive tile
   static constexpr size_t face_elems = 3 * 2 * 5 * kNF; // predicted faces / fluxes
-  static constexpr size_t ht_elems = kGC;               // conic parameter tau of the tile cells
+  static constexpr size_t ht_elems = kGC;               // warm-start values of the tile cells (kRatio)
   static constexpr size_t bytes = (prim_elems + face_elems + ht_elems) * sizeof(S);
 };
 
@@ -498,10 +498,12 @@ template <int d> __device__ __forceinline__ int face_owner(int fi, int side) {
 }
 
 // Riemann flux of face fi along d from the two predicted states in its
-// slots; their Newton solves start from the converged tau of the cells
-// they belong to (a warm start: the predicted state differs from the cell
-// state by half a limited slope and half a time step).
-template <int d, class P, bool PAIR, class E>
+// slots; their Newton solves start warm from the cells they belong to (the
+// predicted state differs from the cell state by half a limited slope and
+// half a time step): hts holds the cells' converged solver variable, or with
+// RATIO its ratio to the cold start (rt), which the solve multiplies by the
+// predicted state's own cold start.
+template <int d, class P, bool PAIR, class E, bool RATIO>
 __device__ __forceinline__ int face_flux(typename P::S* face, const typename P::S* hts, int fi,
                                          int solver, int maxit, int& code, int ori,
                                          const E& eos) {
@@ -517,10 +519,10 @@ __device__ __forceinline__ int face_flux(typename P::S* face, const typename P::
   PrimX<R> WL, WR;
   int sl, sr;
   if constexpr (PAIR) {
-    con2pri_x2<P, E, true>(UL, UR, WL, WR, maxit, sl, sr, gL, gR, ori, eos);
+    con2pri_x2<P, E, true, RATIO>(UL, UR, WL, WR, maxit, sl, sr, gL, gR, ori, eos);
   } else {
-    sl = con2pri<P, E, true>(UL[0], UL[1], UL[2], UL[3], UL[4], WL, maxit, gL, ori, eos);
-    sr = con2pri<P, E, true>(UR[0], UR[1], UR[2], UR[3], UR[4], WR, maxit, gR, ori, eos);
+    sl = con2pri<P, E, true, RATIO>(UL[0], UL[1], UL[2], UL[3], UL[4], WL, maxit, gL, ori, eos);
+    sr = con2pri<P, E, true, RATIO>(UR[0], UR[1], UR[2], UR[3], UR[4], WR, maxit, gR, ori, eos);
   }
   if (sl == 2 || sr == 2) code |= CODE_NOCONV;
   int fail = (sl == 1 || sr == 1);
@@ -589,6 +591,11 @@ __global__ void __launch_bounds__(NT, MINB) patch_kernel(const __grid_constant__
   [[maybe_unused]] __shared__ uint32_t s_stg;
   [[maybe_unused]] __shared__ int s_stage_timeout;
   constexpr bool kStaged = GATHER == 0 || GATHER == 1 || GATHER == 3;
+  // hts holds the tile cells' rt (the ratio of the converged solver
+  // variable to its cold start) where phase 1 converts them, and their
+  // solver variable itself where the primitive cache supplies it (mode 3);
+  // the warm starts of phases 3 and 4 take either
+  constexpr bool kRatio = GATHER != 3;
   auto stage_ok = [&]() {
     // tensor copies need 128-byte aligned destinations (the boxes are laid
     // out on 128-byte boundaries from `stage`)
@@ -772,7 +779,7 @@ __global__ void __launch_bounds__(NT, MINB) patch_kernel(const __grid_constant__
         load_tile(cb, r + kTileNeeded / 2, Ub);
         PrimX<R> Wa, Wb;
         int sa, sb;
-        con2pri_x2<P>(Ua, Ub, Wa, Wb, maxit, sa, sb, S(0), S(0), ori, eos);
+        con2pri_x2<P, E, false, true>(Ua, Ub, Wa, Wb, maxit, sa, sb, S(0), S(0), ori, eos);
         if (sa == 1 || sb == 1) code |= CODE_BAD_INPUT;
         if (sa == 2 || sb == 2) code |= CODE_NOCONV;
         prim[ca] = S(Wa.rho);
@@ -780,8 +787,8 @@ __global__ void __launch_bounds__(NT, MINB) patch_kernel(const __grid_constant__
         prim[2 * kGC + ca] = S(Wa.u[1]);
         prim[3 * kGC + ca] = S(Wa.u[2]);
         prim[4 * kGC + ca] = S(Wa.p);
-        hts[ca] = S(Wa.tau);
-        hts[cb] = S(Wb.tau);
+        hts[ca] = S(Wa.rt);
+        hts[cb] = S(Wb.rt);
         prim[cb] = S(Wb.rho);
         prim[kGC + cb] = S(Wb.u[0]);
         prim[2 * kGC + cb] = S(Wb.u[1]);
@@ -794,7 +801,8 @@ __global__ void __launch_bounds__(NT, MINB) patch_kernel(const __grid_constant__
         S U[5];
         load_tile(c, r, U);
         PrimX<R> W;
-        int st = con2pri<P>(U[0], U[1], U[2], U[3], U[4], W, maxit, S(0), ori, eos);
+        int st = con2pri<P, E, false, true>(U[0], U[1], U[2], U[3], U[4], W, maxit, S(0), ori,
+                                            eos);
         if (st == 1) code |= CODE_BAD_INPUT;
         if (st == 2) code |= CODE_NOCONV;
         prim[c] = S(W.rho);
@@ -802,7 +810,7 @@ __global__ void __launch_bounds__(NT, MINB) patch_kernel(const __grid_constant__
         prim[2 * kGC + c] = S(W.u[1]);
         prim[3 * kGC + c] = S(W.u[2]);
         prim[4 * kGC + c] = S(W.p);
-        hts[c] = S(W.tau);
+        hts[c] = S(W.rt);
       }
     }
     // the last thread, which has the least phase-1 work, converts the step
@@ -861,10 +869,14 @@ __global__ void __launch_bounds__(NT, MINB) patch_kernel(const __grid_constant__
         for (int f = tid; f < 3 * kNF; f += NT) {
           const int d = f / kNF, fi = f - d * kNF;
           if (d == 0)
-            fail |= face_flux<0, P, PAIR>(face, hts, fi, a.riemann, maxit, code, ori, eos);
+            fail |= face_flux<0, P, PAIR, E, kRatio>(face, hts, fi, a.riemann, maxit, code, ori,
+                                                     eos);
           else if (d == 1)
-            fail |= face_flux<1, P, PAIR>(face, hts, fi, a.riemann, maxit, code, ori, eos);
-          else fail |= face_flux<2, P, PAIR>(face, hts, fi, a.riemann, maxit, code, ori, eos);
+            fail |= face_flux<1, P, PAIR, E, kRatio>(face, hts, fi, a.riemann, maxit, code, ori,
+                                                     eos);
+          else
+            fail |= face_flux<2, P, PAIR, E, kRatio>(face, hts, fi, a.riemann, maxit, code, ori,
+                                                     eos);
         }
         fail = __syncthreads_or(fail);
         if (a.flux_only) {
@@ -1041,11 +1053,11 @@ __global__ void __launch_bounds__(NT, MINB) patch_kernel(const __grid_constant__
               PrimX<R> W[NPC];
               int st[NPC];
               if constexpr (PAIR) {
-                con2pri_x2<P, E, true>(Un[0], Un[1], W[0], W[1], maxit, st[0], st[1], g0[0],
-                                       g0[NPC - 1], ori, eos);
+                con2pri_x2<P, E, true, kRatio>(Un[0], Un[1], W[0], W[1], maxit, st[0], st[1],
+                                               g0[0], g0[NPC - 1], ori, eos);
               } else {
-                st[0] = con2pri<P, E, true>(Un[0][0], Un[0][1], Un[0][2], Un[0][3], Un[0][4], W[0],
-                                            maxit, g0[0], ori, eos);
+                st[0] = con2pri<P, E, true, kRatio>(Un[0][0], Un[0][1], Un[0][2], Un[0][3],
+                                                    Un[0][4], W[0], maxit, g0[0], ori, eos);
               }
               if constexpr (GATHER == 3) {
                 // keep the new state's primitives (NaN where unphysical)

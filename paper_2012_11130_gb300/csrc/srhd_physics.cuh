@@ -87,6 +87,8 @@ template <class R> struct PrimX {
   R ht;             // htilde (set by the conversions from conserved variables)
   R tau;            // solver variable: conic parameter h - T - 1 (TM) or htilde
                     // (polytropic), set by the same conversions
+  R rt;             // tau over its cold start (x_start), set by a cold
+                    // conversion that is asked for it (RATIO)
 };
 
 // Equation of state, selected at compile time by a tag:
@@ -559,6 +561,17 @@ __device__ __forceinline__ void prims_from_ht_poly(S D, S Mx, S My, S Mz, R ht, 
   W.p = W.rho * W.T;
 }
 
+// Cold start of the solver variable for A (the root for m = 0): tau_start
+// (TM), poly_start (polytropic). A converged x divided by this start
+// changes slowly between neighbouring states (the start follows A exactly
+// and the ratio only the dependence on m), so a nearby state's ratio times
+// this state's start is a warm start closer to the root than the nearby x
+// itself.
+template <class V> __device__ __forceinline__ V x_start(const EosTM&, V A) { return tau_start(A); }
+template <class V> __device__ __forceinline__ V x_start(const EosPoly& e, V A) {
+  return poly_start(A, ar::c<V>(1.0 - (e.gam - 1.0) / e.gam));
+}
+
 // Solver of Eq. (transcendental equation) per EoS, in the variable x that
 // the warm starts carry (tau for TM, htilde for the polytropic EoS):
 // init(A, m2) fixes the per-state constants, start() gives x0, step(x) the
@@ -612,7 +625,7 @@ __device__ __forceinline__ void prims_from_x(const EosPoly& e, S D, S Mx, S My, 
 
 template <class R> __device__ __forceinline__ void set_nan(PrimX<R>& W) {
   const R nan = R(__longlong_as_double(0x7ff8000000000000ULL));
-  W.rho = W.u[0] = W.u[1] = W.u[2] = W.p = W.T = W.h = W.gamma = W.rg = W.ht = W.tau = nan;
+  W.rho = W.u[0] = W.u[1] = W.u[2] = W.p = W.T = W.h = W.gamma = W.rg = W.ht = W.tau = W.rt = nan;
 }
 
 // Stopping rule of the Newton iterations (per state): the step just applied
@@ -627,8 +640,10 @@ template <class R> __device__ __forceinline__ bool newton_done(R adh, R tau) {
 // (see above); a step that would make tau non-positive halves tau instead.
 // Stops by newton_done or after maxit steps (status 2). guess > 0 is a tau
 // to start from (a warm start from a nearby state); otherwise tau_start(A).
+// With RATIO, a warm guess is a nearby state's rt and the start is guess
+// times this state's x_start(A), and a cold conversion also returns W.rt.
 // The root does not depend on the start.
-template <class P, class E = EosTM, bool WARM = false>
+template <class P, class E = EosTM, bool WARM = false, bool RATIO = false>
 __device__ __forceinline__ int con2pri(typename P::S D, typename P::S Mx, typename P::S My,
                                        typename P::S Mz, typename P::S Et,
                                        PrimX<typename P::S>& W, int maxit,
@@ -643,11 +658,18 @@ __device__ __forceinline__ int con2pri(typename P::S D, typename P::S Mx, typena
   const R A = R(Aa), m2 = R(m2a);
   Solver<E, R> sv;
   R tau;
+  [[maybe_unused]] R t0c = R(1);
   if constexpr (WARM) {
-    tau = guess > R(0) ? guess : R(1);
+    if constexpr (RATIO) {
+      const R x0 = x_start(eos, A);
+      tau = guess > R(0) ? guess * x0 : x0;
+    } else {
+      tau = guess > R(0) ? guess : R(1);
+    }
     sv.prepare(eos, A, m2, tau);
   } else {
     const R t0 = sv.init(eos, A, m2);
+    t0c = t0;
     tau = guess > R(0) ? guess : t0;
   }
   int status = 2;
@@ -659,6 +681,7 @@ __device__ __forceinline__ int con2pri(typename P::S D, typename P::S Mx, typena
     if (newton_done(fabs(dh), tau)) { status = 0; break; }
   }
   prims_from_x(eos, D, Mx, My, Mz, tau, W);
+  if constexpr (RATIO && !WARM) W.rt = qdiv(tau, t0c);
   return status;
 }
 
@@ -667,7 +690,7 @@ __device__ __forceinline__ int con2pri(typename P::S D, typename P::S Mx, typena
 // so that their dependency chains interleave (in float, both lanes of each
 // step are one packed instruction). The loop runs until both have stopped;
 // a state that has stopped is not updated.
-template <class P, class E = EosTM, bool WARM = false>
+template <class P, class E = EosTM, bool WARM = false, bool RATIO = false>
 __device__ __forceinline__ void con2pri_x2(const typename P::S (&Ua)[5],
                                            const typename P::S (&Ub)[5],
                                            PrimX<typename P::S>& Wa, PrimX<typename P::S>& Wb,
@@ -692,11 +715,18 @@ __device__ __forceinline__ void con2pri_x2(const typename P::S (&Ua)[5],
     using namespace pk;
     Solver<E, float2> sv;
     float2 tau;
+    [[maybe_unused]] float2 t0c = make_float2(1.0f, 1.0f);
     if constexpr (WARM) {
-      tau = make_float2(ga > 0.0f ? ga : 1.0f, gb > 0.0f ? gb : 1.0f);
+      if constexpr (RATIO) {
+        const float2 x0 = x_start(eos, make_float2(Aa, Ab));
+        tau = make_float2(ga > 0.0f ? ga * x0.x : x0.x, gb > 0.0f ? gb * x0.y : x0.y);
+      } else {
+        tau = make_float2(ga > 0.0f ? ga : 1.0f, gb > 0.0f ? gb : 1.0f);
+      }
       sv.prepare(eos, make_float2(Aa, Ab), make_float2(m2a, m2b), tau);
     } else {
       const float2 t0 = sv.init(eos, make_float2(Aa, Ab), make_float2(m2a, m2b));
+      t0c = t0;
       tau = make_float2(ga > 0.0f ? ga : t0.x, gb > 0.0f ? gb : t0.y);
     }
     for (int k = 1; k <= maxit && !(da && db); ++k) {
@@ -717,16 +747,29 @@ __device__ __forceinline__ void con2pri_x2(const typename P::S (&Ua)[5],
       prims_from_x(eos, Ua[0], Ua[1], Ua[2], Ua[3], tau.x, Wa);
       prims_from_x(eos, Ub[0], Ub[1], Ub[2], Ub[3], tau.y, Wb);
     }
+    if constexpr (RATIO && !WARM) {
+      Wa.rt = qdiv(tau.x, t0c.x);
+      Wb.rt = qdiv(tau.y, t0c.y);
+    }
   } else {
     Solver<E, R> sva, svb;
     R ta, tb;
+    [[maybe_unused]] R t0ca = R(1), t0cb = R(1);
     if constexpr (WARM) {
-      ta = ga > R(0) ? ga : R(1);
-      tb = gb > R(0) ? gb : R(1);
+      if constexpr (RATIO) {
+        const R x0a = x_start(eos, Aa), x0b = x_start(eos, Ab);
+        ta = ga > R(0) ? ga * x0a : x0a;
+        tb = gb > R(0) ? gb * x0b : x0b;
+      } else {
+        ta = ga > R(0) ? ga : R(1);
+        tb = gb > R(0) ? gb : R(1);
+      }
       sva.prepare(eos, Aa, m2a, ta);
       svb.prepare(eos, Ab, m2b, tb);
     } else {
       const R t0a = sva.init(eos, Aa, m2a), t0b = svb.init(eos, Ab, m2b);
+      t0ca = t0a;
+      t0cb = t0b;
       ta = ga > R(0) ? ga : t0a;
       tb = gb > R(0) ? gb : t0b;
     }
@@ -744,6 +787,10 @@ __device__ __forceinline__ void con2pri_x2(const typename P::S (&Ua)[5],
     }
     prims_from_x(eos, Ua[0], Ua[1], Ua[2], Ua[3], ta, Wa);
     prims_from_x(eos, Ub[0], Ub[1], Ub[2], Ub[3], tb, Wb);
+    if constexpr (RATIO && !WARM) {
+      Wa.rt = qdiv(ta, t0ca);
+      Wb.rt = qdiv(tb, t0cb);
+    }
   }
   sta = da ? 0 : 2;
   stb = db ? 0 : 2;
