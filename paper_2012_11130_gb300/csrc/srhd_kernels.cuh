@@ -592,10 +592,10 @@ __global__ void __launch_bounds__(NT, MINB) patch_kernel(const __grid_constant__
   [[maybe_unused]] __shared__ int s_stage_timeout;
   constexpr bool kStaged = GATHER == 0 || GATHER == 1 || GATHER == 3;
   // hts holds the tile cells' rt (the ratio of the converged solver
-  // variable to its cold start) where phase 1 converts them, and their
-  // solver variable itself where the primitive cache supplies it (mode 3);
-  // the warm starts of phases 3 and 4 take either
-  constexpr bool kRatio = GATHER != 3;
+  // variable to its cold start): from the cold conversions of phase 1, or
+  // from the cached primitives (mode 3, rt_of_prims); the warm starts of
+  // phases 3 and 4 multiply it by each state's own cold start
+  constexpr bool kRatio = true;
   auto stage_ok = [&]() {
     // tensor copies need 128-byte aligned destinations (the boxes are laid
     // out on 128-byte boundaries from `stage`)
@@ -720,9 +720,9 @@ __global__ void __launch_bounds__(NT, MINB) patch_kernel(const __grid_constant__
     // ---- phase 1: primitive tile ------------------------------------------
     if constexpr (GATHER == 3) {
       // the primitives that the previous step kept for the cells of the
-      // tile: a gather, no conversion; the solver variable, the warm start of
-      // the later solves, from T = p / rho in closed form (solver_var_of_T).
-      // A state left unphysical by that step is stored as NaN.
+      // tile: a gather, no conversion; the warm-start ratio of the later
+      // solves from them in closed form (rt_of_prims). A state left
+      // unphysical by that step is stored as NaN.
       const S* pbase = static_cast<const S*>(a.prim_in);
       int r0 = tid;
       if (st1 & 2) {
@@ -735,8 +735,8 @@ __global__ void __launch_bounds__(NT, MINB) patch_kernel(const __grid_constant__
           S w[6];
 #pragma unroll
           for (int v = 0; v < 5; ++v) w[v] = stage[off + v * vs];
-          w[5] = solver_var_of_T(eos, qdiv(w[4], w[0]));
-          if (!(w[0] > S(0) && w[4] > S(0) && isfinite(w[1] + w[2] + w[3] + w[5])))
+          w[5] = rt_of_prims(eos, w[0], w[1], w[2], w[3], w[4]);
+          if (!(w[0] > S(0) && w[4] > S(0) && isfinite(w[1] + w[2] + w[3])))
             code |= CODE_BAD_INPUT;
 #pragma unroll
           for (int v = 0; v < 5; ++v) prim[v * kGC + c] = w[v];
@@ -764,8 +764,8 @@ __global__ void __launch_bounds__(NT, MINB) patch_kernel(const __grid_constant__
 #pragma unroll
           for (int v = 0; v < 5; ++v) w[v] = __ldg(src + v * kNC);
         }
-        w[5] = solver_var_of_T(eos, qdiv(w[4], w[0]));
-        if (!(w[0] > S(0) && w[4] > S(0) && isfinite(w[1] + w[2] + w[3] + w[5])))
+        w[5] = rt_of_prims(eos, w[0], w[1], w[2], w[3], w[4]);
+        if (!(w[0] > S(0) && w[4] > S(0) && isfinite(w[1] + w[2] + w[3])))
           code |= CODE_BAD_INPUT;
 #pragma unroll
         for (int v = 0; v < 5; ++v) prim[v * kGC + c] = w[v];

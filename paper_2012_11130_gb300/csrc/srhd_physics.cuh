@@ -572,6 +572,25 @@ template <class V> __device__ __forceinline__ V x_start(const EosPoly& e, V A) {
   return poly_start(A, ar::c<V>(1.0 - (e.gam - 1.0) / e.gam));
 }
 
+// rt of a state known by its primitives: its solver variable in closed form
+// (solver_var_of_T) over the cold start for its A, with A from the
+// primitives (Et/D as in prim2con, m = h |U|). Only a warm start: where A
+// cancels to <= 0 the result is not positive and the solve starts cold.
+template <class R, class E>
+__device__ __forceinline__ R rt_of_prims(const E& eos, R rho, R u0, R u1, R u2, R p) {
+  const R T = qdiv(p, rho);
+  R ht, hmT;
+  eos_ht(eos, T, ht, hmT);
+  const R uu = u0 * u0 + u1 * u1 + u2 * u2;
+  const R g2 = R(1) + uu;
+  const R rg = rsqrt_r(g2);
+  const R gamma = g2 * rg;
+  const R e = qdiv(uu, gamma + R(1)) + (hmT + ht * uu) * rg;  // Et / D
+  const R h = R(1) + ht;
+  const R A = e * (e + R(2)) - h * h * uu;
+  return qdiv(solver_var_of_T(eos, T), x_start(eos, A));
+}
+
 // Solver of Eq. (transcendental equation) per EoS, in the variable x that
 // the warm starts carry (tau for TM, htilde for the polytropic EoS):
 // init(A, m2) fixes the per-state constants, start() gives x0, step(x) the
