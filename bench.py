@@ -77,10 +77,10 @@ PEAK_FP64_TFLOPS = 1.25
 # only for the kernel sources with the recorded hash.
 # Captured at 128^3 (4096 patches) and scaled by 8 to the 32768-patch launch
 # (profiles/patch_kernel_advection128.md).
-NCU_TRAFFIC = {"sources_sha": "2ad4069fd9a6a840",
-               "mixed_cf": 8 * (141.696512e6 + 23.350528e6),
-               "mixed": 8 * (141.796864e6 + 23.947520e6),
-               "fp64": 8 * (283.335168e6 + 67.212032e6)}
+NCU_TRAFFIC = {"sources_sha": "58f24a62548a8eec",
+               "mixed_cf": 8 * (141.724416e6 + 23.045632e6),
+               "mixed": 8 * (141.782016e6 + 24.145664e6),
+               "fp64": 8 * (283.940096e6 + 67.366144e6)}
 
 
 # The sources that make the patch kernel's device code (its translation units
